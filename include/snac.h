@@ -1,0 +1,169 @@
+/*
+ * snac.h -- C ABI of the GB300 FFT-accelerated multi-block Poisson solver.
+ *
+ * Solves the second-order finite-volume Poisson equation of Costa, "A FFT-accelerated multi-block
+ * finite-difference solver for massively parallel simulations of incompressible flows"
+ * (arXiv 2106.03583): Eq. 8 on a structured grid made of several blocks (Sec. 3.1), stretched along
+ * x and y and uniform along the homogeneous direction z. The solve follows Algorithm 1 (Sec. 2):
+ * a real-to-real transform along z chosen by the boundary pair (Table 1), one multigrid solve of the
+ * reduced equation (Eq. 9) per wavenumber, and the inverse transform -- wrapped in an FP64
+ * defect-correction loop r = f - A p, p += A^-1 r that stops at a relative residual tolerance.
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ *  Layout.    A 3-D field (right-hand side, solution, residual) is one contiguous float64 buffer:
+ *             blocks concatenated in id order, each block stored [z][y][x] with x fastest.
+ *             A mode-space field ("modes") is [q][cell] with q the wavenumber (0..n_z-1) and cell
+ *             running over the x-y cells of all blocks, block by block, [y][x] within a block;
+ *             its element type is the plan's inner type (double for SNAC_FP64, float for
+ *             SNAC_MIXED).
+ *  Memory.    Pointers named d_* are device pointers on the current CUDA device; h_* are host
+ *             pointers. The caller owns every buffer it passes; the library never frees them, never
+ *             writes an input, and keeps no pointer to them after the call returns.
+ *  Streams.   `stream` is a cudaStream_t (passed as void*; NULL = legacy default stream). Every
+ *             call that takes one enqueues its work on it and returns after that work is complete
+ *             (the solve reads residual norms back to the host).
+ *  Plans.     A plan owns its device workspace (level hierarchy, coefficients, eigenvalue shifts,
+ *             transform twiddles, coarse-level factors, scratch). A plan is not re-entrant: one call
+ *             at a time per plan. Distinct plans may run concurrently on distinct streams.
+ *  Errors.    Every function returns SNAC_OK (0) or a negative snac_status. Nothing aborts and no
+ *             exception crosses the ABI. After an error the plan stays usable unless the status is
+ *             SNAC_ERR_CUDA (the CUDA context may then be unusable).
+ */
+#ifndef SNAC_H
+#define SNAC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  SNAC_OK = 0,
+  SNAC_ERR_INVALID_ARG = -1,      /* NULL pointer, bad size, bad enum value                          */
+  SNAC_ERR_LAYOUT = -2,           /* block graph not congruent / not symmetric, z not uniform, n_z
+                                     odd for a periodic z, blocks not coarsenable, ...               */
+  SNAC_ERR_OOM = -3,              /* device allocation failed                                         */
+  SNAC_ERR_CUDA = -4,             /* a CUDA call failed                                               */
+  SNAC_ERR_NOT_CONVERGED = -5,    /* tolerance not reached within max_outer; p holds the last iterate */
+  SNAC_ERR_NONFINITE = -6,        /* a residual norm was NaN or Inf (non-finite input)                */
+  SNAC_ERR_INCOMPATIBLE_RHS = -7, /* singular problem whose right-hand side has a non-zero mean       */
+  SNAC_ERR_TIMEOUT = -8           /* reserved for bounded device-side waits                           */
+} snac_status;
+
+/* Face kinds (Sec. 3.1: Dirichlet, Neumann, block-block connectivity; periodic = the cyclic
+ * connectivity of a block with itself). Homogeneous Dirichlet/Neumann pressure conditions are imposed
+ * at the face (staggered grid): the ghost cell mirrors the first cell with sign -1 / +1. */
+typedef enum {
+  SNAC_BC_DIRICHLET = 0,
+  SNAC_BC_NEUMANN = 1,
+  SNAC_BC_PERIODIC = 2,
+  SNAC_BC_BLOCK = 3
+} snac_bc;
+
+/* One block (Sec. 3.1, Table 2). lo/hi: inclusive index-space corners, n_a = hi[a]-lo[a]+1.
+ * h_dx[a]: host array of n_a cell widths along axis a (copied at plan creation; the grid mapping of
+ * Table 2 is applied by the caller). bc[a][s]: face kind of the lower (s=0) / upper (s=1) face along
+ * axis a. nbr[a][s]: id of the connected block across a SNAC_BC_BLOCK face, else -1.
+ * Rules (checked, SNAC_ERR_LAYOUT otherwise): a connected face coincides with the neighbour's
+ * opposite face (same extent and the same cell widths along it), connectivity is symmetric, every
+ * block spans the whole homogeneous axis with the same n_z, uniform width and boundary pair. */
+typedef struct {
+  int64_t lo[3];
+  int64_t hi[3];
+  const double *h_dx[3];
+  int32_t bc[3][2];
+  int32_t nbr[3][2];
+} snac_block;
+
+typedef enum { SNAC_FP64 = 0, SNAC_MIXED = 1 } snac_precision;
+
+/* Solver options; pass NULL to snac_plan_create for the defaults shown. */
+typedef struct {
+  int32_t precision;   /* SNAC_FP64 (default): every stage in FP64. SNAC_MIXED: transforms and
+                          multigrid in FP32 inside the FP64 defect-correction loop; the outer
+                          residual, the update, the eigenvalue shifts and the coarsest solve stay FP64 */
+  int32_t nu1, nu2;    /* red-black Gauss-Seidel sweeps before / after the coarse correction (2, 2)  */
+  int32_t max_outer;   /* defect-correction iterations (20)                                          */
+  int32_t max_cycles;  /* V-cycles per wavenumber per outer iteration (40)                          */
+  int32_t max_coarse;  /* coarsen while a plane has more than this many cells (64; <= 256)          */
+} snac_options;
+
+/* Result of the last solve of a plan. */
+typedef struct {
+  int32_t status;        /* status of the last solve                                                */
+  int32_t outer_iters;   /* defect-correction iterations performed                                  */
+  int32_t total_cycles;  /* V-cycles summed over wavenumbers and outer iterations                    */
+  int32_t max_mode_cycles; /* largest number of V-cycles of one wavenumber in one outer iteration   */
+  int32_t levels;        /* multigrid levels (1 = direct solve of the plane)                         */
+  int32_t n_modes;       /* n_z                                                                      */
+  double rel_res;        /* final ||f - A p||_2 / ||f||_2 (f after mean removal)                     */
+  double rhs_norm;       /* ||f||_2                                                                  */
+  double removed_mean;   /* volume-weighted mean removed from f (singular problems), else 0         */
+} snac_solve_info;
+
+typedef struct snac_plan snac_plan;
+
+/* Build a plan for the multi-block problem (Sec. 3.1 setup; Table 1 for the homogeneous pair).
+ * homog_axis must be 2 (z). On success *out receives a plan owning its device workspace, allocated
+ * on the current CUDA device. */
+int snac_plan_create(snac_plan **out, int32_t nblocks, const snac_block *blocks, int32_t homog_axis,
+                     const snac_options *opt);
+
+/* Device bytes held by the plan. */
+int snac_plan_workspace_bytes(const snac_plan *plan, size_t *bytes);
+
+/* Solve A p = f (Eq. 8) to ||f - A p|| <= tol ||f|| (Algorithm 1 inside FP64 defect correction).
+ * d_rhs: device float64 3-D field, read only. d_p: device float64 3-D field, in: initial guess (the
+ * latest solution, Sec. 3.3.1), out: solution. Singular problems (periodic or Neumann-Neumann z and
+ * no Dirichlet face in x-y): a volume-weighted mean of f within 1e-12 sum(V|f|) is removed and the
+ * zero-mean solution returned; a larger mean gives SNAC_ERR_INCOMPATIBLE_RHS with p untouched.
+ * A zero f gives p = 0. */
+int snac_poisson_solve(snac_plan *plan, const double *d_rhs, double *d_p, double tol, void *stream);
+
+/* Statistics of the last solve. */
+int snac_plan_info(const snac_plan *plan, snac_solve_info *info);
+
+/* V-cycles of each wavenumber in the last outer iteration of the last solve: h_cycles[n_z]. */
+int snac_plan_mode_cycles(const snac_plan *plan, int32_t *h_cycles, int32_t n);
+
+/* Release the plan and its device workspace. NULL is accepted. */
+int snac_plan_destroy(snac_plan *plan);
+
+/* Static string for a status code. */
+const char *snac_status_string(int status);
+
+/* Detail of the last error raised by plan creation on this thread (empty if none). */
+const char *snac_last_error_message(void);
+
+/* ---- Stages of the solve, one call each (the same kernels the solve uses). ---- */
+
+/* d_out = A d_p, the 3-D operator of Eq. 8 (float64 3-D fields). */
+int snac_apply_operator(snac_plan *plan, const double *d_p, double *d_out, void *stream);
+
+/* d_r = d_rhs - A d_p (float64 3-D fields); h_norms[0] = ||r||_2^2, h_norms[1] = ||rhs||_2^2. */
+int snac_residual(snac_plan *plan, const double *d_rhs, const double *d_p, double *d_r, double *h_norms,
+                  void *stream);
+
+/* Forward transform along z (Table 1 F, Algorithm 1 first loop): d_in float64 3-D field ->
+ * d_modes mode-space field of the plan's inner type. */
+int snac_forward_transform(snac_plan *plan, const double *d_in, void *d_modes, void *stream);
+
+/* Backward transform and update (Algorithm 1 third loop): d_p += F^-1(d_modes), where F^-1 is the
+ * backward transform of Table 1 divided by theta; d_modes of the plan's inner type. */
+int snac_backward_update(snac_plan *plan, const void *d_modes, double *d_p, void *stream);
+
+/* d_out = (A_xy + lambda_q / dz^2) d_u for every wavenumber q: the reduced operator of Eq. 9 on
+ * mode-space fields of the plan's inner type. */
+int snac_mode_operator(snac_plan *plan, const void *d_u, void *d_out, void *stream);
+
+/* ncycles V(nu1, nu2) cycles of the reduced equations (Eq. 9) for every wavenumber, in place on
+ * d_u, with right-hand side d_f (mode-space fields of the plan's inner type). */
+int snac_mode_vcycles(snac_plan *plan, const void *d_f, void *d_u, int32_t ncycles, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SNAC_H */

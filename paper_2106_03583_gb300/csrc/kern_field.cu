@@ -1,0 +1,174 @@
+// FP64 kernels on 3-D fields: the outer residual r = f - A p of the defect-correction loop (Eq. 8),
+// the operator itself, right-hand-side statistics, deterministic reductions, and the mean fix of
+// singular problems.
+#include "snac_impl.h"
+#include "kern_common.cuh"
+
+namespace snac {
+namespace {
+
+constexpr int ZSPLIT = 16;
+
+// Block-wide sum of NV doubles; the result is valid in thread 0.
+template <int NV>
+__device__ __forceinline__ void block_sum(double (&v)[NV], double* sh /* [NV][32] */) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+#pragma unroll
+  for (int k = 0; k < NV; ++k) {
+    double x = warp_sum(v[k]);
+    if (lane == 0) sh[k * 32 + warp] = x;
+  }
+  __syncthreads();
+  if (warp == 0) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+      double x = lane < nwarp ? sh[k * 32 + lane] : 0.0;
+      v[k] = warp_sum(x);
+    }
+  }
+}
+
+// One thread per x-y cell of a tile, looping over the z planes k = blockIdx.y, + gridDim.y, ...
+// mode 0: r = (f - fshift) - A p, partial {||r||^2, ||f - fshift||^2, sum V p}
+// mode 1: r = A p
+// mode 2: partial {sum V f, sum V |f|, ||f||^2}
+__global__ void __launch_bounds__(TILE_THREADS) k_field3d(LevelView<double> L, const Coef<double>* __restrict__ cz,
+                                                           int nz, int periodic_z, int mode, const double* __restrict__ f,
+                                                           const double* __restrict__ p, double* __restrict__ r,
+                                                           double fshift, double* __restrict__ partial) {
+  __shared__ double sh[4 * 32];
+  const TileDev t = L.tiles[blockIdx.x];
+  const BlockDev B = L.blk[t.b];
+  const int i = t.x0 + (threadIdx.x % TILE_X), j = t.y0 + (threadIdx.x / TILE_X);
+  double acc[3] = {0.0, 0.0, 0.0};
+  if (i < B.nx && j < B.ny) {
+    const Coef<double> cx = L.cx[B.xo + i], cy = L.cy[B.yo + j];
+    const long long plane = (long long)B.nx * B.ny;
+    const long long base = (long long)nz * B.off + (long long)j * B.nx + i;  // (k = 0)
+    // neighbours in x-y: block and in-plane index (self on a physical face, where the weight is 0)
+    int bw, be, bs, bn;
+    long long lw, le, ls, ln;
+    nbr_cells(L.blk, B, t.b, i, j, bw, lw, be, le, bs, ls, bn, ln);
+    const long long pw = nz * L.blk[bw].off + lw, pe = nz * L.blk[be].off + le;
+    const long long ps = nz * L.blk[bs].off + ls, pn = nz * L.blk[bn].off + ln;
+    const long long plw = (long long)L.blk[bw].nx * L.blk[bw].ny, ple = (long long)L.blk[be].nx * L.blk[be].ny;
+    const long long pls = (long long)L.blk[bs].nx * L.blk[bs].ny, pln = (long long)L.blk[bn].nx * L.blk[bn].ny;
+    const double area = cx.w * cy.w;
+    const double dxy = cx.d + cy.d;
+    for (int k = blockIdx.y; k < nz; k += gridDim.y) {
+      const long long c = base + k * plane;
+      if (mode == 2) {
+        const double fv = f[c];
+        const double v = area * cz[k].w;
+        acc[0] += v * fv;
+        acc[1] += v * fabs(fv);
+        acc[2] += fv * fv;
+        continue;
+      }
+      const Coef<double> z = cz[k];
+      const int kd = k > 0 ? k - 1 : (periodic_z ? nz - 1 : k);
+      const int ku = k < nz - 1 ? k + 1 : (periodic_z ? 0 : k);
+      const double pc = p[c];
+      double ap = cx.lo * p[pw + k * plw];
+      ap = fma(cx.hi, p[pe + k * ple], ap);
+      ap = fma(cy.lo, p[ps + k * pls], ap);
+      ap = fma(cy.hi, p[pn + k * pln], ap);
+      ap = fma(z.lo, p[base + kd * plane], ap);
+      ap = fma(z.hi, p[base + ku * plane], ap);
+      ap = fma(dxy + z.d, pc, ap);
+      if (mode == 1) {
+        r[c] = ap;
+      } else {
+        const double fv = f[c] - fshift;
+        const double rv = fv - ap;
+        r[c] = rv;
+        acc[0] = fma(rv, rv, acc[0]);
+        acc[1] = fma(fv, fv, acc[1]);
+        acc[2] = fma(area * z.w, pc, acc[2]);
+      }
+    }
+  }
+  if (mode == 1) return;
+  block_sum<3>(acc, sh);
+  if (threadIdx.x == 0) {
+    double* o = partial + 4 * ((long long)blockIdx.y * gridDim.x + blockIdx.x);
+    o[0] = acc[0];
+    o[1] = acc[1];
+    o[2] = acc[2];
+    o[3] = 0.0;
+  }
+}
+
+// Deterministic sum of npart x 4 partials into out[4] (one CTA, fixed order).
+__global__ void __launch_bounds__(1024) k_reduce4(const double* __restrict__ part, int npart, double* __restrict__ out) {
+  __shared__ double sh[4 * 32];
+  double acc[4] = {0, 0, 0, 0};
+  for (int i = threadIdx.x; i < npart; i += blockDim.x) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) acc[k] += part[4 * (long long)i + k];
+  }
+  block_sum<4>(acc, sh);
+  if (threadIdx.x == 0)
+    for (int k = 0; k < 4; ++k) out[k] = acc[k];
+}
+
+// Shift the singular mode-0 correction by a constant so that the updated p has zero volume-weighted
+// mean: sum V (p_old + e) = 0, with sum V e = alpha * sum_xy area * e0 (alpha = dz n / theta) and
+// sum V p_old = sums[2] from the residual pass. One CTA.
+template <typename T>
+__global__ void __launch_bounds__(1024) k_fix_mean(T* __restrict__ u0, const double* __restrict__ area, long long ncell,
+                                                   const double* __restrict__ sums, double alpha, double area_total) {
+  __shared__ double sh[32];
+  __shared__ double kappa;
+  double acc[1] = {0.0};
+  for (long long c = threadIdx.x; c < ncell; c += blockDim.x) acc[0] = fma(area[c], (double)u0[c], acc[0]);
+  block_sum<1>(acc, sh);
+  if (threadIdx.x == 0) kappa = -(sums[2] + alpha * acc[0]) / (alpha * area_total);
+  __syncthreads();
+  const double k = kappa;
+  for (long long c = threadIdx.x; c < ncell; c += blockDim.x) u0[c] = (T)((double)u0[c] + k);
+}
+
+__global__ void k_shift(double* __restrict__ p, long long n, const double* __restrict__ c) {
+  const double s = *c;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    p[i] -= s;
+}
+
+// c = sums[2] / vol_total (the volume-weighted mean of p) written to sums[3]
+__global__ void k_mean_of_p(double* sums, double vol_total) { sums[3] = sums[2] / vol_total; }
+
+}  // namespace
+
+cudaError_t launch_field3d(snac_plan* P, int mode, const double* f, const double* p, double* r, double fshift,
+                           cudaStream_t s) {
+  const HostLevel& l0 = P->lev[0];
+  LevelView<double> L = level_view<double>(l0);
+  dim3 grid((unsigned)l0.tiles.size(), (unsigned)std::min(P->nz, ZSPLIT));
+  k_field3d<<<grid, TILE_THREADS, 0, s>>>(L, P->d_cz, P->nz, P->kind == KIND_PP, mode, f, p, r, fshift, P->d_partial);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess || mode == 1) return e;
+  return launch_reduce_partials(P, (int)(grid.x * grid.y), s);
+}
+
+cudaError_t launch_reduce_partials(snac_plan* P, int npart, cudaStream_t s) {
+  k_reduce4<<<1, 1024, 0, s>>>(P->d_partial, npart, P->d_sums);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fix_mean(snac_plan* P, void* u0, cudaStream_t s) {
+  const double alpha = P->dz * P->nz / P->theta;
+  if (P->precision == SNAC_FP64)
+    k_fix_mean<double><<<1, 1024, 0, s>>>((double*)u0, P->d_area0, P->lev[0].ncell, P->d_sums, alpha, P->area_total);
+  else
+    k_fix_mean<float><<<1, 1024, 0, s>>>((float*)u0, P->d_area0, P->lev[0].ncell, P->d_sums, alpha, P->area_total);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_shift(snac_plan* P, double* p, const double* d_c, cudaStream_t s) {
+  k_mean_of_p<<<1, 1, 0, s>>>(P->d_sums, P->vol_total);
+  k_shift<<<2 * 152, 512, 0, s>>>(p, P->n3, d_c);
+  return cudaGetLastError();
+}
+
+}  // namespace snac

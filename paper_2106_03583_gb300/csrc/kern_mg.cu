@@ -1,0 +1,281 @@
+// Multigrid for the reduced 2-D equations of every wavenumber (Eq. 9, Sec. 2; Algorithm 1 second
+// loop), batched over the active wavenumbers in each launch (grid.y = active mode).
+//
+// Reduced operator of mode q at one level: (A_xy + sigma_q) u, sigma_q = lambda_q / dz^2 (Table 1),
+// with A_xy the x-y part of Eq. 8 rediscretised on the level's widths. V(nu1, nu2) cycle with
+// red-black Gauss-Seidel (colour = parity of the global index-space position), area-weighted
+// restriction of the residual, three-point affine prolongation, and a direct solve of the coarsest
+// plane through the eigen-decomposition of its symmetrised operator.
+#include "kern_common.cuh"
+#include "snac_impl.h"
+
+namespace snac {
+namespace {
+
+template <typename T>
+__device__ __forceinline__ T apply_row(const Coef<T>& cx, const Coef<T>& cy, T diag, T uc, T uw, T ue, T us, T un) {
+  T a = cx.lo * uw;
+  a = fma(cx.hi, ue, a);
+  a = fma(cy.lo, us, a);
+  a = fma(cy.hi, un, a);
+  return fma(diag, uc, a);
+}
+
+// One colour of one Gauss-Seidel sweep: u_c += (f_c - (A u)_c) / diag_c on every cell of that colour.
+template <typename T>
+__global__ void __launch_bounds__(TILE_THREADS) k_smooth(LevelView<T> L, const int* __restrict__ active,
+                                                          const T* __restrict__ sigma, T* __restrict__ u,
+                                                          const T* __restrict__ f, int colour) {
+  const TileDev t = L.tiles[blockIdx.x];
+  const BlockDev B = L.blk[t.b];
+  const int i = t.x0 + (threadIdx.x % TILE_X), j = t.y0 + (threadIdx.x / TILE_X);
+  if (i >= B.nx || j >= B.ny || ((B.par + i + j) & 1) != colour) return;
+  const int q = active[blockIdx.y];
+  const long long base = (long long)q * L.ncell;
+  long long w, e, s, n;
+  nbr_plane(L.blk, B, t.b, i, j, w, e, s, n);
+  const long long c = B.off + (long long)j * B.nx + i;
+  const Coef<T> cx = L.cx[B.xo + i], cy = L.cy[B.yo + j];
+  const T diag = cx.d + cy.d + sigma[q];
+  const T uc = u[base + c];
+  const T au = apply_row(cx, cy, diag, uc, u[base + w], u[base + e], u[base + s], u[base + n]);
+  u[base + c] = fma(f[base + c] - au, recip(diag), uc);
+}
+
+// Coarse right-hand side = area-weighted average of the fine residual over the four children;
+// the coarse iterate starts at zero.
+template <typename T>
+__global__ void __launch_bounds__(TILE_THREADS) k_restrict(LevelView<T> F, LevelView<T> C, const int* __restrict__ active,
+                                                            const T* __restrict__ sigma, const T* __restrict__ uf,
+                                                            const T* __restrict__ ff, T* __restrict__ fc,
+                                                            T* __restrict__ uc) {
+  const TileDev t = C.tiles[blockIdx.x];
+  const BlockDev Bc = C.blk[t.b];
+  const int I = t.x0 + (threadIdx.x % TILE_X), J = t.y0 + (threadIdx.x / TILE_X);
+  if (I >= Bc.nx || J >= Bc.ny) return;
+  const int q = active[blockIdx.y];
+  const BlockDev Bf = F.blk[t.b];
+  const long long bf = (long long)q * F.ncell;
+  const T sg = sigma[q];
+  T acc = 0;
+#pragma unroll
+  for (int dj = 0; dj < 2; ++dj) {
+#pragma unroll
+    for (int di = 0; di < 2; ++di) {
+      const int i = 2 * I + di, j = 2 * J + dj;
+      long long w, e, s, n;
+      nbr_plane(F.blk, Bf, t.b, i, j, w, e, s, n);
+      const long long c = Bf.off + (long long)j * Bf.nx + i;
+      const Coef<T> cx = F.cx[Bf.xo + i], cy = F.cy[Bf.yo + j];
+      const T diag = cx.d + cy.d + sg;
+      const T r = ff[bf + c] - apply_row(cx, cy, diag, uf[bf + c], uf[bf + w], uf[bf + e], uf[bf + s], uf[bf + n]);
+      acc = fma(F.rx[Bf.xo + i] * F.ry[Bf.yo + j], r, acc);
+    }
+  }
+  const long long cc = (long long)q * C.ncell + Bc.off + (long long)J * Bc.nx + I;
+  fc[cc] = acc;
+  uc[cc] = 0;
+}
+
+// u_f += e_C (1 + sx + sy) + nx e_X + ny e_Y: parent C, coarse neighbours X / Y on the fine cell's side.
+template <typename T>
+__global__ void __launch_bounds__(TILE_THREADS) k_prolong(LevelView<T> F, LevelView<T> C, const int* __restrict__ active,
+                                                           T* __restrict__ uf, const T* __restrict__ uc) {
+  const TileDev t = F.tiles[blockIdx.x];
+  const BlockDev Bf = F.blk[t.b];
+  const int i = t.x0 + (threadIdx.x % TILE_X), j = t.y0 + (threadIdx.x / TILE_X);
+  if (i >= Bf.nx || j >= Bf.ny) return;
+  const int q = active[blockIdx.y];
+  const BlockDev Bc = C.blk[t.b];
+  const int I = i >> 1, J = j >> 1;
+  long long w, e, s, n;
+  nbr_plane(C.blk, Bc, t.b, I, J, w, e, s, n);
+  const long long bc = (long long)q * C.ncell;
+  const T eC = uc[bc + Bc.off + (long long)J * Bc.nx + I];
+  const T eX = uc[bc + ((i & 1) ? e : w)];
+  const T eY = uc[bc + ((j & 1) ? n : s)];
+  const PW<T> px = F.px[Bf.xo + i], py = F.py[Bf.yo + j];
+  const T ef = fma(eC, (T)1 + px.self + py.self, fma(px.nbr, eX, py.nbr * eY));
+  const long long c = (long long)q * F.ncell + Bf.off + (long long)j * Bf.nx + i;
+  uf[c] += ef;
+}
+
+// Direct solve of the coarsest plane: with V the cell areas, S = V^1/2 A V^-1/2 = Q Lam Q^T, so
+// (A + sigma)^-1 b = V^-1/2 Q (Lam + sigma)^-1 Q^T V^1/2 b. For a singular mode the null eigenvector
+// (constant in the V-weighted sense) is dropped: the zero-mean solution. One CTA per mode, in FP64.
+template <typename T>
+__global__ void __launch_bounds__(256) k_coarse(const double* __restrict__ Q, const double* __restrict__ lam,
+                                                const double* __restrict__ sqa, int nc, const int* __restrict__ active,
+                                                const double* __restrict__ sigma, const int* __restrict__ singular_mode,
+                                                int null_index, const T* __restrict__ fcoarse, T* __restrict__ ucoarse,
+                                                long long ncell) {
+  __shared__ double b[MAX_COARSE], y[MAX_COARSE];
+  const int q = active[blockIdx.x];
+  const long long base = (long long)q * ncell;
+  for (int i = threadIdx.x; i < nc; i += blockDim.x) b[i] = sqa[i] * (double)fcoarse[base + i];
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+  const double sg = sigma[q];
+  const bool sing = singular_mode[q] != 0;
+  for (int k = warp; k < nc; k += nwarp) {
+    double s = 0.0;
+    for (int i = lane; i < nc; i += 32) s = fma(Q[(long long)i * nc + k], b[i], s);
+    s = warp_sum(s);
+    if (lane == 0) y[k] = (sing && k == null_index) ? 0.0 : s / (lam[k] + sg);
+  }
+  __syncthreads();
+  for (int i = warp; i < nc; i += nwarp) {
+    double s = 0.0;
+    for (int k = lane; k < nc; k += 32) s = fma(Q[(long long)i * nc + k], y[k], s);
+    s = warp_sum(s);
+    if (lane == 0) ucoarse[base + i] = (T)(s / sqa[i]);
+  }
+}
+
+// out = (A_xy + sigma_q) u for every listed mode.
+template <typename T>
+__global__ void __launch_bounds__(TILE_THREADS) k_mode_apply(LevelView<T> L, const int* __restrict__ active,
+                                                              const T* __restrict__ sigma, const T* __restrict__ u,
+                                                              T* __restrict__ out) {
+  const TileDev t = L.tiles[blockIdx.x];
+  const BlockDev B = L.blk[t.b];
+  const int i = t.x0 + (threadIdx.x % TILE_X), j = t.y0 + (threadIdx.x / TILE_X);
+  if (i >= B.nx || j >= B.ny) return;
+  const int q = active[blockIdx.y];
+  const long long base = (long long)q * L.ncell;
+  long long w, e, s, n;
+  nbr_plane(L.blk, B, t.b, i, j, w, e, s, n);
+  const long long c = B.off + (long long)j * B.nx + i;
+  const Coef<T> cx = L.cx[B.xo + i], cy = L.cy[B.yo + j];
+  const T diag = cx.d + cy.d + sigma[q];
+  out[base + c] = apply_row(cx, cy, diag, u[base + c], u[base + w], u[base + e], u[base + s], u[base + n]);
+}
+
+// Per-tile partial sums of (f - (A + sigma) u)^2 for every listed mode (FP64 accumulation).
+template <typename T>
+__global__ void __launch_bounds__(TILE_THREADS) k_mode_resid2(LevelView<T> L, const int* __restrict__ active,
+                                                               const T* __restrict__ sigma, const T* __restrict__ u,
+                                                               const T* __restrict__ f, double* __restrict__ part) {
+  __shared__ double sh[32];
+  const TileDev t = L.tiles[blockIdx.x];
+  const BlockDev B = L.blk[t.b];
+  const int i = t.x0 + (threadIdx.x % TILE_X), j = t.y0 + (threadIdx.x / TILE_X);
+  const int q = active[blockIdx.y];
+  double r2 = 0.0;
+  if (i < B.nx && j < B.ny) {
+    const long long base = (long long)q * L.ncell;
+    long long w, e, s, n;
+    nbr_plane(L.blk, B, t.b, i, j, w, e, s, n);
+    const long long c = B.off + (long long)j * B.nx + i;
+    const Coef<T> cx = L.cx[B.xo + i], cy = L.cy[B.yo + j];
+    const T diag = cx.d + cy.d + sigma[q];
+    const T r = f[base + c] - apply_row(cx, cy, diag, u[base + c], u[base + w], u[base + e], u[base + s], u[base + n]);
+    r2 = (double)r * (double)r;
+  }
+  r2 = warp_sum(r2);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) sh[warp] = r2;
+  __syncthreads();
+  if (warp == 0) {
+    double v = lane < (TILE_THREADS / 32) ? sh[lane] : 0.0;
+    v = warp_sum(v);
+    if (lane == 0) part[(long long)q * L.ntiles + blockIdx.x] = v;
+  }
+}
+
+__global__ void __launch_bounds__(256) k_mode_reduce(const double* __restrict__ part, int ntiles,
+                                                     const int* __restrict__ active, double* __restrict__ norm2) {
+  __shared__ double sh[32];
+  const int q = active[blockIdx.x];
+  double s = 0.0;
+  for (int k = threadIdx.x; k < ntiles; k += blockDim.x) s += part[(long long)q * ntiles + k];
+  s = warp_sum(s);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) sh[warp] = s;
+  __syncthreads();
+  if (warp == 0) {
+    double v = lane < (int)(blockDim.x >> 5) ? sh[lane] : 0.0;
+    v = warp_sum(v);
+    if (lane == 0) norm2[q] = v;
+  }
+}
+
+template <typename T>
+const T* sigma_ptr(const snac_plan* P);
+template <>
+const double* sigma_ptr<double>(const snac_plan* P) { return P->d_sigma64; }
+template <>
+const float* sigma_ptr<float>(const snac_plan* P) { return P->d_sigma32; }
+
+template <typename T>
+cudaError_t vcycle_t(snac_plan* P, int nact, cudaStream_t st) {
+  const int L = (int)P->lev.size() - 1;
+  const T* sg = sigma_ptr<T>(P);
+  const int* act = P->d_active;
+  auto smooth = [&](int l, int nu) {
+    const HostLevel& h = P->lev[l];
+    const LevelView<T> V = level_view<T>(h);
+    dim3 g((unsigned)h.tiles.size(), (unsigned)nact);
+    for (int it = 0; it < nu; ++it)
+      for (int colour = 0; colour < 2; ++colour)
+        k_smooth<T><<<g, TILE_THREADS, 0, st>>>(V, act, sg, (T*)h.d_u, (const T*)h.d_f, colour);
+  };
+  for (int l = 0; l < L; ++l) {
+    smooth(l, P->nu1);
+    const HostLevel& h = P->lev[l];
+    const HostLevel& hc = P->lev[l + 1];
+    dim3 g((unsigned)hc.tiles.size(), (unsigned)nact);
+    k_restrict<T><<<g, TILE_THREADS, 0, st>>>(level_view<T>(h), level_view<T>(hc), act, sg, (const T*)h.d_u,
+                                               (const T*)h.d_f, (T*)hc.d_f, (T*)hc.d_u);
+  }
+  {
+    const HostLevel& h = P->lev[L];
+    k_coarse<T><<<nact, 256, 0, st>>>(P->d_Q, P->d_lam, P->d_sqa, P->nc, act, P->d_sigma64, P->d_singular_mode,
+                                      P->null_index, (const T*)h.d_f, (T*)h.d_u, h.ncell);
+  }
+  for (int l = L - 1; l >= 0; --l) {
+    const HostLevel& h = P->lev[l];
+    const HostLevel& hc = P->lev[l + 1];
+    dim3 g((unsigned)h.tiles.size(), (unsigned)nact);
+    k_prolong<T><<<g, TILE_THREADS, 0, st>>>(level_view<T>(h), level_view<T>(hc), act, (T*)h.d_u, (const T*)hc.d_u);
+    smooth(l, P->nu2);
+  }
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t mode_norms_t(snac_plan* P, int nact, cudaStream_t st) {
+  const HostLevel& h = P->lev[0];
+  dim3 g((unsigned)h.tiles.size(), (unsigned)nact);
+  k_mode_resid2<T><<<g, TILE_THREADS, 0, st>>>(level_view<T>(h), P->d_active, sigma_ptr<T>(P), (const T*)h.d_u,
+                                                (const T*)h.d_f, P->d_mode_part);
+  k_mode_reduce<<<nact, 256, 0, st>>>(P->d_mode_part, (int)h.tiles.size(), P->d_active, P->d_mode_norm2);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t mode_operator_t(snac_plan* P, const void* u, void* out, cudaStream_t st) {
+  const HostLevel& h = P->lev[0];
+  dim3 g((unsigned)h.tiles.size(), (unsigned)P->nz);
+  k_mode_apply<T><<<g, TILE_THREADS, 0, st>>>(level_view<T>(h), P->d_active, sigma_ptr<T>(P), (const T*)u, (T*)out);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_vcycle(snac_plan* P, int nact, cudaStream_t s) {
+  if (nact <= 0) return cudaSuccess;
+  return P->precision == SNAC_FP64 ? vcycle_t<double>(P, nact, s) : vcycle_t<float>(P, nact, s);
+}
+
+cudaError_t launch_mode_norms(snac_plan* P, int nact, cudaStream_t s) {
+  if (nact <= 0) return cudaSuccess;
+  return P->precision == SNAC_FP64 ? mode_norms_t<double>(P, nact, s) : mode_norms_t<float>(P, nact, s);
+}
+
+// Requires d_active = 0..n_z-1.
+cudaError_t launch_mode_operator(snac_plan* P, const void* u, void* out, cudaStream_t s) {
+  return P->precision == SNAC_FP64 ? mode_operator_t<double>(P, u, out, s) : mode_operator_t<float>(P, u, out, s);
+}
+
+}  // namespace snac

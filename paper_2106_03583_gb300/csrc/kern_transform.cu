@@ -1,0 +1,292 @@
+// Real-to-real transforms along the homogeneous direction (Table 1; Algorithm 1, first and third
+// loops), batched over x-y columns. One CTA transforms TC consecutive columns of one block: the
+// columns are loaded row by row (coalesced along x), reordered into a complex sequence of half
+// length m = n/2, transformed by a shared-memory complex FFT (Stockham radix-2 for a power-of-two m,
+// a direct sum otherwise), and post-processed into the real output. Twiddles come from host-built
+// tables; the kernels evaluate no transcendental function.
+//
+// Reductions to a half-length complex FFT (conventions of the unnormalised real-to-real
+// transforms, theta of Table 1):
+//   PP  real DFT in half-complex order: z_j = x_2j + i x_2j+1, split the spectrum into the even and
+//       odd halves (Cooley-Tukey); the inverse runs the same steps backwards.
+//   NN  DCT-II by Makhoul's reordering v = (x_0, x_2, ..., x_3, x_1), Y_k = 2 Re(e^{-i pi k/2n} V_k)
+//       with V the real DFT of v; DCT-III inverts it.
+//   DD  DST-II_k(x) = DCT-II_{n-1-k}((-1)^j x_j); DST-III(X)_j = (-1)^j DCT-III(X reversed)_j.
+//   ND  DCT-IV: t_j = (x_2j + i x_{n-1-2j}) e^{-i pi (4j+1)/4n}, T = FFT_m(t), c_k = T_k e^{-i pi k/n},
+//       Y_2k = 2 Re c_k, Y_{n-1-2k} = -2 Im c_k. It is its own inverse (x 2n).
+//   DN  DST-IV_k(x) = DCT-IV_{n-1-k}((-1)^j x_j), its own inverse (x 2n).
+#include "kern_common.cuh"
+#include "snac_impl.h"
+
+namespace snac {
+namespace {
+
+template <typename T>
+struct Cx {
+  T re, im;
+};
+template <typename T>
+__device__ __forceinline__ Cx<T> cmul(Cx<T> a, Cx<T> b) {
+  return {a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re};
+}
+template <typename T>
+__device__ __forceinline__ Cx<T> conj(Cx<T> a) {
+  return {a.re, -a.im};
+}
+
+// Complex DFT of length m of TC columns held as buf[j * TC + c]. Forward: exp(-2 pi i jk/m);
+// inverse (unnormalised): exp(+2 pi i jk/m). Returns the buffer holding the result.
+template <typename T, int TC>
+__device__ Cx<T>* cfft(Cx<T>* X, Cx<T>* Y, int m, const Cx<T>* __restrict__ tw, bool inverse) {
+  if (m == 1) return X;
+  if ((m & (m - 1)) == 0) {
+    // Stockham autosort: merge pairs of length-Ls transforms into length-2Ls transforms.
+    for (int Ls = 1; Ls < m; Ls <<= 1) {
+      const int r = m / (2 * Ls);
+      for (int idx = threadIdx.x; idx < (m / 2) * TC; idx += blockDim.x) {
+        const int c = idx % TC, t = idx / TC;
+        const int j = t / Ls, k = t - j * Ls;
+        Cx<T> w = tw[k * r];
+        if (inverse) w.im = -w.im;
+        const Cx<T> a = X[(j * Ls + k) * TC + c];
+        const Cx<T> b = cmul(w, X[((j + r) * Ls + k) * TC + c]);
+        Y[(2 * j * Ls + k) * TC + c] = {a.re + b.re, a.im + b.im};
+        Y[(2 * j * Ls + Ls + k) * TC + c] = {a.re - b.re, a.im - b.im};
+      }
+      __syncthreads();
+      Cx<T>* s = X;
+      X = Y;
+      Y = s;
+    }
+    return X;
+  }
+  // direct sum for other lengths
+  for (int idx = threadIdx.x; idx < m * TC; idx += blockDim.x) {
+    const int c = idx % TC, k = idx / TC;
+    Cx<T> acc = {0, 0};
+    for (int j = 0; j < m; ++j) {
+      Cx<T> w = tw[(int)(((long long)j * k) % m)];
+      if (inverse) w.im = -w.im;
+      const Cx<T> p = cmul(w, X[j * TC + c]);
+      acc.re += p.re;
+      acc.im += p.im;
+    }
+    Y[k * TC + c] = acc;
+  }
+  __syncthreads();
+  return Y;
+}
+
+template <typename T>
+struct Tw {
+  const Cx<T>* fft;
+  const Cx<T>* twn;
+  const Cx<T>* tw2n;
+  const Cx<T>* tw4a;
+  const Cx<T>* tw4b;
+};
+
+// X_k (k = 0..m) of the real DFT of the length-n sequence packed as Z = FFT_m(x_2j + i x_2j+1).
+template <typename T, int TC>
+__device__ __forceinline__ Cx<T> rdft_bin(const Cx<T>* R, int k, int m, int c, const Tw<T>& tw) {
+  const Cx<T> zk = R[(k % m) * TC + c];
+  const Cx<T> zc = conj(R[((m - k) % m) * TC + c]);
+  const Cx<T> E = {(T)0.5 * (zk.re + zc.re), (T)0.5 * (zk.im + zc.im)};
+  const Cx<T> d = {zk.re - zc.re, zk.im - zc.im};
+  const Cx<T> O = {(T)0.5 * d.im, (T)-0.5 * d.re};  // d / (2i)
+  const Cx<T> wo = cmul(tw.twn[k], O);
+  return {E.re + wo.re, E.im + wo.im};
+}
+
+// Z_k (k < m) for the inverse real DFT, from half-complex bins X_k and conj(X_{m-k}).
+template <typename T>
+__device__ __forceinline__ Cx<T> irdft_pre(Cx<T> xk, Cx<T> xmk, const Cx<T>& twn_k) {
+  const Cx<T> xc = conj(xmk);
+  const Cx<T> E = {xk.re + xc.re, xk.im + xc.im};
+  const Cx<T> O = cmul({xk.re - xc.re, xk.im - xc.im}, conj(twn_k));
+  return {E.re - O.im, E.im + O.re};  // E + i O
+}
+
+template <typename T, int TC>
+__global__ void __launch_bounds__(256) k_forward(const ChunkDev* __restrict__ chunks, const BlockDev* __restrict__ blk,
+                                                 int n, int kind, Tw<T> tw, const double* __restrict__ in3,
+                                                 T* __restrict__ out, long long ncell) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int m = n / 2;
+  Cx<T>* A = reinterpret_cast<Cx<T>*>(smem);
+  Cx<T>* Bf = A + m * TC;
+  T* xs = reinterpret_cast<T*>(Bf);  // n x TC reals, aliases Bf
+  const ChunkDev ch = chunks[blockIdx.x];
+  const BlockDev B = blk[ch.b];
+  const long long plane = (long long)B.nx * B.ny;
+  const long long base3 = (long long)n * B.off + ch.c0;
+  for (int idx = threadIdx.x; idx < n * TC; idx += blockDim.x) {
+    const int k = idx / TC, c = idx % TC;
+    xs[idx] = c < ch.ncol ? (T)in3[base3 + k * plane + c] : (T)0;
+  }
+  __syncthreads();
+  const bool flip = kind == KIND_DD || kind == KIND_DN;
+  auto x = [&](int k, int c) -> T {
+    const T v = xs[k * TC + c];
+    return (flip && (k & 1)) ? -v : v;
+  };
+  for (int idx = threadIdx.x; idx < m * TC; idx += blockDim.x) {
+    const int j = idx / TC, c = idx % TC;
+    Cx<T> z;
+    if (kind == KIND_PP) {
+      z = {x(2 * j, c), x(2 * j + 1, c)};
+    } else if (kind == KIND_NN || kind == KIND_DD) {
+      const int t0 = 2 * j, t1 = 2 * j + 1;  // v_t = x_2t (t < m), x_{2(n-1-t)+1} (t >= m)
+      z = {t0 < m ? x(2 * t0, c) : x(2 * (n - 1 - t0) + 1, c), t1 < m ? x(2 * t1, c) : x(2 * (n - 1 - t1) + 1, c)};
+    } else {
+      z = cmul(Cx<T>{x(2 * j, c), x(n - 1 - 2 * j, c)}, tw.tw4a[j]);
+    }
+    A[idx] = z;
+  }
+  __syncthreads();
+  const Cx<T>* R = cfft<T, TC>(A, Bf, m, tw.fft, false);
+  for (int idx = threadIdx.x; idx < n * TC; idx += blockDim.x) {
+    const int q = idx / TC, c = idx % TC;
+    T y;
+    if (kind == KIND_PP) {
+      const int k = q <= m ? q : n - q;
+      const Cx<T> X = rdft_bin<T, TC>(R, k, m, c, tw);
+      y = q <= m ? X.re : X.im;
+    } else if (kind == KIND_NN || kind == KIND_DD) {
+      const int qq = kind == KIND_DD ? n - 1 - q : q;
+      const int k = qq <= m ? qq : n - qq;
+      Cx<T> V = rdft_bin<T, TC>(R, k, m, c, tw);
+      if (qq > m) V = conj(V);
+      const Cx<T> w = tw.tw2n[qq];
+      y = (T)2 * (w.re * V.re - w.im * V.im);
+    } else {
+      const int qq = kind == KIND_DN ? n - 1 - q : q;
+      if ((qq & 1) == 0) {
+        const int k = qq / 2;
+        y = (T)2 * cmul(R[k * TC + c], tw.tw4b[k]).re;
+      } else {
+        const int k = (n - 1 - qq) / 2;
+        y = (T)-2 * cmul(R[k * TC + c], tw.tw4b[k]).im;
+      }
+    }
+    if (c < ch.ncol) out[(long long)q * ncell + B.off + ch.c0 + c] = y;
+  }
+}
+
+template <typename T, int TC>
+__global__ void __launch_bounds__(256) k_backward(const ChunkDev* __restrict__ chunks, const BlockDev* __restrict__ blk,
+                                                  int n, int kind, Tw<T> tw, const T* __restrict__ modes,
+                                                  double* __restrict__ p3, long long ncell, double inv_theta) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int m = n / 2;
+  Cx<T>* A = reinterpret_cast<Cx<T>*>(smem);
+  Cx<T>* Bf = A + m * TC;
+  T* xs = reinterpret_cast<T*>(Bf);
+  const ChunkDev ch = chunks[blockIdx.x];
+  const BlockDev B = blk[ch.b];
+  for (int idx = threadIdx.x; idx < n * TC; idx += blockDim.x) {
+    const int q = idx / TC, c = idx % TC;
+    xs[idx] = c < ch.ncol ? modes[(long long)q * ncell + B.off + ch.c0 + c] : (T)0;
+  }
+  __syncthreads();
+  const bool rev = kind == KIND_DD;                 // DST-III reads X reversed
+  const bool flip = kind == KIND_DN;                // DST-IV = DCT-IV of the sign-flipped input, reversed
+  auto X = [&](int k, int c) -> T {
+    if (k >= n) return (T)0;
+    const int kk = rev ? n - 1 - k : k;
+    const T v = xs[kk * TC + c];
+    return (flip && (k & 1)) ? -v : v;
+  };
+  for (int idx = threadIdx.x; idx < m * TC; idx += blockDim.x) {
+    const int k = idx / TC, c = idx % TC;
+    Cx<T> z;
+    if (kind == KIND_PP) {
+      const Cx<T> xk = k == 0 ? Cx<T>{X(0, c), 0} : Cx<T>{X(k, c), X(n - k, c)};
+      const int mk = m - k;
+      const Cx<T> xmk = mk == m ? Cx<T>{X(m, c), 0} : (mk == 0 ? Cx<T>{X(0, c), 0} : Cx<T>{X(mk, c), X(n - mk, c)});
+      z = irdft_pre(xk, xmk, tw.twn[k]);
+    } else if (kind == KIND_NN || kind == KIND_DD) {
+      // V_k = e^{+i pi k/2n} (X_k - i X_{n-k}), the real DFT of the reordered sequence
+      auto V = [&](int kk) -> Cx<T> {
+        Cx<T> v = cmul(conj(tw.tw2n[kk]), Cx<T>{X(kk, c), -X(n - kk, c)});
+        if (kk == 0 || kk == m) v.im = 0;
+        return v;
+      };
+      z = irdft_pre(V(k), V(m - k), tw.twn[k]);
+    } else {
+      z = cmul(Cx<T>{X(2 * k, c), X(n - 1 - 2 * k, c)}, tw.tw4a[k]);
+    }
+    A[idx] = z;
+  }
+  __syncthreads();
+  const bool inv = kind == KIND_PP || kind == KIND_NN || kind == KIND_DD;
+  const Cx<T>* R = cfft<T, TC>(A, Bf, m, tw.fft, inv);
+  const long long plane = (long long)B.nx * B.ny;
+  const long long base3 = (long long)n * B.off + ch.c0;
+  for (int idx = threadIdx.x; idx < n * TC; idx += blockDim.x) {
+    const int j = idx / TC, c = idx % TC;
+    T y;
+    if (kind == KIND_PP) {
+      const Cx<T> z = R[(j >> 1) * TC + c];
+      y = (j & 1) ? z.im : z.re;
+    } else if (kind == KIND_NN || kind == KIND_DD) {
+      const int t = (j & 1) ? n - 1 - (j >> 1) : (j >> 1);  // x_2t = v_t, x_2t+1 = v_{n-1-t}
+      const Cx<T> z = R[(t >> 1) * TC + c];
+      y = (t & 1) ? z.im : z.re;
+      if (kind == KIND_DD && (j & 1)) y = -y;
+    } else {
+      const int qq = kind == KIND_DN ? n - 1 - j : j;
+      if ((qq & 1) == 0) {
+        const int k = qq / 2;
+        y = (T)2 * cmul(R[k * TC + c], tw.tw4b[k]).re;
+      } else {
+        const int k = (n - 1 - qq) / 2;
+        y = (T)-2 * cmul(R[k * TC + c], tw.tw4b[k]).im;
+      }
+    }
+    if (c < ch.ncol) {
+      double* dst = p3 + base3 + j * plane + c;
+      *dst = fma((double)y, inv_theta, *dst);
+    }
+  }
+}
+
+template <typename T>
+Tw<T> make_tw(const snac_plan* P, const void* base) {
+  const Cx<T>* t = reinterpret_cast<const Cx<T>*>(base);
+  return Tw<T>{t + P->tw.fft, t + P->tw.twn, t + P->tw.tw2n, t + P->tw.tw4a, t + P->tw.tw4b};
+}
+
+template <typename T, int TC>
+cudaError_t fwd_t(snac_plan* P, const std::vector<ChunkDev>& ch, const ChunkDev* dch, const void* twb, const double* in3,
+                  void* modes, cudaStream_t s) {
+  const size_t smem = 2 * (size_t)(P->nz / 2) * TC * sizeof(Cx<T>);
+  cudaFuncSetAttribute(k_forward<T, TC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  k_forward<T, TC><<<(unsigned)ch.size(), 256, smem, s>>>(dch, P->lev[0].d_blk, P->nz, P->kind, make_tw<T>(P, twb), in3,
+                                                          (T*)modes, P->lev[0].ncell);
+  return cudaGetLastError();
+}
+
+template <typename T, int TC>
+cudaError_t bwd_t(snac_plan* P, const std::vector<ChunkDev>& ch, const ChunkDev* dch, const void* twb, const void* modes,
+                  double* p3, cudaStream_t s) {
+  const size_t smem = 2 * (size_t)(P->nz / 2) * TC * sizeof(Cx<T>);
+  cudaFuncSetAttribute(k_backward<T, TC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  k_backward<T, TC><<<(unsigned)ch.size(), 256, smem, s>>>(dch, P->lev[0].d_blk, P->nz, P->kind, make_tw<T>(P, twb),
+                                                           (const T*)modes, p3, P->lev[0].ncell, 1.0 / P->theta);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_forward(snac_plan* P, const double* in3, void* modes, cudaStream_t s) {
+  if (P->precision == SNAC_FP64) return fwd_t<double, 8>(P, P->chunks64, P->d_chunks64, P->d_tw64, in3, modes, s);
+  return fwd_t<float, 16>(P, P->chunks32, P->d_chunks32, P->d_tw32, in3, modes, s);
+}
+
+cudaError_t launch_backward_update(snac_plan* P, const void* modes, double* p3, cudaStream_t s) {
+  if (P->precision == SNAC_FP64) return bwd_t<double, 8>(P, P->chunks64, P->d_chunks64, P->d_tw64, modes, p3, s);
+  return bwd_t<float, 16>(P, P->chunks32, P->d_chunks32, P->d_tw32, modes, p3, s);
+}
+
+}  // namespace snac

@@ -1,0 +1,660 @@
+// Plan creation: validation of the block graph, multigrid hierarchy, operator coefficients,
+// eigenvalue shifts, transform twiddles, coarsest-level factorisation and device workspace.
+//
+// Discretisation (Eq. 8, Sec. 2; general non-uniform form, footnote of Sec. 3.3): cell-centred
+// pressure, row of cell i along a stretched axis
+//     [(p_{i+1} - p_i)/h_{i+1/2} - (p_i - p_{i-1})/h_{i-1/2}] / w_i,   h = (w_i + w_nbr)/2,
+// homogeneous Dirichlet / Neumann faces by a mirrored ghost (-p / +p at distance w_i), block-block
+// and periodic faces by the connected cell (Sec. 3.1). The homogeneous axis z is uniform and
+// diagonalised by the transform of Table 1 with eigenvalues lambda_q = 2 (cos(kappa_q dz) - 1).
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "snac_impl.h"
+
+using namespace snac;
+
+namespace snac {
+thread_local std::string g_last_error;
+void set_error(const std::string& s) { g_last_error = s; }
+}  // namespace snac
+
+namespace {
+
+struct HBlock {
+  long long lo[3], hi[3];
+  int n[3];
+  std::vector<double> w[3];
+  int bc[3][2];
+  int nbr[3][2];
+};
+
+int fail(int code, const std::string& msg) {
+  set_error(msg);
+  return code;
+}
+
+// Face number of (axis, side): W, E, S, N = 0..3.
+inline int face(int axis, int side) { return 2 * axis + side; }
+
+int validate(int nb, const snac_block* in, std::vector<HBlock>& out) {
+  out.resize(nb);
+  for (int b = 0; b < nb; ++b) {
+    const snac_block& s = in[b];
+    HBlock& h = out[b];
+    for (int a = 0; a < 3; ++a) {
+      h.lo[a] = s.lo[a];
+      h.hi[a] = s.hi[a];
+      long long n = s.hi[a] - s.lo[a] + 1;
+      if (n < 1 || n > (1LL << 24)) return fail(SNAC_ERR_INVALID_ARG, "block " + std::to_string(b) + ": bad lo/hi");
+      h.n[a] = (int)n;
+      if (!s.h_dx[a]) return fail(SNAC_ERR_INVALID_ARG, "block " + std::to_string(b) + ": h_dx is NULL");
+      h.w[a].assign(s.h_dx[a], s.h_dx[a] + n);
+      for (double w : h.w[a])
+        if (!(w > 0.0) || !std::isfinite(w))
+          return fail(SNAC_ERR_INVALID_ARG, "block " + std::to_string(b) + ": cell widths must be finite and > 0");
+      for (int sd = 0; sd < 2; ++sd) {
+        h.bc[a][sd] = s.bc[a][sd];
+        h.nbr[a][sd] = s.nbr[a][sd];
+        if (h.bc[a][sd] < SNAC_BC_DIRICHLET || h.bc[a][sd] > SNAC_BC_BLOCK)
+          return fail(SNAC_ERR_INVALID_ARG, "block " + std::to_string(b) + ": unknown face kind");
+      }
+    }
+  }
+  // homogeneous axis: same n_z, the same uniform widths, the same pair, not split into blocks
+  const HBlock& b0 = out[0];
+  const int nz = b0.n[2];
+  for (int b = 0; b < nb; ++b) {
+    const HBlock& h = out[b];
+    if (h.n[2] != nz) return fail(SNAC_ERR_LAYOUT, "all blocks must have the same n_z");
+    for (int sd = 0; sd < 2; ++sd)
+      if (h.bc[2][sd] != b0.bc[2][sd]) return fail(SNAC_ERR_LAYOUT, "all blocks must share the z boundary pair");
+    for (int k = 0; k < nz; ++k)
+      if (h.w[2][k] != b0.w[2][k]) return fail(SNAC_ERR_LAYOUT, "all blocks must share the z grid");
+  }
+  for (int k = 0; k < nz; ++k)
+    if (std::fabs(b0.w[2][k] - b0.w[2][0]) > 1e-12 * b0.w[2][0])
+      return fail(SNAC_ERR_LAYOUT, "the homogeneous direction must be uniform (Sec. 2)");
+  if (b0.bc[2][0] == SNAC_BC_BLOCK || b0.bc[2][1] == SNAC_BC_BLOCK)
+    return fail(SNAC_ERR_LAYOUT, "blocks cannot be connected along the homogeneous direction");
+  if ((b0.bc[2][0] == SNAC_BC_PERIODIC) != (b0.bc[2][1] == SNAC_BC_PERIODIC))
+    return fail(SNAC_ERR_LAYOUT, "a periodic z needs both z faces periodic");
+  if (nz % 2) return fail(SNAC_ERR_LAYOUT, "n_z must be even (Table 1)");
+  if (nz > MAX_NZ) return fail(SNAC_ERR_LAYOUT, "n_z above the supported maximum 1024");
+  // x-y connectivity
+  for (int b = 0; b < nb; ++b) {
+    const HBlock& h = out[b];
+    for (int a = 0; a < 2; ++a) {
+      const int o = 1 - a;
+      if ((h.bc[a][0] == SNAC_BC_PERIODIC) != (h.bc[a][1] == SNAC_BC_PERIODIC))
+        return fail(SNAC_ERR_LAYOUT, "block " + std::to_string(b) + ": periodic needs both faces of the axis");
+      for (int sd = 0; sd < 2; ++sd) {
+        if (h.bc[a][sd] != SNAC_BC_BLOCK) continue;
+        const int c = h.nbr[a][sd];
+        if (c < 0 || c >= nb) return fail(SNAC_ERR_LAYOUT, "block " + std::to_string(b) + ": bad neighbour id");
+        const HBlock& g = out[c];
+        if (g.bc[a][1 - sd] != SNAC_BC_BLOCK || g.nbr[a][1 - sd] != b)
+          return fail(SNAC_ERR_LAYOUT, "block " + std::to_string(b) + ": connectivity with block " +
+                                           std::to_string(c) + " is not symmetric");
+        if (g.lo[o] != h.lo[o] || g.hi[o] != h.hi[o])
+          return fail(SNAC_ERR_LAYOUT, "block " + std::to_string(b) + ": face shared with block " +
+                                           std::to_string(c) + " does not coincide");
+        if (g.w[o] != h.w[o])
+          return fail(SNAC_ERR_LAYOUT, "block " + std::to_string(b) + ": grid not congruent with block " +
+                                           std::to_string(c) + " (Sec. 3.1)");
+      }
+    }
+  }
+  return SNAC_OK;
+}
+
+// Cyclic Jacobi eigenvalue iteration for a small symmetric matrix S (n x n, row-major).
+// On return S is (numerically) diagonal with the eigenvalues, Q holds the eigenvectors as columns.
+void jacobi_eigen(int n, std::vector<double>& S, std::vector<double>& Q) {
+  Q.assign((size_t)n * n, 0.0);
+  for (int i = 0; i < n; ++i) Q[(size_t)i * n + i] = 1.0;
+  double norm = 0.0;
+  for (double v : S) norm += v * v;
+  for (int sweep = 0; sweep < 100; ++sweep) {
+    double off = 0.0;
+    for (int p = 0; p < n; ++p)
+      for (int q = p + 1; q < n; ++q) off += S[(size_t)p * n + q] * S[(size_t)p * n + q];
+    if (off <= 1e-32 * norm) break;
+    for (int p = 0; p < n; ++p) {
+      for (int q = p + 1; q < n; ++q) {
+        const double apq = S[(size_t)p * n + q];
+        if (std::fabs(apq) < 1e-300) continue;
+        const double app = S[(size_t)p * n + p], aqq = S[(size_t)q * n + q];
+        const double th = (aqq - app) / (2.0 * apq);
+        const double t = (th >= 0 ? 1.0 : -1.0) / (std::fabs(th) + std::sqrt(th * th + 1.0));
+        const double c = 1.0 / std::sqrt(t * t + 1.0), s = t * c;
+        for (int k = 0; k < n; ++k) {  // columns p, q
+          const double skp = S[(size_t)k * n + p], skq = S[(size_t)k * n + q];
+          S[(size_t)k * n + p] = c * skp - s * skq;
+          S[(size_t)k * n + q] = s * skp + c * skq;
+        }
+        for (int k = 0; k < n; ++k) {  // rows p, q
+          const double spk = S[(size_t)p * n + k], sqk = S[(size_t)q * n + k];
+          S[(size_t)p * n + k] = c * spk - s * sqk;
+          S[(size_t)q * n + k] = s * spk + c * sqk;
+        }
+        for (int k = 0; k < n; ++k) {
+          const double qkp = Q[(size_t)k * n + p], qkq = Q[(size_t)k * n + q];
+          Q[(size_t)k * n + p] = c * qkp - s * qkq;
+          Q[(size_t)k * n + q] = s * qkp + c * qkq;
+        }
+      }
+    }
+  }
+}
+
+template <typename T>
+int dmalloc(snac_plan* P, T** ptr, size_t count) {
+  *ptr = nullptr;
+  if (count == 0) count = 1;
+  void* p = nullptr;
+  cudaError_t e = cudaMalloc(&p, count * sizeof(T));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(e == cudaErrorMemoryAllocation ? SNAC_ERR_OOM : SNAC_ERR_CUDA,
+                std::string("cudaMalloc: ") + cudaGetErrorString(e));
+  }
+  P->allocs.push_back(p);
+  P->bytes += count * sizeof(T);
+  *ptr = (T*)p;
+  return SNAC_OK;
+}
+
+template <typename T>
+int upload(snac_plan* P, T** ptr, const std::vector<T>& v) {
+  int st = dmalloc(P, ptr, v.size());
+  if (st) return st;
+  if (!v.empty() && cudaMemcpy(*ptr, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice) != cudaSuccess)
+    return fail(SNAC_ERR_CUDA, "cudaMemcpy upload failed");
+  return SNAC_OK;
+}
+
+template <typename T>
+std::vector<Coef<float>> to32(const std::vector<Coef<T>>& v) {
+  std::vector<Coef<float>> o(v.size());
+  for (size_t i = 0; i < v.size(); ++i) o[i] = {(float)v[i].lo, (float)v[i].hi, (float)v[i].d, (float)v[i].w};
+  return o;
+}
+std::vector<PW<float>> to32(const std::vector<PW<double>>& v) {
+  std::vector<PW<float>> o(v.size());
+  for (size_t i = 0; i < v.size(); ++i) o[i] = {(float)v[i].self, (float)v[i].nbr};
+  return o;
+}
+std::vector<float> to32(const std::vector<double>& v) { return std::vector<float>(v.begin(), v.end()); }
+
+// Widths of every block along one axis at a level (level-0 widths summed in groups of 2^l).
+std::vector<double> level_widths(const std::vector<double>& w0, int l) {
+  const int g = 1 << l;
+  std::vector<double> w(w0.size() / g, 0.0);
+  for (size_t i = 0; i < w.size(); ++i)
+    for (int k = 0; k < g; ++k) w[i] += w0[i * g + k];
+  return w;
+}
+
+// 1-D operator pieces along one axis of one block: coupling to the lower/upper neighbour with the
+// centre distance h = (w + w_nbr)/2, or the ghost rule of a physical face.
+void axis_coefs(const std::vector<double>& w, int bc_lo, int bc_hi, double w_nlo, double w_nhi,
+                std::vector<Coef<double>>& out) {
+  const int n = (int)w.size();
+  for (int i = 0; i < n; ++i) {
+    Coef<double> c{0.0, 0.0, 0.0, w[i]};
+    for (int sd = 0; sd < 2; ++sd) {
+      const bool inner = sd == 0 ? i > 0 : i < n - 1;
+      const int bc = sd == 0 ? bc_lo : bc_hi;
+      double a = 0.0;
+      if (inner || bc == SNAC_BC_BLOCK || bc == SNAC_BC_PERIODIC) {
+        const double wn = inner ? w[sd == 0 ? i - 1 : i + 1] : (sd == 0 ? w_nlo : w_nhi);
+        a = 1.0 / (0.5 * (w[i] + wn) * w[i]);
+        c.d -= a;
+      } else if (bc == SNAC_BC_DIRICHLET) {
+        c.d -= 2.0 / (w[i] * w[i]);
+      }
+      (sd == 0 ? c.lo : c.hi) = a;
+    }
+    out.push_back(c);
+  }
+}
+
+int build_levels(snac_plan* P, const std::vector<HBlock>& hb) {
+  const int nb = (int)hb.size();
+  long long lox = hb[0].lo[0], loy = hb[0].lo[1];
+  for (const HBlock& h : hb) {
+    lox = std::min(lox, h.lo[0]);
+    loy = std::min(loy, h.lo[1]);
+  }
+  // number of levels
+  int L = 0;
+  for (;;) {
+    long long ncell = 0;
+    bool ok = true;
+    for (const HBlock& h : hb) {
+      const int nx = h.n[0] >> L, ny = h.n[1] >> L;
+      ncell += (long long)nx * ny;
+      const long long rx = h.lo[0] - lox, ry = h.lo[1] - loy;
+      if (nx % 2 || ny % 2 || nx < 4 || ny < 4) ok = false;
+      if (rx % (2LL << L) || ry % (2LL << L)) ok = false;
+    }
+    if (ncell <= P->max_coarse || !ok) break;
+    ++L;
+  }
+  P->lev.assign(L + 1, HostLevel());
+  for (int l = 0; l <= L; ++l) {
+    HostLevel& lv = P->lev[l];
+    lv.nblk = nb;
+    std::vector<std::vector<double>> wx(nb), wy(nb);
+    for (int b = 0; b < nb; ++b) {
+      wx[b] = level_widths(hb[b].w[0], l);
+      wy[b] = level_widths(hb[b].w[1], l);
+    }
+    long long off = 0;
+    int xo = 0, yo = 0;
+    for (int b = 0; b < nb; ++b) {
+      BlockDev d{};
+      d.off = off;
+      d.nx = (int)wx[b].size();
+      d.ny = (int)wy[b].size();
+      d.xo = xo;
+      d.yo = yo;
+      for (int a = 0; a < 2; ++a)
+        for (int sd = 0; sd < 2; ++sd) {
+          const int bc = hb[b].bc[a][sd];
+          d.nbr[face(a, sd)] = bc == SNAC_BC_BLOCK ? hb[b].nbr[a][sd] : (bc == SNAC_BC_PERIODIC ? b : -1);
+        }
+      const long long rx = (hb[b].lo[0] - lox) >> l, ry = (hb[b].lo[1] - loy) >> l;
+      d.par = (int)((rx + ry) & 1);
+      lv.blk.push_back(d);
+      off += (long long)d.nx * d.ny;
+      xo += d.nx;
+      yo += d.ny;
+      for (int y0 = 0; y0 < d.ny; y0 += TILE_Y)
+        for (int x0 = 0; x0 < d.nx; x0 += TILE_X) lv.tiles.push_back({b, x0, y0, 0});
+    }
+    lv.ncell = off;
+    for (int b = 0; b < nb; ++b) {
+      const BlockDev& d = lv.blk[b];
+      auto nbw = [&](int a, int sd) -> double {  // width of the connected cell across a face
+        const int c = d.nbr[face(a, sd)];
+        if (c < 0) return 0.0;
+        const std::vector<double>& w = a == 0 ? wx[c] : wy[c];
+        return sd == 0 ? w.back() : w.front();
+      };
+      axis_coefs(wx[b], hb[b].bc[0][0], hb[b].bc[0][1], nbw(0, 0), nbw(0, 1), lv.cx);
+      axis_coefs(wy[b], hb[b].bc[1][0], hb[b].bc[1][1], nbw(1, 0), nbw(1, 1), lv.cy);
+    }
+  }
+  // transfer weights between level l (fine) and l+1 (coarse)
+  for (int l = 0; l < L; ++l) {
+    HostLevel& fl = P->lev[l];
+    const HostLevel& cl = P->lev[l + 1];
+    for (int b = 0; b < nb; ++b) {
+      for (int a = 0; a < 2; ++a) {
+        const BlockDev& fd = fl.blk[b];
+        const BlockDev& cd = cl.blk[b];
+        const int n = a == 0 ? fd.nx : fd.ny;
+        const int nco = a == 0 ? cd.nx : cd.ny;
+        const Coef<double>* fc = (a == 0 ? fl.cx.data() + fd.xo : fl.cy.data() + fd.yo);
+        const Coef<double>* cc = (a == 0 ? cl.cx.data() + cd.xo : cl.cy.data() + cd.yo);
+        for (int i = 0; i < n; ++i) {
+          const int I = i / 2, sd = i & 1;
+          // fine centre to parent centre: half the sibling's width
+          const double dist = 0.5 * fc[i ^ 1].w;
+          const double W = cc[I].w;
+          double self = 0.0, nbrw = 0.0;
+          const bool inner = sd == 0 ? I > 0 : I < nco - 1;
+          const int bc = hb[b].bc[a][sd];
+          if (inner || bc == SNAC_BC_BLOCK || bc == SNAC_BC_PERIODIC) {
+            double Wn;
+            if (inner) {
+              Wn = cc[sd == 0 ? I - 1 : I + 1].w;
+            } else {
+              const int c = cd.nbr[face(a, sd)];
+              const BlockDev& nd = cl.blk[c];
+              const Coef<double>* nc = a == 0 ? cl.cx.data() + nd.xo : cl.cy.data() + nd.yo;
+              const int nn = a == 0 ? nd.nx : nd.ny;
+              Wn = sd == 0 ? nc[nn - 1].w : nc[0].w;
+            }
+            const double wgt = dist / (0.5 * (W + Wn));
+            self = -wgt;
+            nbrw = wgt;
+          } else if (bc == SNAC_BC_DIRICHLET) {
+            self = -2.0 * dist / W;  // ghost -e_C at the mirrored centre, distance W
+          }
+          (a == 0 ? fl.px : fl.py).push_back({self, nbrw});
+          (a == 0 ? fl.rx : fl.ry).push_back(fc[i].w / W);
+        }
+      }
+    }
+  }
+  return SNAC_OK;
+}
+
+double mode_lambda(int kind, int n, int q) {
+  double m;
+  switch (kind) {
+    case KIND_PP: m = q; break;
+    case KIND_NN: m = 0.5 * q; break;
+    case KIND_DD: m = 0.5 * (q + 1); break;
+    default: m = 0.25 * (2 * q + 1); break;
+  }
+  return 2.0 * (std::cos(2.0 * M_PI * m / n) - 1.0);
+}
+
+// Weight w_q with sum_k x_k^2 = sum_q w_q Xhat_q^2 for the unnormalised transforms of Table 1.
+double parseval_weight(int kind, int n, int q) {
+  switch (kind) {
+    case KIND_PP: return (q == 0 || q == n / 2) ? 1.0 / n : 2.0 / n;
+    case KIND_NN: return q == 0 ? 0.25 / n : 0.5 / n;
+    case KIND_DD: return q == n - 1 ? 0.25 / n : 0.5 / n;
+    default: return 0.5 / n;
+  }
+}
+
+int build_coarse(snac_plan* P) {
+  const HostLevel& lv = P->lev.back();
+  const int n = (int)lv.ncell;
+  if (n > MAX_COARSE)
+    return fail(SNAC_ERR_LAYOUT, "the coarsest multigrid plane has " + std::to_string(n) +
+                                     " cells (> 256): blocks must be divisible by 2 more often");
+  P->nc = n;
+  std::vector<double> A((size_t)n * n, 0.0), area(n);
+  for (int b = 0; b < lv.nblk; ++b) {
+    const BlockDev& d = lv.blk[b];
+    for (int j = 0; j < d.ny; ++j)
+      for (int i = 0; i < d.nx; ++i) {
+        const Coef<double>& cx = lv.cx[d.xo + i];
+        const Coef<double>& cy = lv.cy[d.yo + j];
+        const long long row = d.off + (long long)j * d.nx + i;
+        area[row] = cx.w * cy.w;
+        A[row * n + row] += cx.d + cy.d;
+        auto cell = [&](int bb, int ii, int jj) { return lv.blk[bb].off + (long long)jj * lv.blk[bb].nx + ii; };
+        if (cx.lo != 0.0) {
+          const long long c = i > 0 ? cell(b, i - 1, j) : cell(d.nbr[0], lv.blk[d.nbr[0]].nx - 1, j);
+          A[row * n + c] += cx.lo;
+        }
+        if (cx.hi != 0.0) {
+          const long long c = i < d.nx - 1 ? cell(b, i + 1, j) : cell(d.nbr[1], 0, j);
+          A[row * n + c] += cx.hi;
+        }
+        if (cy.lo != 0.0) {
+          const long long c = j > 0 ? cell(b, i, j - 1) : cell(d.nbr[2], i, lv.blk[d.nbr[2]].ny - 1);
+          A[row * n + c] += cy.lo;
+        }
+        if (cy.hi != 0.0) {
+          const long long c = j < d.ny - 1 ? cell(b, i, j + 1) : cell(d.nbr[3], i, 0);
+          A[row * n + c] += cy.hi;
+        }
+      }
+  }
+  // S = V^1/2 A V^-1/2 is symmetric because V A is (finite-volume fluxes)
+  std::vector<double> S((size_t)n * n), sqa(n);
+  for (int i = 0; i < n; ++i) sqa[i] = std::sqrt(area[i]);
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) S[(size_t)i * n + j] = sqa[i] * A[(size_t)i * n + j] / sqa[j];
+  for (int i = 0; i < n; ++i)
+    for (int j = i + 1; j < n; ++j) {
+      const double m = 0.5 * (S[(size_t)i * n + j] + S[(size_t)j * n + i]);
+      S[(size_t)i * n + j] = S[(size_t)j * n + i] = m;
+    }
+  std::vector<double> Q;
+  jacobi_eigen(n, S, Q);
+  std::vector<double> lam(n);
+  for (int i = 0; i < n; ++i) lam[i] = S[(size_t)i * n + i];
+  P->null_index = -1;
+  if (P->singular) {
+    int k = 0;
+    for (int i = 1; i < n; ++i)
+      if (std::fabs(lam[i]) < std::fabs(lam[k])) k = i;
+    P->null_index = k;
+  }
+  int st;
+  if ((st = upload(P, &P->d_Q, Q)) || (st = upload(P, &P->d_lam, lam)) || (st = upload(P, &P->d_sqa, sqa))) return st;
+  return SNAC_OK;
+}
+
+int build_twiddles(snac_plan* P) {
+  const int n = P->nz, m = n / 2;
+  TwiddleOffsets& t = P->tw;
+  t.fft = 0;
+  t.twn = t.fft + m;
+  t.tw2n = t.twn + m + 1;
+  t.tw4a = t.tw2n + n + 1;
+  t.tw4b = t.tw4a + m;
+  t.total = t.tw4b + m;
+  std::vector<double> tw(2 * (size_t)t.total);
+  auto put = [&](int idx, double ang) {
+    tw[2 * idx] = std::cos(ang);
+    tw[2 * idx + 1] = std::sin(ang);
+  };
+  for (int k = 0; k < m; ++k) put(t.fft + k, -2.0 * M_PI * k / m);
+  for (int k = 0; k <= m; ++k) put(t.twn + k, -2.0 * M_PI * k / n);
+  for (int k = 0; k <= n; ++k) put(t.tw2n + k, -M_PI * k / (2.0 * n));
+  for (int k = 0; k < m; ++k) put(t.tw4a + k, -M_PI * (4.0 * k + 1.0) / (4.0 * n));
+  for (int k = 0; k < m; ++k) put(t.tw4b + k, -M_PI * k / (double)n);
+  int st;
+  if ((st = upload(P, &P->d_tw64, tw))) return st;
+  if ((st = upload(P, &P->d_tw32, to32(tw)))) return st;
+  return SNAC_OK;
+}
+
+int build_chunks(snac_plan* P, int tc, std::vector<ChunkDev>& ch, ChunkDev** d) {
+  const HostLevel& l0 = P->lev[0];
+  for (int b = 0; b < l0.nblk; ++b) {
+    const int cells = l0.blk[b].nx * l0.blk[b].ny;
+    for (int c0 = 0; c0 < cells; c0 += tc) ch.push_back({b, c0, std::min(tc, cells - c0), 0});
+  }
+  return upload(P, d, ch);
+}
+
+int upload_level(snac_plan* P, HostLevel& lv, size_t inner) {
+  int st;
+  if ((st = upload(P, &lv.d_blk, lv.blk)) || (st = upload(P, &lv.d_tiles, lv.tiles)) ||
+      (st = upload(P, &lv.d_cx64, lv.cx)) || (st = upload(P, &lv.d_cy64, lv.cy)) ||
+      (st = upload(P, &lv.d_cx32, to32(lv.cx))) || (st = upload(P, &lv.d_cy32, to32(lv.cy))))
+    return st;
+  if (!lv.px.empty()) {
+    if ((st = upload(P, &lv.d_px64, lv.px)) || (st = upload(P, &lv.d_py64, lv.py)) ||
+        (st = upload(P, &lv.d_px32, to32(lv.px))) || (st = upload(P, &lv.d_py32, to32(lv.py))) ||
+        (st = upload(P, &lv.d_rx64, lv.rx)) || (st = upload(P, &lv.d_ry64, lv.ry)) ||
+        (st = upload(P, &lv.d_rx32, to32(lv.rx))) || (st = upload(P, &lv.d_ry32, to32(lv.ry))))
+      return st;
+  }
+  char* u = nullptr;
+  char* f = nullptr;
+  const size_t cnt = (size_t)P->nz * lv.ncell * inner;
+  if ((st = dmalloc(P, &u, cnt)) || (st = dmalloc(P, &f, cnt))) return st;
+  lv.d_u = u;
+  lv.d_f = f;
+  return SNAC_OK;
+}
+
+void free_plan(snac_plan* P) {
+  if (!P) return;
+  for (void* p : P->allocs) cudaFree(p);
+  if (P->h_sums) cudaFreeHost(P->h_sums);
+  if (P->h_mode_norm2) cudaFreeHost(P->h_mode_norm2);
+  if (P->h_active) cudaFreeHost(P->h_active);
+  delete P;
+}
+
+int create(snac_plan** out, int32_t nblocks, const snac_block* blocks, int32_t homog_axis, const snac_options* opt) {
+  if (!out || !blocks || nblocks < 1) return fail(SNAC_ERR_INVALID_ARG, "out/blocks NULL or nblocks < 1");
+  *out = nullptr;
+  if (homog_axis != 2) return fail(SNAC_ERR_INVALID_ARG, "only homog_axis = 2 (z) is supported");
+  std::vector<HBlock> hb;
+  int st = validate(nblocks, blocks, hb);
+  if (st) return st;
+  snac_plan* P = new (std::nothrow) snac_plan();
+  if (!P) return fail(SNAC_ERR_OOM, "host allocation");
+  if (opt) {
+    P->precision = opt->precision;
+    P->nu1 = opt->nu1;
+    P->nu2 = opt->nu2;
+    P->max_outer = opt->max_outer;
+    P->max_cycles = opt->max_cycles;
+    P->max_coarse = opt->max_coarse;
+    if ((P->precision != SNAC_FP64 && P->precision != SNAC_MIXED) || P->nu1 < 0 || P->nu2 < 0 ||
+        P->nu1 + P->nu2 < 1 || P->nu1 > 16 || P->nu2 > 16 || P->max_outer < 1 || P->max_cycles < 1 ||
+        P->max_coarse < 1 || P->max_coarse > MAX_COARSE) {
+      delete P;
+      return fail(SNAC_ERR_INVALID_ARG, "bad snac_options");
+    }
+  }
+  cudaGetDevice(&P->device);
+  P->nblk = nblocks;
+  P->nz = hb[0].n[2];
+  P->dz = hb[0].w[2][0];
+  const int zl = hb[0].bc[2][0], zh = hb[0].bc[2][1];
+  if (zl == SNAC_BC_PERIODIC) P->kind = KIND_PP;
+  else if (zl == SNAC_BC_NEUMANN && zh == SNAC_BC_NEUMANN) P->kind = KIND_NN;
+  else if (zl == SNAC_BC_DIRICHLET && zh == SNAC_BC_DIRICHLET) P->kind = KIND_DD;
+  else if (zl == SNAC_BC_NEUMANN) P->kind = KIND_ND;
+  else P->kind = KIND_DN;
+  P->theta = P->kind == KIND_PP ? P->nz : 2.0 * P->nz;
+  bool dirichlet_xy = false;
+  for (const HBlock& h : hb)
+    for (int a = 0; a < 2; ++a)
+      for (int sd = 0; sd < 2; ++sd) dirichlet_xy |= h.bc[a][sd] == SNAC_BC_DIRICHLET;
+  P->singular = (P->kind == KIND_PP || P->kind == KIND_NN) && !dirichlet_xy;
+  const size_t inner = P->precision == SNAC_FP64 ? sizeof(double) : sizeof(float);
+  long long off3 = 0;
+  P->vol_total = 0.0;
+  P->area_total = 0.0;
+  for (const HBlock& h : hb) {
+    P->blk_off3.push_back(off3);
+    off3 += (long long)h.n[0] * h.n[1] * h.n[2];
+    double ax = 0, ay = 0;
+    for (double w : h.w[0]) ax += w;
+    for (double w : h.w[1]) ay += w;
+    P->area_total += ax * ay;
+  }
+  P->n3 = off3;
+  P->vol_total = P->area_total * P->dz * P->nz;
+
+  do {
+    if ((st = build_levels(P, hb))) break;
+    for (HostLevel& lv : P->lev)
+      if ((st = upload_level(P, lv, inner))) break;
+    if (st) break;
+    // z operator pieces (uniform spacing, ghosts of the pair)
+    const double iz2 = 1.0 / (P->dz * P->dz);
+    for (int k = 0; k < P->nz; ++k) {
+      const bool per = P->kind == KIND_PP;
+      Coef<double> c{(k > 0 || per) ? iz2 : 0.0, (k < P->nz - 1 || per) ? iz2 : 0.0, 0.0, P->dz};
+      c.d = -(c.lo + c.hi);
+      if (!per && k == 0 && zl == SNAC_BC_DIRICHLET) c.d -= 2.0 * iz2;
+      if (!per && k == P->nz - 1 && zh == SNAC_BC_DIRICHLET) c.d -= 2.0 * iz2;
+      P->cz.push_back(c);
+    }
+    if ((st = upload(P, &P->d_cz, P->cz))) break;
+    for (int q = 0; q < P->nz; ++q) {
+      P->sigma.push_back(mode_lambda(P->kind, P->nz, q) * iz2);
+      P->pweight.push_back(parseval_weight(P->kind, P->nz, q));
+    }
+    if ((st = upload(P, &P->d_sigma64, P->sigma)) || (st = upload(P, &P->d_sigma32, to32(P->sigma)))) break;
+    std::vector<int> sm(P->nz, 0);
+    for (int q = 0; q < P->nz; ++q) sm[q] = (P->singular && mode_lambda(P->kind, P->nz, q) == 0.0) ? 1 : 0;
+    if ((st = upload(P, &P->d_singular_mode, sm))) break;
+    if ((st = build_coarse(P))) break;
+    if ((st = build_twiddles(P))) break;
+    if ((st = build_chunks(P, 8, P->chunks64, &P->d_chunks64))) break;
+    if ((st = build_chunks(P, 16, P->chunks32, &P->d_chunks32))) break;
+    {
+      const HostLevel& l0 = P->lev[0];
+      std::vector<double> area(l0.ncell);
+      for (const BlockDev& d : l0.blk)
+        for (int j = 0; j < d.ny; ++j)
+          for (int i = 0; i < d.nx; ++i) area[d.off + (long long)j * d.nx + i] = l0.cx[d.xo + i].w * l0.cy[d.yo + j].w;
+      if ((st = upload(P, &P->d_area0, area))) break;
+    }
+    if ((st = dmalloc(P, &P->d_r3, (size_t)P->n3))) break;
+    const int zsplit = std::min(P->nz, 16);
+    P->npartial = (int)P->lev[0].tiles.size() * zsplit;
+    if ((st = dmalloc(P, &P->d_partial, (size_t)P->npartial * 4))) break;
+    if ((st = dmalloc(P, &P->d_sums, 8))) break;
+    if ((st = dmalloc(P, &P->d_mode_part, (size_t)P->nz * P->lev[0].tiles.size()))) break;
+    if ((st = dmalloc(P, &P->d_mode_norm2, (size_t)P->nz))) break;
+    if ((st = dmalloc(P, &P->d_active, (size_t)P->nz))) break;
+    if (cudaMallocHost(&P->h_sums, 8 * sizeof(double)) != cudaSuccess ||
+        cudaMallocHost(&P->h_mode_norm2, P->nz * sizeof(double)) != cudaSuccess ||
+        cudaMallocHost(&P->h_active, P->nz * sizeof(int)) != cudaSuccess) {
+      st = fail(SNAC_ERR_OOM, "pinned host allocation");
+      break;
+    }
+  } while (0);
+  if (st) {
+    free_plan(P);
+    return st;
+  }
+  P->mode_cycles.assign(P->nz, 0);
+  P->info.levels = (int)P->lev.size();
+  P->info.n_modes = P->nz;
+  *out = P;
+  return SNAC_OK;
+}
+
+}  // namespace
+
+namespace snac {
+int plan_inner_size(const snac_plan* P) { return P->precision == SNAC_FP64 ? 8 : 4; }
+}  // namespace snac
+
+extern "C" {
+
+int snac_plan_create(snac_plan** out, int32_t nblocks, const snac_block* blocks, int32_t homog_axis,
+                     const snac_options* opt) {
+  try {
+    return create(out, nblocks, blocks, homog_axis, opt);
+  } catch (...) {
+    return fail(SNAC_ERR_OOM, "exception during plan creation");
+  }
+}
+
+int snac_plan_workspace_bytes(const snac_plan* plan, size_t* bytes) {
+  if (!plan || !bytes) return SNAC_ERR_INVALID_ARG;
+  *bytes = plan->bytes;
+  return SNAC_OK;
+}
+
+int snac_plan_info(const snac_plan* plan, snac_solve_info* info) {
+  if (!plan || !info) return SNAC_ERR_INVALID_ARG;
+  *info = plan->info;
+  return SNAC_OK;
+}
+
+int snac_plan_mode_cycles(const snac_plan* plan, int32_t* h_cycles, int32_t n) {
+  if (!plan || !h_cycles || n < plan->nz) return SNAC_ERR_INVALID_ARG;
+  std::copy(plan->mode_cycles.begin(), plan->mode_cycles.end(), h_cycles);
+  return SNAC_OK;
+}
+
+int snac_plan_destroy(snac_plan* plan) {
+  free_plan(plan);
+  return SNAC_OK;
+}
+
+const char* snac_status_string(int status) {
+  switch (status) {
+    case SNAC_OK: return "ok";
+    case SNAC_ERR_INVALID_ARG: return "invalid argument";
+    case SNAC_ERR_LAYOUT: return "invalid block layout";
+    case SNAC_ERR_OOM: return "out of memory";
+    case SNAC_ERR_CUDA: return "CUDA error";
+    case SNAC_ERR_NOT_CONVERGED: return "not converged";
+    case SNAC_ERR_NONFINITE: return "non-finite residual";
+    case SNAC_ERR_INCOMPATIBLE_RHS: return "incompatible right-hand side";
+    case SNAC_ERR_TIMEOUT: return "device wait timed out";
+    default: return "unknown status";
+  }
+}
+
+const char* snac_last_error_message(void) { return snac::g_last_error.c_str(); }
+
+}  // extern "C"

@@ -1,0 +1,196 @@
+// Internal declarations of the CUDA Poisson solver library (libsnac.so).
+//
+// Data model on the device (one plan):
+//   * a "plane" is the set of x-y cells of all blocks at one multigrid level, numbered block by
+//     block, [y][x] within a block (x fastest); block b starts at cell off[b];
+//   * per level: a block table (BlockDev), a tile table (32x8-cell tiles, never straddling blocks),
+//     1-D coefficient arrays along x (per block column) and y (per block row), prolongation and
+//     restriction weights; the 2-D operator of a cell is separable into these 1-D pieces;
+//   * mode-space fields are [q][plane cell] in the inner type T (double or float);
+//   * 3-D caller fields are [block][z][y][x] in double.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "snac.h"
+
+namespace snac {
+
+enum Kind { KIND_PP = 0, KIND_NN = 1, KIND_DD = 2, KIND_ND = 3, KIND_DN = 4 };
+
+constexpr int TILE_X = 32;
+constexpr int TILE_Y = 8;
+constexpr int TILE_THREADS = TILE_X * TILE_Y;
+constexpr int MAX_NZ = 1024;
+constexpr int MAX_COARSE = 256;
+
+// Faces are numbered W, E, S, N = 0..3 (x lower, x upper, y lower, y upper).
+struct BlockDev {
+  long long off;  // first cell of the block in the plane
+  int nx, ny;
+  int xo, yo;     // offsets of the block's columns / rows in the level's 1-D arrays
+  int nbr[4];     // connected block across each face, -1 on a physical (Dirichlet/Neumann) face
+  int par;        // colour of cell (0,0): parity of its global index-space position
+  int pad;
+};
+
+struct TileDev {
+  int b, x0, y0, pad;
+};
+
+// 1-D operator piece of one column (x) or row (y): coupling to the lower and upper neighbour
+// (zero on a physical face), contribution to the diagonal, and the cell width.
+template <typename T>
+struct Coef {
+  T lo, hi, d, w;
+};
+
+// Prolongation weights of one fine column/row: e_f gets self*e_C + nbr*e_X per axis (plus e_C).
+template <typename T>
+struct PW {
+  T self, nbr;
+};
+
+template <typename T>
+struct LevelView {
+  const BlockDev* blk;
+  const TileDev* tiles;
+  const Coef<T>* cx;
+  const Coef<T>* cy;
+  const PW<T>* px;  // weights for prolongation into this level (fine side)
+  const PW<T>* py;
+  const T* rx;      // restriction weights: fine width / parent width
+  const T* ry;
+  long long ncell;
+  int ntiles;
+  int nblk;
+};
+
+// Host-side description of one level.
+struct HostLevel {
+  int nblk = 0;
+  std::vector<BlockDev> blk;
+  std::vector<TileDev> tiles;
+  std::vector<Coef<double>> cx, cy;
+  std::vector<PW<double>> px, py;
+  std::vector<double> rx, ry;
+  long long ncell = 0;
+  // device copies
+  BlockDev* d_blk = nullptr;
+  TileDev* d_tiles = nullptr;
+  Coef<double>* d_cx64 = nullptr;
+  Coef<double>* d_cy64 = nullptr;
+  Coef<float>* d_cx32 = nullptr;
+  Coef<float>* d_cy32 = nullptr;
+  PW<double>* d_px64 = nullptr;
+  PW<double>* d_py64 = nullptr;
+  PW<float>* d_px32 = nullptr;
+  PW<float>* d_py32 = nullptr;
+  double* d_rx64 = nullptr;
+  double* d_ry64 = nullptr;
+  float* d_rx32 = nullptr;
+  float* d_ry32 = nullptr;
+  void* d_u = nullptr;  // mode-space iterate, n_z x ncell of the inner type
+  void* d_f = nullptr;  // mode-space right-hand side
+};
+
+// A chunk of up to TCOLS consecutive columns (cells of one plane) of one block, for the transforms.
+struct ChunkDev {
+  int b, c0, ncol, pad;
+};
+
+struct TwiddleOffsets {
+  int fft, twn, tw2n, tw4a, tw4b, total;
+};
+
+}  // namespace snac
+
+struct snac_plan {
+  int device = 0;
+  int precision = SNAC_FP64;
+  int nu1 = 2, nu2 = 2, max_outer = 20, max_cycles = 40, max_coarse = 64;
+  int nblk = 0;
+  int nz = 0;
+  double dz = 0.0;
+  int kind = 0;
+  double theta = 1.0;
+  bool singular = false;
+  long long n3 = 0;  // cells of the 3-D field
+  double vol_total = 0.0;
+  double area_total = 0.0;
+  std::vector<long long> blk_off3;  // 3-D offset of each block
+  std::vector<snac::HostLevel> lev;
+  // z direction
+  std::vector<snac::Coef<double>> cz;
+  snac::Coef<double>* d_cz = nullptr;
+  // eigenvalue shifts lambda_q / dz^2 and the Parseval weight of every mode
+  std::vector<double> sigma, pweight;
+  double* d_sigma64 = nullptr;
+  float* d_sigma32 = nullptr;
+  // coarsest level: S = V^1/2 A V^-1/2 = Q diag(Lam) Q^T
+  int nc = 0;
+  int null_index = -1;
+  double* d_Q = nullptr;      // nc x nc, row-major, column k = eigenvector k
+  double* d_lam = nullptr;    // nc
+  double* d_sqa = nullptr;    // sqrt(area) of the coarsest cells
+  int* d_singular_mode = nullptr;  // per mode: 1 if the reduced system is singular
+  // transforms
+  snac::TwiddleOffsets tw{};
+  double* d_tw64 = nullptr;  // double2 table
+  float* d_tw32 = nullptr;   // float2 table
+  std::vector<snac::ChunkDev> chunks64, chunks32;
+  snac::ChunkDev* d_chunks64 = nullptr;
+  snac::ChunkDev* d_chunks32 = nullptr;
+  double* d_area0 = nullptr;  // area of every level-0 cell
+  // scratch
+  double* d_r3 = nullptr;       // 3-D residual
+  double* d_partial = nullptr;  // per-CTA partial sums
+  int npartial = 0;
+  double* d_sums = nullptr;     // 4 reduced sums
+  double* d_mode_part = nullptr;  // per-mode, per-tile partial sums of squares
+  double* d_mode_norm2 = nullptr; // per-mode ||r_q||^2
+  int* d_active = nullptr;
+  double* h_sums = nullptr;       // pinned
+  double* h_mode_norm2 = nullptr; // pinned
+  int* h_active = nullptr;        // pinned
+  std::vector<void*> allocs;
+  size_t bytes = 0;
+  // results
+  snac_solve_info info{};
+  std::vector<int32_t> mode_cycles;
+};
+
+namespace snac {
+
+// ---- launchers (field kernels: 3-D FP64 residual and reductions) ----
+// mode 0: r = (f - fshift) - A p; sums = {||r||^2, ||f - fshift||^2, sum V p}
+// mode 1: r = A p
+// mode 2: sums = {sum V f, sum V |f|, ||f||^2}  (p, r unused)
+cudaError_t launch_field3d(snac_plan* P, int mode, const double* f, const double* p, double* r, double fshift,
+                           cudaStream_t s);
+// reduce d_partial[npart][4] into d_sums[4]
+cudaError_t launch_reduce_partials(snac_plan* P, int npart, cudaStream_t s);
+// make the update of the singular mode 0 keep the volume-weighted mean of p at zero
+cudaError_t launch_fix_mean(snac_plan* P, void* u0, cudaStream_t s);
+// p -= c (c read from device d_c)
+cudaError_t launch_shift(snac_plan* P, double* p, const double* d_c, cudaStream_t s);
+
+// ---- transforms ----
+cudaError_t launch_forward(snac_plan* P, const double* in3, void* modes, cudaStream_t s);
+cudaError_t launch_backward_update(snac_plan* P, const void* modes, double* p3, cudaStream_t s);
+
+// ---- multigrid ----
+cudaError_t launch_mode_operator(snac_plan* P, const void* u, void* out, cudaStream_t s);
+// one V-cycle of the active modes on the plan's level buffers (level 0: d_u / d_f)
+cudaError_t launch_vcycle(snac_plan* P, int nactive, cudaStream_t s);
+// per-mode ||f - A u||^2 at level 0 for the active modes -> d_mode_norm2[q]
+cudaError_t launch_mode_norms(snac_plan* P, int nactive, cudaStream_t s);
+
+int plan_inner_size(const snac_plan* P);  // bytes of the inner type
+
+}  // namespace snac

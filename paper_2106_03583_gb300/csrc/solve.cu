@@ -1,0 +1,249 @@
+// The solve: Algorithm 1 (Sec. 2) inside an FP64 defect-correction loop, plus the stage entry points.
+//
+//   repeat:  r = f - A p                     (FP64, 3-D, Eq. 8)         stop when ||r|| <= tol ||f||
+//            r_hat = F r                     (Table 1, along z)
+//            for every wavenumber q:  V-cycles on (A_xy + lambda_q/dz^2) e_q = r_hat_q   (Eq. 9)
+//                                     until its own share of the residual target is met
+//            p += F^-1 e_hat                 (FP64 update)
+//
+// The per-wavenumber stopping rule: with the Parseval weights w_q of the transform
+// (||x||^2 = sum_q w_q ||x_hat_q||^2), the 3-D residual after the update is the inverse transform of
+// the per-mode residuals, so w_q ||r_q||^2 <= target^2 / n_z for every q gives ||r_new|| <= target.
+// Modes with a large |lambda_q| meet it in fewer cycles (Sec. 3.3 and App. B); each cycle only runs
+// the modes still active. A mode whose residual stops falling (the floating-point floor of the inner
+// precision) is retired as well; the outer loop then takes another defect-correction step.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+#include "snac_impl.h"
+
+namespace snac {
+void set_error(const std::string& s);
+}
+
+namespace {
+using namespace snac;
+
+int cuda_fail(cudaError_t e, const char* where) {
+  set_error(std::string(where) + ": " + cudaGetErrorString(e));
+  return SNAC_ERR_CUDA;
+}
+
+#define CK(call)                                   \
+  do {                                             \
+    cudaError_t e_ = (call);                       \
+    if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
+  } while (0)
+
+int check_plan(snac_plan* P) {
+  if (!P) return SNAC_ERR_INVALID_ARG;
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev != P->device) {
+    set_error("the current CUDA device is not the plan's device");
+    return SNAC_ERR_INVALID_ARG;
+  }
+  return SNAC_OK;
+}
+
+int set_active_all(snac_plan* P, cudaStream_t s) {
+  for (int q = 0; q < P->nz; ++q) P->h_active[q] = q;
+  CK(cudaMemcpyAsync(P->d_active, P->h_active, P->nz * sizeof(int), cudaMemcpyHostToDevice, s));
+  return SNAC_OK;
+}
+
+// V-cycles of every mode until its share of `target` is met, it stagnates, or max_cycles.
+int mode_solves(snac_plan* P, double target, cudaStream_t s, int* cycles_out) {
+  const int nz = P->nz;
+  CK(cudaMemsetAsync(P->lev[0].d_u, 0, (size_t)nz * P->lev[0].ncell * plan_inner_size(P), s));
+  int st = set_active_all(P, s);
+  if (st) return st;
+  CK(launch_mode_norms(P, nz, s));
+  CK(cudaMemcpyAsync(P->h_mode_norm2, P->d_mode_norm2, nz * sizeof(double), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  std::vector<double> thr2(nz), prev(nz);
+  std::vector<int> list;
+  for (int q = 0; q < nz; ++q) {
+    thr2[q] = target * target / (nz * P->pweight[q]);
+    prev[q] = P->h_mode_norm2[q];
+    cycles_out[q] = 0;
+    if (!std::isfinite(prev[q])) return SNAC_ERR_NONFINITE;
+    if (prev[q] > thr2[q]) list.push_back(q);
+  }
+  const double stag2 = 0.6 * 0.6;
+  int total = 0;
+  for (int c = 0; c < P->max_cycles && !list.empty(); ++c) {
+    const int nact = (int)list.size();
+    std::copy(list.begin(), list.end(), P->h_active);
+    CK(cudaMemcpyAsync(P->d_active, P->h_active, nact * sizeof(int), cudaMemcpyHostToDevice, s));
+    CK(launch_vcycle(P, nact, s));
+    CK(launch_mode_norms(P, nact, s));
+    CK(cudaMemcpyAsync(P->h_mode_norm2, P->d_mode_norm2, nz * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    std::vector<int> next;
+    for (int q : list) {
+      ++cycles_out[q];
+      ++total;
+      const double r2 = P->h_mode_norm2[q];
+      if (!std::isfinite(r2)) return SNAC_ERR_NONFINITE;
+      const bool done = r2 <= thr2[q] || r2 > stag2 * prev[q];
+      prev[q] = r2;
+      if (!done) next.push_back(q);
+    }
+    list.swap(next);
+  }
+  P->info.total_cycles += total;
+  return SNAC_OK;
+}
+
+int read_sums(snac_plan* P, cudaStream_t s) {
+  CK(cudaMemcpyAsync(P->h_sums, P->d_sums, 4 * sizeof(double), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  return SNAC_OK;
+}
+
+int run_solve(snac_plan* P, const double* f, double* p, double tol, cudaStream_t s) {
+  P->info = snac_solve_info{};
+  P->info.levels = (int)P->lev.size();
+  P->info.n_modes = P->nz;
+  std::fill(P->mode_cycles.begin(), P->mode_cycles.end(), 0);
+  double fshift = 0.0;
+  int st;
+  if (P->singular) {
+    CK(launch_field3d(P, 2, f, nullptr, nullptr, 0.0, s));
+    if ((st = read_sums(P, s))) return st;
+    const double vf = P->h_sums[0], vaf = P->h_sums[1];
+    if (!std::isfinite(vf) || !std::isfinite(vaf)) return SNAC_ERR_NONFINITE;
+    if (std::fabs(vf) > 1e-12 * vaf) {
+      set_error("singular problem: the volume-weighted sum of the right-hand side is not zero");
+      return SNAC_ERR_INCOMPATIBLE_RHS;
+    }
+    fshift = vf / P->vol_total;
+    P->info.removed_mean = fshift;
+  }
+  const bool mixed = P->precision == SNAC_MIXED;
+  double prev_rel = INFINITY;
+  bool updated = false;
+  std::vector<int> cyc(P->nz);
+  for (int k = 0;; ++k) {
+    CK(launch_field3d(P, 0, f, p, P->d_r3, fshift, s));
+    if ((st = read_sums(P, s))) return st;
+    const double rn = std::sqrt(P->h_sums[0]), fn = std::sqrt(P->h_sums[1]);
+    if (!std::isfinite(rn) || !std::isfinite(fn)) return SNAC_ERR_NONFINITE;
+    P->info.rhs_norm = fn;
+    P->info.outer_iters = k;
+    if (fn == 0.0) {  // zero right-hand side: p = 0
+      CK(cudaMemsetAsync(p, 0, (size_t)P->n3 * sizeof(double), s));
+      CK(cudaStreamSynchronize(s));
+      P->info.rel_res = 0.0;
+      return SNAC_OK;
+    }
+    const double rel = rn / fn;
+    P->info.rel_res = rel;
+    const bool done = rel <= tol;
+    const bool give_up = !done && (k >= P->max_outer || rel > 10.0 * prev_rel);
+    if (done || give_up) {
+      if (P->singular && !updated) {  // the initial guess was kept: return its zero-mean shift
+        CK(launch_shift(P, p, P->d_sums + 3, s));
+        CK(cudaStreamSynchronize(s));
+      }
+      return done ? SNAC_OK : SNAC_ERR_NOT_CONVERGED;
+    }
+    prev_rel = rel;
+    // target of this defect-correction step
+    double target = 0.5 * tol * fn;
+    if (mixed) target = std::max(target, 1e-4 * rn);
+    CK(launch_forward(P, P->d_r3, P->lev[0].d_f, s));
+    if ((st = mode_solves(P, target, s, cyc.data()))) return st;
+    for (int q = 0; q < P->nz; ++q) {
+      P->mode_cycles[q] = cyc[q];
+      P->info.max_mode_cycles = std::max(P->info.max_mode_cycles, cyc[q]);
+    }
+    if (P->singular) CK(launch_fix_mean(P, P->lev[0].d_u, s));
+    CK(launch_backward_update(P, P->lev[0].d_u, p, s));
+    updated = true;
+  }
+}
+
+}  // namespace
+
+extern "C" {
+
+int snac_poisson_solve(snac_plan* plan, const double* d_rhs, double* d_p, double tol, void* stream) {
+  int st = check_plan(plan);
+  if (st) return st;
+  if (!d_rhs || !d_p || !(tol > 0.0) || !std::isfinite(tol)) return SNAC_ERR_INVALID_ARG;
+  st = run_solve(plan, d_rhs, d_p, tol, (cudaStream_t)stream);
+  plan->info.status = st;
+  return st;
+}
+
+int snac_apply_operator(snac_plan* plan, const double* d_p, double* d_out, void* stream) {
+  int st = check_plan(plan);
+  if (st) return st;
+  if (!d_p || !d_out) return SNAC_ERR_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  CK(launch_field3d(plan, 1, nullptr, d_p, d_out, 0.0, s));
+  CK(cudaStreamSynchronize(s));
+  return SNAC_OK;
+}
+
+int snac_residual(snac_plan* plan, const double* d_rhs, const double* d_p, double* d_r, double* h_norms, void* stream) {
+  int st = check_plan(plan);
+  if (st) return st;
+  if (!d_rhs || !d_p || !d_r || !h_norms) return SNAC_ERR_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  CK(launch_field3d(plan, 0, d_rhs, d_p, d_r, 0.0, s));
+  if ((st = read_sums(plan, s))) return st;
+  h_norms[0] = plan->h_sums[0];
+  h_norms[1] = plan->h_sums[1];
+  return SNAC_OK;
+}
+
+int snac_forward_transform(snac_plan* plan, const double* d_in, void* d_modes, void* stream) {
+  int st = check_plan(plan);
+  if (st) return st;
+  if (!d_in || !d_modes) return SNAC_ERR_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  CK(launch_forward(plan, d_in, d_modes, s));
+  CK(cudaStreamSynchronize(s));
+  return SNAC_OK;
+}
+
+int snac_backward_update(snac_plan* plan, const void* d_modes, double* d_p, void* stream) {
+  int st = check_plan(plan);
+  if (st) return st;
+  if (!d_modes || !d_p) return SNAC_ERR_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  CK(launch_backward_update(plan, d_modes, d_p, s));
+  CK(cudaStreamSynchronize(s));
+  return SNAC_OK;
+}
+
+int snac_mode_operator(snac_plan* plan, const void* d_u, void* d_out, void* stream) {
+  int st = check_plan(plan);
+  if (st) return st;
+  if (!d_u || !d_out) return SNAC_ERR_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  if ((st = set_active_all(plan, s))) return st;
+  CK(launch_mode_operator(plan, d_u, d_out, s));
+  CK(cudaStreamSynchronize(s));
+  return SNAC_OK;
+}
+
+int snac_mode_vcycles(snac_plan* plan, const void* d_f, void* d_u, int32_t ncycles, void* stream) {
+  int st = check_plan(plan);
+  if (st) return st;
+  if (!d_f || !d_u || ncycles < 0) return SNAC_ERR_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t bytes = (size_t)plan->nz * plan->lev[0].ncell * plan_inner_size(plan);
+  CK(cudaMemcpyAsync(plan->lev[0].d_f, d_f, bytes, cudaMemcpyDeviceToDevice, s));
+  CK(cudaMemcpyAsync(plan->lev[0].d_u, d_u, bytes, cudaMemcpyDeviceToDevice, s));
+  if ((st = set_active_all(plan, s))) return st;
+  for (int c = 0; c < ncycles; ++c) CK(launch_vcycle(plan, plan->nz, s));
+  CK(cudaMemcpyAsync(d_u, plan->lev[0].d_u, bytes, cudaMemcpyDeviceToDevice, s));
+  CK(cudaStreamSynchronize(s));
+  return SNAC_OK;
+}
+
+}  // extern "C"

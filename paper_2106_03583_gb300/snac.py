@@ -1,0 +1,232 @@
+"""Python binding of libsnac.so (ctypes): argument marshalling only.
+
+Every step of the solve runs in the library's CUDA kernels; this module checks tensor arguments,
+builds the C structs of ``include/snac.h`` and forwards device pointers and the current PyTorch
+stream. It raises if the library has not been built: there is no other code path.
+
+    from paper_2106_03583_gb300 import snac, inputs
+    blocks, f = inputs.config("mb2x2")
+    plan = snac.Plan(blocks, precision="fp64")
+    p = torch.zeros_like(rhs)
+    info = plan.solve(rhs, p, tol=1e-10)      # rhs, p: CUDA float64, [block][z][y][x]
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libsnac.so")
+
+SNAC_OK = 0
+STATUS = {0: "OK", -1: "INVALID_ARG", -2: "LAYOUT", -3: "OOM", -4: "CUDA", -5: "NOT_CONVERGED",
+          -6: "NONFINITE", -7: "INCOMPATIBLE_RHS", -8: "TIMEOUT"}
+_BC = {"D": 0, "N": 1, "P": 2, "B": 3}
+_PREC = {"fp64": 0, "mixed": 1}
+
+EXPORTS = ("snac_plan_create", "snac_plan_workspace_bytes", "snac_poisson_solve", "snac_plan_info",
+           "snac_plan_mode_cycles", "snac_plan_destroy", "snac_status_string", "snac_last_error_message",
+           "snac_apply_operator", "snac_residual", "snac_forward_transform", "snac_backward_update",
+           "snac_mode_operator", "snac_mode_vcycles")
+
+
+class SnacError(RuntimeError):
+    def __init__(self, status: int, msg: str = ""):
+        self.status = status
+        self.name = STATUS.get(status, str(status))
+        super().__init__(f"snac: {self.name} ({status}){': ' + msg if msg else ''}")
+
+
+class _Block(ctypes.Structure):
+    _fields_ = [("lo", ctypes.c_int64 * 3), ("hi", ctypes.c_int64 * 3), ("h_dx", ctypes.c_void_p * 3),
+                ("bc", (ctypes.c_int32 * 2) * 3), ("nbr", (ctypes.c_int32 * 2) * 3)]
+
+
+class _Options(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int32), ("nu1", ctypes.c_int32), ("nu2", ctypes.c_int32),
+                ("max_outer", ctypes.c_int32), ("max_cycles", ctypes.c_int32), ("max_coarse", ctypes.c_int32)]
+
+
+class _Info(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("outer_iters", ctypes.c_int32), ("total_cycles", ctypes.c_int32),
+                ("max_mode_cycles", ctypes.c_int32), ("levels", ctypes.c_int32), ("n_modes", ctypes.c_int32),
+                ("rel_res", ctypes.c_double), ("rhs_norm", ctypes.c_double), ("removed_mean", ctypes.c_double)]
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _LIB_PATH
+
+
+def lib() -> ctypes.CDLL:
+    """The loaded libsnac.so (loaded once). Raises ImportError if it was not built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(_LIB_PATH):
+            raise ImportError(f"{_LIB_PATH} is missing: build it with paper_2106_03583_gb300.build.build()")
+        L = ctypes.CDLL(_LIB_PATH)
+        vp, i32, f64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_double
+        sig = {
+            "snac_plan_create": [ctypes.POINTER(vp), i32, ctypes.POINTER(_Block), i32, ctypes.POINTER(_Options)],
+            "snac_plan_workspace_bytes": [vp, ctypes.POINTER(ctypes.c_size_t)],
+            "snac_poisson_solve": [vp, vp, vp, f64, vp],
+            "snac_plan_info": [vp, ctypes.POINTER(_Info)],
+            "snac_plan_mode_cycles": [vp, ctypes.POINTER(i32), i32],
+            "snac_plan_destroy": [vp],
+            "snac_status_string": [ctypes.c_int],
+            "snac_last_error_message": [],
+            "snac_apply_operator": [vp, vp, vp, vp],
+            "snac_residual": [vp, vp, vp, vp, ctypes.POINTER(f64), vp],
+            "snac_forward_transform": [vp, vp, vp, vp],
+            "snac_backward_update": [vp, vp, vp, vp],
+            "snac_mode_operator": [vp, vp, vp, vp],
+            "snac_mode_vcycles": [vp, vp, vp, i32, vp],
+        }
+        for name, args in sig.items():
+            fn = getattr(L, name)
+            fn.argtypes = args
+            fn.restype = ctypes.c_char_p if name in ("snac_status_string", "snac_last_error_message") else ctypes.c_int
+        _lib = L
+    return _lib
+
+
+def _check(status: int):
+    if status != SNAC_OK:
+        msg = lib().snac_last_error_message()
+        raise SnacError(status, msg.decode() if msg else "")
+
+
+def _marshal_blocks(blocks):
+    arr = (_Block * len(blocks))()
+    keep = []
+    for b, blk in enumerate(blocks):
+        c = arr[b]
+        for a in range(3):
+            c.lo[a] = int(blk["lo"][a])
+            c.hi[a] = int(blk["hi"][a])
+            w = np.ascontiguousarray(blk["dx"][a], dtype=np.float64)
+            keep.append(w)
+            c.h_dx[a] = w.ctypes.data
+            for s in range(2):
+                c.bc[a][s] = _BC[blk["bc"][a][s]]
+                c.nbr[a][s] = int(blk["nbr"][a][s])
+    return arr, keep
+
+
+class Plan:
+    """A solver plan for one multi-block problem (``snac_plan_create``)."""
+
+    def __init__(self, blocks, homog_axis: int = 2, precision: str = "fp64", nu1: int = 2, nu2: int = 2,
+                 max_outer: int = 20, max_cycles: int = 40, max_coarse: int = 64):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("snac.Plan needs a CUDA device")
+        if precision not in _PREC:
+            raise ValueError(f"precision must be one of {list(_PREC)}")
+        torch.cuda.init()
+        self.device = torch.device("cuda", torch.cuda.current_device())
+        self.blocks = blocks
+        self.precision = precision
+        self.inner_dtype = torch.float64 if precision == "fp64" else torch.float32
+        arr, keep = _marshal_blocks(blocks)
+        opt = _Options(_PREC[precision], nu1, nu2, max_outer, max_cycles, max_coarse)
+        h = ctypes.c_void_p()
+        _check(lib().snac_plan_create(ctypes.byref(h), len(blocks), arr, homog_axis, ctypes.byref(opt)))
+        del keep
+        self._h = h
+        self.nz = int(blocks[0]["hi"][2] - blocks[0]["lo"][2] + 1)
+        self.ncell = int(sum((b["hi"][0] - b["lo"][0] + 1) * (b["hi"][1] - b["lo"][1] + 1) for b in blocks))
+        self.n3 = self.ncell * self.nz
+
+    # ---- helpers
+    def _stream(self):
+        import torch
+        return ctypes.c_void_p(torch.cuda.current_stream(self.device).cuda_stream)
+
+    def _ptr(self, t, dtype, n, name):
+        import torch
+        if not isinstance(t, torch.Tensor):
+            raise ValueError(f"{name} must be a torch.Tensor")
+        if t.device != self.device or t.dtype != dtype or not t.is_contiguous() or t.numel() != n:
+            raise ValueError(f"{name} must be a contiguous {dtype} tensor on {self.device} with {n} elements")
+        return ctypes.c_void_p(t.data_ptr())
+
+    # ---- the solve
+    def solve(self, rhs, p, tol: float = 1e-10, raise_on_error: bool = True) -> dict:
+        """Solve A p = rhs in place on p (initial guess in, solution out). Returns info()."""
+        import torch
+        st = lib().snac_poisson_solve(self._h, self._ptr(rhs, torch.float64, self.n3, "rhs"),
+                                      self._ptr(p, torch.float64, self.n3, "p"), float(tol), self._stream())
+        if st != SNAC_OK and raise_on_error:
+            _check(st)
+        return self.info()
+
+    def info(self) -> dict:
+        inf = _Info()
+        _check(lib().snac_plan_info(self._h, ctypes.byref(inf)))
+        d = {k: getattr(inf, k) for k, _ in _Info._fields_}
+        d["status_name"] = STATUS.get(d["status"], str(d["status"]))
+        return d
+
+    def mode_cycles(self) -> np.ndarray:
+        out = (ctypes.c_int32 * self.nz)()
+        _check(lib().snac_plan_mode_cycles(self._h, out, self.nz))
+        return np.frombuffer(out, dtype=np.int32).copy()
+
+    @property
+    def workspace_bytes(self) -> int:
+        v = ctypes.c_size_t()
+        _check(lib().snac_plan_workspace_bytes(self._h, ctypes.byref(v)))
+        return int(v.value)
+
+    # ---- stages
+    def apply_operator(self, p, out):
+        import torch
+        _check(lib().snac_apply_operator(self._h, self._ptr(p, torch.float64, self.n3, "p"),
+                                         self._ptr(out, torch.float64, self.n3, "out"), self._stream()))
+
+    def residual(self, rhs, p, r):
+        import torch
+        norms = (ctypes.c_double * 2)()
+        _check(lib().snac_residual(self._h, self._ptr(rhs, torch.float64, self.n3, "rhs"),
+                                   self._ptr(p, torch.float64, self.n3, "p"),
+                                   self._ptr(r, torch.float64, self.n3, "r"), norms, self._stream()))
+        return norms[0], norms[1]
+
+    def forward_transform(self, x, modes):
+        import torch
+        _check(lib().snac_forward_transform(self._h, self._ptr(x, torch.float64, self.n3, "x"),
+                                            self._ptr(modes, self.inner_dtype, self.n3, "modes"), self._stream()))
+
+    def backward_update(self, modes, p):
+        import torch
+        _check(lib().snac_backward_update(self._h, self._ptr(modes, self.inner_dtype, self.n3, "modes"),
+                                          self._ptr(p, torch.float64, self.n3, "p"), self._stream()))
+
+    def mode_operator(self, u, out):
+        _check(lib().snac_mode_operator(self._h, self._ptr(u, self.inner_dtype, self.n3, "u"),
+                                        self._ptr(out, self.inner_dtype, self.n3, "out"), self._stream()))
+
+    def mode_vcycles(self, f, u, ncycles: int = 1):
+        _check(lib().snac_mode_vcycles(self._h, self._ptr(f, self.inner_dtype, self.n3, "f"),
+                                       self._ptr(u, self.inner_dtype, self.n3, "u"), int(ncycles), self._stream()))
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            lib().snac_plan_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

@@ -1,0 +1,81 @@
+"""The C ABI library builds, loads and exports every function declared in include/snac.h; host-side
+validation of block layouts (no GPU needed: these calls return before touching the device)."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_2106_03583_gb300 import build, inputs, snac
+
+from layouts import make
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build.build()
+    return snac.lib()
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "snac.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:const\s+)?\w+\s*\*?\s*(snac_\w+)\s*\(", src, flags=re.M)))
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_functions()
+    assert len(names) >= 14
+    for n in names:
+        assert hasattr(lib, n), n
+    assert set(names) == set(snac.EXPORTS)
+
+
+def test_status_strings(lib):
+    assert lib.snac_status_string(0) == b"ok"
+    for code in range(-8, 0):
+        assert lib.snac_status_string(code) not in (b"", b"unknown status")
+    assert lib.snac_status_string(-99) == b"unknown status"
+
+
+def _create(lib, blocks, homog=2, opt=None):
+    arr, keep = snac._marshal_blocks(blocks)
+    h = ctypes.c_void_p()
+    st = lib.snac_plan_create(ctypes.byref(h), len(blocks), arr, homog, opt)
+    return st, lib.snac_last_error_message().decode()
+
+
+def test_layout_validation(lib):
+    good = make("2x2", n=4, nz=8, zpair="NN")
+    bad = [dict(b) for b in good]
+    bad[0] = dict(bad[0], nbr=((-1, 2), (-1, 2), (-1, -1)))           # asymmetric connectivity
+    st, msg = _create(lib, bad)
+    assert st == -2 and "symmetric" in msg
+    odd = make("1", n=4, nz=7, zpair="PP")
+    st, msg = _create(lib, odd)
+    assert st == -2 and "even" in msg
+    nonuni = make("1", n=4, nz=8, zpair="NN")
+    nonuni[0] = dict(nonuni[0], dx=(nonuni[0]["dx"][0], nonuni[0]["dx"][1], np.linspace(0.1, 0.2, 8)))
+    st, msg = _create(lib, nonuni)
+    assert st == -2 and "uniform" in msg
+    cong = [dict(b) for b in make("1x2", n=4, nz=8, zpair="NN")]
+    wy = cong[1]["dx"][1].copy()
+    wy[0] *= 1.5
+    cong[1] = dict(cong[1], dx=(cong[1]["dx"][0], wy, cong[1]["dx"][2]))
+    st, msg = _create(lib, cong)
+    assert st == -2 and "congruent" in msg
+    st, _ = _create(lib, good, homog=0)
+    assert st == -1
+    neg = [dict(good[0], dx=(-good[0]["dx"][0], good[0]["dx"][1], good[0]["dx"][2]))] + good[1:]
+    st, _ = _create(lib, neg)
+    assert st == -1
+
+
+def test_null_arguments(lib):
+    assert lib.snac_plan_create(None, 1, None, 2, None) == -1
+    assert lib.snac_poisson_solve(None, None, None, 1e-10, None) == -1
+    assert lib.snac_plan_info(None, None) == -1
+    assert lib.snac_plan_destroy(None) == 0
