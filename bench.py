@@ -1,0 +1,331 @@
+#!/usr/bin/env python3
+"""Benchmark of the FFT-accelerated multi-block Poisson solve: solves/s at relative residual 1e-10.
+
+Workload (one step = one complete solve from a zero initial guess, all stages on the GPU):
+  2x2 blocks of 256x256 cells (assembled 512x512; x uniform on [0,2], y two-sided tanh factor 1.5 on
+  [0,2]; Neumann walls) by n_z = 256 Neumann-Neumann (DCT-II) on [0,1]; f = D u for a seeded
+  random-phase velocity field with a k^-5/3 spectrum. 6.7e7 cells, 537 MB per float64 field.
+The headline is the FP64 solve; the mixed-precision solve (FP32 multigrid inside FP64 defect
+correction) of the same problem is reported beside it.
+
+    python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+
+Prints one JSON line (rank 0). With N > 1 (torchrun), every rank solves its own seeded problem
+(independent replicas, no collective on the data path): weak scaling.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Poisson solves/s & HBM GB/s at rel-residual 1e-10, mixed vs FP64; p50/p99 lat"
+WORKLOAD = ("mb2x2: 2x2 blocks of 256x256 cells (assembled 512x512, x uniform [0,2], y tanh 1.5 on [0,2], "
+            "Neumann walls) x n_z=256 Neumann-Neumann (DCT-II) on [0,1]; f = D u, random-phase k^-5/3 "
+            "velocity; zero initial guess each solve")
+FP64_ALU_PEAK = 152 * 2 * 2 * 2.07e9   # SMs x FP64 FMA/clk/SM x 2 flop x max SM clock = 1.259 TFLOP/s
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["snac", "reference"], default="snac")
+    ap.add_argument("--workload", default="mb2x2")
+    ap.add_argument("--tol", type=float, default=1e-10)
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--precisions", default="fp64,mixed")
+    return ap.parse_args()
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi samples every 200 ms while the timed region runs."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.proc = None
+        self.path = None
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as fh:
+            for line in fh:
+                c = [x.strip() for x in line.split(",")]
+                if len(c) < 9:
+                    continue
+                try:
+                    sm.append(float(c[1]))
+                    mx.append(float(c[2]))
+                except ValueError:
+                    continue
+                for n, v in zip(names, c[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(n)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def base_line(args, world):
+    return {"metric": METRIC, "unit": "solves/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD if args.workload == "mb2x2" else args.workload, "tol": args.tol,
+                       "precision": "fp64", "parallelism": f"replicas x{world}",
+                       "l2": "inputs larger than L2 (537 MB per float64 field), no flush"}}
+
+
+def _oracle_setup(blocks):
+    from oracle import grid as ogrid
+    from oracle import mg as omg
+    g = ogrid.Grid(blocks)
+    return g, omg.Multigrid(g.plane)
+
+
+def cpu_baseline(args, blocks, f, n_sample, setup=None, t_transforms=None):
+    """The oracle as it stands on a bounded sample: both full transforms plus n_sample of the n_z
+    per-wavenumber multigrid solves; the per-wavenumber time is scaled to all n_z. The transforms'
+    time is measured by a solve without wavenumbers (once, or given)."""
+    import numpy as np
+    from oracle import solve as osv
+    g, mg = setup or _oracle_setup(blocks)
+    nz = g.nz
+    sample = [int(q) for q in np.linspace(0, nz - 1, n_sample).round()]
+    if t_transforms is None:
+        t0 = time.perf_counter()
+        osv.solve(blocks, f, modes=[], mg=mg)
+        t_transforms = time.perf_counter() - t0
+    t1 = time.perf_counter()
+    osv.solve(blocks, f, modes=sample, mg=mg)
+    t2 = time.perf_counter()
+    t_mode = max((t2 - t1) - t_transforms, 0.0) / len(sample)
+    t_full = t_transforms + t_mode * nz
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    return {"value": 1.0 / t_full, "unit": "solves/s", "cores": cores, "kind": "oracle",
+            "sample": (f"both O(n^2) transforms in full + {len(sample)} of {nz} wavenumber multigrid solves "
+                       f"(q={sample}) at 1e-13; per-wavenumber time x{nz}; numpy/BLAS threads for transforms, "
+                       f"single-threaded sparse multigrid; {t2 - t1:.1f} s of CPU work"),
+            "seconds_per_solve_est": t_full, "t_transforms": t_transforms}
+
+
+def run_reference(args):
+    world, rank, _ = dist()
+    if rank != 0:
+        return
+    from paper_2106_03583_gb300 import inputs
+    blocks, f = inputs.config(args.workload, seed=args.seed)
+    setup = _oracle_setup(blocks)
+    first = cpu_baseline(args, blocks, f, 2, setup)
+    ttr = first["t_transforms"]
+    for _ in range(max(args.warmup - 1, 0)):
+        cpu_baseline(args, blocks, f, 2, setup, ttr)
+    vals = []
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        vals.append(cpu_baseline(args, blocks, f, 2, setup, ttr))
+    wall = time.perf_counter() - t0
+    v = statistics.median(x["value"] for x in vals)
+    line = base_line(args, 1)
+    line.update({"impl": "reference", "value": v, "ms_per_step": 1e3 / v, "n_gpus": world,
+                 "cpu_baseline": dict(vals[0], value=v),
+                 "e2e": {"value": v, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+                 "wall_s": wall})
+    print(json.dumps(line), flush=True)
+
+
+def roofline(stats, precision, hbm_peak, hbm_kind, K):
+    """The dominant kernel (largest summed CUDA-event time) against its bound."""
+    name = max(stats, key=lambda k: stats[k]["ms"])
+    s = stats[name]
+    per = max(s["launches"], 1)
+    dur_s = s["ms"] / per * 1e-3
+    if precision == "fp64" and name in ("smooth", "restrict", "prolong", "mode_resid", "field3d", "mode_apply"):
+        ach = s["flops"] / per / dur_s / 1e12
+        r = {"bound": "alu", "achieved": ach, "peak": FP64_ALU_PEAK / 1e12, "unit": "TFLOP/s",
+             "peak_kind": "derived FP64: 152 SMs x 2 FMA/clk x 2 flop x 2.07 GHz"}
+    else:
+        ach = s["bytes"] / per / dur_s / 1e9
+        r = {"bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s", "peak_kind": hbm_kind}
+    r.update({"frac": r["achieved"] / r["peak"], "traffic": None, "kernel": name, "launches_per_step": per / K,
+              "avg_launch_us": dur_s * 1e6})
+    return r
+
+
+def run_snac(args):
+    import numpy as np
+    import torch
+    world, rank, local = dist()
+    if world > 1:
+        import torch.distributed as td
+        td.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    from paper_2106_03583_gb300 import build, inputs, snac
+    build.build()
+    hbm_peak, hbm_kind = peaks()
+    blocks, f_np = inputs.config(args.workload, seed=args.seed + rank)
+    n3 = len(f_np)
+    f = torch.from_numpy(f_np).cuda()
+    p = torch.zeros_like(f)
+    K, W = args.steps, args.warmup
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    def max_over_ranks(x):
+        if world == 1:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        return float(t.item())
+
+    results = {}
+    clocks = None
+    for prec in args.precisions.split(","):
+        plan = snac.Plan(blocks, precision=prec)
+        for _ in range(W):
+            p.zero_()
+            plan.solve(f, p, tol=args.tol)
+        plan.reset_stats()
+        plan.set_profiling(True)
+        ck = Clocks(local) if rank == 0 else None
+        barrier()
+        torch.cuda.synchronize()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(K + 1)]
+        ev[0].record()
+        infos = []
+        for k in range(K):
+            p.zero_()
+            infos.append(plan.solve(f, p, tol=args.tol))
+            ev[k + 1].record()
+        torch.cuda.synchronize()
+        barrier()
+        ck_res = ck.stop() if ck else None
+        step_ms = [ev[k].elapsed_time(ev[k + 1]) for k in range(K)]
+        total_ms = max_over_ranks(ev[0].elapsed_time(ev[K]))
+        stats = plan.kernel_stats()
+        plan.set_profiling(False)
+        launches = sum(s["launches"] for s in stats.values())
+        bytes_model = sum(s["bytes"] for s in stats.values()) / K
+        # e2e through the public API: host (pinned) rhs in, solution back to host, every step
+        f_host = torch.from_numpy(f_np).pin_memory()
+        p_host = torch.empty(n3, dtype=torch.float64).pin_memory()
+        f_dev = torch.empty_like(f)
+        for _ in range(1):
+            f_dev.copy_(f_host, non_blocking=True)
+            p.zero_()
+            plan.solve(f_dev, p, tol=args.tol)
+            p_host.copy_(p, non_blocking=True)
+        barrier()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(K):
+            f_dev.copy_(f_host, non_blocking=True)
+            p.zero_()
+            plan.solve(f_dev, p, tol=args.tol)
+            p_host.copy_(p, non_blocking=True)
+        e1.record()
+        torch.cuda.synchronize()
+        barrier()
+        e2e_ms = max_over_ranks(e0.elapsed_time(e1))
+        ok = all(i["status"] == 0 and i["rel_res"] <= args.tol for i in infos)
+        results[prec] = {
+            "value": world * K / (total_ms * 1e-3), "ms_per_step": total_ms / K,
+            "p50_ms": statistics.median(step_ms), "p99_ms": float(np.percentile(step_ms, 99)),
+            "hbm_gbs_model": bytes_model / (total_ms / K * 1e-3) / 1e9,
+            "roofline": roofline(stats, prec, hbm_peak, hbm_kind, K),
+            "e2e": {"value": world * K / (e2e_ms * 1e-3), "unit": "solves/s", "h2d_bytes_per_step": 8 * n3,
+                    "d2h_bytes_per_step": 8 * n3},
+            "gpu_launches": launches,
+            "rel_res": infos[-1]["rel_res"], "outer_iters": infos[-1]["outer_iters"],
+            "total_cycles": infos[-1]["total_cycles"], "max_mode_cycles": infos[-1]["max_mode_cycles"],
+            "all_converged": ok,
+            "kernels": {k: {"launches": v["launches"], "ms": round(v["ms"], 3),
+                            "share": round(v["ms"] / max(sum(x["ms"] for x in stats.values()), 1e-30), 4)}
+                        for k, v in stats.items() if v["launches"]},
+            "clocks": ck_res,
+        }
+        if prec == "fp64":
+            clocks = ck_res
+        plan.close()
+    if rank != 0:
+        return
+    main = results.get("fp64") or next(iter(results.values()))
+    line = base_line(args, world)
+    line.update({"value": main["value"], "ms_per_step": main["ms_per_step"],
+                 "p50_ms": main["p50_ms"], "p99_ms": main["p99_ms"], "hbm_gbs_model": main["hbm_gbs_model"],
+                 "roofline": main["roofline"], "e2e": main["e2e"], "gpu_launches": main["gpu_launches"],
+                 "clocks": clocks, "rel_res": main["rel_res"], "all_converged": main["all_converged"],
+                 "kernels": main["kernels"]})
+    line["config"]["n_cells"] = n3
+    if "mixed" in results:
+        m = dict(results["mixed"])
+        m.pop("clocks", None)
+        line["mixed"] = m
+    if not args.no_cpu_baseline and world == 1:
+        line["cpu_baseline"] = cpu_baseline(args, blocks, f_np, 8)
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_snac(args)
+
+
+if __name__ == "__main__":
+    main()

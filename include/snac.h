@@ -138,6 +138,29 @@ const char *snac_status_string(int status);
 /* Detail of the last error raised by plan creation on this thread (empty if none). */
 const char *snac_last_error_message(void);
 
+/* ---- Kernel statistics (tracing) ---- */
+
+/* Per-kernel counters of a plan: launches (always counted), and with profiling enabled the summed
+ * CUDA-event duration of those launches, measured on the stream they were launched on. bytes and
+ * flops are the algorithmic DRAM bytes and floating-point operations of the counted launches (the
+ * minimum the operation must move / compute, not a hardware counter). name is a static string. */
+typedef struct {
+  const char *name;
+  int64_t launches;
+  double ms;
+  double bytes;
+  double flops;
+} snac_kernel_stat;
+
+/* enable != 0: record a CUDA event pair around every kernel launch of the plan (default off). */
+int snac_plan_set_profiling(snac_plan *plan, int32_t enable);
+
+/* Copy up to n per-kernel statistics into h_out; *count receives the number of kernel kinds. */
+int snac_plan_kernel_stats(const snac_plan *plan, snac_kernel_stat *h_out, int32_t n, int32_t *count);
+
+/* Zero the per-kernel statistics. */
+int snac_plan_reset_stats(snac_plan *plan);
+
 /* ---- Stages of the solve, one call each (the same kernels the solve uses). ---- */
 
 /* d_out = A d_p, the 3-D operator of Eq. 8 (float64 3-D fields). */

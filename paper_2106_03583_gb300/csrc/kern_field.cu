@@ -145,19 +145,28 @@ cudaError_t launch_field3d(snac_plan* P, int mode, const double* f, const double
   const HostLevel& l0 = P->lev[0];
   LevelView<double> L = level_view<double>(l0);
   dim3 grid((unsigned)l0.tiles.size(), (unsigned)std::min(P->nz, ZSPLIT));
-  k_field3d<<<grid, TILE_THREADS, 0, s>>>(L, P->d_cz, P->nz, P->kind == KIND_PP, mode, f, p, r, fshift, P->d_partial);
+  const double n3 = (double)P->n3;
+  {
+    // algorithmic bytes: read f and p, write r (mode 0); read p, write A p (1); read f (2)
+    LaunchScope ls(P, K_FIELD3D, (mode == 0 ? 24.0 : mode == 1 ? 16.0 : 8.0) * n3,
+                   (mode == 0 ? 23.0 : mode == 1 ? 14.0 : 7.0) * n3, s);
+    k_field3d<<<grid, TILE_THREADS, 0, s>>>(L, P->d_cz, P->nz, P->kind == KIND_PP, mode, f, p, r, fshift, P->d_partial);
+  }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess || mode == 1) return e;
   return launch_reduce_partials(P, (int)(grid.x * grid.y), s);
 }
 
 cudaError_t launch_reduce_partials(snac_plan* P, int npart, cudaStream_t s) {
+  LaunchScope ls(P, K_REDUCE, 32.0 * npart, 4.0 * npart, s);
   k_reduce4<<<1, 1024, 0, s>>>(P->d_partial, npart, P->d_sums);
   return cudaGetLastError();
 }
 
 cudaError_t launch_fix_mean(snac_plan* P, void* u0, cudaStream_t s) {
   const double alpha = P->dz * P->nz / P->theta;
+  const double nc = (double)P->lev[0].ncell;
+  LaunchScope ls(P, K_FIX_MEAN, nc * (8.0 + 2.0 * plan_inner_size(P)), 3.0 * nc, s);
   if (P->precision == SNAC_FP64)
     k_fix_mean<double><<<1, 1024, 0, s>>>((double*)u0, P->d_area0, P->lev[0].ncell, P->d_sums, alpha, P->area_total);
   else
@@ -166,7 +175,11 @@ cudaError_t launch_fix_mean(snac_plan* P, void* u0, cudaStream_t s) {
 }
 
 cudaError_t launch_shift(snac_plan* P, double* p, const double* d_c, cudaStream_t s) {
-  k_mean_of_p<<<1, 1, 0, s>>>(P->d_sums, P->vol_total);
+  {
+    LaunchScope ls(P, K_SHIFT, 16.0, 1.0, s);
+    k_mean_of_p<<<1, 1, 0, s>>>(P->d_sums, P->vol_total);
+  }
+  LaunchScope ls(P, K_SHIFT, 16.0 * P->n3, (double)P->n3, s);
   k_shift<<<2 * 152, 512, 0, s>>>(p, P->n3, d_c);
   return cudaGetLastError();
 }

@@ -212,24 +212,32 @@ cudaError_t vcycle_t(snac_plan* P, int nact, cudaStream_t st) {
   const int L = (int)P->lev.size() - 1;
   const T* sg = sigma_ptr<T>(P);
   const int* act = P->d_active;
+  const double w = sizeof(T);
   auto smooth = [&](int l, int nu) {
     const HostLevel& h = P->lev[l];
     const LevelView<T> V = level_view<T>(h);
     dim3 g((unsigned)h.tiles.size(), (unsigned)nact);
+    const double cells = (double)h.ncell * nact;
     for (int it = 0; it < nu; ++it)
-      for (int colour = 0; colour < 2; ++colour)
+      for (int colour = 0; colour < 2; ++colour) {
+        // Gauss-Seidel half-sweep: read the other colour and f of this colour, write this colour
+        LaunchScope ls(P, K_SMOOTH, 1.5 * w * cells, 17.0 * 0.5 * cells, st);
         k_smooth<T><<<g, TILE_THREADS, 0, st>>>(V, act, sg, (T*)h.d_u, (const T*)h.d_f, colour);
+      }
   };
   for (int l = 0; l < L; ++l) {
     smooth(l, P->nu1);
     const HostLevel& h = P->lev[l];
     const HostLevel& hc = P->lev[l + 1];
     dim3 g((unsigned)hc.tiles.size(), (unsigned)nact);
+    const double cells = (double)h.ncell * nact;
+    LaunchScope ls(P, K_RESTRICT, 2.5 * w * cells, 15.0 * cells, st);
     k_restrict<T><<<g, TILE_THREADS, 0, st>>>(level_view<T>(h), level_view<T>(hc), act, sg, (const T*)h.d_u,
                                                (const T*)h.d_f, (T*)hc.d_f, (T*)hc.d_u);
   }
   {
     const HostLevel& h = P->lev[L];
+    LaunchScope ls(P, K_COARSE, 2.0 * w * P->nc * nact + 8.0 * P->nc * P->nc, 4.0 * P->nc * P->nc * nact, st);
     k_coarse<T><<<nact, 256, 0, st>>>(P->d_Q, P->d_lam, P->d_sqa, P->nc, act, P->d_sigma64, P->d_singular_mode,
                                       P->null_index, (const T*)h.d_f, (T*)h.d_u, h.ncell);
   }
@@ -237,7 +245,11 @@ cudaError_t vcycle_t(snac_plan* P, int nact, cudaStream_t st) {
     const HostLevel& h = P->lev[l];
     const HostLevel& hc = P->lev[l + 1];
     dim3 g((unsigned)h.tiles.size(), (unsigned)nact);
-    k_prolong<T><<<g, TILE_THREADS, 0, st>>>(level_view<T>(h), level_view<T>(hc), act, (T*)h.d_u, (const T*)hc.d_u);
+    {
+      const double cells = (double)h.ncell * nact;
+      LaunchScope ls(P, K_PROLONG, 2.25 * w * cells, 8.0 * cells, st);
+      k_prolong<T><<<g, TILE_THREADS, 0, st>>>(level_view<T>(h), level_view<T>(hc), act, (T*)h.d_u, (const T*)hc.d_u);
+    }
     smooth(l, P->nu2);
   }
   return cudaGetLastError();
@@ -247,8 +259,13 @@ template <typename T>
 cudaError_t mode_norms_t(snac_plan* P, int nact, cudaStream_t st) {
   const HostLevel& h = P->lev[0];
   dim3 g((unsigned)h.tiles.size(), (unsigned)nact);
-  k_mode_resid2<T><<<g, TILE_THREADS, 0, st>>>(level_view<T>(h), P->d_active, sigma_ptr<T>(P), (const T*)h.d_u,
+  const double cells = (double)h.ncell * nact;
+  {
+    LaunchScope ls(P, K_MODE_RESID, 2.0 * sizeof(T) * cells, 14.0 * cells, st);
+    k_mode_resid2<T><<<g, TILE_THREADS, 0, st>>>(level_view<T>(h), P->d_active, sigma_ptr<T>(P), (const T*)h.d_u,
                                                 (const T*)h.d_f, P->d_mode_part);
+  }
+  LaunchScope ls(P, K_MODE_REDUCE, 8.0 * h.tiles.size() * nact, (double)h.tiles.size() * nact, st);
   k_mode_reduce<<<nact, 256, 0, st>>>(P->d_mode_part, (int)h.tiles.size(), P->d_active, P->d_mode_norm2);
   return cudaGetLastError();
 }
@@ -257,6 +274,8 @@ template <typename T>
 cudaError_t mode_operator_t(snac_plan* P, const void* u, void* out, cudaStream_t st) {
   const HostLevel& h = P->lev[0];
   dim3 g((unsigned)h.tiles.size(), (unsigned)P->nz);
+  const double cells = (double)h.ncell * P->nz;
+  LaunchScope ls(P, K_MODE_APPLY, 2.0 * sizeof(T) * cells, 12.0 * cells, st);
   k_mode_apply<T><<<g, TILE_THREADS, 0, st>>>(level_view<T>(h), P->d_active, sigma_ptr<T>(P), (const T*)u, (T*)out);
   return cudaGetLastError();
 }

@@ -15,6 +15,8 @@
 //   ND  DCT-IV: t_j = (x_2j + i x_{n-1-2j}) e^{-i pi (4j+1)/4n}, T = FFT_m(t), c_k = T_k e^{-i pi k/n},
 //       Y_2k = 2 Re c_k, Y_{n-1-2k} = -2 Im c_k. It is its own inverse (x 2n).
 //   DN  DST-IV_k(x) = DCT-IV_{n-1-k}((-1)^j x_j), its own inverse (x 2n).
+#include <cmath>
+
 #include "kern_common.cuh"
 #include "snac_impl.h"
 
@@ -262,6 +264,9 @@ cudaError_t fwd_t(snac_plan* P, const std::vector<ChunkDev>& ch, const ChunkDev*
                   void* modes, cudaStream_t s) {
   const size_t smem = 2 * (size_t)(P->nz / 2) * TC * sizeof(Cx<T>);
   cudaFuncSetAttribute(k_forward<T, TC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  const double n3 = (double)P->n3;
+  // read the FP64 field, write the modes; FFT model 2.5 log2(n) flops per point plus pre/post-processing
+  LaunchScope ls(P, K_FORWARD, (8.0 + sizeof(T)) * n3, (2.5 * std::log2((double)P->nz) + 8.0) * n3, s);
   k_forward<T, TC><<<(unsigned)ch.size(), 256, smem, s>>>(dch, P->lev[0].d_blk, P->nz, P->kind, make_tw<T>(P, twb), in3,
                                                           (T*)modes, P->lev[0].ncell);
   return cudaGetLastError();
@@ -272,6 +277,9 @@ cudaError_t bwd_t(snac_plan* P, const std::vector<ChunkDev>& ch, const ChunkDev*
                   double* p3, cudaStream_t s) {
   const size_t smem = 2 * (size_t)(P->nz / 2) * TC * sizeof(Cx<T>);
   cudaFuncSetAttribute(k_backward<T, TC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  const double n3 = (double)P->n3;
+  // read the modes, read and write the FP64 field
+  LaunchScope ls(P, K_BACKWARD, (16.0 + sizeof(T)) * n3, (2.5 * std::log2((double)P->nz) + 10.0) * n3, s);
   k_backward<T, TC><<<(unsigned)ch.size(), 256, smem, s>>>(dch, P->lev[0].d_blk, P->nz, P->kind, make_tw<T>(P, twb),
                                                            (const T*)modes, p3, P->lev[0].ncell, 1.0 / P->theta);
   return cudaGetLastError();

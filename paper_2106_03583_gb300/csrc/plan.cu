@@ -477,6 +477,7 @@ int upload_level(snac_plan* P, HostLevel& lv, size_t inner) {
 
 void free_plan(snac_plan* P) {
   if (!P) return;
+  profile_release(P);
   for (void* p : P->allocs) cudaFree(p);
   if (P->h_sums) cudaFreeHost(P->h_sums);
   if (P->h_mode_norm2) cudaFreeHost(P->h_mode_norm2);

@@ -108,6 +108,22 @@ struct TwiddleOffsets {
   int fft, twn, tw2n, tw4a, tw4b, total;
 };
 
+// Kernel kinds counted by the tracing facility.
+enum KernelKind {
+  K_FIELD3D = 0, K_REDUCE, K_FIX_MEAN, K_SHIFT, K_FORWARD, K_BACKWARD, K_SMOOTH, K_RESTRICT, K_PROLONG,
+  K_COARSE, K_MODE_RESID, K_MODE_REDUCE, K_MODE_APPLY, K_COUNT
+};
+
+struct KernelStat {
+  long long launches = 0;
+  double ms = 0.0, bytes = 0.0, flops = 0.0;
+};
+
+struct PendingEvent {
+  int kind;
+  cudaEvent_t a, b;
+};
+
 }  // namespace snac
 
 struct snac_plan {
@@ -163,6 +179,11 @@ struct snac_plan {
   // results
   snac_solve_info info{};
   std::vector<int32_t> mode_cycles;
+  // tracing
+  bool profiling = false;
+  snac::KernelStat kstats[snac::K_COUNT];
+  std::vector<snac::PendingEvent> pending;
+  std::vector<cudaEvent_t> event_pool;
 };
 
 namespace snac {
@@ -192,5 +213,23 @@ cudaError_t launch_vcycle(snac_plan* P, int nactive, cudaStream_t s);
 cudaError_t launch_mode_norms(snac_plan* P, int nactive, cudaStream_t s);
 
 int plan_inner_size(const snac_plan* P);  // bytes of the inner type
+
+// Counts one launch of `kind` with its algorithmic bytes / flops; with profiling on, brackets it
+// with a CUDA event pair on stream s (construct just before the launch, destroy just after).
+class LaunchScope {
+ public:
+  LaunchScope(snac_plan* P, int kind, double bytes, double flops, cudaStream_t s);
+  ~LaunchScope();
+
+ private:
+  snac_plan* P_;
+  int kind_;
+  cudaStream_t s_;
+  cudaEvent_t b_ = nullptr;
+};
+
+// Accumulate the durations of completed event pairs (call after a stream synchronisation).
+void profile_resolve(snac_plan* P);
+void profile_release(snac_plan* P);
 
 }  // namespace snac

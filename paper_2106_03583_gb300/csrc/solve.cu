@@ -61,6 +61,7 @@ int mode_solves(snac_plan* P, double target, cudaStream_t s, int* cycles_out) {
   CK(launch_mode_norms(P, nz, s));
   CK(cudaMemcpyAsync(P->h_mode_norm2, P->d_mode_norm2, nz * sizeof(double), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
+    profile_resolve(P);
   std::vector<double> thr2(nz), prev(nz);
   std::vector<int> list;
   for (int q = 0; q < nz; ++q) {
@@ -80,6 +81,7 @@ int mode_solves(snac_plan* P, double target, cudaStream_t s, int* cycles_out) {
     CK(launch_mode_norms(P, nact, s));
     CK(cudaMemcpyAsync(P->h_mode_norm2, P->d_mode_norm2, nz * sizeof(double), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
+    profile_resolve(P);
     std::vector<int> next;
     for (int q : list) {
       ++cycles_out[q];
@@ -99,6 +101,7 @@ int mode_solves(snac_plan* P, double target, cudaStream_t s, int* cycles_out) {
 int read_sums(snac_plan* P, cudaStream_t s) {
   CK(cudaMemcpyAsync(P->h_sums, P->d_sums, 4 * sizeof(double), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
+    profile_resolve(P);
   return SNAC_OK;
 }
 
@@ -135,6 +138,7 @@ int run_solve(snac_plan* P, const double* f, double* p, double tol, cudaStream_t
     if (fn == 0.0) {  // zero right-hand side: p = 0
       CK(cudaMemsetAsync(p, 0, (size_t)P->n3 * sizeof(double), s));
       CK(cudaStreamSynchronize(s));
+    profile_resolve(P);
       P->info.rel_res = 0.0;
       return SNAC_OK;
     }
@@ -146,6 +150,7 @@ int run_solve(snac_plan* P, const double* f, double* p, double tol, cudaStream_t
       if (P->singular && !updated) {  // the initial guess was kept: return its zero-mean shift
         CK(launch_shift(P, p, P->d_sums + 3, s));
         CK(cudaStreamSynchronize(s));
+    profile_resolve(P);
       }
       return done ? SNAC_OK : SNAC_ERR_NOT_CONVERGED;
     }
@@ -185,6 +190,7 @@ int snac_apply_operator(snac_plan* plan, const double* d_p, double* d_out, void*
   cudaStream_t s = (cudaStream_t)stream;
   CK(launch_field3d(plan, 1, nullptr, d_p, d_out, 0.0, s));
   CK(cudaStreamSynchronize(s));
+  profile_resolve(plan);
   return SNAC_OK;
 }
 
@@ -207,6 +213,7 @@ int snac_forward_transform(snac_plan* plan, const double* d_in, void* d_modes, v
   cudaStream_t s = (cudaStream_t)stream;
   CK(launch_forward(plan, d_in, d_modes, s));
   CK(cudaStreamSynchronize(s));
+  profile_resolve(plan);
   return SNAC_OK;
 }
 
@@ -217,6 +224,7 @@ int snac_backward_update(snac_plan* plan, const void* d_modes, double* d_p, void
   cudaStream_t s = (cudaStream_t)stream;
   CK(launch_backward_update(plan, d_modes, d_p, s));
   CK(cudaStreamSynchronize(s));
+  profile_resolve(plan);
   return SNAC_OK;
 }
 
@@ -228,6 +236,7 @@ int snac_mode_operator(snac_plan* plan, const void* d_u, void* d_out, void* stre
   if ((st = set_active_all(plan, s))) return st;
   CK(launch_mode_operator(plan, d_u, d_out, s));
   CK(cudaStreamSynchronize(s));
+  profile_resolve(plan);
   return SNAC_OK;
 }
 
@@ -243,6 +252,7 @@ int snac_mode_vcycles(snac_plan* plan, const void* d_f, void* d_u, int32_t ncycl
   for (int c = 0; c < ncycles; ++c) CK(launch_vcycle(plan, plan->nz, s));
   CK(cudaMemcpyAsync(d_u, plan->lev[0].d_u, bytes, cudaMemcpyDeviceToDevice, s));
   CK(cudaStreamSynchronize(s));
+  profile_resolve(plan);
   return SNAC_OK;
 }
 

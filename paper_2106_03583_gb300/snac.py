@@ -28,7 +28,8 @@ _PREC = {"fp64": 0, "mixed": 1}
 EXPORTS = ("snac_plan_create", "snac_plan_workspace_bytes", "snac_poisson_solve", "snac_plan_info",
            "snac_plan_mode_cycles", "snac_plan_destroy", "snac_status_string", "snac_last_error_message",
            "snac_apply_operator", "snac_residual", "snac_forward_transform", "snac_backward_update",
-           "snac_mode_operator", "snac_mode_vcycles")
+           "snac_mode_operator", "snac_mode_vcycles", "snac_plan_set_profiling", "snac_plan_kernel_stats",
+           "snac_plan_reset_stats")
 
 
 class SnacError(RuntimeError):
@@ -46,6 +47,11 @@ class _Block(ctypes.Structure):
 class _Options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("nu1", ctypes.c_int32), ("nu2", ctypes.c_int32),
                 ("max_outer", ctypes.c_int32), ("max_cycles", ctypes.c_int32), ("max_coarse", ctypes.c_int32)]
+
+
+class _KStat(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char_p), ("launches", ctypes.c_int64), ("ms", ctypes.c_double),
+                ("bytes", ctypes.c_double), ("flops", ctypes.c_double)]
 
 
 class _Info(ctypes.Structure):
@@ -84,6 +90,9 @@ def lib() -> ctypes.CDLL:
             "snac_backward_update": [vp, vp, vp, vp],
             "snac_mode_operator": [vp, vp, vp, vp],
             "snac_mode_vcycles": [vp, vp, vp, i32, vp],
+            "snac_plan_set_profiling": [vp, i32],
+            "snac_plan_kernel_stats": [vp, ctypes.POINTER(_KStat), i32, ctypes.POINTER(i32)],
+            "snac_plan_reset_stats": [vp],
         }
         for name, args in sig.items():
             fn = getattr(L, name)
@@ -175,6 +184,22 @@ class Plan:
         out = (ctypes.c_int32 * self.nz)()
         _check(lib().snac_plan_mode_cycles(self._h, out, self.nz))
         return np.frombuffer(out, dtype=np.int32).copy()
+
+    # ---- tracing
+    def set_profiling(self, enable: bool):
+        """CUDA-event timing of every kernel launch of this plan (launch counts are always kept)."""
+        _check(lib().snac_plan_set_profiling(self._h, 1 if enable else 0))
+
+    def reset_stats(self):
+        _check(lib().snac_plan_reset_stats(self._h))
+
+    def kernel_stats(self) -> dict:
+        """{kernel: {launches, ms, bytes, flops}}: bytes/flops are algorithmic, ms needs profiling."""
+        n = ctypes.c_int32()
+        buf = (_KStat * 32)()
+        _check(lib().snac_plan_kernel_stats(self._h, buf, 32, ctypes.byref(n)))
+        return {buf[k].name.decode(): {"launches": buf[k].launches, "ms": buf[k].ms, "bytes": buf[k].bytes,
+                                       "flops": buf[k].flops} for k in range(n.value)}
 
     @property
     def workspace_bytes(self) -> int:
