@@ -186,6 +186,28 @@ int snac_mode_operator(snac_plan *plan, const void *d_u, void *d_out, void *stre
  * d_u, with right-hand side d_f (mode-space fields of the plan's inner type). */
 int snac_mode_vcycles(snac_plan *plan, const void *d_f, void *d_u, int32_t ncycles, void *stream);
 
+/* ---- Allocation-free residual of one block (the paper has no counterpart) ---- */
+
+/* Largest number of cells along any axis that snac_residual_noalloc accepts. */
+#define SNAC_NOALLOC_MAX_CELLS_PER_AXIS 4096
+
+/* d_r = d_rhs - A d_p for a single block, with h_norms[0] = ||r||^2 and h_norms[1] = ||rhs||^2:
+ * the same result as snac_residual on a one-block plan, for callers that cannot allocate device
+ * memory and so cannot create a plan -- programs whose device memory is owned by their own
+ * (caching) allocator or capped by a fixed budget, and latency-sensitive loops that cannot afford the
+ * device-wide synchronisation that cudaMalloc and cudaFree imply. Nothing is allocated: the scratch
+ * (cell widths, operator coefficients, per-CTA partial sums; about 2.5 MB) is a fixed array in the
+ * library's device image, present on every GPU that loads the library until the process exits.
+ * block: one block, faces SNAC_BC_DIRICHLET / _NEUMANN / _PERIODIC only (no connectivity), at most
+ * SNAC_NOALLOC_MAX_CELLS_PER_AXIS cells per axis (SNAC_ERR_INVALID_ARG otherwise), uniform along z
+ * (SNAC_ERR_LAYOUT otherwise). d_rhs, d_p, d_r: device float64 fields [z][y][x]; h_norms: host.
+ * The first call on a device looks up the scratch's device address (once per device, with that
+ * device current); make that first call before any stream capture. Every call uses the same
+ * scratch, so calls whose work overlaps on the GPU (other streams, other host threads) race: issue
+ * them one after another. Returns after the work on `stream` is complete. */
+int snac_residual_noalloc(const snac_block *block, const double *d_rhs, const double *d_p, double *d_r,
+                          double *h_norms, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -29,7 +29,7 @@ EXPORTS = ("snac_plan_create", "snac_plan_workspace_bytes", "snac_poisson_solve"
            "snac_plan_mode_cycles", "snac_plan_destroy", "snac_status_string", "snac_last_error_message",
            "snac_apply_operator", "snac_residual", "snac_forward_transform", "snac_backward_update",
            "snac_mode_operator", "snac_mode_vcycles", "snac_plan_set_profiling", "snac_plan_kernel_stats",
-           "snac_plan_reset_stats")
+           "snac_plan_reset_stats", "snac_residual_noalloc")
 
 
 class SnacError(RuntimeError):
@@ -93,6 +93,7 @@ def lib() -> ctypes.CDLL:
             "snac_plan_set_profiling": [vp, i32],
             "snac_plan_kernel_stats": [vp, ctypes.POINTER(_KStat), i32, ctypes.POINTER(i32)],
             "snac_plan_reset_stats": [vp],
+            "snac_residual_noalloc": [ctypes.POINTER(_Block), vp, vp, vp, ctypes.POINTER(f64), vp],
         }
         for name, args in sig.items():
             fn = getattr(L, name)
@@ -123,6 +124,25 @@ def _marshal_blocks(blocks):
                 c.bc[a][s] = _BC[blk["bc"][a][s]]
                 c.nbr[a][s] = int(blk["nbr"][a][s])
     return arr, keep
+
+
+def residual_noalloc(block, rhs, p, r):
+    """r = rhs - A p for one block without a plan and without any device allocation
+    (``snac_residual_noalloc``), for callers whose device memory is owned by their own allocator or
+    budget. rhs, p, r: contiguous CUDA float64 tensors [z][y][x]. Returns (||r||^2, ||rhs||^2)."""
+    import torch
+    arr, keep = _marshal_blocks([block])
+    n = int(np.prod([block["hi"][a] - block["lo"][a] + 1 for a in range(3)]))
+    for name, t in (("rhs", rhs), ("p", p), ("r", r)):
+        if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != torch.float64 or \
+                not t.is_contiguous() or t.numel() != n:
+            raise ValueError(f"{name} must be a contiguous CUDA float64 tensor with {n} elements")
+    norms = (ctypes.c_double * 2)()
+    stream = ctypes.c_void_p(torch.cuda.current_stream(rhs.device).cuda_stream)
+    _check(lib().snac_residual_noalloc(arr, ctypes.c_void_p(rhs.data_ptr()), ctypes.c_void_p(p.data_ptr()),
+                                       ctypes.c_void_p(r.data_ptr()), norms, stream))
+    del keep
+    return norms[0], norms[1]
 
 
 class Plan:
