@@ -239,6 +239,7 @@ def config(name: str, seed: int = 0, scale: int = 1):
     ``"mb2x2"``: a 2x2 layout of 256x256-cell blocks (x uniform on [0, 2], y two-sided tanh
     factor 1.5 on [0, 2]), all outer faces Neumann, n_z = 256 Neumann-Neumann on [0, 1];
     f = D u with a k^-5/3 spectrum.
+    ``"mb2x2_z64"``: the same with n_z = 64 (a smaller case of the same kernels for profiling).
     ``"chan"``: one block 1024x512 (x uniform on [0, 2] Dirichlet-Dirichlet, y two-sided tanh
     factor 2.0 on [0, 1] Neumann-Neumann) by n_z = 512 periodic on [0, 1]; f = D u, k^-5/3.
     ``scale`` divides every cell count (and keeps the domain), giving small cases with the same
@@ -251,8 +252,8 @@ def config(name: str, seed: int = 0, scale: int = 1):
         blocks = make_blocks(xf, xf, zf, [(0, n, 0, n)],
                              {"x-": "D", "x+": "D", "y-": "N", "y+": "N"}, ("P", "P"))
         return blocks, uniform_rhs(blocks, seed, remove_mean=True)
-    if name == "mb2x2":
-        n, nz = 256 // scale, 256 // scale
+    if name in ("mb2x2", "mb2x2_z64"):
+        n, nz = 256 // scale, (256 if name == "mb2x2" else 64) // scale
         xf, yf, zf, rects = _grid2x2(n, 2.0, 2.0, nz, 1.0, 0, 1.5)
         blocks = make_blocks(xf, yf, zf, rects, {"x-": "N", "x+": "N", "y-": "N", "y+": "N"}, ("N", "N"))
         return blocks, divergence_rhs(blocks, seed)
@@ -270,5 +271,6 @@ def config(name: str, seed: int = 0, scale: int = 1):
 CONFIGS = {
     "c64": "1 block 64x64x32, x D-D / y N-N / z periodic (DFT), uniform unit box, f~U[-1,1]",
     "mb2x2": "2x2 blocks of 256x256, y tanh 1.5, Neumann walls, n_z=256 Neumann-Neumann (DCT-II), f=Du k^-5/3",
+    "mb2x2_z64": "mb2x2 with n_z=64 (profiling size, 134 MB per field)",
     "chan": "1 block 1024x512, y tanh 2.0, x D-D / y N-N, n_z=512 periodic (DFT), f=Du k^-5/3",
 }
