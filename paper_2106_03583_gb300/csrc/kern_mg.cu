@@ -21,30 +21,56 @@ __device__ __forceinline__ T apply_row(const Coef<T>& cx, const Coef<T>& cy, T d
   return fma(diag, uc, a);
 }
 
-// One colour of one Gauss-Seidel sweep: u_c += (f_c - (A u)_c) / diag_c on every cell of that colour.
-template <typename T>
-__global__ void __launch_bounds__(TILE_THREADS) k_smooth(LevelView<T> L, const int* __restrict__ active,
-                                                          const T* __restrict__ sigma, T* __restrict__ u,
-                                                          const T* __restrict__ f, int colour) {
+// One colour of one Gauss-Seidel sweep: u_c = (f_c - sum_nbr a u_nbr) / diag_c on every cell of that
+// colour. 128 threads cover a 32x8 tile: each thread owns the one cell of its row pair that has the
+// colour, so every lane of every warp works. FP64 plans read the precomputed inverse diagonal (the
+// FP64 pipe is the bound there); FP32 plans form it on the fly.
+constexpr int COLOUR_THREADS = 128;
+
+template <typename T, bool PRE_INV>
+__global__ void __launch_bounds__(COLOUR_THREADS) k_smooth(LevelView<T> L, const int* __restrict__ active,
+                                                            const T* __restrict__ sigma, const double* __restrict__ invd,
+                                                            T* __restrict__ u, const T* __restrict__ f, int colour) {
   const TileDev t = L.tiles[blockIdx.x];
   const BlockDev B = L.blk[t.b];
-  const int i = t.x0 + (threadIdx.x % TILE_X), j = t.y0 + (threadIdx.x / TILE_X);
-  if (i >= B.nx || j >= B.ny || ((B.par + i + j) & 1) != colour) return;
+  const int j = t.y0 + (threadIdx.x >> 4);
+  const int i = t.x0 + 2 * (threadIdx.x & 15) + ((colour ^ B.par ^ j) & 1);
+  if (i >= B.nx || j >= B.ny) return;
   const int q = active[blockIdx.y];
   const long long base = (long long)q * L.ncell;
   long long w, e, s, n;
   nbr_plane(L.blk, B, t.b, i, j, w, e, s, n);
   const long long c = B.off + (long long)j * B.nx + i;
   const Coef<T> cx = L.cx[B.xo + i], cy = L.cy[B.yo + j];
-  const T diag = cx.d + cy.d + sigma[q];
-  const T uc = u[base + c];
-  const T au = apply_row(cx, cy, diag, uc, u[base + w], u[base + e], u[base + s], u[base + n]);
-  u[base + c] = fma(f[base + c] - au, recip(diag), uc);
+  T id;
+  if constexpr (PRE_INV) {
+    id = invd[base + c];
+  } else {
+    id = recip(cx.d + cy.d + sigma[q]);
+  }
+  T a = cx.lo * u[base + w];
+  a = fma(cx.hi, u[base + e], a);
+  a = fma(cy.lo, u[base + s], a);
+  a = fma(cy.hi, u[base + n], a);
+  u[base + c] = (f[base + c] - a) * id;
+}
+
+__global__ void __launch_bounds__(TILE_THREADS) k_invd(LevelView<double> L, const double* __restrict__ sigma,
+                                                        double* __restrict__ invd) {
+  const TileDev t = L.tiles[blockIdx.x];
+  const BlockDev B = L.blk[t.b];
+  const int i = t.x0 + (threadIdx.x % TILE_X), j = t.y0 + (threadIdx.x / TILE_X);
+  if (i >= B.nx || j >= B.ny) return;
+  const int q = blockIdx.y;
+  const long long c = B.off + (long long)j * B.nx + i;
+  invd[(long long)q * L.ncell + c] = 1.0 / (L.cx[B.xo + i].d + L.cy[B.yo + j].d + sigma[q]);
 }
 
 // Coarse right-hand side = area-weighted average of the fine residual over the four children;
 // the coarse iterate starts at zero.
-template <typename T>
+// After a red-black sweep ending on black, every black cell has zero residual (its update solved its
+// own row), so with RED_ONLY only the two red children of each coarse cell are evaluated.
+template <typename T, bool RED_ONLY>
 __global__ void __launch_bounds__(TILE_THREADS) k_restrict(LevelView<T> F, LevelView<T> C, const int* __restrict__ active,
                                                             const T* __restrict__ sigma, const T* __restrict__ uf,
                                                             const T* __restrict__ ff, T* __restrict__ fc,
@@ -63,6 +89,7 @@ __global__ void __launch_bounds__(TILE_THREADS) k_restrict(LevelView<T> F, Level
 #pragma unroll
     for (int di = 0; di < 2; ++di) {
       const int i = 2 * I + di, j = 2 * J + dj;
+      if (RED_ONLY && ((Bf.par + i + j) & 1)) continue;
       long long w, e, s, n;
       nbr_plane(F.blk, Bf, t.b, i, j, w, e, s, n);
       const long long c = Bf.off + (long long)j * Bf.nx + i;
@@ -151,15 +178,23 @@ __global__ void __launch_bounds__(TILE_THREADS) k_mode_apply(LevelView<T> L, con
   out[base + c] = apply_row(cx, cy, diag, u[base + c], u[base + w], u[base + e], u[base + s], u[base + n]);
 }
 
-// Per-tile partial sums of (f - (A + sigma) u)^2 for every listed mode (FP64 accumulation).
-template <typename T>
+// Per-tile partial sums of (f - (A + sigma) u)^2 for every listed mode (FP64 accumulation). With
+// RED_ONLY (after a sweep ending on black) only the red cells carry a residual.
+template <typename T, bool RED_ONLY>
 __global__ void __launch_bounds__(TILE_THREADS) k_mode_resid2(LevelView<T> L, const int* __restrict__ active,
                                                                const T* __restrict__ sigma, const T* __restrict__ u,
                                                                const T* __restrict__ f, double* __restrict__ part) {
   __shared__ double sh[32];
   const TileDev t = L.tiles[blockIdx.x];
   const BlockDev B = L.blk[t.b];
-  const int i = t.x0 + (threadIdx.x % TILE_X), j = t.y0 + (threadIdx.x / TILE_X);
+  int i, j;
+  if (RED_ONLY) {
+    j = t.y0 + (threadIdx.x >> 4);
+    i = t.x0 + 2 * (threadIdx.x & 15) + ((B.par ^ j) & 1);
+  } else {
+    i = t.x0 + (threadIdx.x % TILE_X);
+    j = t.y0 + (threadIdx.x / TILE_X);
+  }
   const int q = active[blockIdx.y];
   double r2 = 0.0;
   if (i < B.nx && j < B.ny) {
@@ -177,7 +212,7 @@ __global__ void __launch_bounds__(TILE_THREADS) k_mode_resid2(LevelView<T> L, co
   if (lane == 0) sh[warp] = r2;
   __syncthreads();
   if (warp == 0) {
-    double v = lane < (TILE_THREADS / 32) ? sh[lane] : 0.0;
+    double v = lane < (int)(blockDim.x >> 5) ? sh[lane] : 0.0;
     v = warp_sum(v);
     if (lane == 0) part[(long long)q * L.ntiles + blockIdx.x] = v;
   }
@@ -213,6 +248,7 @@ cudaError_t vcycle_t(snac_plan* P, int nact, cudaStream_t st) {
   const T* sg = sigma_ptr<T>(P);
   const int* act = P->d_active;
   const double w = sizeof(T);
+  constexpr bool pre_inv = sizeof(T) == 8;
   auto smooth = [&](int l, int nu) {
     const HostLevel& h = P->lev[l];
     const LevelView<T> V = level_view<T>(h);
@@ -221,8 +257,8 @@ cudaError_t vcycle_t(snac_plan* P, int nact, cudaStream_t st) {
     for (int it = 0; it < nu; ++it)
       for (int colour = 0; colour < 2; ++colour) {
         // Gauss-Seidel half-sweep: read the other colour and f of this colour, write this colour
-        LaunchScope ls(P, K_SMOOTH, 1.5 * w * cells, 17.0 * 0.5 * cells, st);
-        k_smooth<T><<<g, TILE_THREADS, 0, st>>>(V, act, sg, (T*)h.d_u, (const T*)h.d_f, colour);
+        LaunchScope ls(P, K_SMOOTH, 1.5 * w * cells, (pre_inv ? 9.0 : 12.0) * 0.5 * cells, st);
+        k_smooth<T, pre_inv><<<g, COLOUR_THREADS, 0, st>>>(V, act, sg, h.d_invd, (T*)h.d_u, (const T*)h.d_f, colour);
       }
   };
   for (int l = 0; l < L; ++l) {
@@ -231,9 +267,13 @@ cudaError_t vcycle_t(snac_plan* P, int nact, cudaStream_t st) {
     const HostLevel& hc = P->lev[l + 1];
     dim3 g((unsigned)hc.tiles.size(), (unsigned)nact);
     const double cells = (double)h.ncell * nact;
-    LaunchScope ls(P, K_RESTRICT, 2.5 * w * cells, 15.0 * cells, st);
-    k_restrict<T><<<g, TILE_THREADS, 0, st>>>(level_view<T>(h), level_view<T>(hc), act, sg, (const T*)h.d_u,
-                                               (const T*)h.d_f, (T*)hc.d_f, (T*)hc.d_u);
+    LaunchScope ls(P, K_RESTRICT, 2.5 * w * cells, (P->nu1 > 0 ? 7.5 : 15.0) * cells, st);
+    if (P->nu1 > 0)
+      k_restrict<T, true><<<g, TILE_THREADS, 0, st>>>(level_view<T>(h), level_view<T>(hc), act, sg, (const T*)h.d_u,
+                                                      (const T*)h.d_f, (T*)hc.d_f, (T*)hc.d_u);
+    else
+      k_restrict<T, false><<<g, TILE_THREADS, 0, st>>>(level_view<T>(h), level_view<T>(hc), act, sg, (const T*)h.d_u,
+                                                       (const T*)h.d_f, (T*)hc.d_f, (T*)hc.d_u);
   }
   {
     const HostLevel& h = P->lev[L];
@@ -256,14 +296,20 @@ cudaError_t vcycle_t(snac_plan* P, int nact, cudaStream_t st) {
 }
 
 template <typename T>
-cudaError_t mode_norms_t(snac_plan* P, int nact, cudaStream_t st) {
+cudaError_t mode_norms_t(snac_plan* P, int nact, bool after_cycle, cudaStream_t st) {
   const HostLevel& h = P->lev[0];
   dim3 g((unsigned)h.tiles.size(), (unsigned)nact);
   const double cells = (double)h.ncell * nact;
   {
-    LaunchScope ls(P, K_MODE_RESID, 2.0 * sizeof(T) * cells, 14.0 * cells, st);
-    k_mode_resid2<T><<<g, TILE_THREADS, 0, st>>>(level_view<T>(h), P->d_active, sigma_ptr<T>(P), (const T*)h.d_u,
-                                                (const T*)h.d_f, P->d_mode_part);
+    // after post-smoothing only the red cells carry a residual (read u everywhere, f on red cells)
+    const bool red = after_cycle && P->nu2 > 0 && P->lev.size() > 1;
+    LaunchScope ls(P, K_MODE_RESID, (red ? 1.5 : 2.0) * sizeof(T) * cells, (red ? 7.0 : 14.0) * cells, st);
+    if (red)
+      k_mode_resid2<T, true><<<g, COLOUR_THREADS, 0, st>>>(level_view<T>(h), P->d_active, sigma_ptr<T>(P),
+                                                           (const T*)h.d_u, (const T*)h.d_f, P->d_mode_part);
+    else
+      k_mode_resid2<T, false><<<g, TILE_THREADS, 0, st>>>(level_view<T>(h), P->d_active, sigma_ptr<T>(P),
+                                                          (const T*)h.d_u, (const T*)h.d_f, P->d_mode_part);
   }
   LaunchScope ls(P, K_MODE_REDUCE, 8.0 * h.tiles.size() * nact, (double)h.tiles.size() * nact, st);
   k_mode_reduce<<<nact, 256, 0, st>>>(P->d_mode_part, (int)h.tiles.size(), P->d_active, P->d_mode_norm2);
@@ -282,14 +328,24 @@ cudaError_t mode_operator_t(snac_plan* P, const void* u, void* out, cudaStream_t
 
 }  // namespace
 
+cudaError_t launch_inverse_diagonals(snac_plan* P, cudaStream_t s) {
+  for (size_t l = 0; l + 1 < P->lev.size(); ++l) {
+    const HostLevel& h = P->lev[l];
+    dim3 g((unsigned)h.tiles.size(), (unsigned)P->nz);
+    k_invd<<<g, TILE_THREADS, 0, s>>>(level_view<double>(h), P->d_sigma64, h.d_invd);
+  }
+  return cudaGetLastError();
+}
+
 cudaError_t launch_vcycle(snac_plan* P, int nact, cudaStream_t s) {
   if (nact <= 0) return cudaSuccess;
   return P->precision == SNAC_FP64 ? vcycle_t<double>(P, nact, s) : vcycle_t<float>(P, nact, s);
 }
 
-cudaError_t launch_mode_norms(snac_plan* P, int nact, cudaStream_t s) {
+cudaError_t launch_mode_norms(snac_plan* P, int nact, bool after_cycle, cudaStream_t s) {
   if (nact <= 0) return cudaSuccess;
-  return P->precision == SNAC_FP64 ? mode_norms_t<double>(P, nact, s) : mode_norms_t<float>(P, nact, s);
+  return P->precision == SNAC_FP64 ? mode_norms_t<double>(P, nact, after_cycle, s)
+                                   : mode_norms_t<float>(P, nact, after_cycle, s);
 }
 
 // Requires d_active = 0..n_z-1.

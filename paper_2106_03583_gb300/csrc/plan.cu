@@ -564,6 +564,15 @@ int create(snac_plan** out, int32_t nblocks, const snac_block* blocks, int32_t h
     for (int q = 0; q < P->nz; ++q) sm[q] = (P->singular && mode_lambda(P->kind, P->nz, q) == 0.0) ? 1 : 0;
     if ((st = upload(P, &P->d_singular_mode, sm))) break;
     if ((st = build_coarse(P))) break;
+    if (P->precision == SNAC_FP64) {
+      for (size_t l = 0; l + 1 < P->lev.size(); ++l)
+        if ((st = dmalloc(P, &P->lev[l].d_invd, (size_t)P->nz * P->lev[l].ncell))) break;
+      if (st) break;
+      if (launch_inverse_diagonals(P, 0) != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess) {
+        st = fail(SNAC_ERR_CUDA, "computing the inverse diagonals failed");
+        break;
+      }
+    }
     if ((st = build_twiddles(P))) break;
     if ((st = build_chunks(P, 8, P->chunks64, &P->d_chunks64))) break;
     if ((st = build_chunks(P, 16, P->chunks32, &P->d_chunks32))) break;

@@ -97,6 +97,7 @@ struct HostLevel {
   float* d_ry32 = nullptr;
   void* d_u = nullptr;  // mode-space iterate, n_z x ncell of the inner type
   void* d_f = nullptr;  // mode-space right-hand side
+  double* d_invd = nullptr;  // FP64 plans, smoothed levels: 1 / (A_xy + sigma_q)_cc per mode and cell
 };
 
 // A chunk of up to TCOLS consecutive columns (cells of one plane) of one block, for the transforms.
@@ -207,10 +208,13 @@ cudaError_t launch_backward_update(snac_plan* P, const void* modes, double* p3, 
 
 // ---- multigrid ----
 cudaError_t launch_mode_operator(snac_plan* P, const void* u, void* out, cudaStream_t s);
+// 1 / diagonal of every mode's reduced operator on every smoothed level (FP64 plans), once per plan
+cudaError_t launch_inverse_diagonals(snac_plan* P, cudaStream_t s);
 // one V-cycle of the active modes on the plan's level buffers (level 0: d_u / d_f)
 cudaError_t launch_vcycle(snac_plan* P, int nactive, cudaStream_t s);
-// per-mode ||f - A u||^2 at level 0 for the active modes -> d_mode_norm2[q]
-cudaError_t launch_mode_norms(snac_plan* P, int nactive, cudaStream_t s);
+// per-mode ||f - A u||^2 at level 0 for the active modes -> d_mode_norm2[q]; after_cycle: u is the
+// result of a V-cycle (post-smoothing ended on black, so only red cells carry a residual)
+cudaError_t launch_mode_norms(snac_plan* P, int nactive, bool after_cycle, cudaStream_t s);
 
 int plan_inner_size(const snac_plan* P);  // bytes of the inner type
 

@@ -58,7 +58,7 @@ int mode_solves(snac_plan* P, double target, cudaStream_t s, int* cycles_out) {
   CK(cudaMemsetAsync(P->lev[0].d_u, 0, (size_t)nz * P->lev[0].ncell * plan_inner_size(P), s));
   int st = set_active_all(P, s);
   if (st) return st;
-  CK(launch_mode_norms(P, nz, s));
+  CK(launch_mode_norms(P, nz, false, s));
   CK(cudaMemcpyAsync(P->h_mode_norm2, P->d_mode_norm2, nz * sizeof(double), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
     profile_resolve(P);
@@ -78,7 +78,7 @@ int mode_solves(snac_plan* P, double target, cudaStream_t s, int* cycles_out) {
     std::copy(list.begin(), list.end(), P->h_active);
     CK(cudaMemcpyAsync(P->d_active, P->h_active, nact * sizeof(int), cudaMemcpyHostToDevice, s));
     CK(launch_vcycle(P, nact, s));
-    CK(launch_mode_norms(P, nact, s));
+    CK(launch_mode_norms(P, nact, true, s));
     CK(cudaMemcpyAsync(P->h_mode_norm2, P->d_mode_norm2, nz * sizeof(double), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     profile_resolve(P);
