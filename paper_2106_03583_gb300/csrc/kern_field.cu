@@ -29,11 +29,13 @@ __device__ __forceinline__ void block_sum(double (&v)[NV], double* sh /* [NV][32
 }
 
 // One thread per x-y cell of a tile, looping over the z planes k = blockIdx.y, + gridDim.y, ...
-// mode 0: r = (f - fshift) - A p, partial {||r||^2, ||f - fshift||^2, sum V p}
-// mode 1: r = A p
-// mode 2: partial {sum V f, sum V |f|, ||f||^2}
+// MODE 0: r = (f - fshift) - A p; partial {||r||^2, ||f - fshift||^2 (NEED_F2), sum V p (NEED_VP)}
+// MODE 1: r = A p
+// MODE 2: partial {sum V f, sum V |f|, ||f||^2}
+// Only the sums a caller needs are formed: the kernel is bound by the FP64 pipe.
+template <int MODE, bool NEED_F2, bool NEED_VP>
 __global__ void __launch_bounds__(TILE_THREADS) k_field3d(LevelView<double> L, const Coef<double>* __restrict__ cz,
-                                                           int nz, int periodic_z, int mode, const double* __restrict__ f,
+                                                           int nz, int periodic_z, const double* __restrict__ f,
                                                            const double* __restrict__ p, double* __restrict__ r,
                                                            double fshift, double* __restrict__ partial) {
   __shared__ double sh[4 * 32];
@@ -57,7 +59,7 @@ __global__ void __launch_bounds__(TILE_THREADS) k_field3d(LevelView<double> L, c
     const double dxy = cx.d + cy.d;
     for (int k = blockIdx.y; k < nz; k += gridDim.y) {
       const long long c = base + k * plane;
-      if (mode == 2) {
+      if (MODE == 2) {
         const double fv = f[c];
         const double v = area * cz[k].w;
         acc[0] += v * fv;
@@ -76,19 +78,19 @@ __global__ void __launch_bounds__(TILE_THREADS) k_field3d(LevelView<double> L, c
       ap = fma(z.lo, p[base + kd * plane], ap);
       ap = fma(z.hi, p[base + ku * plane], ap);
       ap = fma(dxy + z.d, pc, ap);
-      if (mode == 1) {
+      if (MODE == 1) {
         r[c] = ap;
       } else {
         const double fv = f[c] - fshift;
         const double rv = fv - ap;
         r[c] = rv;
         acc[0] = fma(rv, rv, acc[0]);
-        acc[1] = fma(fv, fv, acc[1]);
-        acc[2] = fma(area * z.w, pc, acc[2]);
+        if (NEED_F2) acc[1] = fma(fv, fv, acc[1]);
+        if (NEED_VP) acc[2] = fma(area * z.w, pc, acc[2]);
       }
     }
   }
-  if (mode == 1) return;
+  if (MODE == 1) return;
   block_sum<3>(acc, sh);
   if (threadIdx.x == 0) {
     double* o = partial + 4 * ((long long)blockIdx.y * gridDim.x + blockIdx.x);
@@ -112,21 +114,31 @@ __global__ void __launch_bounds__(1024) k_reduce4(const double* __restrict__ par
     for (int k = 0; k < 4; ++k) out[k] = acc[k];
 }
 
-// Shift the singular mode-0 correction by a constant so that the updated p has zero volume-weighted
-// mean: sum V (p_old + e) = 0, with sum V e = alpha * sum_xy area * e0 (alpha = dz n / theta) and
-// sum V p_old = sums[2] from the residual pass. One CTA.
+// The singular mode-0 correction is shifted by a constant so that the updated p has zero
+// volume-weighted mean: sum V (p_old + e) = 0, with sum V e = alpha * sum_xy area * e0
+// (alpha = dz n / theta) and sum V p_old = sums[2] from the residual pass. Two passes over the
+// mode-0 plane: per-CTA partial sums of area * e0, then (after their reduction into sums[4]) the shift.
 template <typename T>
-__global__ void __launch_bounds__(1024) k_fix_mean(T* __restrict__ u0, const double* __restrict__ area, long long ncell,
-                                                   const double* __restrict__ sums, double alpha, double area_total) {
+__global__ void __launch_bounds__(256) k_area_dot(const T* __restrict__ u0, const double* __restrict__ area,
+                                                  long long ncell, double* __restrict__ partial) {
   __shared__ double sh[32];
-  __shared__ double kappa;
   double acc[1] = {0.0};
-  for (long long c = threadIdx.x; c < ncell; c += blockDim.x) acc[0] = fma(area[c], (double)u0[c], acc[0]);
+  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < ncell; c += (long long)gridDim.x * blockDim.x)
+    acc[0] = fma(area[c], (double)u0[c], acc[0]);
   block_sum<1>(acc, sh);
-  if (threadIdx.x == 0) kappa = -(sums[2] + alpha * acc[0]) / (alpha * area_total);
-  __syncthreads();
-  const double k = kappa;
-  for (long long c = threadIdx.x; c < ncell; c += blockDim.x) u0[c] = (T)((double)u0[c] + k);
+  if (threadIdx.x == 0) {
+    double* o = partial + 4 * (long long)blockIdx.x;
+    o[0] = acc[0];
+    o[1] = o[2] = o[3] = 0.0;
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_fix_apply(T* __restrict__ u0, long long ncell, const double* __restrict__ sums,
+                                                   double alpha, double area_total) {
+  const double kappa = -(sums[2] + alpha * sums[4]) / (alpha * area_total);
+  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < ncell; c += (long long)gridDim.x * blockDim.x)
+    u0[c] = (T)((double)u0[c] + kappa);
 }
 
 __global__ void k_shift(double* __restrict__ p, long long n, const double* __restrict__ c) {
@@ -138,39 +150,58 @@ __global__ void k_shift(double* __restrict__ p, long long n, const double* __res
 // c = sums[2] / vol_total (the volume-weighted mean of p) written to sums[3]
 __global__ void k_mean_of_p(double* sums, double vol_total) { sums[3] = sums[2] / vol_total; }
 
+template <int MODE, bool F2, bool VP>
+void field3d_t(const LevelView<double>& L, dim3 grid, snac_plan* P, const double* f, const double* p, double* r,
+               double fshift, cudaStream_t s) {
+  k_field3d<MODE, F2, VP><<<grid, TILE_THREADS, 0, s>>>(L, P->d_cz, P->nz, P->kind == KIND_PP, f, p, r, fshift,
+                                                         P->d_partial);
+}
+
 }  // namespace
 
 cudaError_t launch_field3d(snac_plan* P, int mode, const double* f, const double* p, double* r, double fshift,
-                           cudaStream_t s) {
+                           bool need_f2, bool need_vp, cudaStream_t s) {
   const HostLevel& l0 = P->lev[0];
   LevelView<double> L = level_view<double>(l0);
   dim3 grid((unsigned)l0.tiles.size(), (unsigned)std::min(P->nz, ZSPLIT));
   const double n3 = (double)P->n3;
   {
     // algorithmic bytes: read f and p, write r (mode 0); read p, write A p (1); read f (2)
-    LaunchScope ls(P, K_FIELD3D, (mode == 0 ? 24.0 : mode == 1 ? 16.0 : 8.0) * n3,
-                   (mode == 0 ? 23.0 : mode == 1 ? 14.0 : 7.0) * n3, s);
-    k_field3d<<<grid, TILE_THREADS, 0, s>>>(L, P->d_cz, P->nz, P->kind == KIND_PP, mode, f, p, r, fshift, P->d_partial);
+    const double fl = mode == 0 ? 19.0 + (need_f2 ? 2.0 : 0.0) + (need_vp ? 3.0 : 0.0) : mode == 1 ? 14.0 : 7.0;
+    LaunchScope ls(P, K_FIELD3D, (mode == 0 ? 24.0 : mode == 1 ? 16.0 : 8.0) * n3, fl * n3, s);
+    if (mode == 1) field3d_t<1, false, false>(L, grid, P, f, p, r, fshift, s);
+    else if (mode == 2) field3d_t<2, false, false>(L, grid, P, f, p, r, fshift, s);
+    else if (need_f2 && need_vp) field3d_t<0, true, true>(L, grid, P, f, p, r, fshift, s);
+    else if (need_f2) field3d_t<0, true, false>(L, grid, P, f, p, r, fshift, s);
+    else if (need_vp) field3d_t<0, false, true>(L, grid, P, f, p, r, fshift, s);
+    else field3d_t<0, false, false>(L, grid, P, f, p, r, fshift, s);
   }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess || mode == 1) return e;
-  return launch_reduce_partials(P, (int)(grid.x * grid.y), s);
+  return launch_reduce_partials(P, (int)(grid.x * grid.y), P->d_sums, s);
 }
 
-cudaError_t launch_reduce_partials(snac_plan* P, int npart, cudaStream_t s) {
+cudaError_t launch_reduce_partials(snac_plan* P, int npart, double* out, cudaStream_t s) {
   LaunchScope ls(P, K_REDUCE, 32.0 * npart, 4.0 * npart, s);
-  k_reduce4<<<1, 1024, 0, s>>>(P->d_partial, npart, P->d_sums);
+  k_reduce4<<<1, 1024, 0, s>>>(P->d_partial, npart, out);
   return cudaGetLastError();
 }
 
 cudaError_t launch_fix_mean(snac_plan* P, void* u0, cudaStream_t s) {
   const double alpha = P->dz * P->nz / P->theta;
-  const double nc = (double)P->lev[0].ncell;
-  LaunchScope ls(P, K_FIX_MEAN, nc * (8.0 + 2.0 * plan_inner_size(P)), 3.0 * nc, s);
-  if (P->precision == SNAC_FP64)
-    k_fix_mean<double><<<1, 1024, 0, s>>>((double*)u0, P->d_area0, P->lev[0].ncell, P->d_sums, alpha, P->area_total);
-  else
-    k_fix_mean<float><<<1, 1024, 0, s>>>((float*)u0, P->d_area0, P->lev[0].ncell, P->d_sums, alpha, P->area_total);
+  const long long n = P->lev[0].ncell;
+  const int w = plan_inner_size(P);
+  const int ctas = std::min(MEAN_CTAS, P->npartial);  // one partial per CTA, d_partial holds npartial
+  {
+    LaunchScope ls(P, K_FIX_MEAN, (double)n * (8.0 + w), 2.0 * n, s);
+    if (w == 8) k_area_dot<double><<<ctas, 256, 0, s>>>((const double*)u0, P->d_area0, n, P->d_partial);
+    else k_area_dot<float><<<ctas, 256, 0, s>>>((const float*)u0, P->d_area0, n, P->d_partial);
+  }
+  cudaError_t e = launch_reduce_partials(P, ctas, P->d_sums + 4, s);
+  if (e != cudaSuccess) return e;
+  LaunchScope ls(P, K_FIX_MEAN, 2.0 * n * w, (double)n, s);
+  if (w == 8) k_fix_apply<double><<<MEAN_CTAS, 256, 0, s>>>((double*)u0, n, P->d_sums, alpha, P->area_total);
+  else k_fix_apply<float><<<MEAN_CTAS, 256, 0, s>>>((float*)u0, n, P->d_sums, alpha, P->area_total);
   return cudaGetLastError();
 }
 

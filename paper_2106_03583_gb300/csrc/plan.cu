@@ -501,7 +501,8 @@ int create(snac_plan** out, int32_t nblocks, const snac_block* blocks, int32_t h
     P->max_outer = opt->max_outer;
     P->max_cycles = opt->max_cycles;
     P->max_coarse = opt->max_coarse;
-    if ((P->precision != SNAC_FP64 && P->precision != SNAC_MIXED) || P->nu1 < 0 || P->nu2 < 0 ||
+    P->inner_reduction = opt->inner_reduction;
+    if (!(P->inner_reduction > 0.0 && P->inner_reduction < 1.0) || (P->precision != SNAC_FP64 && P->precision != SNAC_MIXED) || P->nu1 < 0 || P->nu2 < 0 ||
         P->nu1 + P->nu2 < 1 || P->nu1 > 16 || P->nu2 > 16 || P->max_outer < 1 || P->max_cycles < 1 ||
         P->max_coarse < 1 || P->max_coarse > MAX_COARSE) {
       delete P;
@@ -586,7 +587,8 @@ int create(snac_plan** out, int32_t nblocks, const snac_block* blocks, int32_t h
     }
     if ((st = dmalloc(P, &P->d_r3, (size_t)P->n3))) break;
     const int zsplit = std::min(P->nz, 16);
-    P->npartial = (int)P->lev[0].tiles.size() * zsplit;
+    // per-CTA partial sums: the 3-D residual grid (tiles x z split) or a plane reduction (MEAN_CTAS)
+    P->npartial = std::max((int)P->lev[0].tiles.size() * zsplit, MEAN_CTAS);
     if ((st = dmalloc(P, &P->d_partial, (size_t)P->npartial * 4))) break;
     if ((st = dmalloc(P, &P->d_sums, 8))) break;
     if ((st = dmalloc(P, &P->d_mode_part, (size_t)P->nz * P->lev[0].tiles.size()))) break;

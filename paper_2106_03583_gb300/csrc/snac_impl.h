@@ -28,6 +28,7 @@ constexpr int TILE_Y = 8;
 constexpr int TILE_THREADS = TILE_X * TILE_Y;
 constexpr int MAX_NZ = 1024;
 constexpr int MAX_COARSE = 256;
+constexpr int MEAN_CTAS = 2 * 152;  // CTAs of the grid-stride reductions over one mode plane
 
 // Faces are numbered W, E, S, N = 0..3 (x lower, x upper, y lower, y upper).
 struct BlockDev {
@@ -131,6 +132,7 @@ struct snac_plan {
   int device = 0;
   int precision = SNAC_FP64;
   int nu1 = 2, nu2 = 2, max_outer = 20, max_cycles = 40, max_coarse = 64;
+  double inner_reduction = 1e-3;
   int nblk = 0;
   int nz = 0;
   double dz = 0.0;
@@ -190,13 +192,13 @@ struct snac_plan {
 namespace snac {
 
 // ---- launchers (field kernels: 3-D FP64 residual and reductions) ----
-// mode 0: r = (f - fshift) - A p; sums = {||r||^2, ||f - fshift||^2, sum V p}
+// mode 0: r = (f - fshift) - A p; d_sums = {||r||^2, ||f - fshift||^2 if need_f2, sum V p if need_vp}
 // mode 1: r = A p
-// mode 2: sums = {sum V f, sum V |f|, ||f||^2}  (p, r unused)
+// mode 2: d_sums = {sum V f, sum V |f|, ||f||^2}  (p, r unused)
 cudaError_t launch_field3d(snac_plan* P, int mode, const double* f, const double* p, double* r, double fshift,
-                           cudaStream_t s);
-// reduce d_partial[npart][4] into d_sums[4]
-cudaError_t launch_reduce_partials(snac_plan* P, int npart, cudaStream_t s);
+                           bool need_f2, bool need_vp, cudaStream_t s);
+// reduce d_partial[npart][4] into out[4] (device)
+cudaError_t launch_reduce_partials(snac_plan* P, int npart, double* out, cudaStream_t s);
 // make the update of the singular mode 0 keep the volume-weighted mean of p at zero
 cudaError_t launch_fix_mean(snac_plan* P, void* u0, cudaStream_t s);
 // p -= c (c read from device d_c)

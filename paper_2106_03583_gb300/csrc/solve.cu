@@ -113,7 +113,7 @@ int run_solve(snac_plan* P, const double* f, double* p, double tol, cudaStream_t
   double fshift = 0.0;
   int st;
   if (P->singular) {
-    CK(launch_field3d(P, 2, f, nullptr, nullptr, 0.0, s));
+    CK(launch_field3d(P, 2, f, nullptr, nullptr, 0.0, false, false, s));
     if ((st = read_sums(P, s))) return st;
     const double vf = P->h_sums[0], vaf = P->h_sums[1];
     if (!std::isfinite(vf) || !std::isfinite(vaf)) return SNAC_ERR_NONFINITE;
@@ -125,13 +125,15 @@ int run_solve(snac_plan* P, const double* f, double* p, double tol, cudaStream_t
     P->info.removed_mean = fshift;
   }
   const bool mixed = P->precision == SNAC_MIXED;
-  double prev_rel = INFINITY;
+  double prev_rel = INFINITY, fn = 0.0;
   bool updated = false;
   std::vector<int> cyc(P->nz);
   for (int k = 0;; ++k) {
-    CK(launch_field3d(P, 0, f, p, P->d_r3, fshift, s));
+    // ||f|| is needed once; sum V p only for singular problems (zero-mean update)
+    CK(launch_field3d(P, 0, f, p, P->d_r3, fshift, k == 0, P->singular, s));
     if ((st = read_sums(P, s))) return st;
-    const double rn = std::sqrt(P->h_sums[0]), fn = std::sqrt(P->h_sums[1]);
+    if (k == 0) fn = std::sqrt(P->h_sums[1]);
+    const double rn = std::sqrt(P->h_sums[0]);
     if (!std::isfinite(rn) || !std::isfinite(fn)) return SNAC_ERR_NONFINITE;
     P->info.rhs_norm = fn;
     P->info.outer_iters = k;
@@ -157,7 +159,7 @@ int run_solve(snac_plan* P, const double* f, double* p, double tol, cudaStream_t
     prev_rel = rel;
     // target of this defect-correction step
     double target = 0.5 * tol * fn;
-    if (mixed) target = std::max(target, 1e-4 * rn);
+    if (mixed) target = std::max(target, P->inner_reduction * rn);
     CK(launch_forward(P, P->d_r3, P->lev[0].d_f, s));
     if ((st = mode_solves(P, target, s, cyc.data()))) return st;
     for (int q = 0; q < P->nz; ++q) {
@@ -188,7 +190,7 @@ int snac_apply_operator(snac_plan* plan, const double* d_p, double* d_out, void*
   if (st) return st;
   if (!d_p || !d_out) return SNAC_ERR_INVALID_ARG;
   cudaStream_t s = (cudaStream_t)stream;
-  CK(launch_field3d(plan, 1, nullptr, d_p, d_out, 0.0, s));
+  CK(launch_field3d(plan, 1, nullptr, d_p, d_out, 0.0, false, false, s));
   CK(cudaStreamSynchronize(s));
   profile_resolve(plan);
   return SNAC_OK;
@@ -199,7 +201,7 @@ int snac_residual(snac_plan* plan, const double* d_rhs, const double* d_p, doubl
   if (st) return st;
   if (!d_rhs || !d_p || !d_r || !h_norms) return SNAC_ERR_INVALID_ARG;
   cudaStream_t s = (cudaStream_t)stream;
-  CK(launch_field3d(plan, 0, d_rhs, d_p, d_r, 0.0, s));
+  CK(launch_field3d(plan, 0, d_rhs, d_p, d_r, 0.0, true, false, s));
   if ((st = read_sums(plan, s))) return st;
   h_norms[0] = plan->h_sums[0];
   h_norms[1] = plan->h_sums[1];
