@@ -262,9 +262,17 @@ cudaError_t vcycle_t(snac_plan* P, int nact, cudaStream_t st) {
       }
   };
   for (int l = 0; l < L; ++l) {
-    smooth(l, P->nu1);
     const HostLevel& h = P->lev[l];
     const HostLevel& hc = P->lev[l + 1];
+    if (h.fused) {
+      // the coarse iterate of a fused level below starts at zero without being read; a per-colour
+      // level below reads it, so it is written as zero
+      const bool zero_coarse = l + 1 < L && !hc.fused;
+      cudaError_t e = launch_fused_down(P, l, nact, l > 0, zero_coarse, st);
+      if (e != cudaSuccess) return e;
+      continue;
+    }
+    smooth(l, P->nu1);
     dim3 g((unsigned)hc.tiles.size(), (unsigned)nact);
     const double cells = (double)h.ncell * nact;
     LaunchScope ls(P, K_RESTRICT, 2.5 * w * cells, (P->nu1 > 0 ? 7.5 : 15.0) * cells, st);
@@ -284,6 +292,11 @@ cudaError_t vcycle_t(snac_plan* P, int nact, cudaStream_t st) {
   for (int l = L - 1; l >= 0; --l) {
     const HostLevel& h = P->lev[l];
     const HostLevel& hc = P->lev[l + 1];
+    if (h.fused) {
+      cudaError_t e = launch_fused_up(P, l, nact, l == 0, st);
+      if (e != cudaSuccess) return e;
+      continue;
+    }
     dim3 g((unsigned)h.tiles.size(), (unsigned)nact);
     {
       const double cells = (double)h.ncell * nact;
@@ -298,6 +311,11 @@ cudaError_t vcycle_t(snac_plan* P, int nact, cudaStream_t st) {
 template <typename T>
 cudaError_t mode_norms_t(snac_plan* P, int nact, bool after_cycle, cudaStream_t st) {
   const HostLevel& h = P->lev[0];
+  if (after_cycle && h.fused) {  // the level-0 up kernel left one partial per fused tile
+    LaunchScope ls(P, K_MODE_REDUCE, 8.0 * h.ftiles.size() * nact, (double)h.ftiles.size() * nact, st);
+    k_mode_reduce<<<nact, 256, 0, st>>>(P->d_mode_part, (int)h.ftiles.size(), P->d_active, P->d_mode_norm2);
+    return cudaGetLastError();
+  }
   dim3 g((unsigned)h.tiles.size(), (unsigned)nact);
   const double cells = (double)h.ncell * nact;
   {

@@ -502,6 +502,7 @@ int create(snac_plan** out, int32_t nblocks, const snac_block* blocks, int32_t h
     P->max_cycles = opt->max_cycles;
     P->max_coarse = opt->max_coarse;
     P->inner_reduction = opt->inner_reduction;
+    P->fused = opt->fused;
     if (!(P->inner_reduction > 0.0 && P->inner_reduction < 1.0) || (P->precision != SNAC_FP64 && P->precision != SNAC_MIXED) || P->nu1 < 0 || P->nu2 < 0 ||
         P->nu1 + P->nu2 < 1 || P->nu1 > 16 || P->nu2 > 16 || P->max_outer < 1 || P->max_cycles < 1 ||
         P->max_coarse < 1 || P->max_coarse > MAX_COARSE) {
@@ -565,6 +566,25 @@ int create(snac_plan** out, int32_t nblocks, const snac_block* blocks, int32_t h
     for (int q = 0; q < P->nz; ++q) sm[q] = (P->singular && mode_lambda(P->kind, P->nz, q) == 0.0) ? 1 : 0;
     if ((st = upload(P, &P->d_singular_mode, sm))) break;
     if ((st = build_coarse(P))) break;
+    // fused FP32 tile kernels on the levels whose blocks all keep the halo inside their neighbours
+    const bool want_fused = P->fused == 1 || (P->fused < 0 && P->precision == SNAC_MIXED);
+    if (want_fused && P->nu1 <= 2 && P->nu2 <= 2) {
+      for (size_t l = 0; l + 1 < P->lev.size(); ++l) {
+        HostLevel& lv = P->lev[l];
+        bool ok = true;
+        for (const BlockDev& d : lv.blk) ok = ok && d.nx >= FUSED_MIN_BLOCK && d.ny >= FUSED_MIN_BLOCK;
+        if (!ok) continue;
+        lv.fused = true;
+        char* u2 = nullptr;
+        if ((st = dmalloc(P, &u2, (size_t)P->nz * lv.ncell * inner))) break;
+        lv.d_u2 = u2;
+        for (int b = 0; b < lv.nblk; ++b)
+          for (int y0 = 0; y0 < lv.blk[b].ny; y0 += FTILE_Y)
+            for (int x0 = 0; x0 < lv.blk[b].nx; x0 += FTILE_X) lv.ftiles.push_back({b, x0, y0, 0});
+        if ((st = upload(P, &lv.d_ftiles, lv.ftiles))) break;
+      }
+      if (st) break;
+    }
     if (P->precision == SNAC_FP64) {
       for (size_t l = 0; l + 1 < P->lev.size(); ++l)
         if ((st = dmalloc(P, &P->lev[l].d_invd, (size_t)P->nz * P->lev[l].ncell))) break;
@@ -591,6 +611,7 @@ int create(snac_plan** out, int32_t nblocks, const snac_block* blocks, int32_t h
     P->npartial = std::max((int)P->lev[0].tiles.size() * zsplit, MEAN_CTAS);
     if ((st = dmalloc(P, &P->d_partial, (size_t)P->npartial * 4))) break;
     if ((st = dmalloc(P, &P->d_sums, 8))) break;
+    // per-mode, per-tile partial sums (basic tiles; the fused tiles are fewer)
     if ((st = dmalloc(P, &P->d_mode_part, (size_t)P->nz * P->lev[0].tiles.size()))) break;
     if ((st = dmalloc(P, &P->d_mode_norm2, (size_t)P->nz))) break;
     if ((st = dmalloc(P, &P->d_active, (size_t)P->nz))) break;

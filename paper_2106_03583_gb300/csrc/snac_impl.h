@@ -29,6 +29,9 @@ constexpr int TILE_THREADS = TILE_X * TILE_Y;
 constexpr int MAX_NZ = 1024;
 constexpr int MAX_COARSE = 256;
 constexpr int MEAN_CTAS = 2 * 152;  // CTAs of the grid-stride reductions over one mode plane
+constexpr int FTILE_X = 64;         // tile of the fused FP32 multigrid kernels
+constexpr int FTILE_Y = 32;
+constexpr int FUSED_MIN_BLOCK = 16;  // fused kernels on levels whose blocks are all this wide
 
 // Faces are numbered W, E, S, N = 0..3 (x lower, x upper, y lower, y upper).
 struct BlockDev {
@@ -99,6 +102,10 @@ struct HostLevel {
   void* d_u = nullptr;  // mode-space iterate, n_z x ncell of the inner type
   void* d_f = nullptr;  // mode-space right-hand side
   double* d_invd = nullptr;  // FP64 plans, smoothed levels: 1 / (A_xy + sigma_q)_cc per mode and cell
+  bool fused = false;        // this level runs the fused tile kernels
+  void* d_u2 = nullptr;      // fused levels: second iterate buffer (the tiles read one, write the other)
+  std::vector<TileDev> ftiles;  // FTILE_X x FTILE_Y tiles (fused levels)
+  TileDev* d_ftiles = nullptr;
 };
 
 // A chunk of up to TCOLS consecutive columns (cells of one plane) of one block, for the transforms.
@@ -113,7 +120,7 @@ struct TwiddleOffsets {
 // Kernel kinds counted by the tracing facility.
 enum KernelKind {
   K_FIELD3D = 0, K_REDUCE, K_FIX_MEAN, K_SHIFT, K_FORWARD, K_BACKWARD, K_SMOOTH, K_RESTRICT, K_PROLONG,
-  K_COARSE, K_MODE_RESID, K_MODE_REDUCE, K_MODE_APPLY, K_COUNT
+  K_COARSE, K_MODE_RESID, K_MODE_REDUCE, K_MODE_APPLY, K_FDOWN, K_FUP, K_COUNT
 };
 
 struct KernelStat {
@@ -133,6 +140,7 @@ struct snac_plan {
   int precision = SNAC_FP64;
   int nu1 = 2, nu2 = 2, max_outer = 20, max_cycles = 40, max_coarse = 64;
   double inner_reduction = 1e-3;
+  int fused = -1;
   int nblk = 0;
   int nz = 0;
   double dz = 0.0;
@@ -217,6 +225,11 @@ cudaError_t launch_vcycle(snac_plan* P, int nactive, cudaStream_t s);
 // per-mode ||f - A u||^2 at level 0 for the active modes -> d_mode_norm2[q]; after_cycle: u is the
 // result of a V-cycle (post-smoothing ended on black, so only red cells carry a residual)
 cudaError_t launch_mode_norms(snac_plan* P, int nactive, bool after_cycle, cudaStream_t s);
+
+// fused FP32 levels: smoothing + residual + restriction (down), prolongation + smoothing (+ level-0
+// residual norm partials into d_mode_part) (up)
+cudaError_t launch_fused_down(snac_plan* P, int l, int nact, bool zero_u, bool zero_coarse, cudaStream_t s);
+cudaError_t launch_fused_up(snac_plan* P, int l, int nact, bool norms, cudaStream_t s);
 
 int plan_inner_size(const snac_plan* P);  // bytes of the inner type
 

@@ -47,7 +47,7 @@ class _Block(ctypes.Structure):
 class _Options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("nu1", ctypes.c_int32), ("nu2", ctypes.c_int32),
                 ("max_outer", ctypes.c_int32), ("max_cycles", ctypes.c_int32), ("max_coarse", ctypes.c_int32),
-                ("inner_reduction", ctypes.c_double)]
+                ("fused", ctypes.c_int32), ("inner_reduction", ctypes.c_double)]
 
 
 class _KStat(ctypes.Structure):
@@ -150,7 +150,8 @@ class Plan:
     """A solver plan for one multi-block problem (``snac_plan_create``)."""
 
     def __init__(self, blocks, homog_axis: int = 2, precision: str = "fp64", nu1: int = 2, nu2: int = 2,
-                 max_outer: int = 20, max_cycles: int = 40, max_coarse: int = 64, inner_reduction: float = 1e-3):
+                 max_outer: int = 20, max_cycles: int = 40, max_coarse: int = 64, inner_reduction: float = 1e-3,
+                 fused: int = -1):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("snac.Plan needs a CUDA device")
@@ -162,7 +163,7 @@ class Plan:
         self.precision = precision
         self.inner_dtype = torch.float64 if precision == "fp64" else torch.float32
         arr, keep = _marshal_blocks(blocks)
-        opt = _Options(_PREC[precision], nu1, nu2, max_outer, max_cycles, max_coarse, inner_reduction)
+        opt = _Options(_PREC[precision], nu1, nu2, max_outer, max_cycles, max_coarse, fused, inner_reduction)
         h = ctypes.c_void_p()
         _check(lib().snac_plan_create(ctypes.byref(h), len(blocks), arr, homog_axis, ctypes.byref(opt)))
         del keep
