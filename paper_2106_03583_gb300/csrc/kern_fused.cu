@@ -1,311 +1,378 @@
-// Fused multigrid tile kernels for FP32 plans (the reduced equations of Eq. 9; Algorithm 1, second
-// loop). On GB300 the FP32 multigrid is bound by HBM traffic, so each level of a V-cycle runs as two
-// kernels that keep a tile of the plane in shared memory:
+// Fused multigrid tile kernels (the reduced equations of Eq. 9; Algorithm 1, second loop). On
+// GB300 the FP32 multigrid is bound by memory latency and instruction issue, so each level of a
+// V-cycle runs as two kernels that keep a tile of one mode's plane on chip:
 //
-//   k_fdown: load u, f on the tile plus a halo of FH cells -> nu1 red-black sweeps in shared memory
-//            -> write the tile's u -> residual on its red cells -> area-weighted restriction into the
-//            coarse right-hand side;
-//   k_fup:   load u, f on the tile plus halo and the coarse correction around it -> three-point
-//            prolongation and correction -> nu2 sweeps -> write the tile's u (on level 0 also the
+//   k_fdown: load u, f on a 52x52 tile plus a halo of FUSED_HALO = 6 cells (a 64x64 window) -> nu1
+//            red-black Gauss-Seidel sweeps -> store the tile's u -> residual on its red cells ->
+//            area-weighted restriction into the coarse right-hand side;
+//   k_fup:   load u, f on the window and the coarse correction around it -> three-point
+//            prolongation and correction -> nu2 sweeps -> store the tile's u (on level 0 also the
 //            per-mode sums of squared residuals).
 //
-// Each red-black half-sweep makes one more ring of the window stale, so after 2 nu half-sweeps the
-// tile plus one ring is exact when FH >= 2 nu + 1 (FH = 5 allows nu <= 2): the result equals the
-// global Gauss-Seidel sweep. Window cells outside the tile's block belong to the connected blocks
-// (a 3x3 table of regions built from the block connectivity, corners through either neighbour);
-// each window cell uses the coefficients of the block that owns it, so sweeps across block
-// interfaces are exact too. Cells with no owner (beyond a physical face, a re-entrant corner) stay 0
-// and are never coupled (their coupling coefficient is 0). The halo must fit inside the neighbouring
-// blocks: levels whose blocks are all at least 16 cells wide use these kernels.
+// A CTA starts with one copy of its tile's tables (FusedTab: coefficients, weights and the plane
+// offsets of every window row and column, built on the host), then one round of cell loads: no
+// chain of dependent loads through the block and neighbour descriptors.
+//
+// Registers. Warp w holds window rows 4w..4w+3, lane k holds columns 2k (parity 0) and 2k+1
+// (parity 1) of those rows: u, f and 1/diag of 8 cells per thread. In a row the cells of one colour
+// all have the same column parity, so a colour update of a row is one cell per lane: the west/east
+// neighbours come from the thread itself or from one warp shuffle, the south/north neighbours from
+// the thread's own registers; only the first and last row of each strip pass through shared memory
+// (once per half-sweep). Coarse cells are exactly (row pair) x (column pair): restriction and
+// prolongation stay in registers too.
+//
+// Exactness. Every interior window cell is updated in every half-sweep; the window's edge is never
+// updated, so stale values enter from the edge one cell per half-sweep. After 2 nu <= FUSED_HALO - 2
+// half-sweeps the tile and the ring around it (used by the residual) equal the global Gauss-Seidel
+// sweep. Window cells outside the tile's block belong to the connected blocks and use that block's
+// coefficients, so sweeps across block interfaces are exact too. Cells with no owner (beyond a
+// physical face, a re-entrant corner, or past the clipped window of a ragged tile) carry f = 0 and
+// a zero inverse diagonal, so they stay 0; their coupling coefficients are 0. The halo must fit in
+// the neighbouring blocks: levels whose blocks are all at least FUSED_MIN_BLOCK cells wide.
+//
+// Each tile reads one iterate buffer and writes the other (neighbouring CTAs store their smoothed
+// tiles while this one may still be loading its halo).
+#include "fused_tab.h"
 #include "kern_common.cuh"
 #include "snac_impl.h"
 
 namespace snac {
 namespace {
 
-constexpr int FH = 5;
-constexpr int WX = FTILE_X + 2 * FH, WY = FTILE_Y + 2 * FH;  // window
-constexpr int CWX = FTILE_X / 2 + 8, CWY = FTILE_Y / 2 + 8;  // coarse window (parents +- 1 ring)
-constexpr int FTHREADS = 256;
-
-struct Regions {
-  int blk[3][3];  // [ry][rx], ry/rx = 0 (south/west), 1 (the tile's block), 2 (north/east); -1: none
-};
-
-__device__ __forceinline__ int nbr_of(const BlockDev* blk, int b, int f) { return b < 0 ? -1 : blk[b].nbr[f]; }
-
-__device__ void build_regions(const BlockDev* __restrict__ blk, int b, Regions& R) {
-  const BlockDev& B = blk[b];
-  const int W = B.nbr[0], E = B.nbr[1], S = B.nbr[2], N = B.nbr[3];
-  R.blk[1][1] = b;
-  R.blk[1][0] = W;
-  R.blk[1][2] = E;
-  R.blk[0][1] = S;
-  R.blk[2][1] = N;
-  int sw = nbr_of(blk, W, 2);
-  if (sw < 0) sw = nbr_of(blk, S, 0);
-  int se = nbr_of(blk, E, 2);
-  if (se < 0) se = nbr_of(blk, S, 1);
-  int nw = nbr_of(blk, W, 3);
-  if (nw < 0) nw = nbr_of(blk, N, 0);
-  int ne = nbr_of(blk, E, 3);
-  if (ne < 0) ne = nbr_of(blk, N, 1);
-  R.blk[0][0] = sw;
-  R.blk[0][2] = se;
-  R.blk[2][0] = nw;
-  R.blk[2][2] = ne;
-}
-
-// Region index of a block-local coordinate along one axis, and the coordinate inside that region's
-// block (n = the tile block's extent, nr = the region block's extent).
-__device__ __forceinline__ int region_of(int i, int n) { return i < 0 ? 0 : (i >= n ? 2 : 1); }
-__device__ __forceinline__ int local_in(int i, int r, int n, int nr) { return r == 0 ? i + nr : (r == 2 ? i - n : i); }
+constexpr int FH = FUSED_HALO;
+constexpr int WN = FWN;
+constexpr int HW = FHW;
+constexpr int CW = FCW;
+constexpr int RPW = 4;  // rows per warp
+constexpr int FTHREADS = 512;
+constexpr int FWARPS = FTHREADS / 32;
+static_assert(FTILE_X == FTILE_Y && HW == 32 && FWARPS * RPW == WN, "the fused kernels assume a 64x64 window");
+static_assert(FH % 2 == 0 && 2 * 2 <= FH - 2, "nu <= 2 sweeps must stay exact inside the halo");
 
 template <typename T>
 struct Shared {
-  T u[WY][WX];
-  T f[WY][WX];
-  Coef<T> xc[3][WX];  // x-pieces of window column wi in region row ry
-  Coef<T> yc[3][WY];  // y-pieces of window row wj in region column rx
-  PW<T> px[3][WX];
-  PW<T> py[3][WY];
-  T e[CWY][CWX];
-  Regions R;
-  double wsum[FTHREADS / 32];
+  FusedTab<T> tab;
+  T halo[2][FWARPS][2][2][HW];  // [buffer][warp][first/last row][parity][lane]
+  T e[CW][CW];                  // coarse correction around the tile (k_fup)
+  double wsum[FWARPS];
 };
 
-// Per-CTA set-up: regions, coefficient (and prolongation weight) tables, window of u and f.
-template <typename T, bool PROLONG>
-__device__ void load_window(Shared<T>& S, const LevelView<T>& F, const TileDev& t, int tw, int th, long long base,
-                            const T* __restrict__ u, const T* __restrict__ f, bool zero_u) {
-  // u is never the buffer the same launch writes: neighbouring CTAs store their smoothed tiles while
-  // this one may still be loading its halo (the caller alternates two iterate buffers)
-  if (threadIdx.x == 0) build_regions(F.blk, t.b, S.R);
+// Per-thread state: rows RPW w .. RPW w + RPW - 1 of window columns 2k, 2k+1.
+template <typename T>
+struct Cells {
+  T u[RPW][2], f[RPW][2], inv[RPW][2];
+};
+
+// Copy the tile's tables into shared memory (16-byte words).
+template <typename T>
+__device__ __forceinline__ void copy_tab(Shared<T>& S, const FusedTab<T>* __restrict__ tab) {
+  static_assert(sizeof(FusedTab<T>) % 16 == 0, "FusedTab is copied in 16-byte words");
+  const uint4* src = reinterpret_cast<const uint4*>(tab);
+  uint4* dst = reinterpret_cast<uint4*>(&S.tab);
+  for (int i = threadIdx.x; i < (int)(sizeof(FusedTab<T>) / 16); i += FTHREADS) dst[i] = src[i];
+}
+
+// The thread's 2 RPW cells of u (unless zero), f and 1/diag.
+template <typename T>
+__device__ __forceinline__ void load_cells(Cells<T>& C, const FusedTab<T>& tb, long long base, const T* __restrict__ u,
+                                           const T* __restrict__ f, bool zero_u, T sg) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int col = tb.col[lane], rx = tb.colrx[lane];
+#pragma unroll
+  for (int r = 0; r < RPW; ++r) {
+    const int wj = RPW * warp + r;
+    const int ro = tb.rowoff[rx][wj];
+    T u0 = 0, u1 = 0, f0 = 0, f1 = 0, i0 = 0, i1 = 0;
+    if (col != FUSED_NONE && ro != FUSED_NONE) {
+      const long long a = base + ro + col;  // even: block sizes and offsets are even
+      if (!zero_u) {
+        u0 = u[a];
+        u1 = u[a + 1];
+      }
+      f0 = f[a];
+      f1 = f[a + 1];
+      const int ry = tb.rowry[wj];
+      const T yd = tb.yd[rx][wj] + sg;
+      i0 = (T)1 / (tb.xd[ry][0][lane] + yd);
+      i1 = (T)1 / (tb.xd[ry][1][lane] + yd);
+    }
+    C.u[r][0] = u0;
+    C.u[r][1] = u1;
+    C.f[r][0] = f0;
+    C.f[r][1] = f1;
+    C.inv[r][0] = i0;
+    C.inv[r][1] = i1;
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ void write_halo(Shared<T>& S, const Cells<T>& C, int buf) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  S.halo[buf][warp][0][0][lane] = C.u[0][0];
+  S.halo[buf][warp][0][1][lane] = C.u[0][1];
+  S.halo[buf][warp][1][0][lane] = C.u[RPW - 1][0];
+  S.halo[buf][warp][1][1][lane] = C.u[RPW - 1][1];
+}
+
+template <typename T>
+__device__ __forceinline__ void read_edges(const Shared<T>& S, int buf, T (&sedge)[2], T (&nedge)[2]) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int p = 0; p < 2; ++p) {
+    sedge[p] = warp > 0 ? S.halo[buf][warp - 1][1][p][lane] : (T)0;
+    nedge[p] = warp < FWARPS - 1 ? S.halo[buf][warp + 1][0][p][lane] : (T)0;
+  }
+}
+
+// Gauss-Seidel update of row r of the strip, the colour's cells having column parity P.
+template <typename T, int P>
+__device__ __forceinline__ void update_row(Cells<T>& C, const FusedTab<T>& tb, int r, int wj, int ry, int rx, T sn,
+                                           T nn) {
+  const int lane = threadIdx.x & 31;
+  T w, e;
+  if (P == 0) {
+    w = __shfl_up_sync(0xffffffffu, C.u[r][1], 1);
+    e = C.u[r][1];
+  } else {
+    w = C.u[r][0];
+    e = __shfl_down_sync(0xffffffffu, C.u[r][0], 1);
+  }
+  const FP2<T> cx = tb.xc[ry][P][lane];
+  const FP2<T> cy = tb.yc[rx][wj];
+  T a = cx.a * w;
+  a = fma(cx.b, e, a);
+  a = fma(cy.a, sn, a);
+  a = fma(cy.b, nn, a);
+  const T v = (C.f[r][P] - a) * C.inv[r][P];
+  const bool edge = (P == 0 && lane == 0) || (P == 1 && lane == HW - 1) || wj == 0 || wj == WN - 1;
+  if (!edge) C.u[r][P] = v;
+}
+
+// One half-sweep of the strip; P0 = column parity of the colour in the strip's first row.
+template <typename T, int P0>
+__device__ __forceinline__ void half_sweep(Cells<T>& C, const FusedTab<T>& tb, const int (&ry)[RPW], int rx,
+                                           const T (&sedge)[2], const T (&nedge)[2]) {
+  const int warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int r = 0; r < RPW; ++r) {
+    const int wj = RPW * warp + r;
+    constexpr int PA = P0, PB = P0 ^ 1;
+    if ((r & 1) == 0) {
+      const T sn = r > 0 ? C.u[r > 0 ? r - 1 : 0][PA] : sedge[PA];
+      const T nn = r < RPW - 1 ? C.u[r < RPW - 1 ? r + 1 : 0][PA] : nedge[PA];
+      update_row<T, PA>(C, tb, r, wj, ry[r], rx, sn, nn);
+    } else {
+      const T sn = r > 0 ? C.u[r > 0 ? r - 1 : 0][PB] : sedge[PB];
+      const T nn = r < RPW - 1 ? C.u[r < RPW - 1 ? r + 1 : 0][PB] : nedge[PB];
+      update_row<T, PB>(C, tb, r, wj, ry[r], rx, sn, nn);
+    }
+  }
+}
+
+// nu red-black sweeps of the whole window. On return the strip-edge rows of the final state are in
+// S.halo[buf] (for the residuals that follow).
+template <typename T>
+__device__ void sweeps(Cells<T>& C, Shared<T>& S, int nu, int& buf) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int ry[RPW];
+#pragma unroll
+  for (int r = 0; r < RPW; ++r) ry[r] = S.tab.rowry[RPW * warp + r];
+  const int rx = S.tab.colrx[lane];
+  const int pbase = S.tab.pbase;
+  buf = 0;
+  write_halo(S, C, buf);
   __syncthreads();
-  const BlockDev& B = F.blk[t.b];
-  const int x0 = t.x0 - FH, y0 = t.y0 - FH;
-  for (int idx = threadIdx.x; idx < 3 * WX; idx += blockDim.x) {
-    const int ry = idx / WX, wi = idx % WX;
-    const int i = x0 + wi, rx = region_of(i, B.nx);
-    const int rb = S.R.blk[ry][rx];
-    Coef<T> c{0, 0, -1, 1};
-    PW<T> w{0, 0};
-    if (rb >= 0 && wi < tw + 2 * FH) {
-      const BlockDev& RB = F.blk[rb];
-      const int ii = local_in(i, rx, B.nx, RB.nx);
-      if (ii >= 0 && ii < RB.nx) {
-        c = F.cx[RB.xo + ii];
-        if (PROLONG) w = F.px[RB.xo + ii];
-      }
-    }
-    S.xc[ry][wi] = c;
-    if (PROLONG) S.px[ry][wi] = w;
-  }
-  for (int idx = threadIdx.x; idx < 3 * WY; idx += blockDim.x) {
-    const int rx = idx / WY, wj = idx % WY;
-    const int j = y0 + wj, ry = region_of(j, B.ny);
-    const int rb = S.R.blk[ry][rx];
-    Coef<T> c{0, 0, -1, 1};
-    PW<T> w{0, 0};
-    if (rb >= 0 && wj < th + 2 * FH) {
-      const BlockDev& RB = F.blk[rb];
-      const int jj = local_in(j, ry, B.ny, RB.ny);
-      if (jj >= 0 && jj < RB.ny) {
-        c = F.cy[RB.yo + jj];
-        if (PROLONG) w = F.py[RB.yo + jj];
-      }
-    }
-    S.yc[rx][wj] = c;
-    if (PROLONG) S.py[rx][wj] = w;
-  }
-  for (int idx = threadIdx.x; idx < WX * WY; idx += blockDim.x) {
-    const int wj = idx / WX, wi = idx % WX;
-    T uv = 0, fv = 0;
-    if (wi < tw + 2 * FH && wj < th + 2 * FH) {
-      const int i = x0 + wi, j = y0 + wj;
-      const int rx = region_of(i, B.nx), ry = region_of(j, B.ny);
-      const int rb = S.R.blk[ry][rx];
-      if (rb >= 0) {
-        const BlockDev& RB = F.blk[rb];
-        const int ii = local_in(i, rx, B.nx, RB.nx), jj = local_in(j, ry, B.ny, RB.ny);
-        if (ii >= 0 && ii < RB.nx && jj >= 0 && jj < RB.ny) {
-          const long long a = base + RB.off + (long long)jj * RB.nx + ii;
-          if (!zero_u) uv = u[a];
-          fv = f[a];
-        }
-      }
-    }
-    S.u[wj][wi] = uv;
-    S.f[wj][wi] = fv;
-  }
-}
-
-// Is window cell (wi, wj) owned by a block (inside the clipped window)?
-template <typename T>
-__device__ __forceinline__ bool owned(const Shared<T>& S, const BlockDev& B, int x0w, int y0w, int wi, int wj, int tw,
-                                      int th) {
-  if (wi >= tw + 2 * FH || wj >= th + 2 * FH) return false;
-  const int rx = region_of(x0w + wi, B.nx), ry = region_of(y0w + wj, B.ny);
-  return S.R.blk[ry][rx] >= 0;
-}
-
-// nu red-black Gauss-Seidel sweeps on the window; half-sweep s updates the ring-s-shrunk window.
-template <typename T>
-__device__ void sweeps(Shared<T>& S, const BlockDev& B, int tx0, int ty0, int tw, int th, T sg, int nu) {
-  const int x0w = tx0 - FH, y0w = ty0 - FH;
-  for (int s = 1; s <= 2 * nu; ++s) {
-    const int colour = (s - 1) & 1;
-    const int wx1 = tw + 2 * FH - s, wy1 = th + 2 * FH - s;  // exclusive upper bounds
-    const int rows = wy1 - s, half = (wx1 - s + 1) / 2;
-    for (int idx = threadIdx.x; idx < rows * half; idx += blockDim.x) {
-      const int wj = s + idx / half;
-      const int k = idx - (idx / half) * half;
-      const int base = B.par + x0w + y0w + wj;
-      const int wi = s + 2 * k + ((colour - base - s) & 1);
-      if (wi >= wx1) continue;
-      const int rx = region_of(x0w + wi, B.nx), ry = region_of(y0w + wj, B.ny);
-      if (S.R.blk[ry][rx] < 0) continue;
-      const Coef<T> cx = S.xc[ry][wi], cy = S.yc[rx][wj];
-      T a = cx.lo * S.u[wj][wi - 1];
-      a = fma(cx.hi, S.u[wj][wi + 1], a);
-      a = fma(cy.lo, S.u[wj - 1][wi], a);
-      a = fma(cy.hi, S.u[wj + 1][wi], a);
-      S.u[wj][wi] = (S.f[wj][wi] - a) / (cx.d + cy.d + sg);
-    }
+  for (int s = 0; s < 2 * nu; ++s) {
+    const int colour = s & 1;
+    T sedge[2], nedge[2];
+    read_edges(S, buf, sedge, nedge);
+    const int p0 = (colour - pbase - RPW * warp) & 1;
+    if (p0 == 0) half_sweep<T, 0>(C, S.tab, ry, rx, sedge, nedge);
+    else half_sweep<T, 1>(C, S.tab, ry, rx, sedge, nedge);
+    buf ^= 1;
+    write_halo(S, C, buf);
     __syncthreads();
   }
 }
 
-// Residual of window cell (wi, wj) of the tile's own block.
-template <typename T>
-__device__ __forceinline__ T resid_at(const Shared<T>& S, int wi, int wj, T sg) {
-  const Coef<T> cx = S.xc[1][wi], cy = S.yc[1][wj];
-  T a = cx.lo * S.u[wj][wi - 1];
-  a = fma(cx.hi, S.u[wj][wi + 1], a);
-  a = fma(cy.lo, S.u[wj - 1][wi], a);
-  a = fma(cy.hi, S.u[wj + 1][wi], a);
-  a = fma(cx.d + cy.d + sg, S.u[wj][wi], a);
-  return S.f[wj][wi] - a;
+// Residual of the cell of parity P in row r (the tile block's own coefficients: tile rows only).
+template <typename T, int P>
+__device__ __forceinline__ T resid_row(const Cells<T>& C, const FusedTab<T>& tb, int r, int wj, T sn, T nn, T sg) {
+  const int lane = threadIdx.x & 31;
+  T w, e;
+  if (P == 0) {
+    w = __shfl_up_sync(0xffffffffu, C.u[r][1], 1);
+    e = C.u[r][1];
+  } else {
+    w = C.u[r][0];
+    e = __shfl_down_sync(0xffffffffu, C.u[r][0], 1);
+  }
+  const FP2<T> cx = tb.xc[1][P][lane];
+  const FP2<T> cy = tb.yc[1][wj];
+  T a = cx.a * w;
+  a = fma(cx.b, e, a);
+  a = fma(cy.a, sn, a);
+  a = fma(cy.b, nn, a);
+  a = fma(tb.xd[1][P][lane] + tb.yd[1][wj] + sg, C.u[r][P], a);
+  return C.f[r][P] - a;
 }
 
-template <typename T>
-__device__ void store_tile(const Shared<T>& S, const BlockDev& B, const TileDev& t, int tw, int th, long long base,
-                           T* __restrict__ u) {
-  for (int idx = threadIdx.x; idx < FTILE_X * FTILE_Y; idx += blockDim.x) {
-    const int ti = idx % FTILE_X, tj = idx / FTILE_X;
-    if (ti < tw && tj < th) u[base + B.off + (long long)(t.y0 + tj) * B.nx + t.x0 + ti] = S.u[tj + FH][ti + FH];
+// rr[r] = residual of the red cell of row r (the black cells carry none after a sweep ending on
+// black); P0 = column parity of the red cells in the strip's first row.
+template <typename T, int P0>
+__device__ __forceinline__ void red_residuals(const Cells<T>& C, const FusedTab<T>& tb, const T (&sedge)[2],
+                                              const T (&nedge)[2], T sg, T (&rr)[RPW]) {
+  const int warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int r = 0; r < RPW; ++r) {
+    const int wj = RPW * warp + r;
+    constexpr int PA = P0, PB = P0 ^ 1;
+    if ((r & 1) == 0) {
+      const T sn = r > 0 ? C.u[r > 0 ? r - 1 : 0][PA] : sedge[PA];
+      const T nn = r < RPW - 1 ? C.u[r < RPW - 1 ? r + 1 : 0][PA] : nedge[PA];
+      rr[r] = resid_row<T, PA>(C, tb, r, wj, sn, nn, sg);
+    } else {
+      const T sn = r > 0 ? C.u[r > 0 ? r - 1 : 0][PB] : sedge[PB];
+      const T nn = r < RPW - 1 ? C.u[r < RPW - 1 ? r + 1 : 0][PB] : nedge[PB];
+      rr[r] = resid_row<T, PB>(C, tb, r, wj, sn, nn, sg);
+    }
   }
 }
 
+// Red residuals of the strip; returns the column parity of the red cells in its first row.
 template <typename T>
-__global__ void __launch_bounds__(FTHREADS) k_fdown(LevelView<T> F, LevelView<T> C, const TileDev* __restrict__ ftiles,
-                                                     const int* __restrict__ active, const T* __restrict__ sigma,
-                                                     const T* __restrict__ u, T* __restrict__ u_out,
-                                                     const T* __restrict__ f, T* __restrict__ fc,
-                                                     T* __restrict__ uc, int nu, int zero_u, int zero_coarse) {
+__device__ __forceinline__ int strip_residuals(const Cells<T>& C, const Shared<T>& S, int buf, T sg, T (&rr)[RPW]) {
+  const int warp = threadIdx.x >> 5;
+  T sedge[2], nedge[2];
+  read_edges(S, buf, sedge, nedge);
+  const int p0 = (0 - S.tab.pbase - RPW * warp) & 1;
+  if (p0 == 0) red_residuals<T, 0>(C, S.tab, sedge, nedge, sg, rr);
+  else red_residuals<T, 1>(C, S.tab, sedge, nedge, sg, rr);
+  return p0;
+}
+
+__device__ __forceinline__ bool in_tile(int w, int extent) { return w >= FH && w < FH + extent; }
+
+// Store the tile's u (window rows/columns FH .. FH + extent; region 1 is the tile's own block).
+template <typename T>
+__device__ __forceinline__ void store_tile(const Cells<T>& C, const FusedTab<T>& tb, long long base, T* __restrict__ u) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (!in_tile(2 * lane, tb.tw)) return;
+  const int col = tb.col[lane];
+#pragma unroll
+  for (int r = 0; r < RPW; ++r) {
+    const int wj = RPW * warp + r;
+    if (!in_tile(wj, tb.th)) continue;
+    const long long a = base + tb.rowoff[1][wj] + col;
+    u[a] = C.u[r][0];
+    u[a + 1] = C.u[r][1];
+  }
+}
+
+// One CTA per (fused tile, active mode).
+template <typename T>
+__global__ void __launch_bounds__(FTHREADS, 2)
+    k_fdown(const FusedTab<T>* __restrict__ tabs, long long fncell, long long cncell, const int* __restrict__ active,
+            const T* __restrict__ sigma, const T* __restrict__ u, T* __restrict__ u_out, const T* __restrict__ f,
+            T* __restrict__ fc, T* __restrict__ uc, int nu, int zero_u, int zero_coarse) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Shared<T>& S = *reinterpret_cast<Shared<T>*>(smem_raw);
-  const TileDev t = ftiles[blockIdx.x];
   const int q = active[blockIdx.y];
-  const BlockDev B = F.blk[t.b];
-  const int tw = min(FTILE_X, B.nx - t.x0), th = min(FTILE_Y, B.ny - t.y0);
-  const long long base = (long long)q * F.ncell;
+  copy_tab(S, tabs + blockIdx.x);
   const T sg = sigma[q];
-  load_window<T, false>(S, F, t, tw, th, base, u, f, zero_u != 0);
   __syncthreads();
-  sweeps(S, B, t.x0, t.y0, tw, th, sg, nu);
-  store_tile(S, B, t, tw, th, base, u_out);
-  // restriction of the residual: after a sweep ending on black only red children carry one
-  const BlockDev Bc = C.blk[t.b];
-  const long long cbase = (long long)q * C.ncell;
-  const int cw = (tw + 1) / 2, ch = (th + 1) / 2;
-  for (int idx = threadIdx.x; idx < cw * ch; idx += blockDim.x) {
-    const int ci = idx % cw, cj = idx / cw;
-    const int I = t.x0 / 2 + ci, J = t.y0 / 2 + cj;
-    if (I >= Bc.nx || J >= Bc.ny) continue;
-    T acc = 0;
+  const FusedTab<T>& tb = S.tab;
+  const long long base = (long long)q * fncell;
+  Cells<T> C;
+  load_cells(C, tb, base, u, f, zero_u != 0, sg);
+  int buf;
+  sweeps(C, S, nu, buf);
+  store_tile(C, tb, base, u_out);
+  // restriction: coarse cell = (column pair k, row pair (2h, 2h+1)) of the strip; its red children
+  // are one per row, the black ones carry no residual after the sweep
+  T rr[RPW];
+  const int p0 = strip_residuals(C, S, buf, sg, rr);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (!in_tile(2 * lane, tb.tw)) return;
+  const long long cbase = (long long)q * cncell + tb.cout0 + lane;
+  const T wx[2] = {tb.rx[0][lane], tb.rx[1][lane]};
 #pragma unroll
-    for (int dj = 0; dj < 2; ++dj)
-#pragma unroll
-      for (int di = 0; di < 2; ++di) {
-        const int i = 2 * I + di, j = 2 * J + dj;
-        if (nu > 0 && ((B.par + i + j) & 1)) continue;
-        const T r = resid_at(S, i - t.x0 + FH, j - t.y0 + FH, sg);
-        acc = fma(F.rx[B.xo + i] * F.ry[B.yo + j], r, acc);
-      }
-    const long long cc = cbase + Bc.off + (long long)J * Bc.nx + I;
+  for (int h = 0; h < RPW / 2; ++h) {
+    const int wj = RPW * warp + 2 * h;
+    if (!in_tile(wj, tb.th)) continue;
+    const T acc = fma(wx[p0 ^ 1] * tb.ry[wj + 1], rr[2 * h + 1], wx[p0] * tb.ry[wj] * rr[2 * h]);
+    const long long cc = cbase + (long long)(wj / 2) * tb.cnx;
     fc[cc] = acc;
     if (zero_coarse) uc[cc] = 0;
   }
 }
 
 template <typename T>
-__global__ void __launch_bounds__(FTHREADS) k_fup(LevelView<T> F, LevelView<T> C, const TileDev* __restrict__ ftiles,
-                                                   int nftiles, const int* __restrict__ active,
-                                                   const T* __restrict__ sigma, const T* __restrict__ u,
-                                                   T* __restrict__ u_out, const T* __restrict__ f,
-                                                   const T* __restrict__ uc, int nu, double* __restrict__ part) {
+__global__ void __launch_bounds__(FTHREADS, 2)
+    k_fup(const FusedTab<T>* __restrict__ tabs, int nftiles, long long fncell, long long cncell,
+          const int* __restrict__ active, const T* __restrict__ sigma, const T* __restrict__ u, T* __restrict__ u_out,
+          const T* __restrict__ f, const T* __restrict__ uc, int nu, double* __restrict__ part) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Shared<T>& S = *reinterpret_cast<Shared<T>*>(smem_raw);
-  const TileDev t = ftiles[blockIdx.x];
   const int q = active[blockIdx.y];
-  const BlockDev B = F.blk[t.b];
-  const int tw = min(FTILE_X, B.nx - t.x0), th = min(FTILE_Y, B.ny - t.y0);
-  const long long base = (long long)q * F.ncell;
+  copy_tab(S, tabs + blockIdx.x);
   const T sg = sigma[q];
-  load_window<T, true>(S, F, t, tw, th, base, u, f, false);
-  // coarse window: parents of the window cells and one more ring, in the coarse block's coordinates
-  const BlockDev Bc = C.blk[t.b];
-  const int cx0 = t.x0 / 2 - 4, cy0 = t.y0 / 2 - 4;
-  const long long cbase = (long long)q * C.ncell;
-  for (int idx = threadIdx.x; idx < CWX * CWY; idx += blockDim.x) {
-    const int cj = idx / CWX, ci = idx % CWX;
-    const int I = cx0 + ci, J = cy0 + cj;
-    const int rx = region_of(I, Bc.nx), ry = region_of(J, Bc.ny);
-    const int rb = S.R.blk[ry][rx];
-    T v = 0;
-    if (rb >= 0) {
-      const BlockDev& RB = C.blk[rb];
-      const int ii = local_in(I, rx, Bc.nx, RB.nx), jj = local_in(J, ry, Bc.ny, RB.ny);
-      if (ii >= 0 && ii < RB.nx && jj >= 0 && jj < RB.ny) v = uc[cbase + RB.off + (long long)jj * RB.nx + ii];
+  __syncthreads();
+  const FusedTab<T>& tb = S.tab;
+  const long long base = (long long)q * fncell;
+  const long long cbase = (long long)q * cncell;
+  // coarse window: parents of the window cells and one more ring
+  for (int idx = threadIdx.x; idx < CW * CW; idx += FTHREADS) {
+    const int cj = idx / CW, ci = idx % CW;
+    const int cc = tb.ccol[ci];
+    const int ro = tb.crowoff[tb.ccolrx[ci]][cj];
+    S.e[cj][ci] = (cc != FUSED_NONE && ro != FUSED_NONE) ? uc[cbase + ro + cc] : (T)0;
+  }
+  Cells<T> C;
+  load_cells(C, tb, base, u, f, false, sg);
+  __syncthreads();
+  // three-point prolongation onto the thread's owned cells: parent column lane + 1 of the coarse
+  // window (both columns of the pair), parent row (RPW / 2) warp + r / 2 + 1
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int rxc = tb.colrx[lane];
+#pragma unroll
+  for (int r = 0; r < RPW; ++r) {
+    const int wj = RPW * warp + r;
+    const int ry = tb.rowry[wj];
+    const int cj = (RPW / 2) * warp + r / 2 + 1;
+    const int cjy = (r & 1) ? cj + 1 : cj - 1;
+    const int ci = lane + 1;
+    const FP2<T> wy = tb.py[rxc][wj];
+#pragma unroll
+    for (int p = 0; p < 2; ++p) {
+      if (C.inv[r][p] == (T)0) continue;  // unowned cell
+      const FP2<T> wx = tb.px[ry][p][lane];
+      const T eC = S.e[cj][ci];
+      const T eX = S.e[cj][p ? ci + 1 : ci - 1];
+      const T eY = S.e[cjy][ci];
+      C.u[r][p] += fma(eC, (T)1 + wx.a + wy.a, fma(wx.b, eX, wy.b * eY));
     }
-    S.e[cj][ci] = v;
   }
-  __syncthreads();
-  // three-point prolongation of the coarse correction onto every owned window cell
-  const int x0w = t.x0 - FH, y0w = t.y0 - FH;
-  for (int idx = threadIdx.x; idx < WX * WY; idx += blockDim.x) {
-    const int wj = idx / WX, wi = idx % WX;
-    if (!owned(S, B, x0w, y0w, wi, wj, tw, th)) continue;
-    const int i = x0w + wi, j = y0w + wj;
-    const int rx = region_of(i, B.nx), ry = region_of(j, B.ny);
-    const int ci = (i >> 1) - cx0, cj = (j >> 1) - cy0;
-    const PW<T> px = S.px[ry][wi], py = S.py[rx][wj];
-    const T eC = S.e[cj][ci];
-    const T eX = S.e[cj][(i & 1) ? ci + 1 : ci - 1];
-    const T eY = S.e[(j & 1) ? cj + 1 : cj - 1][ci];
-    S.u[wj][wi] += fma(eC, (T)1 + px.self + py.self, fma(px.nbr, eX, py.nbr * eY));
-  }
-  __syncthreads();
-  sweeps(S, B, t.x0, t.y0, tw, th, sg, nu);
-  store_tile(S, B, t, tw, th, base, u_out);
+  int buf;
+  sweeps(C, S, nu, buf);
+  store_tile(C, tb, base, u_out);
   if (part == nullptr) return;
-  // sum of squared residuals of the tile (only red cells carry one after a sweep ending on black)
+  // sum of squared residuals over the tile's cells (only red cells carry one after a sweep)
+  T rr[RPW];
+  strip_residuals(C, S, buf, sg, rr);
   double r2 = 0.0;
-  for (int idx = threadIdx.x; idx < FTILE_X * FTILE_Y; idx += blockDim.x) {
-    const int ti = idx % FTILE_X, tj = idx / FTILE_X;
-    if (ti >= tw || tj >= th) continue;
-    if (nu > 0 && ((B.par + t.x0 + ti + t.y0 + tj) & 1)) continue;
-    const T r = resid_at(S, ti + FH, tj + FH, sg);
-    r2 += (double)r * (double)r;
+  if (in_tile(2 * lane, tb.tw)) {
+#pragma unroll
+    for (int r = 0; r < RPW; ++r)
+      if (in_tile(RPW * warp + r, tb.th)) r2 += (double)rr[r] * (double)rr[r];
   }
   r2 = warp_sum(r2);
-  if ((threadIdx.x & 31) == 0) S.wsum[threadIdx.x >> 5] = r2;
+  if (lane == 0) S.wsum[warp] = r2;
   __syncthreads();
   if (threadIdx.x == 0) {
-    double s = 0.0;
-    for (int w = 0; w < FTHREADS / 32; ++w) s += S.wsum[w];
-    part[(long long)q * nftiles + blockIdx.x] = s;
+    double sum = 0.0;
+    for (int w = 0; w < FWARPS; ++w) sum += S.wsum[w];
+    part[(long long)q * nftiles + blockIdx.x] = sum;
   }
 }
 
@@ -321,7 +388,7 @@ cudaError_t fused_down_t(snac_plan* P, int l, int nact, bool zero_u, bool zero_c
   LaunchScope ls(P, K_FDOWN, w * cells * ((zero_u ? 2.0 : 3.0) + 0.25 + (zero_coarse ? 0.25 : 0.0)),
                  cells * (2.0 * P->nu1 * 11.0 + 7.5), s);
   // iterate: read d_u, write d_u2 (the up kernel of this level reads d_u2 and writes d_u back)
-  k_fdown<T><<<g, FTHREADS, smem, s>>>(level_view<T>(h), level_view<T>(hc), h.d_ftiles, P->d_active, sigma,
+  k_fdown<T><<<g, FTHREADS, smem, s>>>((const FusedTab<T>*)h.d_ftab, h.ncell, hc.ncell, P->d_active, sigma,
                                        (const T*)h.d_u, (T*)h.d_u2, (const T*)h.d_f, (T*)hc.d_f, (T*)hc.d_u, P->nu1,
                                        zero_u ? 1 : 0, zero_coarse ? 1 : 0);
   return cudaGetLastError();
@@ -337,7 +404,7 @@ cudaError_t fused_up_t(snac_plan* P, int l, int nact, bool norms, const T* sigma
   cudaFuncSetAttribute(k_fup<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   // read u, f and the coarse correction, write u
   LaunchScope ls(P, K_FUP, w * cells * 3.25, cells * (8.0 + 2.0 * P->nu2 * 11.0 + (norms ? 7.0 : 0.0)), s);
-  k_fup<T><<<g, FTHREADS, smem, s>>>(level_view<T>(h), level_view<T>(hc), h.d_ftiles, (int)h.ftiles.size(),
+  k_fup<T><<<g, FTHREADS, smem, s>>>((const FusedTab<T>*)h.d_ftab, (int)h.ftiles.size(), h.ncell, hc.ncell,
                                      P->d_active, sigma, (const T*)h.d_u2, (T*)h.d_u, (const T*)h.d_f,
                                      (const T*)hc.d_u, P->nu2, norms ? P->d_mode_part : nullptr);
   return cudaGetLastError();

@@ -218,6 +218,32 @@ __global__ void __launch_bounds__(TILE_THREADS) k_mode_resid2(LevelView<T> L, co
   }
 }
 
+// Per-tile partial sums of f^2 (the residual of a zero iterate) for every listed mode: a plain
+// streaming pass over the plane, one partial per CTA-row of MODE_SQ_CTAS CTAs.
+constexpr int MODE_SQ_CTAS = 64;
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_mode_sumsq(const T* __restrict__ f, long long ncell, const int* __restrict__ active,
+                                                    double* __restrict__ part) {
+  __shared__ double sh[32];
+  const int q = active[blockIdx.y];
+  const T* fq = f + (long long)q * ncell;
+  double s = 0.0;
+  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < ncell; c += (long long)gridDim.x * blockDim.x) {
+    const double v = (double)fq[c];
+    s = fma(v, v, s);
+  }
+  s = warp_sum(s);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) sh[warp] = s;
+  __syncthreads();
+  if (warp == 0) {
+    double v = lane < (int)(blockDim.x >> 5) ? sh[lane] : 0.0;
+    v = warp_sum(v);
+    if (lane == 0) part[(long long)q * MODE_SQ_CTAS + blockIdx.x] = v;
+  }
+}
+
 __global__ void __launch_bounds__(256) k_mode_reduce(const double* __restrict__ part, int ntiles,
                                                      const int* __restrict__ active, double* __restrict__ norm2) {
   __shared__ double sh[32];
@@ -311,6 +337,15 @@ cudaError_t vcycle_t(snac_plan* P, int nact, cudaStream_t st) {
 template <typename T>
 cudaError_t mode_norms_t(snac_plan* P, int nact, bool after_cycle, cudaStream_t st) {
   const HostLevel& h = P->lev[0];
+  if (!after_cycle) {  // zero iterate: the residual is the right-hand side itself
+    {
+      LaunchScope ls(P, K_MODE_RESID, (double)sizeof(T) * h.ncell * nact, 2.0 * h.ncell * nact, st);
+      k_mode_sumsq<T><<<dim3(MODE_SQ_CTAS, nact), 256, 0, st>>>((const T*)h.d_f, h.ncell, P->d_active, P->d_mode_part);
+    }
+    LaunchScope ls(P, K_MODE_REDUCE, 8.0 * MODE_SQ_CTAS * nact, (double)MODE_SQ_CTAS * nact, st);
+    k_mode_reduce<<<nact, 256, 0, st>>>(P->d_mode_part, MODE_SQ_CTAS, P->d_active, P->d_mode_norm2);
+    return cudaGetLastError();
+  }
   if (after_cycle && h.fused) {  // the level-0 up kernel left one partial per fused tile
     LaunchScope ls(P, K_MODE_REDUCE, 8.0 * h.ftiles.size() * nact, (double)h.ftiles.size() * nact, st);
     k_mode_reduce<<<nact, 256, 0, st>>>(P->d_mode_part, (int)h.ftiles.size(), P->d_active, P->d_mode_norm2);

@@ -13,6 +13,7 @@
 #include <cstring>
 #include <new>
 
+#include "fused_tab.h"
 #include "snac_impl.h"
 
 using namespace snac;
@@ -485,6 +486,112 @@ void free_plan(snac_plan* P) {
   delete P;
 }
 
+// Per-tile tables of the fused kernels of one level (the window's region blocks, coefficients,
+// weights and plane offsets, in the shared-memory layout of FusedTab).
+template <typename T>
+int upload_fused_tabs(snac_plan* P, HostLevel& lv, const HostLevel& lc) {
+  auto region = [](int i, int n) { return i < 0 ? 0 : (i >= n ? 2 : 1); };
+  auto local = [](int i, int r, int n, int nr) { return r == 0 ? i + nr : (r == 2 ? i - n : i); };
+  auto nb = [&](int b, int f) { return b < 0 ? -1 : lv.blk[b].nbr[f]; };
+  if (lv.ncell >= (1LL << 30) || lc.ncell >= (1LL << 30))
+    return fail(SNAC_ERR_INVALID_ARG, "fused levels need planes of fewer than 2^30 cells (set fused = 0)");
+  std::vector<FusedTab<T>> tabs(lv.ftiles.size());
+  const int H = FUSED_HALO;
+  for (size_t n = 0; n < lv.ftiles.size(); ++n) {
+    const TileDev& t = lv.ftiles[n];
+    FusedTab<T>& tb = tabs[n];
+    std::memset(&tb, 0, sizeof tb);
+    const BlockDev& d = lv.blk[t.b];
+    const BlockDev& dc = lc.blk[t.b];
+    // the blocks around the tile's block, [ry][rx]: faces directly, corners through either neighbour
+    const int W = d.nbr[0], E = d.nbr[1], S = d.nbr[2], N = d.nbr[3];
+    const int R[3][3] = {{nb(W, 2) >= 0 ? nb(W, 2) : nb(S, 0), S, nb(E, 2) >= 0 ? nb(E, 2) : nb(S, 1)},
+                         {W, t.b, E},
+                         {nb(W, 3) >= 0 ? nb(W, 3) : nb(N, 0), N, nb(E, 3) >= 0 ? nb(E, 3) : nb(N, 1)}};
+    tb.tw = std::min(FTILE_X, d.nx - t.x0);
+    tb.th = std::min(FTILE_Y, d.ny - t.y0);
+    const int x0w = t.x0 - H, y0w = t.y0 - H;  // even
+    tb.pbase = ((d.par + x0w + y0w) % 2 + 2) % 2;
+    tb.cnx = dc.nx;
+    tb.cout0 = (int)(dc.off + (long long)(y0w / 2) * dc.nx + x0w / 2);
+    for (int k = 0; k < FHW; ++k) {
+      const int i = x0w + 2 * k, rx = region(i, d.nx);
+      const bool ok = 2 * k < tb.tw + 2 * H;
+      tb.col[k] = ok ? i : FUSED_NONE;
+      tb.colrx[k] = rx;
+      for (int ry = 0; ry < 3; ++ry)
+        for (int p = 0; p < 2; ++p) {
+          const int rb = R[ry][rx];
+          if (!ok || rb < 0) continue;
+          const BlockDev& B = lv.blk[rb];
+          const int ii = local(i + p, rx, d.nx, B.nx);
+          if (ii < 0 || ii >= B.nx) return fail(SNAC_ERR_INVALID_ARG, "fused window leaves its neighbour blocks");
+          const Coef<double>& c = lv.cx[B.xo + ii];
+          const PW<double>& w = lv.px[B.xo + ii];
+          tb.xc[ry][p][k] = FP2<T>{(T)c.lo, (T)c.hi};
+          tb.xd[ry][p][k] = (T)c.d;
+          tb.px[ry][p][k] = FP2<T>{(T)w.self, (T)w.nbr};
+        }
+      if (2 * k >= H && 2 * k < H + tb.tw) {
+        tb.rx[0][k] = (T)lv.rx[d.xo + i];
+        tb.rx[1][k] = (T)lv.rx[d.xo + i + 1];
+      }
+    }
+    for (int wj = 0; wj < FWN; ++wj) {
+      const int j = y0w + wj, ry = region(j, d.ny);
+      tb.rowry[wj] = ry;
+      if (j >= 0 && j < d.ny) tb.ry[wj] = (T)lv.ry[d.yo + j];
+      for (int rx = 0; rx < 3; ++rx) {
+        const int rb = R[ry][rx];
+        tb.rowoff[rx][wj] = FUSED_NONE;
+        if (wj >= tb.th + 2 * H || rb < 0) continue;
+        const BlockDev& B = lv.blk[rb];
+        const int jj = local(j, ry, d.ny, B.ny);
+        if (jj < 0 || jj >= B.ny) return fail(SNAC_ERR_INVALID_ARG, "fused window leaves its neighbour blocks");
+        const Coef<double>& c = lv.cy[B.yo + jj];
+        const PW<double>& w = lv.py[B.yo + jj];
+        tb.yc[rx][wj] = FP2<T>{(T)c.lo, (T)c.hi};
+        tb.yd[rx][wj] = (T)c.d;
+        tb.py[rx][wj] = FP2<T>{(T)w.self, (T)w.nbr};
+        const long long shift = rx == 0 ? B.nx : (rx == 2 ? -(long long)d.nx : 0);
+        tb.rowoff[rx][wj] = (int)(B.off + (long long)jj * B.nx + shift);
+      }
+    }
+    // coarse window: a column is kept where it lies inside every region block of its region column
+    // (the columns the prolongation reads always do: they stay within 4 cells of the tile's block)
+    const int cx0 = x0w / 2 - 1, cy0 = y0w / 2 - 1;
+    for (int ci = 0; ci < FCW; ++ci) {
+      const int I = cx0 + ci, rx = region(I, dc.nx);
+      bool ok = true;
+      for (int ry = 0; ry < 3; ++ry) {
+        const int rb = R[ry][rx];
+        if (rb < 0) continue;
+        const int ii = local(I, rx, dc.nx, lc.blk[rb].nx);
+        ok = ok && ii >= 0 && ii < lc.blk[rb].nx;
+      }
+      tb.ccol[ci] = ok ? I : FUSED_NONE;
+      tb.ccolrx[ci] = rx;
+    }
+    for (int cj = 0; cj < FCW; ++cj) {
+      const int J = cy0 + cj, ry = region(J, dc.ny);
+      for (int rx = 0; rx < 3; ++rx) {
+        const int rb = R[ry][rx];
+        tb.crowoff[rx][cj] = FUSED_NONE;
+        if (rb < 0) continue;
+        const BlockDev& B = lc.blk[rb];
+        const int jj = local(J, ry, dc.ny, B.ny);
+        if (jj < 0 || jj >= B.ny) continue;
+        const long long shift = rx == 0 ? B.nx : (rx == 2 ? -(long long)dc.nx : 0);
+        tb.crowoff[rx][cj] = (int)(B.off + (long long)jj * B.nx + shift);
+      }
+    }
+  }
+  FusedTab<T>* d = nullptr;
+  const int st = upload(P, &d, tabs);
+  lv.d_ftab = d;
+  return st;
+}
+
 int create(snac_plan** out, int32_t nblocks, const snac_block* blocks, int32_t homog_axis, const snac_options* opt) {
   if (!out || !blocks || nblocks < 1) return fail(SNAC_ERR_INVALID_ARG, "out/blocks NULL or nblocks < 1");
   *out = nullptr;
@@ -568,7 +675,7 @@ int create(snac_plan** out, int32_t nblocks, const snac_block* blocks, int32_t h
     if ((st = build_coarse(P))) break;
     // fused FP32 tile kernels on the levels whose blocks all keep the halo inside their neighbours
     const bool want_fused = P->fused == 1 || (P->fused < 0 && P->precision == SNAC_MIXED);
-    if (want_fused && P->nu1 <= 2 && P->nu2 <= 2) {
+    if (want_fused && P->nu1 >= 1 && P->nu2 >= 1 && P->nu1 <= 2 && P->nu2 <= 2) {
       for (size_t l = 0; l + 1 < P->lev.size(); ++l) {
         HostLevel& lv = P->lev[l];
         bool ok = true;
@@ -581,7 +688,9 @@ int create(snac_plan** out, int32_t nblocks, const snac_block* blocks, int32_t h
         for (int b = 0; b < lv.nblk; ++b)
           for (int y0 = 0; y0 < lv.blk[b].ny; y0 += FTILE_Y)
             for (int x0 = 0; x0 < lv.blk[b].nx; x0 += FTILE_X) lv.ftiles.push_back({b, x0, y0, 0});
-        if ((st = upload(P, &lv.d_ftiles, lv.ftiles))) break;
+        if (P->precision == SNAC_FP64) st = upload_fused_tabs<double>(P, lv, P->lev[l + 1]);
+        else st = upload_fused_tabs<float>(P, lv, P->lev[l + 1]);
+        if (st) break;
       }
       if (st) break;
     }
@@ -612,7 +721,7 @@ int create(snac_plan** out, int32_t nblocks, const snac_block* blocks, int32_t h
     if ((st = dmalloc(P, &P->d_partial, (size_t)P->npartial * 4))) break;
     if ((st = dmalloc(P, &P->d_sums, 8))) break;
     // per-mode, per-tile partial sums (basic tiles; the fused tiles are fewer)
-    if ((st = dmalloc(P, &P->d_mode_part, (size_t)P->nz * P->lev[0].tiles.size()))) break;
+    if ((st = dmalloc(P, &P->d_mode_part, (size_t)P->nz * std::max<size_t>(P->lev[0].tiles.size(), 64)))) break;
     if ((st = dmalloc(P, &P->d_mode_norm2, (size_t)P->nz))) break;
     if ((st = dmalloc(P, &P->d_active, (size_t)P->nz))) break;
     if (cudaMallocHost(&P->h_sums, 8 * sizeof(double)) != cudaSuccess ||

@@ -29,8 +29,8 @@ constexpr int TILE_THREADS = TILE_X * TILE_Y;
 constexpr int MAX_NZ = 1024;
 constexpr int MAX_COARSE = 256;
 constexpr int MEAN_CTAS = 2 * 152;  // CTAs of the grid-stride reductions over one mode plane
-constexpr int FTILE_X = 64;         // tile of the fused FP32 multigrid kernels
-constexpr int FTILE_Y = 32;
+constexpr int FTILE_X = 52;         // tile of the fused multigrid kernels (64x64 window with the halo)
+constexpr int FTILE_Y = 52;
 constexpr int FUSED_MIN_BLOCK = 16;  // fused kernels on levels whose blocks are all this wide
 
 // Faces are numbered W, E, S, N = 0..3 (x lower, x upper, y lower, y upper).
@@ -105,7 +105,7 @@ struct HostLevel {
   bool fused = false;        // this level runs the fused tile kernels
   void* d_u2 = nullptr;      // fused levels: second iterate buffer (the tiles read one, write the other)
   std::vector<TileDev> ftiles;  // FTILE_X x FTILE_Y tiles (fused levels)
-  TileDev* d_ftiles = nullptr;
+  void* d_ftab = nullptr;       // per fused tile: its FusedTab<T> (T = the level's arithmetic type)
 };
 
 // A chunk of up to TCOLS consecutive columns (cells of one plane) of one block, for the transforms.
@@ -223,7 +223,8 @@ cudaError_t launch_inverse_diagonals(snac_plan* P, cudaStream_t s);
 // one V-cycle of the active modes on the plan's level buffers (level 0: d_u / d_f)
 cudaError_t launch_vcycle(snac_plan* P, int nactive, cudaStream_t s);
 // per-mode ||f - A u||^2 at level 0 for the active modes -> d_mode_norm2[q]; after_cycle: u is the
-// result of a V-cycle (post-smoothing ended on black, so only red cells carry a residual)
+// result of a V-cycle (post-smoothing ended on black, so only red cells carry a residual); otherwise
+// u is zero and the norm is that of f
 cudaError_t launch_mode_norms(snac_plan* P, int nactive, bool after_cycle, cudaStream_t s);
 
 // fused FP32 levels: smoothing + residual + restriction (down), prolongation + smoothing (+ level-0
