@@ -9,9 +9,11 @@
 //            prolongation and correction -> nu2 sweeps -> store the tile's u (on level 0 also the
 //            per-mode sums of squared residuals).
 //
-// A CTA starts with one copy of its tile's tables (FusedTab: coefficients, weights and the plane
-// offsets of every window row and column, built on the host), then one round of cell loads: no
-// chain of dependent loads through the block and neighbour descriptors.
+// A CTA copies its tile's tables once (FusedTab: coefficients, weights and the plane offsets of
+// every window row and column, built on the host) and then runs the tile for a run of consecutive
+// active modes. While it smooths one mode, the next mode's cells (and, going up, its coarse
+// correction window) stream into shared memory with per-thread asynchronous copies (cp.async), so
+// the global-load latency of a mode is hidden behind the previous mode's sweeps.
 //
 // Registers. Warp w holds window rows 4w..4w+3, lane k holds columns 2k (parity 0) and 2k+1
 // (parity 1) of those rows: u, f and 1/diag of 8 cells per thread. In a row the cells of one colour
@@ -32,6 +34,8 @@
 //
 // Each tile reads one iterate buffer and writes the other (neighbouring CTAs store their smoothed
 // tiles while this one may still be loading its halo).
+#include <algorithm>
+
 #include "fused_tab.h"
 #include "kern_common.cuh"
 #include "snac_impl.h"
@@ -50,12 +54,30 @@ static_assert(FTILE_X == FTILE_Y && HW == 32 && FWARPS * RPW == WN, "the fused k
 static_assert(FH % 2 == 0 && 2 * 2 <= FH - 2, "nu <= 2 sweeps must stay exact inside the halo");
 
 template <typename T>
+struct alignas(2 * sizeof(T)) Pair {
+  T a, b;
+};
+
+template <typename T>
 struct Shared {
   FusedTab<T> tab;
-  T halo[2][FWARPS][2][2][HW];  // [buffer][warp][first/last row][parity][lane]
-  T e[CW][CW];                  // coarse correction around the tile (k_fup)
+  Pair<T> stage[RPW][2][FTHREADS];  // next mode's u, f column pairs, each thread's own slots
+  T halo[2][FWARPS][2][2][HW];      // [buffer][warp][first/last row][parity][lane]
+  T e[2][CW][CW];                   // coarse correction around the tile, this mode and the next (k_fup)
   double wsum[FWARPS];
 };
+
+// Per-thread asynchronous global -> shared copies (completion is tracked by the issuing thread).
+template <int BYTES>
+__device__ __forceinline__ void cp_async(void* dst, const void* src) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(dst);
+  if constexpr (BYTES == 16)
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(src) : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(s), "l"(src), "n"(BYTES) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
 // Per-thread state: rows RPW w .. RPW w + RPW - 1 of window columns 2k, 2k+1.
 template <typename T>
@@ -72,11 +94,30 @@ __device__ __forceinline__ void copy_tab(Shared<T>& S, const FusedTab<T>* __rest
   for (int i = threadIdx.x; i < (int)(sizeof(FusedTab<T>) / 16); i += FTHREADS) dst[i] = src[i];
 }
 
-// The thread's 2 RPW cells of u (unless zero), f and 1/diag.
+// Start the copies of the thread's cells of one mode (u unless it is zero, and f) into its own
+// staging slots. Cells with no owner are not copied.
 template <typename T>
-__device__ __forceinline__ void load_cells(Cells<T>& C, const FusedTab<T>& tb, long long base, const T* __restrict__ u,
-                                           const T* __restrict__ f, bool zero_u, T sg) {
+__device__ __forceinline__ void prefetch_cells(Shared<T>& S, long long base, const T* __restrict__ u,
+                                               const T* __restrict__ f, bool load_u) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const FusedTab<T>& tb = S.tab;
+  const int col = tb.col[lane], rx = tb.colrx[lane];
+  if (col == FUSED_NONE) return;
+#pragma unroll
+  for (int r = 0; r < RPW; ++r) {
+    const int ro = tb.rowoff[rx][RPW * warp + r];
+    if (ro == FUSED_NONE) continue;
+    const long long a = base + ro + col;  // even: block sizes and offsets are even
+    if (load_u) cp_async<2 * sizeof(T)>(&S.stage[r][0][threadIdx.x], u + a);
+    cp_async<2 * sizeof(T)>(&S.stage[r][1][threadIdx.x], f + a);
+  }
+}
+
+// The thread's 2 RPW cells of u (zero if asked), f and 1/diag, from its completed staging slots.
+template <typename T>
+__device__ __forceinline__ void take_cells(Cells<T>& C, const Shared<T>& S, bool zero_u, T sg) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const FusedTab<T>& tb = S.tab;
   const int col = tb.col[lane], rx = tb.colrx[lane];
 #pragma unroll
   for (int r = 0; r < RPW; ++r) {
@@ -84,13 +125,14 @@ __device__ __forceinline__ void load_cells(Cells<T>& C, const FusedTab<T>& tb, l
     const int ro = tb.rowoff[rx][wj];
     T u0 = 0, u1 = 0, f0 = 0, f1 = 0, i0 = 0, i1 = 0;
     if (col != FUSED_NONE && ro != FUSED_NONE) {
-      const long long a = base + ro + col;  // even: block sizes and offsets are even
       if (!zero_u) {
-        u0 = u[a];
-        u1 = u[a + 1];
+        const Pair<T> v = S.stage[r][0][threadIdx.x];
+        u0 = v.a;
+        u1 = v.b;
       }
-      f0 = f[a];
-      f1 = f[a + 1];
+      const Pair<T> g = S.stage[r][1][threadIdx.x];
+      f0 = g.a;
+      f1 = g.b;
       const int ry = tb.rowry[wj];
       const T yd = tb.yd[rx][wj] + sg;
       i0 = (T)1 / (tb.xd[ry][0][lane] + yd);
@@ -102,6 +144,19 @@ __device__ __forceinline__ void load_cells(Cells<T>& C, const FusedTab<T>& tb, l
     C.f[r][1] = f1;
     C.inv[r][0] = i0;
     C.inv[r][1] = i1;
+  }
+}
+
+// Start the copies of one mode's coarse correction window into S.e[buf] (zero where no owner).
+template <typename T>
+__device__ __forceinline__ void prefetch_coarse(Shared<T>& S, int buf, long long cbase, const T* __restrict__ uc) {
+  const FusedTab<T>& tb = S.tab;
+  for (int idx = threadIdx.x; idx < CW * CW; idx += FTHREADS) {
+    const int cj = idx / CW, ci = idx % CW;
+    const int cc = tb.ccol[ci];
+    const int ro = tb.crowoff[tb.ccolrx[ci]][cj];
+    if (cc != FUSED_NONE && ro != FUSED_NONE) cp_async<sizeof(T)>(&S.e[buf][cj][ci], uc + cbase + ro + cc);
+    else S.e[buf][cj][ci] = (T)0;
   }
 }
 
@@ -171,8 +226,10 @@ __device__ __forceinline__ void half_sweep(Cells<T>& C, const FusedTab<T>& tb, c
 
 // nu red-black sweeps of the whole window. On return the strip-edge rows of the final state are in
 // S.halo[buf] (for the residuals that follow).
-template <typename T>
-__device__ void sweeps(Cells<T>& C, Shared<T>& S, int nu, int& buf) {
+// `after_first_barrier` runs once every thread has passed the barrier that follows the first
+// write of the halo rows (all earlier shared-memory reads of the CTA are then complete).
+template <typename T, typename Hook>
+__device__ void sweeps(Cells<T>& C, Shared<T>& S, int nu, int& buf, Hook&& after_first_barrier) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   int ry[RPW];
 #pragma unroll
@@ -182,6 +239,7 @@ __device__ void sweeps(Cells<T>& C, Shared<T>& S, int nu, int& buf) {
   buf = 0;
   write_halo(S, C, buf);
   __syncthreads();
+  after_first_barrier();
   for (int s = 0; s < 2 * nu; ++s) {
     const int colour = s & 1;
     T sedge[2], nedge[2];
@@ -269,110 +327,148 @@ __device__ __forceinline__ void store_tile(const Cells<T>& C, const FusedTab<T>&
   }
 }
 
-// One CTA per (fused tile, active mode).
+// Modes per CTA: enough CTAs for about three waves of two per multiprocessor, at most 8 modes.
+inline int modes_per_cta(int sms, int ntiles, int nact) {
+  const long long mpc = (long long)ntiles * nact / (3LL * 2 * sms);
+  return (int)std::min<long long>(8, std::max<long long>(1, mpc));
+}
+
+// CTA (tile blockIdx.x, modes active[m0 .. m1)), m0 = blockIdx.y * mpc.
 template <typename T>
 __global__ void __launch_bounds__(FTHREADS, 2)
     k_fdown(const FusedTab<T>* __restrict__ tabs, long long fncell, long long cncell, const int* __restrict__ active,
-            const T* __restrict__ sigma, const T* __restrict__ u, T* __restrict__ u_out, const T* __restrict__ f,
-            T* __restrict__ fc, T* __restrict__ uc, int nu, int zero_u, int zero_coarse) {
+            int nact, int mpc, const T* __restrict__ sigma, const T* __restrict__ u, T* __restrict__ u_out,
+            const T* __restrict__ f, T* __restrict__ fc, T* __restrict__ uc, int nu, int zero_u, int zero_coarse) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Shared<T>& S = *reinterpret_cast<Shared<T>*>(smem_raw);
-  const int q = active[blockIdx.y];
+  const int m0 = blockIdx.y * mpc, m1 = min(nact, m0 + mpc);
   copy_tab(S, tabs + blockIdx.x);
-  const T sg = sigma[q];
   __syncthreads();
   const FusedTab<T>& tb = S.tab;
-  const long long base = (long long)q * fncell;
-  Cells<T> C;
-  load_cells(C, tb, base, u, f, zero_u != 0, sg);
-  int buf;
-  sweeps(C, S, nu, buf);
-  store_tile(C, tb, base, u_out);
-  // restriction: coarse cell = (column pair k, row pair (2h, 2h+1)) of the strip; its red children
-  // are one per row, the black ones carry no residual after the sweep
-  T rr[RPW];
-  const int p0 = strip_residuals(C, S, buf, sg, rr);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  if (!in_tile(2 * lane, tb.tw)) return;
-  const long long cbase = (long long)q * cncell + tb.cout0 + lane;
-  const T wx[2] = {tb.rx[0][lane], tb.rx[1][lane]};
+  int q = active[m0];
+  T sg = sigma[q];
+  prefetch_cells(S, (long long)q * fncell, u, f, zero_u == 0);
+  cp_async_commit();
+  for (int mi = m0; mi < m1; ++mi) {
+    const int qn = mi + 1 < m1 ? active[mi + 1] : -1;
+    const long long base = (long long)q * fncell;
+    cp_async_wait_all();
+    Cells<T> C;
+    take_cells(C, S, zero_u != 0, sg);
+    int buf;
+    T sgn = 0;
+    sweeps(C, S, nu, buf, [&] {
+      if (qn >= 0) {
+        sgn = sigma[qn];
+        prefetch_cells(S, (long long)qn * fncell, u, f, zero_u == 0);
+        cp_async_commit();
+      }
+    });
+    store_tile(C, tb, base, u_out);
+    // restriction: coarse cell = (column pair k, row pair (2h, 2h+1)) of the strip; its red children
+    // are one per row, the black ones carry no residual after the sweep
+    T rr[RPW];
+    const int p0 = strip_residuals(C, S, buf, sg, rr);
+    if (in_tile(2 * lane, tb.tw)) {
+      const long long cbase = (long long)q * cncell + tb.cout0 + lane;
+      const T wx[2] = {tb.rx[0][lane], tb.rx[1][lane]};
 #pragma unroll
-  for (int h = 0; h < RPW / 2; ++h) {
-    const int wj = RPW * warp + 2 * h;
-    if (!in_tile(wj, tb.th)) continue;
-    const T acc = fma(wx[p0 ^ 1] * tb.ry[wj + 1], rr[2 * h + 1], wx[p0] * tb.ry[wj] * rr[2 * h]);
-    const long long cc = cbase + (long long)(wj / 2) * tb.cnx;
-    fc[cc] = acc;
-    if (zero_coarse) uc[cc] = 0;
+      for (int h = 0; h < RPW / 2; ++h) {
+        const int wj = RPW * warp + 2 * h;
+        if (!in_tile(wj, tb.th)) continue;
+        const T acc = fma(wx[p0 ^ 1] * tb.ry[wj + 1], rr[2 * h + 1], wx[p0] * tb.ry[wj] * rr[2 * h]);
+        const long long cc = cbase + (long long)(wj / 2) * tb.cnx;
+        fc[cc] = acc;
+        if (zero_coarse) uc[cc] = 0;
+      }
+    }
+    __syncthreads();  // the next mode rewrites the halo rows
+    q = qn;
+    sg = sgn;
   }
 }
 
 template <typename T>
 __global__ void __launch_bounds__(FTHREADS, 2)
     k_fup(const FusedTab<T>* __restrict__ tabs, int nftiles, long long fncell, long long cncell,
-          const int* __restrict__ active, const T* __restrict__ sigma, const T* __restrict__ u, T* __restrict__ u_out,
-          const T* __restrict__ f, const T* __restrict__ uc, int nu, double* __restrict__ part) {
+          const int* __restrict__ active, int nact, int mpc, const T* __restrict__ sigma, const T* __restrict__ u,
+          T* __restrict__ u_out, const T* __restrict__ f, const T* __restrict__ uc, int nu, double* __restrict__ part) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Shared<T>& S = *reinterpret_cast<Shared<T>*>(smem_raw);
-  const int q = active[blockIdx.y];
+  const int m0 = blockIdx.y * mpc, m1 = min(nact, m0 + mpc);
   copy_tab(S, tabs + blockIdx.x);
-  const T sg = sigma[q];
   __syncthreads();
   const FusedTab<T>& tb = S.tab;
-  const long long base = (long long)q * fncell;
-  const long long cbase = (long long)q * cncell;
-  // coarse window: parents of the window cells and one more ring
-  for (int idx = threadIdx.x; idx < CW * CW; idx += FTHREADS) {
-    const int cj = idx / CW, ci = idx % CW;
-    const int cc = tb.ccol[ci];
-    const int ro = tb.crowoff[tb.ccolrx[ci]][cj];
-    S.e[cj][ci] = (cc != FUSED_NONE && ro != FUSED_NONE) ? uc[cbase + ro + cc] : (T)0;
-  }
-  Cells<T> C;
-  load_cells(C, tb, base, u, f, false, sg);
-  __syncthreads();
-  // three-point prolongation onto the thread's owned cells: parent column lane + 1 of the coarse
-  // window (both columns of the pair), parent row (RPW / 2) warp + r / 2 + 1
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int rxc = tb.colrx[lane];
+  int q = active[m0];
+  T sg = sigma[q];
+  prefetch_cells(S, (long long)q * fncell, u, f, true);
+  prefetch_coarse(S, 0, (long long)q * cncell, uc);
+  cp_async_commit();
+  for (int mi = m0; mi < m1; ++mi) {
+    const int qn = mi + 1 < m1 ? active[mi + 1] : -1;
+    const int eb = (mi - m0) & 1;
+    const long long base = (long long)q * fncell;
+    cp_async_wait_all();
+    __syncthreads();  // every thread's part of the coarse window is in place
+    Cells<T> C;
+    take_cells(C, S, false, sg);
+    // three-point prolongation onto the thread's owned cells: parent column lane + 1 of the coarse
+    // window (both columns of the pair), parent row (RPW / 2) warp + r / 2 + 1
+    const int rxc = tb.colrx[lane];
 #pragma unroll
-  for (int r = 0; r < RPW; ++r) {
-    const int wj = RPW * warp + r;
-    const int ry = tb.rowry[wj];
-    const int cj = (RPW / 2) * warp + r / 2 + 1;
-    const int cjy = (r & 1) ? cj + 1 : cj - 1;
-    const int ci = lane + 1;
-    const FP2<T> wy = tb.py[rxc][wj];
+    for (int r = 0; r < RPW; ++r) {
+      const int wj = RPW * warp + r;
+      const int ry = tb.rowry[wj];
+      const int cj = (RPW / 2) * warp + r / 2 + 1;
+      const int cjy = (r & 1) ? cj + 1 : cj - 1;
+      const int ci = lane + 1;
+      const FP2<T> wy = tb.py[rxc][wj];
 #pragma unroll
-    for (int p = 0; p < 2; ++p) {
-      if (C.inv[r][p] == (T)0) continue;  // unowned cell
-      const FP2<T> wx = tb.px[ry][p][lane];
-      const T eC = S.e[cj][ci];
-      const T eX = S.e[cj][p ? ci + 1 : ci - 1];
-      const T eY = S.e[cjy][ci];
-      C.u[r][p] += fma(eC, (T)1 + wx.a + wy.a, fma(wx.b, eX, wy.b * eY));
+      for (int p = 0; p < 2; ++p) {
+        if (C.inv[r][p] == (T)0) continue;  // unowned cell
+        const FP2<T> wx = tb.px[ry][p][lane];
+        const T eC = S.e[eb][cj][ci];
+        const T eX = S.e[eb][cj][p ? ci + 1 : ci - 1];
+        const T eY = S.e[eb][cjy][ci];
+        C.u[r][p] += fma(eC, (T)1 + wx.a + wy.a, fma(wx.b, eX, wy.b * eY));
+      }
     }
-  }
-  int buf;
-  sweeps(C, S, nu, buf);
-  store_tile(C, tb, base, u_out);
-  if (part == nullptr) return;
-  // sum of squared residuals over the tile's cells (only red cells carry one after a sweep)
-  T rr[RPW];
-  strip_residuals(C, S, buf, sg, rr);
-  double r2 = 0.0;
-  if (in_tile(2 * lane, tb.tw)) {
+    int buf;
+    T sgn = 0;
+    // the next mode's window goes to the other coarse buffer, last read by the previous mode
+    sweeps(C, S, nu, buf, [&] {
+      if (qn >= 0) {
+        sgn = sigma[qn];
+        prefetch_cells(S, (long long)qn * fncell, u, f, true);
+        prefetch_coarse(S, eb ^ 1, (long long)qn * cncell, uc);
+        cp_async_commit();
+      }
+    });
+    store_tile(C, tb, base, u_out);
+    if (part != nullptr) {
+      // sum of squared residuals over the tile's cells (only red cells carry one after a sweep)
+      T rr[RPW];
+      strip_residuals(C, S, buf, sg, rr);
+      double r2 = 0.0;
+      if (in_tile(2 * lane, tb.tw)) {
 #pragma unroll
-    for (int r = 0; r < RPW; ++r)
-      if (in_tile(RPW * warp + r, tb.th)) r2 += (double)rr[r] * (double)rr[r];
-  }
-  r2 = warp_sum(r2);
-  if (lane == 0) S.wsum[warp] = r2;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double sum = 0.0;
-    for (int w = 0; w < FWARPS; ++w) sum += S.wsum[w];
-    part[(long long)q * nftiles + blockIdx.x] = sum;
+        for (int r = 0; r < RPW; ++r)
+          if (in_tile(RPW * warp + r, tb.th)) r2 += (double)rr[r] * (double)rr[r];
+      }
+      r2 = warp_sum(r2);
+      if (lane == 0) S.wsum[warp] = r2;
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        double sum = 0.0;
+        for (int w = 0; w < FWARPS; ++w) sum += S.wsum[w];
+        part[(long long)q * nftiles + blockIdx.x] = sum;
+      }
+    }
+    __syncthreads();  // the next mode rewrites the halo rows and wsum
+    q = qn;
+    sg = sgn;
   }
 }
 
@@ -380,7 +476,9 @@ template <typename T>
 cudaError_t fused_down_t(snac_plan* P, int l, int nact, bool zero_u, bool zero_coarse, const T* sigma, cudaStream_t s) {
   const HostLevel& h = P->lev[l];
   const HostLevel& hc = P->lev[l + 1];
-  dim3 g((unsigned)h.ftiles.size(), (unsigned)nact);
+  const int nt = (int)h.ftiles.size();
+  const int mpc = modes_per_cta(P->sms, nt, nact);
+  dim3 g((unsigned)nt, (unsigned)((nact + mpc - 1) / mpc));
   const double cells = (double)h.ncell * nact, w = sizeof(T);
   const size_t smem = sizeof(Shared<T>);
   cudaFuncSetAttribute(k_fdown<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -388,7 +486,7 @@ cudaError_t fused_down_t(snac_plan* P, int l, int nact, bool zero_u, bool zero_c
   LaunchScope ls(P, K_FDOWN, w * cells * ((zero_u ? 2.0 : 3.0) + 0.25 + (zero_coarse ? 0.25 : 0.0)),
                  cells * (2.0 * P->nu1 * 11.0 + 7.5), s);
   // iterate: read d_u, write d_u2 (the up kernel of this level reads d_u2 and writes d_u back)
-  k_fdown<T><<<g, FTHREADS, smem, s>>>((const FusedTab<T>*)h.d_ftab, h.ncell, hc.ncell, P->d_active, sigma,
+  k_fdown<T><<<g, FTHREADS, smem, s>>>((const FusedTab<T>*)h.d_ftab, h.ncell, hc.ncell, P->d_active, nact, mpc, sigma,
                                        (const T*)h.d_u, (T*)h.d_u2, (const T*)h.d_f, (T*)hc.d_f, (T*)hc.d_u, P->nu1,
                                        zero_u ? 1 : 0, zero_coarse ? 1 : 0);
   return cudaGetLastError();
@@ -398,15 +496,17 @@ template <typename T>
 cudaError_t fused_up_t(snac_plan* P, int l, int nact, bool norms, const T* sigma, cudaStream_t s) {
   const HostLevel& h = P->lev[l];
   const HostLevel& hc = P->lev[l + 1];
-  dim3 g((unsigned)h.ftiles.size(), (unsigned)nact);
+  const int nt = (int)h.ftiles.size();
+  const int mpc = modes_per_cta(P->sms, nt, nact);
+  dim3 g((unsigned)nt, (unsigned)((nact + mpc - 1) / mpc));
   const double cells = (double)h.ncell * nact, w = sizeof(T);
   const size_t smem = sizeof(Shared<T>);
   cudaFuncSetAttribute(k_fup<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   // read u, f and the coarse correction, write u
   LaunchScope ls(P, K_FUP, w * cells * 3.25, cells * (8.0 + 2.0 * P->nu2 * 11.0 + (norms ? 7.0 : 0.0)), s);
-  k_fup<T><<<g, FTHREADS, smem, s>>>((const FusedTab<T>*)h.d_ftab, (int)h.ftiles.size(), h.ncell, hc.ncell,
-                                     P->d_active, sigma, (const T*)h.d_u2, (T*)h.d_u, (const T*)h.d_f,
-                                     (const T*)hc.d_u, P->nu2, norms ? P->d_mode_part : nullptr);
+  k_fup<T><<<g, FTHREADS, smem, s>>>((const FusedTab<T>*)h.d_ftab, nt, h.ncell, hc.ncell, P->d_active, nact, mpc,
+                                     sigma, (const T*)h.d_u2, (T*)h.d_u, (const T*)h.d_f, (const T*)hc.d_u, P->nu2,
+                                     norms ? P->d_mode_part : nullptr);
   return cudaGetLastError();
 }
 

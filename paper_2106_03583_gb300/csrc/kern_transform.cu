@@ -43,11 +43,12 @@ __device__ Cx<T>* cfft(Cx<T>* X, Cx<T>* Y, int m, const Cx<T>* __restrict__ tw, 
   if (m == 1) return X;
   if ((m & (m - 1)) == 0) {
     // Stockham autosort: merge pairs of length-Ls transforms into length-2Ls transforms.
-    for (int Ls = 1; Ls < m; Ls <<= 1) {
+    int lg = 0;
+    for (int Ls = 1; Ls < m; Ls <<= 1, ++lg) {
       const int r = m / (2 * Ls);
       for (int idx = threadIdx.x; idx < (m / 2) * TC; idx += blockDim.x) {
         const int c = idx % TC, t = idx / TC;
-        const int j = t / Ls, k = t - j * Ls;
+        const int j = t >> lg, k = t & (Ls - 1);
         Cx<T> w = tw[k * r];
         if (inverse) w.im = -w.im;
         const Cx<T> a = X[(j * Ls + k) * TC + c];
@@ -91,8 +92,8 @@ struct Tw {
 // X_k (k = 0..m) of the real DFT of the length-n sequence packed as Z = FFT_m(x_2j + i x_2j+1).
 template <typename T, int TC>
 __device__ __forceinline__ Cx<T> rdft_bin(const Cx<T>* R, int k, int m, int c, const Tw<T>& tw) {
-  const Cx<T> zk = R[(k % m) * TC + c];
-  const Cx<T> zc = conj(R[((m - k) % m) * TC + c]);
+  const Cx<T> zk = R[(k == m ? 0 : k) * TC + c];
+  const Cx<T> zc = conj(R[(k == 0 ? 0 : m - k) * TC + c]);
   const Cx<T> E = {(T)0.5 * (zk.re + zc.re), (T)0.5 * (zk.im + zc.im)};
   const Cx<T> d = {zk.re - zc.re, zk.im - zc.im};
   const Cx<T> O = {(T)0.5 * d.im, (T)-0.5 * d.re};  // d / (2i)

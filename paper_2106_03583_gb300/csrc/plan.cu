@@ -618,6 +618,10 @@ int create(snac_plan** out, int32_t nblocks, const snac_block* blocks, int32_t h
     }
   }
   cudaGetDevice(&P->device);
+  if (cudaDeviceGetAttribute(&P->sms, cudaDevAttrMultiProcessorCount, P->device) != cudaSuccess || P->sms < 1) {
+    cudaGetLastError();
+    P->sms = 152;
+  }
   P->nblk = nblocks;
   P->nz = hb[0].n[2];
   P->dz = hb[0].w[2][0];

@@ -137,6 +137,7 @@ struct PendingEvent {
 
 struct snac_plan {
   int device = 0;
+  int sms = 152;             // multiprocessors of the device (grid sizing)
   int precision = SNAC_FP64;
   int nu1 = 2, nu2 = 2, max_outer = 20, max_cycles = 40, max_coarse = 64;
   double inner_reduction = 1e-3;
