@@ -29,15 +29,17 @@ __device__ __forceinline__ void block_sum(double (&v)[NV], double* sh /* [NV][32
 }
 
 // One thread per x-y cell of a tile, looping over the z planes k = blockIdx.y, + gridDim.y, ...
+// The z ends carry their boundary condition as a mirrored ghost (coefficient +-1/dz^2 on the cell
+// itself, cz[k].lo / hi), so the diagonal dxy + zd is the same on every plane and is formed once
+// per column. Only the sums a caller needs are formed: the kernel is bound by the FP64 pipe.
 // MODE 0: r = (f - fshift) - A p; partial {||r||^2, ||f - fshift||^2 (NEED_F2), sum V p (NEED_VP)}
 // MODE 1: r = A p
-// MODE 2: partial {sum V f, sum V |f|, ||f||^2}
-// Only the sums a caller needs are formed: the kernel is bound by the FP64 pipe.
-template <int MODE, bool NEED_F2, bool NEED_VP>
+template <int MODE, bool SHIFT, bool NEED_F2, bool NEED_VP>
 __global__ void __launch_bounds__(TILE_THREADS) k_field3d(LevelView<double> L, const Coef<double>* __restrict__ cz,
-                                                           int nz, int periodic_z, const double* __restrict__ f,
-                                                           const double* __restrict__ p, double* __restrict__ r,
-                                                           double fshift, double* __restrict__ partial) {
+                                                           int nz, int periodic_z, double zd, double dz,
+                                                           const double* __restrict__ f, const double* __restrict__ p,
+                                                           double* __restrict__ r, double fshift,
+                                                           double* __restrict__ partial) {
   __shared__ double sh[4 * 32];
   const TileDev t = L.tiles[blockIdx.x];
   const BlockDev B = L.blk[t.b];
@@ -55,18 +57,10 @@ __global__ void __launch_bounds__(TILE_THREADS) k_field3d(LevelView<double> L, c
     const long long ps = nz * L.blk[bs].off + ls, pn = nz * L.blk[bn].off + ln;
     const long long plw = (long long)L.blk[bw].nx * L.blk[bw].ny, ple = (long long)L.blk[be].nx * L.blk[be].ny;
     const long long pls = (long long)L.blk[bs].nx * L.blk[bs].ny, pln = (long long)L.blk[bn].nx * L.blk[bn].ny;
-    const double area = cx.w * cy.w;
-    const double dxy = cx.d + cy.d;
+    const double dg = cx.d + cy.d + zd;
+    const double va = cx.w * cy.w * dz;
     for (int k = blockIdx.y; k < nz; k += gridDim.y) {
       const long long c = base + k * plane;
-      if (MODE == 2) {
-        const double fv = f[c];
-        const double v = area * cz[k].w;
-        acc[0] += v * fv;
-        acc[1] += v * fabs(fv);
-        acc[2] += fv * fv;
-        continue;
-      }
       const Coef<double> z = cz[k];
       const int kd = k > 0 ? k - 1 : (periodic_z ? nz - 1 : k);
       const int ku = k < nz - 1 ? k + 1 : (periodic_z ? 0 : k);
@@ -77,16 +71,16 @@ __global__ void __launch_bounds__(TILE_THREADS) k_field3d(LevelView<double> L, c
       ap = fma(cy.hi, p[pn + k * pln], ap);
       ap = fma(z.lo, p[base + kd * plane], ap);
       ap = fma(z.hi, p[base + ku * plane], ap);
-      ap = fma(dxy + z.d, pc, ap);
+      ap = fma(dg, pc, ap);
       if (MODE == 1) {
         r[c] = ap;
       } else {
-        const double fv = f[c] - fshift;
+        const double fv = SHIFT ? f[c] - fshift : f[c];
         const double rv = fv - ap;
         r[c] = rv;
         acc[0] = fma(rv, rv, acc[0]);
         if (NEED_F2) acc[1] = fma(fv, fv, acc[1]);
-        if (NEED_VP) acc[2] = fma(area * z.w, pc, acc[2]);
+        if (NEED_VP) acc[2] = fma(va, pc, acc[2]);
       }
     }
   }
@@ -101,8 +95,51 @@ __global__ void __launch_bounds__(TILE_THREADS) k_field3d(LevelView<double> L, c
   }
 }
 
+// Before the first residual: statistics of the right-hand side and whether the initial guess is
+// zero. partial {sum V f, sum V |f|, ||f||^2, sum f} (the first two and the last only for singular
+// problems); *nonzero = 1 if any p has a bit set other than its sign.
+template <bool SING>
+__global__ void __launch_bounds__(TILE_THREADS) k_prepass(LevelView<double> L, int nz, double dz,
+                                                           const double* __restrict__ f, const double* __restrict__ p,
+                                                           double* __restrict__ partial, int* __restrict__ nonzero) {
+  __shared__ double sh[4 * 32];
+  const TileDev t = L.tiles[blockIdx.x];
+  const BlockDev B = L.blk[t.b];
+  const int i = t.x0 + (threadIdx.x % TILE_X), j = t.y0 + (threadIdx.x / TILE_X);
+  double acc[4] = {0.0, 0.0, 0.0, 0.0};
+  unsigned long long bits = 0;
+  if (i < B.nx && j < B.ny) {
+    const double va = L.cx[B.xo + i].w * L.cy[B.yo + j].w * dz;
+    const long long plane = (long long)B.nx * B.ny;
+    const long long base = (long long)nz * B.off + (long long)j * B.nx + i;
+    for (int k = blockIdx.y; k < nz; k += gridDim.y) {
+      const long long c = base + k * plane;
+      const double fv = f[c];
+      bits |= (unsigned long long)__double_as_longlong(p[c]);
+      if (SING) {
+        acc[0] = fma(va, fv, acc[0]);
+        acc[1] = fma(va, fabs(fv), acc[1]);
+        acc[3] += fv;
+      }
+      acc[2] = fma(fv, fv, acc[2]);
+    }
+  }
+  block_sum<4>(acc, sh);
+  const int any = __syncthreads_or((bits << 1) != 0ull);  // the shift drops the sign bit (-0.0 is zero)
+  if (threadIdx.x == 0) {
+    double* o = partial + 4 * ((long long)blockIdx.y * gridDim.x + blockIdx.x);
+    o[0] = acc[0];
+    o[1] = acc[1];
+    o[2] = acc[2];
+    o[3] = acc[3];
+    if (any) atomicOr(nonzero, 1);
+  }
+}
+
 // Deterministic sum of npart x 4 partials into out[4] (one CTA, fixed order).
-__global__ void __launch_bounds__(1024) k_reduce4(const double* __restrict__ part, int npart, double* __restrict__ out) {
+// With `flag`, also out_flag = (double)*flag (read after the kernels that set it).
+__global__ void __launch_bounds__(1024) k_reduce4(const double* __restrict__ part, int npart, double* __restrict__ out,
+                                                  const int* __restrict__ flag, double* __restrict__ out_flag) {
   __shared__ double sh[4 * 32];
   double acc[4] = {0, 0, 0, 0};
   for (int i = threadIdx.x; i < npart; i += blockDim.x) {
@@ -110,8 +147,10 @@ __global__ void __launch_bounds__(1024) k_reduce4(const double* __restrict__ par
     for (int k = 0; k < 4; ++k) acc[k] += part[4 * (long long)i + k];
   }
   block_sum<4>(acc, sh);
-  if (threadIdx.x == 0)
+  if (threadIdx.x == 0) {
     for (int k = 0; k < 4; ++k) out[k] = acc[k];
+    if (flag) *out_flag = (double)*flag;
+  }
 }
 
 // The singular mode-0 correction is shifted by a constant so that the updated p has zero
@@ -150,40 +189,71 @@ __global__ void k_shift(double* __restrict__ p, long long n, const double* __res
 // c = sums[2] / vol_total (the volume-weighted mean of p) written to sums[3]
 __global__ void k_mean_of_p(double* sums, double vol_total) { sums[3] = sums[2] / vol_total; }
 
-template <int MODE, bool F2, bool VP>
+template <int MODE, bool SH, bool F2, bool VP>
 void field3d_t(const LevelView<double>& L, dim3 grid, snac_plan* P, const double* f, const double* p, double* r,
                double fshift, cudaStream_t s) {
-  k_field3d<MODE, F2, VP><<<grid, TILE_THREADS, 0, s>>>(L, P->d_cz, P->nz, P->kind == KIND_PP, f, p, r, fshift,
-                                                         P->d_partial);
+  k_field3d<MODE, SH, F2, VP><<<grid, TILE_THREADS, 0, s>>>(L, P->d_cz, P->nz, P->kind == KIND_PP, P->cz[0].d, P->dz, f,
+                                                             p, r, fshift, P->d_partial);
+}
+
+template <bool SH>
+void residual_t(const LevelView<double>& L, dim3 grid, snac_plan* P, const double* f, const double* p, double* r,
+                double fshift, bool need_f2, bool need_vp, cudaStream_t s) {
+  if (need_f2 && need_vp) field3d_t<0, SH, true, true>(L, grid, P, f, p, r, fshift, s);
+  else if (need_f2) field3d_t<0, SH, true, false>(L, grid, P, f, p, r, fshift, s);
+  else if (need_vp) field3d_t<0, SH, false, true>(L, grid, P, f, p, r, fshift, s);
+  else field3d_t<0, SH, false, false>(L, grid, P, f, p, r, fshift, s);
+}
+
+dim3 field_grid(const snac_plan* P) {
+  return dim3((unsigned)P->lev[0].tiles.size(), (unsigned)std::min(P->nz, ZSPLIT));
 }
 
 }  // namespace
 
 cudaError_t launch_field3d(snac_plan* P, int mode, const double* f, const double* p, double* r, double fshift,
                            bool need_f2, bool need_vp, cudaStream_t s) {
-  const HostLevel& l0 = P->lev[0];
-  LevelView<double> L = level_view<double>(l0);
-  dim3 grid((unsigned)l0.tiles.size(), (unsigned)std::min(P->nz, ZSPLIT));
+  LevelView<double> L = level_view<double>(P->lev[0]);
+  const dim3 grid = field_grid(P);
   const double n3 = (double)P->n3;
   {
-    // algorithmic bytes: read f and p, write r (mode 0); read p, write A p (1); read f (2)
-    const double fl = mode == 0 ? 19.0 + (need_f2 ? 2.0 : 0.0) + (need_vp ? 3.0 : 0.0) : mode == 1 ? 14.0 : 7.0;
-    LaunchScope ls(P, K_FIELD3D, (mode == 0 ? 24.0 : mode == 1 ? 16.0 : 8.0) * n3, fl * n3, s);
-    if (mode == 1) field3d_t<1, false, false>(L, grid, P, f, p, r, fshift, s);
-    else if (mode == 2) field3d_t<2, false, false>(L, grid, P, f, p, r, fshift, s);
-    else if (need_f2 && need_vp) field3d_t<0, true, true>(L, grid, P, f, p, r, fshift, s);
-    else if (need_f2) field3d_t<0, true, false>(L, grid, P, f, p, r, fshift, s);
-    else if (need_vp) field3d_t<0, false, true>(L, grid, P, f, p, r, fshift, s);
-    else field3d_t<0, false, false>(L, grid, P, f, p, r, fshift, s);
+    // algorithmic bytes: read f and p, write r (mode 0); read p, write A p (mode 1)
+    const double fl = mode == 0 ? 17.0 + (fshift != 0.0 ? 1.0 : 0.0) + (need_f2 ? 2.0 : 0.0) + (need_vp ? 2.0 : 0.0)
+                                : 13.0;
+    LaunchScope ls(P, K_FIELD3D, (mode == 0 ? 24.0 : 16.0) * n3, fl * n3, s);
+    if (mode == 1) field3d_t<1, false, false, false>(L, grid, P, f, p, r, fshift, s);
+    else if (fshift != 0.0) residual_t<true>(L, grid, P, f, p, r, fshift, need_f2, need_vp, s);
+    else residual_t<false>(L, grid, P, f, p, r, fshift, need_f2, need_vp, s);
   }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess || mode == 1) return e;
   return launch_reduce_partials(P, (int)(grid.x * grid.y), P->d_sums, s);
 }
 
+cudaError_t launch_prepass(snac_plan* P, const double* f, const double* p, cudaStream_t s) {
+  LevelView<double> L = level_view<double>(P->lev[0]);
+  const dim3 grid = field_grid(P);
+  const double n3 = (double)P->n3;
+  cudaError_t e = cudaMemsetAsync(P->d_flag, 0, sizeof(int), s);
+  if (e != cudaSuccess) return e;
+  {
+    // read f and p
+    LaunchScope ls(P, K_FIELD3D, 16.0 * n3, (P->singular ? 7.0 : 2.0) * n3, s);
+    if (P->singular)
+      k_prepass<true><<<grid, TILE_THREADS, 0, s>>>(L, P->nz, P->dz, f, p, P->d_partial, P->d_flag);
+    else
+      k_prepass<false><<<grid, TILE_THREADS, 0, s>>>(L, P->nz, P->dz, f, p, P->d_partial, P->d_flag);
+  }
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  const int npart = (int)(grid.x * grid.y);
+  LaunchScope ls(P, K_REDUCE, 32.0 * npart, 4.0 * npart, s);
+  k_reduce4<<<1, 1024, 0, s>>>(P->d_partial, npart, P->d_sums, P->d_flag, P->d_sums + SUM_NONZERO);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_reduce_partials(snac_plan* P, int npart, double* out, cudaStream_t s) {
   LaunchScope ls(P, K_REDUCE, 32.0 * npart, 4.0 * npart, s);
-  k_reduce4<<<1, 1024, 0, s>>>(P->d_partial, npart, out);
+  k_reduce4<<<1, 1024, 0, s>>>(P->d_partial, npart, out, nullptr, nullptr);
   return cudaGetLastError();
 }
 

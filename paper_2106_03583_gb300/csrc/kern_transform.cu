@@ -113,7 +113,7 @@ __device__ __forceinline__ Cx<T> irdft_pre(Cx<T> xk, Cx<T> xmk, const Cx<T>& twn
 template <typename T, int TC>
 __global__ void __launch_bounds__(256) k_forward(const ChunkDev* __restrict__ chunks, const BlockDev* __restrict__ blk,
                                                  int n, int kind, Tw<T> tw, const double* __restrict__ in3,
-                                                 T* __restrict__ out, long long ncell) {
+                                                 T* __restrict__ out, long long ncell, T sub0) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int m = n / 2;
   Cx<T>* A = reinterpret_cast<Cx<T>*>(smem);
@@ -172,6 +172,7 @@ __global__ void __launch_bounds__(256) k_forward(const ChunkDev* __restrict__ ch
         y = (T)-2 * cmul(R[k * TC + c], tw.tw4b[k]).im;
       }
     }
+    if (q == 0) y -= sub0;  // F(x - shift0) = F(x) - shift0 F(1); F(1) is zero outside mode 0
     if (c < ch.ncol) out[(long long)q * ncell + B.off + ch.c0 + c] = y;
   }
 }
@@ -262,14 +263,18 @@ Tw<T> make_tw(const snac_plan* P, const void* base) {
 
 template <typename T, int TC>
 cudaError_t fwd_t(snac_plan* P, const std::vector<ChunkDev>& ch, const ChunkDev* dch, const void* twb, const double* in3,
-                  void* modes, cudaStream_t s) {
+                  void* modes, double shift0, cudaStream_t s) {
+  // F(1) in mode 0: n for the real DFT (half-complex), 2n for the DCT-II; the other kinds have no
+  // zero eigenvalue and are never shifted
+  const double f1 = P->kind == KIND_PP ? (double)P->nz : 2.0 * P->nz;
+  const T sub0 = (T)(shift0 * f1);
   const size_t smem = 2 * (size_t)(P->nz / 2) * TC * sizeof(Cx<T>);
   cudaFuncSetAttribute(k_forward<T, TC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   const double n3 = (double)P->n3;
   // read the FP64 field, write the modes; FFT model 2.5 log2(n) flops per point plus pre/post-processing
   LaunchScope ls(P, K_FORWARD, (8.0 + sizeof(T)) * n3, (2.5 * std::log2((double)P->nz) + 8.0) * n3, s);
   k_forward<T, TC><<<(unsigned)ch.size(), 256, smem, s>>>(dch, P->lev[0].d_blk, P->nz, P->kind, make_tw<T>(P, twb), in3,
-                                                          (T*)modes, P->lev[0].ncell);
+                                                          (T*)modes, P->lev[0].ncell, sub0);
   return cudaGetLastError();
 }
 
@@ -288,9 +293,11 @@ cudaError_t bwd_t(snac_plan* P, const std::vector<ChunkDev>& ch, const ChunkDev*
 
 }  // namespace
 
-cudaError_t launch_forward(snac_plan* P, const double* in3, void* modes, cudaStream_t s) {
-  if (P->precision == SNAC_FP64) return fwd_t<double, 8>(P, P->chunks64, P->d_chunks64, P->d_tw64, in3, modes, s);
-  return fwd_t<float, 16>(P, P->chunks32, P->d_chunks32, P->d_tw32, in3, modes, s);
+cudaError_t launch_forward(snac_plan* P, const double* in3, void* modes, double shift0, cudaStream_t s) {
+  if (shift0 != 0.0 && P->kind != KIND_PP && P->kind != KIND_NN) return cudaErrorInvalidValue;
+  if (P->precision == SNAC_FP64)
+    return fwd_t<double, 8>(P, P->chunks64, P->d_chunks64, P->d_tw64, in3, modes, shift0, s);
+  return fwd_t<float, 16>(P, P->chunks32, P->d_chunks32, P->d_tw32, in3, modes, shift0, s);
 }
 
 cudaError_t launch_backward_update(snac_plan* P, const void* modes, double* p3, cudaStream_t s) {

@@ -657,14 +657,15 @@ int create(snac_plan** out, int32_t nblocks, const snac_block* blocks, int32_t h
     for (HostLevel& lv : P->lev)
       if ((st = upload_level(P, lv, inner))) break;
     if (st) break;
-    // z operator pieces (uniform spacing, ghosts of the pair)
+    // z operator pieces (uniform spacing). The ends are written as a mirrored ghost on the cell
+    // itself: Neumann ghost = p_0 (coefficient +1/dz^2), Dirichlet ghost = -p_0 (-1/dz^2); the
+    // diagonal is then -2/dz^2 on every plane.
     const double iz2 = 1.0 / (P->dz * P->dz);
     for (int k = 0; k < P->nz; ++k) {
       const bool per = P->kind == KIND_PP;
-      Coef<double> c{(k > 0 || per) ? iz2 : 0.0, (k < P->nz - 1 || per) ? iz2 : 0.0, 0.0, P->dz};
-      c.d = -(c.lo + c.hi);
-      if (!per && k == 0 && zl == SNAC_BC_DIRICHLET) c.d -= 2.0 * iz2;
-      if (!per && k == P->nz - 1 && zh == SNAC_BC_DIRICHLET) c.d -= 2.0 * iz2;
+      Coef<double> c{iz2, iz2, -2.0 * iz2, P->dz};
+      if (!per && k == 0) c.lo = zl == SNAC_BC_DIRICHLET ? -iz2 : iz2;
+      if (!per && k == P->nz - 1) c.hi = zh == SNAC_BC_DIRICHLET ? -iz2 : iz2;
       P->cz.push_back(c);
     }
     if ((st = upload(P, &P->d_cz, P->cz))) break;
@@ -723,12 +724,12 @@ int create(snac_plan** out, int32_t nblocks, const snac_block* blocks, int32_t h
     // per-CTA partial sums: the 3-D residual grid (tiles x z split) or a plane reduction (MEAN_CTAS)
     P->npartial = std::max((int)P->lev[0].tiles.size() * zsplit, MEAN_CTAS);
     if ((st = dmalloc(P, &P->d_partial, (size_t)P->npartial * 4))) break;
-    if ((st = dmalloc(P, &P->d_sums, 8))) break;
+    if ((st = dmalloc(P, &P->d_sums, SUM_SLOTS)) || (st = dmalloc(P, &P->d_flag, 1))) break;
     // per-mode, per-tile partial sums (basic tiles; the fused tiles are fewer)
     if ((st = dmalloc(P, &P->d_mode_part, (size_t)P->nz * std::max<size_t>(P->lev[0].tiles.size(), 64)))) break;
     if ((st = dmalloc(P, &P->d_mode_norm2, (size_t)P->nz))) break;
     if ((st = dmalloc(P, &P->d_active, (size_t)P->nz))) break;
-    if (cudaMallocHost(&P->h_sums, 8 * sizeof(double)) != cudaSuccess ||
+    if (cudaMallocHost(&P->h_sums, SUM_SLOTS * sizeof(double)) != cudaSuccess ||
         cudaMallocHost(&P->h_mode_norm2, P->nz * sizeof(double)) != cudaSuccess ||
         cudaMallocHost(&P->h_active, P->nz * sizeof(int)) != cudaSuccess) {
       st = fail(SNAC_ERR_OOM, "pinned host allocation");

@@ -28,7 +28,9 @@ constexpr int TILE_Y = 8;
 constexpr int TILE_THREADS = TILE_X * TILE_Y;
 constexpr int MAX_NZ = 1024;
 constexpr int MAX_COARSE = 256;
-constexpr int MEAN_CTAS = 2 * 152;  // CTAs of the grid-stride reductions over one mode plane
+constexpr int MEAN_CTAS = 2 * 152;
+constexpr int SUM_SLOTS = 16;     // d_sums / h_sums: [0..3] residual or pre-pass, [4..7] mean fix
+constexpr int SUM_NONZERO = 8;    // d_sums slot of the pre-pass's nonzero-guess flag  // CTAs of the grid-stride reductions over one mode plane
 constexpr int FTILE_X = 52;         // tile of the fused multigrid kernels (64x64 window with the halo)
 constexpr int FTILE_Y = 52;
 constexpr int FUSED_MIN_BLOCK = 16;  // fused kernels on levels whose blocks are all this wide
@@ -179,7 +181,8 @@ struct snac_plan {
   double* d_r3 = nullptr;       // 3-D residual
   double* d_partial = nullptr;  // per-CTA partial sums
   int npartial = 0;
-  double* d_sums = nullptr;     // 4 reduced sums
+  double* d_sums = nullptr;     // reduced sums (SUM_SLOTS)
+  int* d_flag = nullptr;        // nonzero-initial-guess flag of the pre-pass
   double* d_mode_part = nullptr;  // per-mode, per-tile partial sums of squares
   double* d_mode_norm2 = nullptr; // per-mode ||r_q||^2
   int* d_active = nullptr;
@@ -203,9 +206,11 @@ namespace snac {
 // ---- launchers (field kernels: 3-D FP64 residual and reductions) ----
 // mode 0: r = (f - fshift) - A p; d_sums = {||r||^2, ||f - fshift||^2 if need_f2, sum V p if need_vp}
 // mode 1: r = A p
-// mode 2: d_sums = {sum V f, sum V |f|, ||f||^2}  (p, r unused)
 cudaError_t launch_field3d(snac_plan* P, int mode, const double* f, const double* p, double* r, double fshift,
                            bool need_f2, bool need_vp, cudaStream_t s);
+// d_sums = {sum V f, sum V |f|, ||f||^2, sum f} (V sums only for singular plans) and
+// d_sums[SUM_NONZERO] = 1 if p has a nonzero entry, else 0
+cudaError_t launch_prepass(snac_plan* P, const double* f, const double* p, cudaStream_t s);
 // reduce d_partial[npart][4] into out[4] (device)
 cudaError_t launch_reduce_partials(snac_plan* P, int npart, double* out, cudaStream_t s);
 // make the update of the singular mode 0 keep the volume-weighted mean of p at zero
@@ -214,7 +219,8 @@ cudaError_t launch_fix_mean(snac_plan* P, void* u0, cudaStream_t s);
 cudaError_t launch_shift(snac_plan* P, double* p, const double* d_c, cudaStream_t s);
 
 // ---- transforms ----
-cudaError_t launch_forward(snac_plan* P, const double* in3, void* modes, cudaStream_t s);
+// modes = F(in3 - shift0) along z (shift0 != 0 only for the kinds with a zero eigenvalue)
+cudaError_t launch_forward(snac_plan* P, const double* in3, void* modes, double shift0, cudaStream_t s);
 cudaError_t launch_backward_update(snac_plan* P, const void* modes, double* p3, cudaStream_t s);
 
 // ---- multigrid ----

@@ -98,8 +98,8 @@ int mode_solves(snac_plan* P, double target, cudaStream_t s, int* cycles_out) {
   return SNAC_OK;
 }
 
-int read_sums(snac_plan* P, cudaStream_t s) {
-  CK(cudaMemcpyAsync(P->h_sums, P->d_sums, 4 * sizeof(double), cudaMemcpyDeviceToHost, s));
+int read_sums(snac_plan* P, cudaStream_t s, int n = 4) {
+  CK(cudaMemcpyAsync(P->h_sums, P->d_sums, n * sizeof(double), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
     profile_resolve(P);
   return SNAC_OK;
@@ -112,9 +112,14 @@ int run_solve(snac_plan* P, const double* f, double* p, double tol, cudaStream_t
   std::fill(P->mode_cycles.begin(), P->mode_cycles.end(), 0);
   double fshift = 0.0;
   int st;
+  // pre-pass: statistics of f, and whether the initial guess is zero (then r = f - fshift at k = 0
+  // and the first residual pass is not needed)
+  CK(launch_prepass(P, f, p, s));
+  if ((st = read_sums(P, s, SUM_NONZERO + 1))) return st;
+  const bool p_zero = P->h_sums[SUM_NONZERO] == 0.0;
+  const double f2 = P->h_sums[2], sum_f = P->h_sums[3];
+  if (!std::isfinite(f2)) return SNAC_ERR_NONFINITE;
   if (P->singular) {
-    CK(launch_field3d(P, 2, f, nullptr, nullptr, 0.0, false, false, s));
-    if ((st = read_sums(P, s))) return st;
     const double vf = P->h_sums[0], vaf = P->h_sums[1];
     if (!std::isfinite(vf) || !std::isfinite(vaf)) return SNAC_ERR_NONFINITE;
     if (std::fabs(vf) > 1e-12 * vaf) {
@@ -124,23 +129,32 @@ int run_solve(snac_plan* P, const double* f, double* p, double tol, cudaStream_t
     fshift = vf / P->vol_total;
     P->info.removed_mean = fshift;
   }
+  // ||f - fshift||^2 = ||f||^2 - fshift (2 sum f - N fshift)
+  const double fn_pre = std::sqrt(std::max(0.0, f2 - fshift * (2.0 * sum_f - (double)P->n3 * fshift)));
   const bool mixed = P->precision == SNAC_MIXED;
   double prev_rel = INFINITY, fn = 0.0;
   bool updated = false;
   std::vector<int> cyc(P->nz);
   for (int k = 0;; ++k) {
-    // ||f|| is needed once; sum V p only for singular problems (zero-mean update)
-    CK(launch_field3d(P, 0, f, p, P->d_r3, fshift, k == 0, P->singular, s));
-    if ((st = read_sums(P, s))) return st;
-    if (k == 0) fn = std::sqrt(P->h_sums[1]);
-    const double rn = std::sqrt(P->h_sums[0]);
+    const bool from_f = k == 0 && p_zero;
+    double rn;
+    if (from_f) {
+      fn = rn = fn_pre;
+      if (P->singular) CK(cudaMemsetAsync(P->d_sums + 2, 0, sizeof(double), s));  // sum V p = 0
+    } else {
+      // ||f|| is needed once; sum V p only for singular problems (zero-mean update)
+      CK(launch_field3d(P, 0, f, p, P->d_r3, fshift, k == 0, P->singular, s));
+      if ((st = read_sums(P, s))) return st;
+      if (k == 0) fn = std::sqrt(P->h_sums[1]);
+      rn = std::sqrt(P->h_sums[0]);
+    }
     if (!std::isfinite(rn) || !std::isfinite(fn)) return SNAC_ERR_NONFINITE;
     P->info.rhs_norm = fn;
     P->info.outer_iters = k;
     if (fn == 0.0) {  // zero right-hand side: p = 0
       CK(cudaMemsetAsync(p, 0, (size_t)P->n3 * sizeof(double), s));
       CK(cudaStreamSynchronize(s));
-    profile_resolve(P);
+      profile_resolve(P);
       P->info.rel_res = 0.0;
       return SNAC_OK;
     }
@@ -152,7 +166,7 @@ int run_solve(snac_plan* P, const double* f, double* p, double tol, cudaStream_t
       if (P->singular && !updated) {  // the initial guess was kept: return its zero-mean shift
         CK(launch_shift(P, p, P->d_sums + 3, s));
         CK(cudaStreamSynchronize(s));
-    profile_resolve(P);
+        profile_resolve(P);
       }
       return done ? SNAC_OK : SNAC_ERR_NOT_CONVERGED;
     }
@@ -160,7 +174,8 @@ int run_solve(snac_plan* P, const double* f, double* p, double tol, cudaStream_t
     // target of this defect-correction step
     double target = 0.5 * tol * fn;
     if (mixed) target = std::max(target, P->inner_reduction * rn);
-    CK(launch_forward(P, P->d_r3, P->lev[0].d_f, s));
+    if (from_f) CK(launch_forward(P, f, P->lev[0].d_f, fshift, s));
+    else CK(launch_forward(P, P->d_r3, P->lev[0].d_f, 0.0, s));
     if ((st = mode_solves(P, target, s, cyc.data()))) return st;
     for (int q = 0; q < P->nz; ++q) {
       P->mode_cycles[q] = cyc[q];
@@ -213,7 +228,7 @@ int snac_forward_transform(snac_plan* plan, const double* d_in, void* d_modes, v
   if (st) return st;
   if (!d_in || !d_modes) return SNAC_ERR_INVALID_ARG;
   cudaStream_t s = (cudaStream_t)stream;
-  CK(launch_forward(plan, d_in, d_modes, s));
+  CK(launch_forward(plan, d_in, d_modes, 0.0, s));
   CK(cudaStreamSynchronize(s));
   profile_resolve(plan);
   return SNAC_OK;

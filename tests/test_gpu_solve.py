@@ -92,6 +92,32 @@ def test_warm_start_and_constant_shift():
     assert rel(host(p), p1) <= 1e-12
 
 
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("zpair,walls", [("NN", ("N", "N", "N", "N")), ("DD", ("D", "N", "N", "N"))])
+def test_zero_guess_shortcut_matches_residual_path(precision, zpair, walls):
+    """A zero initial guess skips the first residual pass (r = f - mean). The returned solution and
+    ||f - mean|| agree with a run whose guess is a tiny nonzero vector (the full residual path), and
+    a guess of negative zeros counts as zero."""
+    import torch
+    blocks = make("2x2", n=16, nz=8, zpair=zpair, walls=walls, stretched=True)
+    g = ogrid.Grid(blocks)
+    f = inputs.divergence_rhs(blocks, 5)
+    vol = g.from_planes(g.vol)
+    mean = np.dot(vol, f) / vol.sum() if g.singular else 0.0
+    p0, info0, pl = gpu_solve(blocks, f, precision)
+    assert info0["status"] == 0 and info0["rel_res"] <= TOL
+    assert abs(info0["rhs_norm"] - np.linalg.norm(f - mean)) <= 1e-12 * np.linalg.norm(f)
+    tiny = np.zeros_like(f)
+    tiny[7] = 1e-300
+    p = dev(tiny)
+    info1 = pl.solve(dev(f), p, tol=TOL)
+    assert abs(info1["rhs_norm"] - info0["rhs_norm"]) <= 1e-13 * info0["rhs_norm"]
+    assert rel(host(p), p0) <= 1e-9
+    p = torch.full((len(f),), -0.0, dtype=torch.float64, device="cuda")
+    info2 = pl.solve(dev(f), p, tol=TOL)
+    assert info2["outer_iters"] == info0["outer_iters"] and rel(host(p), p0) <= 1e-15
+
+
 def test_errors():
     import torch
     blocks = make("2x2", n=8, nz=8, zpair="NN", walls=("N", "N", "N", "N"))
