@@ -33,6 +33,16 @@ WORKLOAD = ("mb2x2: 2x2 blocks of 256x256 cells (assembled 512x512, x uniform [0
             "Neumann walls) x n_z=256 Neumann-Neumann (DCT-II) on [0,1]; f = D u, random-phase k^-5/3 "
             "velocity; zero initial guess each solve")
 FP64_ALU_PEAK = 152 * 2 * 2 * 2.07e9   # SMs x FP64 FMA/clk/SM x 2 flop x max SM clock = 1.259 TFLOP/s
+# kernels whose arithmetic is FP64 in every plan, and those that are FP64 in an FP64 plan: their
+# roof is the FP64 pipe, not HBM
+FP64_ALWAYS = {"field3d"}
+FP64_IN_FP64_PLAN = {"smooth", "restrict", "prolong", "mode_resid", "mode_apply", "forward_transform",
+                     "backward_update", "coarse_solve"}
+# DRAM traffic of one ncu-captured launch (dram__bytes_read.sum + dram__bytes_write.sum) divided by that
+# launch's algorithmic bytes, with the sha256 of the kernel's source file when it was captured. The
+# bench scales the ratio to its own launches (traffic grows in proportion to the cells processed) and
+# reports null once the source differs from the captured one. Captures: profiles/*.md.
+TRAFFIC = {}
 
 
 def parse():
@@ -116,11 +126,12 @@ def dist():
     return world, rank, local
 
 
-def base_line(args, world):
+def base_line(args, world, precision="fp64"):
+    dtype = "f64" if precision == "fp64" else "f32 multigrid and transforms, f64 residual and update"
     return {"metric": METRIC, "unit": "solves/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": dtype, "data": "synthetic",
             "config": {"workload": WORKLOAD if args.workload == "mb2x2" else args.workload, "tol": args.tol,
-                       "precision": "fp64", "parallelism": f"replicas x{world}",
+                       "precision": precision, "parallelism": f"replicas x{world}",
                        "l2": "inputs larger than L2 (537 MB per float64 field), no flush"}}
 
 
@@ -182,21 +193,38 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def _sha256(rel):
+    import hashlib
+    try:
+        with open(os.path.join(ROOT, rel), "rb") as fh:
+            return hashlib.sha256(fh.read()).hexdigest()
+    except OSError:
+        return None
+
+
+def traffic_per_launch(name, precision, alg_bytes_per_launch):
+    t = TRAFFIC.get((name, precision))
+    if not t or _sha256(t["src"]) != t["sha256"]:
+        return None
+    return t["ratio"] * alg_bytes_per_launch
+
+
 def roofline(stats, precision, hbm_peak, hbm_kind, K):
     """The dominant kernel (largest summed CUDA-event time) against its bound."""
     name = max(stats, key=lambda k: stats[k]["ms"])
     s = stats[name]
     per = max(s["launches"], 1)
     dur_s = s["ms"] / per * 1e-3
-    if precision == "fp64" and name in ("smooth", "restrict", "prolong", "mode_resid", "field3d", "mode_apply"):
+    if name in FP64_ALWAYS or (precision == "fp64" and name in FP64_IN_FP64_PLAN):
         ach = s["flops"] / per / dur_s / 1e12
         r = {"bound": "alu", "achieved": ach, "peak": FP64_ALU_PEAK / 1e12, "unit": "TFLOP/s",
              "peak_kind": "derived FP64: 152 SMs x 2 FMA/clk x 2 flop x 2.07 GHz"}
     else:
         ach = s["bytes"] / per / dur_s / 1e9
         r = {"bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s", "peak_kind": hbm_kind}
-    r.update({"frac": r["achieved"] / r["peak"], "traffic": None, "kernel": name, "launches_per_step": per / K,
-              "avg_launch_us": dur_s * 1e6})
+    r.update({"frac": r["achieved"] / r["peak"], "traffic": traffic_per_launch(name, precision, s["bytes"] / per),
+              "kernel": name, "launches_per_step": per / K, "avg_launch_us": dur_s * 1e6,
+              "alg_bytes_per_launch": s["bytes"] / per})
     return r
 
 
@@ -295,20 +323,21 @@ def run_snac(args):
                         for k, v in stats.items() if v["launches"]},
             "clocks": ck_res,
         }
-        if prec == "fp64":
+        if clocks is None or prec == "fp64":
             clocks = ck_res
         plan.close()
     if rank != 0:
         return
-    main = results.get("fp64") or next(iter(results.values()))
-    line = base_line(args, world)
+    main_prec = "fp64" if "fp64" in results else next(iter(results))
+    main = results[main_prec]
+    line = base_line(args, world, main_prec)
     line.update({"value": main["value"], "ms_per_step": main["ms_per_step"],
                  "p50_ms": main["p50_ms"], "p99_ms": main["p99_ms"], "hbm_gbs_model": main["hbm_gbs_model"],
                  "roofline": main["roofline"], "e2e": main["e2e"], "gpu_launches": main["gpu_launches"],
                  "clocks": clocks, "rel_res": main["rel_res"], "all_converged": main["all_converged"],
                  "kernels": main["kernels"]})
     line["config"]["n_cells"] = n3
-    if "mixed" in results:
+    if "mixed" in results and main_prec != "mixed":
         m = dict(results["mixed"])
         m.pop("clocks", None)
         line["mixed"] = m

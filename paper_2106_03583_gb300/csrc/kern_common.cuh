@@ -11,6 +11,15 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
+// Warp sum in the kernel's own type: FP32 kernels keep their partial norms in FP32 up to the warp
+// (GB300 issues FP64 at 1/64 of the FP32 rate) and widen one value per warp.
+template <typename T>
+__device__ __forceinline__ T warp_sum_t(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
 // The four x-y neighbours of cell (i, j) of block b: (block, index within that block's plane).
 // Inside the block the neighbour is the adjacent cell; across a connected (or periodic) face the
 // facing cell of the connected block (faces coincide, Sec. 3.1); on a physical face the cell itself

@@ -451,14 +451,14 @@ __global__ void __launch_bounds__(FTHREADS, 2)
       // sum of squared residuals over the tile's cells (only red cells carry one after a sweep)
       T rr[RPW];
       strip_residuals(C, S, buf, sg, rr);
-      double r2 = 0.0;
+      T r2 = 0;
       if (in_tile(2 * lane, tb.tw)) {
 #pragma unroll
         for (int r = 0; r < RPW; ++r)
-          if (in_tile(RPW * warp + r, tb.th)) r2 += (double)rr[r] * (double)rr[r];
+          if (in_tile(RPW * warp + r, tb.th)) r2 = fma(rr[r], rr[r], r2);
       }
-      r2 = warp_sum(r2);
-      if (lane == 0) S.wsum[warp] = r2;
+      r2 = warp_sum_t(r2);  // in the kernel's type, widened once per warp
+      if (lane == 0) S.wsum[warp] = (double)r2;
       __syncthreads();
       if (threadIdx.x == 0) {
         double sum = 0.0;

@@ -196,7 +196,7 @@ __global__ void __launch_bounds__(TILE_THREADS) k_mode_resid2(LevelView<T> L, co
     j = t.y0 + (threadIdx.x / TILE_X);
   }
   const int q = active[blockIdx.y];
-  double r2 = 0.0;
+  T r2 = 0;
   if (i < B.nx && j < B.ny) {
     const long long base = (long long)q * L.ncell;
     long long w, e, s, n;
@@ -205,11 +205,11 @@ __global__ void __launch_bounds__(TILE_THREADS) k_mode_resid2(LevelView<T> L, co
     const Coef<T> cx = L.cx[B.xo + i], cy = L.cy[B.yo + j];
     const T diag = cx.d + cy.d + sigma[q];
     const T r = f[base + c] - apply_row(cx, cy, diag, u[base + c], u[base + w], u[base + e], u[base + s], u[base + n]);
-    r2 = (double)r * (double)r;
+    r2 = r * r;
   }
-  r2 = warp_sum(r2);
+  r2 = warp_sum_t(r2);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  if (lane == 0) sh[warp] = r2;
+  if (lane == 0) sh[warp] = (double)r2;
   __syncthreads();
   if (warp == 0) {
     double v = lane < (int)(blockDim.x >> 5) ? sh[lane] : 0.0;
@@ -228,14 +228,14 @@ __global__ void __launch_bounds__(256) k_mode_sumsq(const T* __restrict__ f, lon
   __shared__ double sh[32];
   const int q = active[blockIdx.y];
   const T* fq = f + (long long)q * ncell;
-  double s = 0.0;
+  T s = 0;
   for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < ncell; c += (long long)gridDim.x * blockDim.x) {
-    const double v = (double)fq[c];
+    const T v = fq[c];
     s = fma(v, v, s);
   }
-  s = warp_sum(s);
+  s = warp_sum_t(s);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  if (lane == 0) sh[warp] = s;
+  if (lane == 0) sh[warp] = (double)s;
   __syncthreads();
   if (warp == 0) {
     double v = lane < (int)(blockDim.x >> 5) ? sh[lane] : 0.0;

@@ -110,10 +110,11 @@ __device__ __forceinline__ Cx<T> irdft_pre(Cx<T> xk, Cx<T> xmk, const Cx<T>& twn
   return {E.re - O.im, E.im + O.re};  // E + i O
 }
 
-template <typename T, int TC>
+template <typename T, int TC, int KIND>
 __global__ void __launch_bounds__(256) k_forward(const ChunkDev* __restrict__ chunks, const BlockDev* __restrict__ blk,
-                                                 int n, int kind, Tw<T> tw, const double* __restrict__ in3,
+                                                 int n, Tw<T> tw, const double* __restrict__ in3,
                                                  T* __restrict__ out, long long ncell, T sub0) {
+  constexpr int kind = KIND;
   extern __shared__ __align__(16) unsigned char smem[];
   const int m = n / 2;
   Cx<T>* A = reinterpret_cast<Cx<T>*>(smem);
@@ -177,10 +178,11 @@ __global__ void __launch_bounds__(256) k_forward(const ChunkDev* __restrict__ ch
   }
 }
 
-template <typename T, int TC>
+template <typename T, int TC, int KIND>
 __global__ void __launch_bounds__(256) k_backward(const ChunkDev* __restrict__ chunks, const BlockDev* __restrict__ blk,
-                                                  int n, int kind, Tw<T> tw, const T* __restrict__ modes,
+                                                  int n, Tw<T> tw, const T* __restrict__ modes,
                                                   double* __restrict__ p3, long long ncell, double inv_theta) {
+  constexpr int kind = KIND;
   extern __shared__ __align__(16) unsigned char smem[];
   const int m = n / 2;
   Cx<T>* A = reinterpret_cast<Cx<T>*>(smem);
@@ -269,12 +271,21 @@ cudaError_t fwd_t(snac_plan* P, const std::vector<ChunkDev>& ch, const ChunkDev*
   const double f1 = P->kind == KIND_PP ? (double)P->nz : 2.0 * P->nz;
   const T sub0 = (T)(shift0 * f1);
   const size_t smem = 2 * (size_t)(P->nz / 2) * TC * sizeof(Cx<T>);
-  cudaFuncSetAttribute(k_forward<T, TC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   const double n3 = (double)P->n3;
   // read the FP64 field, write the modes; FFT model 2.5 log2(n) flops per point plus pre/post-processing
   LaunchScope ls(P, K_FORWARD, (8.0 + sizeof(T)) * n3, (2.5 * std::log2((double)P->nz) + 8.0) * n3, s);
-  k_forward<T, TC><<<(unsigned)ch.size(), 256, smem, s>>>(dch, P->lev[0].d_blk, P->nz, P->kind, make_tw<T>(P, twb), in3,
-                                                          (T*)modes, P->lev[0].ncell, sub0);
+  auto go = [&](auto kern) {
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    kern<<<(unsigned)ch.size(), 256, smem, s>>>(dch, P->lev[0].d_blk, P->nz, make_tw<T>(P, twb), in3, (T*)modes,
+                                                P->lev[0].ncell, sub0);
+  };
+  switch (P->kind) {
+    case KIND_PP: go(k_forward<T, TC, KIND_PP>); break;
+    case KIND_NN: go(k_forward<T, TC, KIND_NN>); break;
+    case KIND_DD: go(k_forward<T, TC, KIND_DD>); break;
+    case KIND_ND: go(k_forward<T, TC, KIND_ND>); break;
+    default: go(k_forward<T, TC, KIND_DN>); break;
+  }
   return cudaGetLastError();
 }
 
@@ -282,12 +293,21 @@ template <typename T, int TC>
 cudaError_t bwd_t(snac_plan* P, const std::vector<ChunkDev>& ch, const ChunkDev* dch, const void* twb, const void* modes,
                   double* p3, cudaStream_t s) {
   const size_t smem = 2 * (size_t)(P->nz / 2) * TC * sizeof(Cx<T>);
-  cudaFuncSetAttribute(k_backward<T, TC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   const double n3 = (double)P->n3;
   // read the modes, read and write the FP64 field
   LaunchScope ls(P, K_BACKWARD, (16.0 + sizeof(T)) * n3, (2.5 * std::log2((double)P->nz) + 10.0) * n3, s);
-  k_backward<T, TC><<<(unsigned)ch.size(), 256, smem, s>>>(dch, P->lev[0].d_blk, P->nz, P->kind, make_tw<T>(P, twb),
-                                                           (const T*)modes, p3, P->lev[0].ncell, 1.0 / P->theta);
+  auto go = [&](auto kern) {
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    kern<<<(unsigned)ch.size(), 256, smem, s>>>(dch, P->lev[0].d_blk, P->nz, make_tw<T>(P, twb), (const T*)modes, p3,
+                                                P->lev[0].ncell, 1.0 / P->theta);
+  };
+  switch (P->kind) {
+    case KIND_PP: go(k_backward<T, TC, KIND_PP>); break;
+    case KIND_NN: go(k_backward<T, TC, KIND_NN>); break;
+    case KIND_DD: go(k_backward<T, TC, KIND_DD>); break;
+    case KIND_ND: go(k_backward<T, TC, KIND_ND>); break;
+    default: go(k_backward<T, TC, KIND_DN>); break;
+  }
   return cudaGetLastError();
 }
 

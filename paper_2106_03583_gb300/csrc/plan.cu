@@ -703,7 +703,12 @@ int create(snac_plan** out, int32_t nblocks, const snac_block* blocks, int32_t h
       for (size_t l = 0; l + 1 < P->lev.size(); ++l)
         if ((st = dmalloc(P, &P->lev[l].d_invd, (size_t)P->nz * P->lev[l].ncell))) break;
       if (st) break;
-      if (launch_inverse_diagonals(P, 0) != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess) {
+      // on a private non-blocking stream: plan creation does not wait for other streams' work
+      cudaStream_t cs = nullptr;
+      bool ok = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) == cudaSuccess;
+      ok = ok && launch_inverse_diagonals(P, cs) == cudaSuccess && cudaStreamSynchronize(cs) == cudaSuccess;
+      if (cs) cudaStreamDestroy(cs);
+      if (!ok) {
         st = fail(SNAC_ERR_CUDA, "computing the inverse diagonals failed");
         break;
       }
