@@ -169,20 +169,21 @@ __device__ __forceinline__ void write_halo(Shared<T>& S, const Cells<T>& C, int 
   S.halo[buf][warp][1][1][lane] = C.u[RPW - 1][1];
 }
 
-template <typename T>
-__device__ __forceinline__ void read_edges(const Shared<T>& S, int buf, T (&sedge)[2], T (&nedge)[2]) {
+static_assert(RPW % 2 == 0, "a strip's last row has the parity of its second row");
+
+// The strip-edge neighbours a pass over the strip uses when its first row has colour parity PA:
+// row 0 reads the south strip's last row at parity PA, row RPW - 1 the north strip's first row at
+// parity PA ^ 1 (zero beyond the window).
+template <typename T, int PA>
+__device__ __forceinline__ void edge_values(const Shared<T>& S, int buf, T& south, T& north) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-  for (int p = 0; p < 2; ++p) {
-    sedge[p] = warp > 0 ? S.halo[buf][warp - 1][1][p][lane] : (T)0;
-    nedge[p] = warp < FWARPS - 1 ? S.halo[buf][warp + 1][0][p][lane] : (T)0;
-  }
+  south = warp > 0 ? S.halo[buf][warp - 1][1][PA][lane] : (T)0;
+  north = warp < FWARPS - 1 ? S.halo[buf][warp + 1][0][PA ^ 1][lane] : (T)0;
 }
 
 // Gauss-Seidel update of row r of the strip, the colour's cells having column parity P.
 template <typename T, int P>
-__device__ __forceinline__ void update_row(Cells<T>& C, const FusedTab<T>& tb, int r, int wj, int ry, int rx, T sn,
-                                           T nn) {
+__device__ __forceinline__ void update_row(Cells<T>& C, FP2<T> cx, FP2<T> cy, int r, int wj, T sn, T nn) {
   const int lane = threadIdx.x & 31;
   T w, e;
   if (P == 0) {
@@ -192,8 +193,6 @@ __device__ __forceinline__ void update_row(Cells<T>& C, const FusedTab<T>& tb, i
     w = C.u[r][0];
     e = __shfl_down_sync(0xffffffffu, C.u[r][0], 1);
   }
-  const FP2<T> cx = tb.xc[ry][P][lane];
-  const FP2<T> cy = tb.yc[rx][wj];
   T a = cx.a * w;
   a = fma(cx.b, e, a);
   a = fma(cy.a, sn, a);
@@ -203,23 +202,32 @@ __device__ __forceinline__ void update_row(Cells<T>& C, const FusedTab<T>& tb, i
   if (!edge) C.u[r][P] = v;
 }
 
-// One half-sweep of the strip; P0 = column parity of the colour in the strip's first row.
-template <typename T, int P0>
-__device__ __forceinline__ void half_sweep(Cells<T>& C, const FusedTab<T>& tb, const int (&ry)[RPW], int rx,
-                                           const T (&sedge)[2], const T (&nedge)[2]) {
-  const int warp = threadIdx.x >> 5;
+// One half-sweep of the strip; P0 = column parity of the colour in the strip's first row. UNI: all
+// rows of the strip lie in one region row, so the x coefficients are one pair per parity.
+template <typename T, int P0, bool UNI>
+__device__ __forceinline__ void half_sweep(Cells<T>& C, const Shared<T>& S, int buf, const int (&ry)[RPW], int rx) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  constexpr int PA = P0, PB = P0 ^ 1;
+  const FusedTab<T>& tb = S.tab;
+  T south, north;
+  edge_values<T, PA>(S, buf, south, north);
+  FP2<T> cxa, cxb;
+  if (UNI) {
+    cxa = tb.xc[ry[0]][PA][lane];
+    cxb = tb.xc[ry[0]][PB][lane];
+  }
 #pragma unroll
   for (int r = 0; r < RPW; ++r) {
     const int wj = RPW * warp + r;
-    constexpr int PA = P0, PB = P0 ^ 1;
-    if ((r & 1) == 0) {
-      const T sn = r > 0 ? C.u[r > 0 ? r - 1 : 0][PA] : sedge[PA];
-      const T nn = r < RPW - 1 ? C.u[r < RPW - 1 ? r + 1 : 0][PA] : nedge[PA];
-      update_row<T, PA>(C, tb, r, wj, ry[r], rx, sn, nn);
-    } else {
-      const T sn = r > 0 ? C.u[r > 0 ? r - 1 : 0][PB] : sedge[PB];
-      const T nn = r < RPW - 1 ? C.u[r < RPW - 1 ? r + 1 : 0][PB] : nedge[PB];
-      update_row<T, PB>(C, tb, r, wj, ry[r], rx, sn, nn);
+    const FP2<T> cy = tb.yc[rx][wj];
+    if ((r & 1) == 0) {  // parity PA; never the last row
+      const T sn = r > 0 ? C.u[r > 0 ? r - 1 : 0][PA] : south;
+      const T nn = C.u[r < RPW - 1 ? r + 1 : 0][PA];
+      update_row<T, PA>(C, UNI ? cxa : tb.xc[ry[r]][PA][lane], cy, r, wj, sn, nn);
+    } else {             // parity PB; never the first row
+      const T sn = C.u[r > 0 ? r - 1 : 0][PB];
+      const T nn = r < RPW - 1 ? C.u[r < RPW - 1 ? r + 1 : 0][PB] : north;
+      update_row<T, PB>(C, UNI ? cxb : tb.xc[ry[r]][PB][lane], cy, r, wj, sn, nn);
     }
   }
 }
@@ -234,6 +242,7 @@ __device__ void sweeps(Cells<T>& C, Shared<T>& S, int nu, int& buf, Hook&& after
   int ry[RPW];
 #pragma unroll
   for (int r = 0; r < RPW; ++r) ry[r] = S.tab.rowry[RPW * warp + r];
+  const bool uni = ry[0] == ry[RPW - 1];  // region rows are monotonic in the row
   const int rx = S.tab.colrx[lane];
   const int pbase = S.tab.pbase;
   buf = 0;
@@ -242,21 +251,23 @@ __device__ void sweeps(Cells<T>& C, Shared<T>& S, int nu, int& buf, Hook&& after
   after_first_barrier();
   for (int s = 0; s < 2 * nu; ++s) {
     const int colour = s & 1;
-    T sedge[2], nedge[2];
-    read_edges(S, buf, sedge, nedge);
     const int p0 = (colour - pbase - RPW * warp) & 1;
-    if (p0 == 0) half_sweep<T, 0>(C, S.tab, ry, rx, sedge, nedge);
-    else half_sweep<T, 1>(C, S.tab, ry, rx, sedge, nedge);
+    if (uni) {
+      if (p0 == 0) half_sweep<T, 0, true>(C, S, buf, ry, rx);
+      else half_sweep<T, 1, true>(C, S, buf, ry, rx);
+    } else {
+      if (p0 == 0) half_sweep<T, 0, false>(C, S, buf, ry, rx);
+      else half_sweep<T, 1, false>(C, S, buf, ry, rx);
+    }
     buf ^= 1;
     write_halo(S, C, buf);
     __syncthreads();
   }
 }
 
-// Residual of the cell of parity P in row r (the tile block's own coefficients: tile rows only).
+// Residual of the cell of parity P in row r with the tile block's own coefficients (tile rows only).
 template <typename T, int P>
-__device__ __forceinline__ T resid_row(const Cells<T>& C, const FusedTab<T>& tb, int r, int wj, T sn, T nn, T sg) {
-  const int lane = threadIdx.x & 31;
+__device__ __forceinline__ T resid_row(const Cells<T>& C, FP2<T> cx, T xd, FP2<T> cy, T yd, int r, T sn, T nn) {
   T w, e;
   if (P == 0) {
     w = __shfl_up_sync(0xffffffffu, C.u[r][1], 1);
@@ -265,34 +276,38 @@ __device__ __forceinline__ T resid_row(const Cells<T>& C, const FusedTab<T>& tb,
     w = C.u[r][0];
     e = __shfl_down_sync(0xffffffffu, C.u[r][0], 1);
   }
-  const FP2<T> cx = tb.xc[1][P][lane];
-  const FP2<T> cy = tb.yc[1][wj];
   T a = cx.a * w;
   a = fma(cx.b, e, a);
   a = fma(cy.a, sn, a);
   a = fma(cy.b, nn, a);
-  a = fma(tb.xd[1][P][lane] + tb.yd[1][wj] + sg, C.u[r][P], a);
+  a = fma(xd + yd, C.u[r][P], a);
   return C.f[r][P] - a;
 }
 
 // rr[r] = residual of the red cell of row r (the black cells carry none after a sweep ending on
 // black); P0 = column parity of the red cells in the strip's first row.
 template <typename T, int P0>
-__device__ __forceinline__ void red_residuals(const Cells<T>& C, const FusedTab<T>& tb, const T (&sedge)[2],
-                                              const T (&nedge)[2], T sg, T (&rr)[RPW]) {
-  const int warp = threadIdx.x >> 5;
+__device__ __forceinline__ void red_residuals(const Cells<T>& C, const Shared<T>& S, int buf, T sg, T (&rr)[RPW]) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  constexpr int PA = P0, PB = P0 ^ 1;
+  const FusedTab<T>& tb = S.tab;
+  T south, north;
+  edge_values<T, PA>(S, buf, south, north);
+  const FP2<T> cxa = tb.xc[1][PA][lane], cxb = tb.xc[1][PB][lane];
+  const T xda = tb.xd[1][PA][lane] + sg, xdb = tb.xd[1][PB][lane] + sg;
 #pragma unroll
   for (int r = 0; r < RPW; ++r) {
     const int wj = RPW * warp + r;
-    constexpr int PA = P0, PB = P0 ^ 1;
+    const FP2<T> cy = tb.yc[1][wj];
+    const T yd = tb.yd[1][wj];
     if ((r & 1) == 0) {
-      const T sn = r > 0 ? C.u[r > 0 ? r - 1 : 0][PA] : sedge[PA];
-      const T nn = r < RPW - 1 ? C.u[r < RPW - 1 ? r + 1 : 0][PA] : nedge[PA];
-      rr[r] = resid_row<T, PA>(C, tb, r, wj, sn, nn, sg);
+      const T sn = r > 0 ? C.u[r > 0 ? r - 1 : 0][PA] : south;
+      const T nn = C.u[r < RPW - 1 ? r + 1 : 0][PA];
+      rr[r] = resid_row<T, PA>(C, cxa, xda, cy, yd, r, sn, nn);
     } else {
-      const T sn = r > 0 ? C.u[r > 0 ? r - 1 : 0][PB] : sedge[PB];
-      const T nn = r < RPW - 1 ? C.u[r < RPW - 1 ? r + 1 : 0][PB] : nedge[PB];
-      rr[r] = resid_row<T, PB>(C, tb, r, wj, sn, nn, sg);
+      const T sn = C.u[r > 0 ? r - 1 : 0][PB];
+      const T nn = r < RPW - 1 ? C.u[r < RPW - 1 ? r + 1 : 0][PB] : north;
+      rr[r] = resid_row<T, PB>(C, cxb, xdb, cy, yd, r, sn, nn);
     }
   }
 }
@@ -301,11 +316,9 @@ __device__ __forceinline__ void red_residuals(const Cells<T>& C, const FusedTab<
 template <typename T>
 __device__ __forceinline__ int strip_residuals(const Cells<T>& C, const Shared<T>& S, int buf, T sg, T (&rr)[RPW]) {
   const int warp = threadIdx.x >> 5;
-  T sedge[2], nedge[2];
-  read_edges(S, buf, sedge, nedge);
   const int p0 = (0 - S.tab.pbase - RPW * warp) & 1;
-  if (p0 == 0) red_residuals<T, 0>(C, S.tab, sedge, nedge, sg, rr);
-  else red_residuals<T, 1>(C, S.tab, sedge, nedge, sg, rr);
+  if (p0 == 0) red_residuals<T, 0>(C, S, buf, sg, rr);
+  else red_residuals<T, 1>(C, S, buf, sg, rr);
   return p0;
 }
 
