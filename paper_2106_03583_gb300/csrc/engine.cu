@@ -1,0 +1,414 @@
+// Serving engine (include/snac_engine.h): admission under a device-memory budget, a cache of
+// resident plans, and worker threads that each drive their own CUDA stream. Host code only; every
+// step of a solve runs in the library's kernels through snac_plan_create / snac_poisson_solve.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <list>
+#include <map>
+#include <mutex>
+#include <new>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "snac_engine.h"
+#include "snac_impl.h"
+
+namespace {
+
+using Clock = std::chrono::steady_clock;
+const Clock::time_point g_epoch = Clock::now();
+
+double now_s() { return std::chrono::duration<double>(Clock::now() - g_epoch).count(); }
+
+struct PlanSlot {
+  std::string key;
+  snac_plan* plan = nullptr;
+  uint64_t bytes = 0;
+  bool busy = false;
+  uint64_t last_use = 0;
+};
+
+enum class State { Queued, Ready, Running, Done };
+
+struct Request {
+  int64_t ticket = 0;
+  std::vector<std::vector<double>> dx;  // copies of the cell widths, 3 per block
+  std::vector<snac_block> blocks;       // h_dx pointing into dx
+  int32_t homog_axis = 2;
+  bool has_opt = false;
+  snac_options opt{};
+  const double* h_rhs = nullptr;
+  double* h_p = nullptr;
+  double tol = 0.0;
+  long long n3 = 0;
+  std::string key;
+  uint64_t buf_bytes = 0;      // device copies of f and p
+  uint64_t plan_estimate = 0;  // reservation while its plan is built
+  // progress
+  State state = State::Queued;
+  PlanSlot* slot = nullptr;
+  bool build_plan = false;
+  int status = SNAC_OK;
+  snac_solve_info info{};
+  snac_request_times times{};
+};
+
+template <typename T>
+void put(std::string& k, const T& v) {
+  k.append(reinterpret_cast<const char*>(&v), sizeof(T));
+}
+
+// Identity of a problem: everything snac_plan_create reads.
+std::string problem_key(const Request& r) {
+  std::string k;
+  put(k, r.homog_axis);
+  put(k, (int32_t)r.blocks.size());
+  for (size_t b = 0; b < r.blocks.size(); ++b) {
+    const snac_block& s = r.blocks[b];
+    for (int a = 0; a < 3; ++a) {
+      put(k, s.lo[a]);
+      put(k, s.hi[a]);
+      for (int sd = 0; sd < 2; ++sd) {
+        put(k, s.bc[a][sd]);
+        put(k, s.nbr[a][sd]);
+      }
+      k.append(reinterpret_cast<const char*>(r.dx[3 * b + a].data()), r.dx[3 * b + a].size() * sizeof(double));
+    }
+  }
+  put(k, (int32_t)r.has_opt);
+  if (r.has_opt) {
+    put(k, r.opt.precision);
+    put(k, r.opt.nu1);
+    put(k, r.opt.nu2);
+    put(k, r.opt.max_outer);
+    put(k, r.opt.max_cycles);
+    put(k, r.opt.max_coarse);
+    put(k, r.opt.fused);
+    put(k, r.opt.inner_reduction);
+  }
+  return k;
+}
+
+// Device bytes of a plan before it exists: the level hierarchy (u, f and, FP64, the inverse
+// diagonals, x 4/3 over levels; FP32 fused levels add a second iterate), the residual field and the
+// small tables, rounded up. Replaced by the plan's own count once it is built.
+uint64_t plan_estimate(long long n3, bool fp64) {
+  const double per_cell = fp64 ? 64.0 : 40.0;
+  return (uint64_t)(per_cell * (double)n3) + (64ull << 20);
+}
+
+}  // namespace
+
+struct snac_engine {
+  int device = 0;
+  snac_engine_options opt{};
+  std::mutex mu;
+  std::condition_variable cv_work, cv_done;
+  std::deque<Request*> queue;  // waiting for admission, arrival order
+  std::deque<Request*> ready;  // admitted, waiting for a worker
+  std::map<int64_t, Request*> tickets;
+  std::list<PlanSlot*> plans;
+  uint64_t used = 0, peak = 0, use_clock = 0;
+  int running = 0;
+  int64_t completed = 0, built = 0, evicted = 0, next_ticket = 1;
+  bool stopping = false;
+  std::vector<std::thread> threads;
+
+  void account(int64_t delta) {
+    used = (uint64_t)((int64_t)used + delta);
+    peak = std::max(peak, used);
+  }
+
+  // Idle plans beyond the cache size, least recently used first (caller holds mu).
+  void trim_cache(std::vector<snac_plan*>& dead) {
+    int idle = 0;
+    for (PlanSlot* s : plans) idle += s->busy ? 0 : 1;
+    while (idle > opt.max_cached_plans && evict_one(nullptr, dead)) --idle;
+  }
+
+  // Release the least recently used idle plan other than `keep` (caller holds mu).
+  bool evict_one(const PlanSlot* keep, std::vector<snac_plan*>& dead) {
+    auto victim = plans.end();
+    for (auto it = plans.begin(); it != plans.end(); ++it)
+      if (!(*it)->busy && *it != keep && (victim == plans.end() || (*it)->last_use < (*victim)->last_use)) victim = it;
+    if (victim == plans.end()) return false;
+    dead.push_back((*victim)->plan);
+    account(-(int64_t)(*victim)->bytes);
+    delete *victim;
+    plans.erase(victim);
+    ++evicted;
+    return true;
+  }
+
+  // Admit waiting requests, first fit in arrival order (caller holds mu).
+  void admit(std::vector<snac_plan*>& dead) {
+    for (auto it = queue.begin(); it != queue.end();) {
+      Request* r = *it;
+      PlanSlot* idle = nullptr;
+      for (PlanSlot* s : plans)
+        if (!s->busy && s->key == r->key && (!idle || s->last_use > idle->last_use)) idle = s;
+      const uint64_t need = r->buf_bytes + (idle ? 0 : r->plan_estimate);
+      while (used + need > opt.hbm_budget && evict_one(idle, dead)) {
+      }
+      if (used + need > opt.hbm_budget) {
+        ++it;
+        continue;
+      }
+      account((int64_t)need);
+      if (idle) {
+        idle->busy = true;
+        r->slot = idle;
+      } else {
+        r->build_plan = true;
+      }
+      r->state = State::Ready;
+      r->times.t_admit = now_s();
+      ready.push_back(r);
+      it = queue.erase(it);
+      cv_work.notify_one();
+    }
+  }
+
+  void worker(int id);
+  int run(Request* r, cudaStream_t s);
+};
+
+namespace {
+
+void destroy_plans(const std::vector<snac_plan*>& dead) {
+  for (snac_plan* p : dead) snac_plan_destroy(p);
+}
+
+}  // namespace
+
+// One request on stream s: build its plan if needed, copy f in, solve from zero, copy p out.
+int snac_engine::run(Request* r, cudaStream_t s) {
+  int st = SNAC_OK;
+  if (r->build_plan) {
+    snac_plan* pl = nullptr;
+    st = snac_plan_create(&pl, (int32_t)r->blocks.size(), r->blocks.data(), r->homog_axis,
+                          r->has_opt ? &r->opt : nullptr);
+    size_t bytes = 0;
+    if (st == SNAC_OK) snac_plan_workspace_bytes(pl, &bytes);
+    std::lock_guard<std::mutex> lk(mu);
+    account(-(int64_t)r->plan_estimate);
+    if (st != SNAC_OK) return st;
+    PlanSlot* slot = new (std::nothrow) PlanSlot{r->key, pl, (uint64_t)bytes, true, 0};
+    if (!slot) {
+      snac_plan_destroy(pl);
+      return SNAC_ERR_OOM;
+    }
+    account((int64_t)bytes);
+    plans.push_back(slot);
+    r->slot = slot;
+    ++built;
+  }
+  r->times.plan_reused = r->build_plan ? 0 : 1;
+  const size_t nb = (size_t)r->n3 * sizeof(double);
+  double *d_f = nullptr, *d_p = nullptr;
+  if (cudaMallocAsync((void**)&d_f, nb, s) != cudaSuccess || cudaMallocAsync((void**)&d_p, nb, s) != cudaSuccess) {
+    cudaGetLastError();
+    if (d_f) cudaFreeAsync(d_f, s);
+    cudaStreamSynchronize(s);
+    return SNAC_ERR_OOM;
+  }
+  bool ok = cudaMemcpyAsync(d_f, r->h_rhs, nb, cudaMemcpyHostToDevice, s) == cudaSuccess &&
+            cudaMemsetAsync(d_p, 0, nb, s) == cudaSuccess;
+  if (ok) {
+    st = snac_poisson_solve(r->slot->plan, d_f, d_p, r->tol, s);
+    snac_plan_info(r->slot->plan, &r->info);
+    if ((st == SNAC_OK || st == SNAC_ERR_NOT_CONVERGED) &&
+        cudaMemcpyAsync(r->h_p, d_p, nb, cudaMemcpyDeviceToHost, s) != cudaSuccess)
+      st = SNAC_ERR_CUDA;
+  } else {
+    st = SNAC_ERR_CUDA;
+  }
+  cudaFreeAsync(d_f, s);
+  cudaFreeAsync(d_p, s);
+  if (cudaStreamSynchronize(s) != cudaSuccess && st == SNAC_OK) st = SNAC_ERR_CUDA;
+  return st;
+}
+
+void snac_engine::worker(int id) {
+  cudaSetDevice(device);
+  cudaStream_t s = nullptr;
+  cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+  for (;;) {
+    Request* r = nullptr;
+    {
+      std::unique_lock<std::mutex> lk(mu);
+      cv_work.wait(lk, [&] { return stopping || !ready.empty(); });
+      if (ready.empty()) break;
+      r = ready.front();
+      ready.pop_front();
+      r->state = State::Running;
+      ++running;
+    }
+    r->times.t_start = now_s();
+    r->times.worker = id;
+    const int st = s ? run(r, s) : SNAC_ERR_CUDA;
+    r->times.t_done = now_s();
+    std::vector<snac_plan*> dead;
+    {
+      std::lock_guard<std::mutex> lk(mu);
+      account(-(int64_t)r->buf_bytes);
+      if (r->slot) {
+        r->slot->busy = false;
+        r->slot->last_use = ++use_clock;
+      }
+      r->status = st;
+      r->info.status = st;
+      r->state = State::Done;
+      --running;
+      ++completed;
+      trim_cache(dead);
+      admit(dead);
+    }
+    cv_done.notify_all();
+    destroy_plans(dead);
+  }
+  if (s) cudaStreamDestroy(s);
+}
+
+extern "C" {
+
+double snac_engine_clock(void) { return now_s(); }
+
+int snac_engine_create(snac_engine** out, const snac_engine_options* opt) {
+  if (!out) return SNAC_ERR_INVALID_ARG;
+  *out = nullptr;
+  snac_engine_options o{4, 64, 150000000000ull};
+  if (opt) o = *opt;
+  if (o.workers < 1 || o.workers > 64 || o.max_cached_plans < 0 || o.max_cached_plans > 4096 || o.hbm_budget == 0)
+    return SNAC_ERR_INVALID_ARG;
+  snac_engine* e = new (std::nothrow) snac_engine();
+  if (!e) return SNAC_ERR_OOM;
+  e->opt = o;
+  if (cudaGetDevice(&e->device) != cudaSuccess) {
+    cudaGetLastError();
+    delete e;
+    return SNAC_ERR_CUDA;
+  }
+  try {
+    for (int w = 0; w < o.workers; ++w) e->threads.emplace_back(&snac_engine::worker, e, w);
+  } catch (...) {
+    {
+      std::lock_guard<std::mutex> lk(e->mu);
+      e->stopping = true;
+    }
+    e->cv_work.notify_all();
+    for (std::thread& t : e->threads) t.join();
+    delete e;
+    return SNAC_ERR_OOM;
+  }
+  *out = e;
+  return SNAC_OK;
+}
+
+int snac_engine_submit(snac_engine* e, int32_t nblocks, const snac_block* blocks, int32_t homog_axis,
+                       const snac_options* opt, const double* h_rhs, double* h_p, double tol, int64_t* ticket) {
+  if (!e || !blocks || nblocks < 1 || !h_rhs || !h_p || !ticket || !(tol > 0.0) || !std::isfinite(tol))
+    return SNAC_ERR_INVALID_ARG;
+  if (homog_axis != 2) return SNAC_ERR_INVALID_ARG;
+  int st = snac::check_layout(nblocks, blocks);
+  if (st) return st;
+  Request* r = new (std::nothrow) Request();
+  if (!r) return SNAC_ERR_OOM;
+  r->homog_axis = homog_axis;
+  r->has_opt = opt != nullptr;
+  if (opt) r->opt = *opt;
+  r->h_rhs = h_rhs;
+  r->h_p = h_p;
+  r->tol = tol;
+  r->blocks.assign(blocks, blocks + nblocks);
+  r->dx.resize(3 * (size_t)nblocks);
+  long long n3 = 0;
+  for (int b = 0; b < nblocks; ++b) {
+    long long cells = 1;
+    for (int a = 0; a < 3; ++a) {
+      const long long n = blocks[b].hi[a] - blocks[b].lo[a] + 1;
+      r->dx[3 * b + a].assign(blocks[b].h_dx[a], blocks[b].h_dx[a] + n);
+      r->blocks[b].h_dx[a] = r->dx[3 * b + a].data();
+      cells *= n;
+    }
+    n3 += cells;
+  }
+  r->n3 = n3;
+  r->key = problem_key(*r);
+  r->buf_bytes = 16ull * (uint64_t)n3;
+  r->plan_estimate = plan_estimate(n3, !(opt && opt->precision == SNAC_MIXED));
+  if (r->buf_bytes + r->plan_estimate > e->opt.hbm_budget) {
+    delete r;
+    return SNAC_ERR_OOM;
+  }
+  std::vector<snac_plan*> dead;
+  {
+    std::lock_guard<std::mutex> lk(e->mu);
+    if (e->stopping) {
+      delete r;
+      return SNAC_ERR_INVALID_ARG;
+    }
+    r->ticket = e->next_ticket++;
+    r->times.t_submit = now_s();
+    e->tickets[r->ticket] = r;
+    e->queue.push_back(r);
+    e->admit(dead);
+    *ticket = r->ticket;
+  }
+  destroy_plans(dead);
+  return SNAC_OK;
+}
+
+int snac_engine_wait(snac_engine* e, int64_t ticket, snac_solve_info* info, snac_request_times* times) {
+  if (!e) return SNAC_ERR_INVALID_ARG;
+  std::unique_lock<std::mutex> lk(e->mu);
+  auto it = e->tickets.find(ticket);
+  if (it == e->tickets.end()) return SNAC_ERR_INVALID_ARG;
+  Request* r = it->second;
+  e->cv_done.wait(lk, [&] { return r->state == State::Done; });
+  if (info) *info = r->info;
+  if (times) *times = r->times;
+  const int st = r->status;
+  e->tickets.erase(it);
+  delete r;
+  return st;
+}
+
+int snac_engine_get_stats(snac_engine* e, snac_engine_stats* st) {
+  if (!e || !st) return SNAC_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lk(e->mu);
+  st->bytes_in_use = e->used;
+  st->bytes_peak = e->peak;
+  st->plans_cached = (int32_t)e->plans.size();
+  st->queued = (int32_t)e->queue.size();
+  st->running = (int32_t)(e->ready.size() + e->running);
+  st->completed = e->completed;
+  st->plans_built = e->built;
+  st->plans_evicted = e->evicted;
+  return SNAC_OK;
+}
+
+int snac_engine_destroy(snac_engine* e) {
+  if (!e) return SNAC_OK;
+  {
+    std::unique_lock<std::mutex> lk(e->mu);
+    e->cv_done.wait(lk, [&] { return e->queue.empty() && e->ready.empty() && e->running == 0; });
+    e->stopping = true;
+  }
+  e->cv_work.notify_all();
+  for (std::thread& t : e->threads) t.join();
+  for (PlanSlot* s : e->plans) {
+    snac_plan_destroy(s->plan);
+    delete s;
+  }
+  for (auto& kv : e->tickets) delete kv.second;
+  delete e;
+  return SNAC_OK;
+}
+
+}  // extern "C"

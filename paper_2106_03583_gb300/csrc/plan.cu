@@ -756,6 +756,12 @@ int create(snac_plan** out, int32_t nblocks, const snac_block* blocks, int32_t h
 
 namespace snac {
 int plan_inner_size(const snac_plan* P) { return P->precision == SNAC_FP64 ? 8 : 4; }
+
+int check_layout(int nblocks, const snac_block* blocks) {
+  if (!blocks || nblocks < 1) return fail(SNAC_ERR_INVALID_ARG, "blocks NULL or nblocks < 1");
+  std::vector<HBlock> hb;
+  return validate(nblocks, blocks, hb);
+}
 }  // namespace snac
 
 extern "C" {

@@ -240,6 +240,8 @@ cudaError_t launch_fused_down(snac_plan* P, int l, int nact, bool zero_u, bool z
 cudaError_t launch_fused_up(snac_plan* P, int l, int nact, bool norms, cudaStream_t s);
 
 int plan_inner_size(const snac_plan* P);  // bytes of the inner type
+// the block-layout checks of plan creation (sizes, widths, face kinds, z pair, connectivity)
+int check_layout(int nblocks, const snac_block* blocks);
 
 // Counts one launch of `kind` with its algorithmic bytes / flops; with profiling on, brackets it
 // with a CUDA event pair on stream s (construct just before the launch, destroy just after).

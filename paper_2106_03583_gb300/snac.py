@@ -29,7 +29,9 @@ EXPORTS = ("snac_plan_create", "snac_plan_workspace_bytes", "snac_poisson_solve"
            "snac_plan_mode_cycles", "snac_plan_destroy", "snac_status_string", "snac_last_error_message",
            "snac_apply_operator", "snac_residual", "snac_forward_transform", "snac_backward_update",
            "snac_mode_operator", "snac_mode_vcycles", "snac_plan_set_profiling", "snac_plan_kernel_stats",
-           "snac_plan_reset_stats", "snac_residual_noalloc")
+           "snac_plan_reset_stats", "snac_residual_noalloc",
+           "snac_engine_create", "snac_engine_submit", "snac_engine_wait", "snac_engine_get_stats",
+           "snac_engine_clock", "snac_engine_destroy")
 
 
 class SnacError(RuntimeError):
@@ -59,6 +61,21 @@ class _Info(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int32), ("outer_iters", ctypes.c_int32), ("total_cycles", ctypes.c_int32),
                 ("max_mode_cycles", ctypes.c_int32), ("levels", ctypes.c_int32), ("n_modes", ctypes.c_int32),
                 ("rel_res", ctypes.c_double), ("rhs_norm", ctypes.c_double), ("removed_mean", ctypes.c_double)]
+
+
+class _EngineOptions(ctypes.Structure):
+    _fields_ = [("workers", ctypes.c_int32), ("max_cached_plans", ctypes.c_int32), ("hbm_budget", ctypes.c_uint64)]
+
+
+class _Times(ctypes.Structure):
+    _fields_ = [("t_submit", ctypes.c_double), ("t_admit", ctypes.c_double), ("t_start", ctypes.c_double),
+                ("t_done", ctypes.c_double), ("worker", ctypes.c_int32), ("plan_reused", ctypes.c_int32)]
+
+
+class _EngineStats(ctypes.Structure):
+    _fields_ = [("bytes_in_use", ctypes.c_uint64), ("bytes_peak", ctypes.c_uint64), ("plans_cached", ctypes.c_int32),
+                ("queued", ctypes.c_int32), ("running", ctypes.c_int32), ("completed", ctypes.c_int64),
+                ("plans_built", ctypes.c_int64), ("plans_evicted", ctypes.c_int64)]
 
 
 _lib = None
@@ -95,11 +112,19 @@ def lib() -> ctypes.CDLL:
             "snac_plan_kernel_stats": [vp, ctypes.POINTER(_KStat), i32, ctypes.POINTER(i32)],
             "snac_plan_reset_stats": [vp],
             "snac_residual_noalloc": [ctypes.POINTER(_Block), vp, vp, vp, ctypes.POINTER(f64), vp],
+            "snac_engine_create": [ctypes.POINTER(vp), ctypes.POINTER(_EngineOptions)],
+            "snac_engine_submit": [vp, i32, ctypes.POINTER(_Block), i32, ctypes.POINTER(_Options), vp, vp, f64,
+                                   ctypes.POINTER(ctypes.c_int64)],
+            "snac_engine_wait": [vp, ctypes.c_int64, ctypes.POINTER(_Info), ctypes.POINTER(_Times)],
+            "snac_engine_get_stats": [vp, ctypes.POINTER(_EngineStats)],
+            "snac_engine_clock": [],
+            "snac_engine_destroy": [vp],
         }
         for name, args in sig.items():
             fn = getattr(L, name)
             fn.argtypes = args
-            fn.restype = ctypes.c_char_p if name in ("snac_status_string", "snac_last_error_message") else ctypes.c_int
+            fn.restype = ctypes.c_char_p if name in ("snac_status_string", "snac_last_error_message") else \
+                ctypes.c_double if name == "snac_engine_clock" else ctypes.c_int
         _lib = L
     return _lib
 
@@ -265,6 +290,87 @@ class Plan:
         if getattr(self, "_h", None) is not None and self._h.value:
             lib().snac_plan_destroy(self._h)
             self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+class Engine:
+    """Serving engine (``include/snac_engine.h``): solves of different problems submitted at any time,
+    admitted under a device-memory budget, run concurrently by ``workers`` threads / CUDA streams
+    with resident cached plans. Host arrays in, host arrays out.
+
+        eng = snac.Engine(workers=4, hbm_budget=150e9)
+        t = eng.submit(blocks, f, tol=1e-10, precision="mixed")
+        p, info, times = eng.wait(t)
+    """
+
+    def __init__(self, workers: int = 4, hbm_budget: float = 150e9, max_cached_plans: int = 64):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("snac.Engine needs a CUDA device")
+        torch.cuda.init()
+        opt = _EngineOptions(int(workers), int(max_cached_plans), int(hbm_budget))
+        h = ctypes.c_void_p()
+        _check(lib().snac_engine_create(ctypes.byref(h), ctypes.byref(opt)))
+        self._h = h
+        self._live = {}   # ticket -> (rhs, p) kept alive until wait
+
+    def submit(self, blocks, rhs, tol: float = 1e-10, precision: str = "fp64", homog_axis: int = 2, nu1: int = 2,
+               nu2: int = 2, max_outer: int = 20, max_cycles: int = 40, max_coarse: int = 64,
+               inner_reduction: float = 1e-3, fused: int = -1) -> int:
+        if precision not in _PREC:
+            raise ValueError(f"precision must be one of {list(_PREC)}")
+        n3 = int(sum(np.prod([b["hi"][a] - b["lo"][a] + 1 for a in range(3)]) for b in blocks))
+        rhs = np.ascontiguousarray(rhs, dtype=np.float64)
+        if rhs.shape != (n3,):
+            raise ValueError(f"rhs must be a float64 array of {n3} elements")
+        p = np.empty(n3, dtype=np.float64)
+        arr, keep = _marshal_blocks(blocks)
+        opt = _Options(_PREC[precision], nu1, nu2, max_outer, max_cycles, max_coarse, fused, inner_reduction)
+        t = ctypes.c_int64()
+        _check(lib().snac_engine_submit(self._h, len(blocks), arr, homog_axis, ctypes.byref(opt),
+                                        ctypes.c_void_p(rhs.ctypes.data), ctypes.c_void_p(p.ctypes.data),
+                                        float(tol), ctypes.byref(t)))
+        del keep   # the engine copied the block descriptions
+        self._live[t.value] = (rhs, p)
+        return t.value
+
+    def wait(self, ticket: int, raise_on_error: bool = True):
+        """(solution, info dict, times dict) of a request; blocks until it is complete."""
+        inf, tm = _Info(), _Times()
+        st = lib().snac_engine_wait(self._h, int(ticket), ctypes.byref(inf), ctypes.byref(tm))
+        rhs, p = self._live.pop(ticket, (None, None))
+        if st != SNAC_OK and raise_on_error:
+            _check(st)
+        info = {k: getattr(inf, k) for k, _ in _Info._fields_}
+        info["status"] = st
+        info["status_name"] = STATUS.get(st, str(st))
+        return p, info, {k: getattr(tm, k) for k, _ in _Times._fields_}
+
+    def stats(self) -> dict:
+        s = _EngineStats()
+        _check(lib().snac_engine_get_stats(self._h, ctypes.byref(s)))
+        return {k: getattr(s, k) for k, _ in _EngineStats._fields_}
+
+    @staticmethod
+    def clock() -> float:
+        return float(lib().snac_engine_clock())
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            lib().snac_engine_destroy(self._h)
+            self._h = ctypes.c_void_p()
+            self._live.clear()
 
     def __del__(self):
         try:

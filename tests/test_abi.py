@@ -21,9 +21,12 @@ def lib():
 
 
 def declared_functions():
-    src = open(os.path.join(ROOT, "include", "snac.h")).read()
-    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"^\s*(?:const\s+)?\w+\s*\*?\s*(snac_\w+)\s*\(", src, flags=re.M)))
+    names = set()
+    for h in ("snac.h", "snac_engine.h"):
+        src = open(os.path.join(ROOT, "include", h)).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        names |= set(re.findall(r"^\s*(?:const\s+)?\w+\s*\*?\s*(snac_\w+)\s*\(", src, flags=re.M))
+    return sorted(names)
 
 
 def test_every_declared_symbol_is_exported(lib):
@@ -79,3 +82,21 @@ def test_null_arguments(lib):
     assert lib.snac_poisson_solve(None, None, None, 1e-10, None) == -1
     assert lib.snac_plan_info(None, None) == -1
     assert lib.snac_plan_destroy(None) == 0
+
+
+def test_engine_argument_checks(lib):
+    """Engine calls reject bad arguments before touching a device."""
+    h = ctypes.c_void_p()
+    bad = snac._EngineOptions(0, 64, 10**9)
+    assert lib.snac_engine_create(ctypes.byref(h), ctypes.byref(bad)) == -1
+    bad = snac._EngineOptions(4, -1, 10**9)
+    assert lib.snac_engine_create(ctypes.byref(h), ctypes.byref(bad)) == -1
+    bad = snac._EngineOptions(4, 8, 0)
+    assert lib.snac_engine_create(ctypes.byref(h), ctypes.byref(bad)) == -1
+    assert lib.snac_engine_create(None, None) == -1
+    t = ctypes.c_int64()
+    assert lib.snac_engine_submit(None, 1, None, 2, None, None, None, 1e-10, ctypes.byref(t)) == -1
+    assert lib.snac_engine_wait(None, 1, None, None) == -1
+    assert lib.snac_engine_get_stats(None, None) == -1
+    assert lib.snac_engine_destroy(None) == 0
+    assert lib.snac_engine_clock() >= 0.0
