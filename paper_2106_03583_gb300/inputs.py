@@ -35,6 +35,7 @@ __all__ = [
     "divergence_rhs",
     "config",
     "CONFIGS",
+    "random_problem",
 ]
 
 
@@ -266,6 +267,40 @@ def config(name: str, seed: int = 0, scale: int = 1):
                              {"x-": "D", "x+": "D", "y-": "N", "y+": "N"}, ("P", "P"))
         return blocks, divergence_rhs(blocks, seed)
     raise ValueError(f"unknown workload {name!r}")
+
+
+def random_problem(rng, xy_exp=(5, 9), z_exp=(5, 8), rhs="divergence"):
+    """One problem of the mixed workloads (many independent solves, or a stream of requests).
+
+    Sizes are log-uniform per axis: n_x = 2^ex, n_y = 2^ey with ex, ey uniform in ``xy_exp``, and
+    n_z = 2^ez with ez uniform in ``z_exp``; cubic cells of width 1/64. The x-y grid is cut into 1 to
+    4 blocks (one block, halves along x or y, an L of three quarters, 2x2 quarters); every wall and
+    the z pair (PP, NN, DD, ND, DN) are drawn at random. ``rhs``: ``"divergence"`` (f = D u,
+    k^-5/3) or ``"uniform"`` (U[-1, 1]), compatible whenever the problem is singular.
+    Returns (blocks, f, description)."""
+    ex, ey = (int(v) for v in rng.integers(xy_exp[0], xy_exp[1] + 1, 2))
+    ez = int(rng.integers(z_exp[0], z_exp[1] + 1))
+    nx, ny, nz = 2 ** ex, 2 ** ey, 2 ** ez
+    hx, hy = nx // 2, ny // 2
+    nblk = int(rng.integers(1, 5))
+    if nblk == 1:
+        rects = [(0, nx, 0, ny)]
+    elif nblk == 2:
+        rects = [(0, hx, 0, ny), (hx, nx, 0, ny)] if rng.random() < 0.5 else [(0, nx, 0, hy), (0, nx, hy, ny)]
+    elif nblk == 3:
+        rects = [(0, hx, 0, hy), (hx, nx, 0, hy), (0, hx, hy, ny)]
+    else:
+        rects = [(0, hx, 0, hy), (hx, nx, 0, hy), (0, hx, hy, ny), (hx, nx, hy, ny)]
+    zp = str(rng.choice(["PP", "NN", "DD", "ND", "DN"]))
+    walls = {k: ("D" if rng.random() < 0.5 else "N") for k in ("x-", "x+", "y-", "y+")}
+    h = 1.0 / 64.0
+    blocks = make_blocks(np.arange(nx + 1) * h, np.arange(ny + 1) * h, np.arange(nz + 1) * h, rects, walls,
+                         ("P", "P") if zp == "PP" else (zp[0], zp[1]), inner_wall="N")
+    singular = zp in ("PP", "NN") and "D" not in walls.values()
+    seed = int(rng.integers(0, 2 ** 31))
+    f = divergence_rhs(blocks, seed) if rhs == "divergence" else uniform_rhs(blocks, seed, remove_mean=singular)
+    desc = f"{nx}x{ny}x{nz} {len(rects)} block(s) z {zp} walls {''.join(walls.values())}"
+    return blocks, f, desc
 
 
 CONFIGS = {
