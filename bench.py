@@ -42,7 +42,21 @@ FP64_IN_FP64_PLAN = {"smooth", "restrict", "prolong", "mode_resid", "mode_apply"
 # launch's algorithmic bytes, with the sha256 of the kernel's source file when it was captured. The
 # bench scales the ratio to its own launches (traffic grows in proportion to the cells processed) and
 # reports null once the source differs from the captured one. Captures: profiles/*.md.
-TRAFFIC = {}
+_FUSED = {"src": "paper_2106_03583_gb300/csrc/kern_fused.cu",
+          "sha256": "77084ceec5df844310d568fabd7f986f99d05ca61a7637f6bd6cdb5b96b45305",
+          "capture": "profiles/k_fdown_k_fup_mixed_mb2x2_z64.md"}
+_FIELD = {"src": "paper_2106_03583_gb300/csrc/kern_field.cu",
+          "sha256": "871328280ff874a297663f07866e7d4cb7d6d83cfff8ea5c962959bc66b408d7",
+          "capture": "profiles/k_field3d_transforms_mixed_mb2x2_z64.md", "ratio": 400.707 / 402.653}
+TRAFFIC = {
+    ("fused_up", "mixed"): dict(_FUSED, ratio=196.475 / 218.104),     # level-0 up kernel, 64 modes
+    ("fused_down", "mixed"): dict(_FUSED, ratio=188.596 / 218.104),   # level-0 down kernel, 64 modes
+    ("field3d", "mixed"): _FIELD,
+    ("field3d", "fp64"): _FIELD,
+    ("smooth", "fp64"): {"src": "paper_2106_03583_gb300/csrc/kern_mg.cu",
+                         "sha256": "b4fac5f3080c517ed35652afcea4b97090178c56bb29b40695452a804e3f9462",
+                         "capture": "profiles/k_smooth_fp64_mb2x2_z64.md", "ratio": 507.089 / 201.327},
+}
 
 
 def parse():
