@@ -195,14 +195,14 @@ def run_reference(args):
     from paper_2106_03583_gb300 import inputs
     blocks, f = inputs.config(args.workload, seed=args.seed)
     setup = _oracle_setup(blocks)
-    first = cpu_baseline(args, blocks, f, 2, setup)
+    first = cpu_baseline(args, blocks, f, 4, setup)
     ttr = first["t_transforms"]
     for _ in range(max(args.warmup - 1, 0)):
-        cpu_baseline(args, blocks, f, 2, setup, ttr)
+        cpu_baseline(args, blocks, f, 4, setup, ttr)
     vals = []
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        vals.append(cpu_baseline(args, blocks, f, 2, setup, ttr))
+        vals.append(cpu_baseline(args, blocks, f, 4, setup, ttr))
     wall = time.perf_counter() - t0
     v = statistics.median(x["value"] for x in vals)
     line = base_line(args, 1)
@@ -362,7 +362,7 @@ def run_snac(args):
         m.pop("clocks", None)
         line["mixed"] = m
     if not args.no_cpu_baseline and world == 1:
-        line["cpu_baseline"] = cpu_baseline(args, blocks, f_np, 8)
+        line["cpu_baseline"] = cpu_baseline(args, blocks, f_np, 32)
     print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
