@@ -146,6 +146,26 @@ def dist():
     return world, rank, local
 
 
+def rank_seed(seed, rank):
+    """Each rank solves its own seeded problem (independent replicas)."""
+    return seed + rank
+
+
+def max_over_ranks(x, world, device):
+    """The largest value over the ranks (the slowest rank's time); x itself on one rank."""
+    if world == 1:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(world, steps, max_ms):
+    """Solves per second of the whole job: every rank did `steps` solves within max_ms."""
+    return world * steps / (max_ms * 1e-3)
+
+
 def base_line(args, world, precision="fp64"):
     dtype = "f64" if precision == "fp64" else "f32 multigrid and transforms, f64 residual and update"
     return {"metric": METRIC, "unit": "solves/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -259,7 +279,7 @@ def run_snac(args):
     from paper_2106_03583_gb300 import build, inputs, snac
     build.build()
     hbm_peak, hbm_kind = peaks()
-    blocks, f_np = inputs.config(args.workload, seed=args.seed + rank)
+    blocks, f_np = inputs.config(args.workload, seed=rank_seed(args.seed, rank))
     n3 = len(f_np)
     f = torch.from_numpy(f_np).cuda()
     p = torch.zeros_like(f)
@@ -268,13 +288,6 @@ def run_snac(args):
     def barrier():
         if world > 1:
             torch.distributed.barrier()
-
-    def max_over_ranks(x):
-        if world == 1:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        return float(t.item())
 
     results = {}
     clocks = None
@@ -299,7 +312,7 @@ def run_snac(args):
         barrier()
         ck_res = ck.stop() if ck else None
         step_ms = [ev[k].elapsed_time(ev[k + 1]) for k in range(K)]
-        total_ms = max_over_ranks(ev[0].elapsed_time(ev[K]))
+        total_ms = max_over_ranks(ev[0].elapsed_time(ev[K]), world, "cuda")
         stats = plan.kernel_stats()
         plan.set_profiling(False)
         launches = sum(s["launches"] for s in stats.values())
@@ -325,14 +338,14 @@ def run_snac(args):
         e1.record()
         torch.cuda.synchronize()
         barrier()
-        e2e_ms = max_over_ranks(e0.elapsed_time(e1))
+        e2e_ms = max_over_ranks(e0.elapsed_time(e1), world, "cuda")
         ok = all(i["status"] == 0 and i["rel_res"] <= args.tol for i in infos)
         results[prec] = {
-            "value": world * K / (total_ms * 1e-3), "ms_per_step": total_ms / K,
+            "value": whole_job_rate(world, K, total_ms), "ms_per_step": total_ms / K,
             "p50_ms": statistics.median(step_ms), "p99_ms": float(np.percentile(step_ms, 99)),
             "hbm_gbs_model": bytes_model / (total_ms / K * 1e-3) / 1e9,
             "roofline": roofline(stats, prec, hbm_peak, hbm_kind, K),
-            "e2e": {"value": world * K / (e2e_ms * 1e-3), "unit": "solves/s", "h2d_bytes_per_step": 8 * n3,
+            "e2e": {"value": whole_job_rate(world, K, e2e_ms), "unit": "solves/s", "h2d_bytes_per_step": 8 * n3,
                     "d2h_bytes_per_step": 8 * n3},
             "gpu_launches": launches,
             "rel_res": infos[-1]["rel_res"], "outer_iters": infos[-1]["outer_iters"],
