@@ -42,9 +42,41 @@ template <typename T, int TC>
 __device__ Cx<T>* cfft(Cx<T>* X, Cx<T>* Y, int m, const Cx<T>* __restrict__ tw, bool inverse) {
   if (m == 1) return X;
   if ((m & (m - 1)) == 0) {
-    // Stockham autosort: merge pairs of length-Ls transforms into length-2Ls transforms.
-    int lg = 0;
-    for (int Ls = 1; Ls < m; Ls <<= 1, ++lg) {
+    // Stockham autosort: merge groups of four length-Ls transforms into length-4Ls transforms while
+    // four remain (radix 4: three twiddle products per four points), then pairs (radix 2) once, if
+    // log2(m) is odd. Output stage q of a group: y_q = sum_p (w^(p k) x_p) omega_4^(p q).
+    int lg = 0, Ls = 1;
+    for (; (m / Ls) % 4 == 0; Ls <<= 2, lg += 2) {
+      const int r = m / (4 * Ls);
+      for (int idx = threadIdx.x; idx < (m / 4) * TC; idx += blockDim.x) {
+        const int c = idx % TC, t = idx / TC;
+        const int j = t >> lg, k = t & (Ls - 1);
+        Cx<T> w1 = tw[k * r], w2 = tw[2 * k * r], w3 = tw[3 * k * r];
+        if (inverse) {
+          w1.im = -w1.im;
+          w2.im = -w2.im;
+          w3.im = -w3.im;
+        }
+        const Cx<T> a0 = X[(j * Ls + k) * TC + c];
+        const Cx<T> a1 = cmul(w1, X[((j + r) * Ls + k) * TC + c]);
+        const Cx<T> a2 = cmul(w2, X[((j + 2 * r) * Ls + k) * TC + c]);
+        const Cx<T> a3 = cmul(w3, X[((j + 3 * r) * Ls + k) * TC + c]);
+        const Cx<T> s02 = {a0.re + a2.re, a0.im + a2.im}, d02 = {a0.re - a2.re, a0.im - a2.im};
+        const Cx<T> s13 = {a1.re + a3.re, a1.im + a3.im}, d13 = {a1.re - a3.re, a1.im - a3.im};
+        // omega_4 d13: -i d13 forward, +i d13 inverse
+        const Cx<T> od = inverse ? Cx<T>{-d13.im, d13.re} : Cx<T>{d13.im, -d13.re};
+        const int o = (4 * j * Ls + k) * TC + c;
+        Y[o] = {s02.re + s13.re, s02.im + s13.im};
+        Y[o + Ls * TC] = {d02.re + od.re, d02.im + od.im};
+        Y[o + 2 * Ls * TC] = {s02.re - s13.re, s02.im - s13.im};
+        Y[o + 3 * Ls * TC] = {d02.re - od.re, d02.im - od.im};
+      }
+      __syncthreads();
+      Cx<T>* s = X;
+      X = Y;
+      Y = s;
+    }
+    for (; Ls < m; Ls <<= 1, ++lg) {
       const int r = m / (2 * Ls);
       for (int idx = threadIdx.x; idx < (m / 2) * TC; idx += blockDim.x) {
         const int c = idx % TC, t = idx / TC;
