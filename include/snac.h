@@ -90,7 +90,7 @@ typedef struct {
   int32_t max_cycles;  /* V-cycles per wavenumber per outer iteration (40)                          */
   int32_t max_coarse;  /* coarsen while a plane has more than this many cells (64; <= 256)          */
   int32_t fused;       /* fused tile kernels (smoothing + restriction, prolongation + smoothing in
-                          shared memory) on levels whose blocks are all >= 16 cells wide:
+                          shared memory) on levels whose blocks are all >= 8 cells wide:
                           -1 = auto (on for SNAC_MIXED, off for SNAC_FP64), 0 = off, 1 = on         */
   double inner_reduction; /* mixed plans: residual reduction asked of the FP32 multigrid in each
                              defect-correction step, in (0, 1) (1e-3); FP64 plans solve each step to

@@ -25,6 +25,10 @@ constexpr int FWN = FTILE_X + 2 * FUSED_HALO;  // window side (64)
 constexpr int FHW = FWN / 2;                   // column pairs (32)
 constexpr int FCW = FWN / 2 + 2;               // coarse window side (34)
 constexpr int FUSED_NONE = INT_MIN;            // row or column with no owner
+// the window reaches FUSED_HALO cells into each neighbouring block, and its coarse window (parents
+// plus one ring) FUSED_HALO / 2 + 1 coarse cells into the neighbour's coarse block
+static_assert(FUSED_MIN_BLOCK >= FUSED_HALO && FUSED_MIN_BLOCK / 2 >= FUSED_HALO / 2 + 1,
+              "fused levels need blocks wide enough to hold the halo");
 
 template <typename T>
 struct FP2 {

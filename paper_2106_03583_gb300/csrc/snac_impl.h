@@ -33,7 +33,7 @@ constexpr int SUM_SLOTS = 16;     // d_sums / h_sums: [0..3] residual or pre-pas
 constexpr int SUM_NONZERO = 8;    // d_sums slot of the pre-pass's nonzero-guess flag  // CTAs of the grid-stride reductions over one mode plane
 constexpr int FTILE_X = 52;         // tile of the fused multigrid kernels (64x64 window with the halo)
 constexpr int FTILE_Y = 52;
-constexpr int FUSED_MIN_BLOCK = 16;  // fused kernels on levels whose blocks are all this wide
+constexpr int FUSED_MIN_BLOCK = 8;   // fused kernels on levels whose blocks are all this wide (>= the halo)
 
 // Faces are numbered W, E, S, N = 0..3 (x lower, x upper, y lower, y upper).
 struct BlockDev {

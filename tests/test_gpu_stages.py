@@ -126,7 +126,7 @@ def test_vcycle_matches_oracle(case):
 
 
 FUSED_CASES = [
-    ("2x2", 32, 8, "NN", ("N", "N", "N", "N"), True),      # fused levels 0 and 1, per-colour level 2
+    ("2x2", 32, 8, "NN", ("N", "N", "N", "N"), True),      # fused levels 0..2 (blocks 32, 16, 8)
     ("L", 24, 6, "DD", ("N", "D", "D", "N"), True),        # ragged 24x24 tiles, re-entrant corner
     ("1", 40, 4, "ND", ("D", "N", "N", "N"), True),        # 80x80: ragged 64+16 tiles, four fused levels
     ("2x2", 24, 8, "PP", ("N", "N", "N", "N"), True, (True, True)),   # periodic wrap across blocks
@@ -166,7 +166,7 @@ def _mean_free(g, X):
 
 @pytest.mark.parametrize("case", FUSED_CASES)
 def test_vcycle_fused_matches_oracle(case):
-    """The fused tile kernels (levels whose blocks are >= 16 wide; each tile reads one iterate
+    """The fused tile kernels (levels whose blocks are >= 8 wide; each tile reads one iterate
     buffer and writes the other) reproduce the oracle's V(2,2) cycles: to rounding when run in FP64
     from a random iterate, and in FP32 from a zero iterate as accurately as the per-colour FP32
     kernels do (the FP32 error itself grows with the conditioning of the low modes)."""
