@@ -218,9 +218,16 @@ def dzz_matrix(kind: str, n: int, dz: float) -> np.ndarray:
 
 
 class Grid:
-    """The whole 3-D multi-block problem: x-y plane, z pair, uniform dz."""
+    """The whole 3-D multi-block problem: x-y plane, z pair, uniform dz.
 
-    def __init__(self, blocks):
+    ``shift`` (<= 0) gives the Helmholtz form (A + shift I) p = f that the method solves unchanged
+    (Sec. 3.3, footnote: the solver applies to the more general Helmholtz equation): every reduced
+    equation (Eq. 9) takes the same extra diagonal term, and a nonzero shift removes the null space."""
+
+    def __init__(self, blocks, shift: float = 0.0):
+        if not shift <= 0.0:
+            raise ValueError("the Helmholtz shift must be <= 0 (A + shift I stays negative definite)")
+        self.shift = float(shift)
         validate(blocks)
         self.blocks = blocks
         self.plane = Plane(blocks)
@@ -232,7 +239,7 @@ class Grid:
             raise LayoutError("periodic homogeneous axis needs an even n_z (Table 1)")
         self.Dzz = dzz_matrix(self.kind, self.nz, self.dz)
         # the singular problem: a zero eigenvalue along z and no Dirichlet face in x-y
-        self.singular = (self.kind in ("PP", "NN")) and not self.plane.has_dirichlet
+        self.singular = (self.kind in ("PP", "NN")) and not self.plane.has_dirichlet and self.shift == 0.0
         self.vol = np.outer(np.full(self.nz, self.dz), self.plane.area)     # (n_z, n_xy)
 
     # ---- layout conversion: caller [block][z][y][x] <-> planes (n_z, n_xy)
@@ -257,13 +264,19 @@ class Grid:
 
     # ---- the 3-D operator of Eq. 8
     def apply(self, P):
-        """A p on planes: the x-y operator on every plane plus the z operator on every column."""
-        return (self.plane.A @ P.T).T + self.Dzz @ P
+        """A p on planes: the x-y operator on every plane plus the z operator on every column (plus
+        shift p)."""
+        out = (self.plane.A @ P.T).T + self.Dzz @ P
+        if self.shift != 0.0:
+            out = out + self.shift * P
+        return out
 
     def matrix(self):
         """The assembled sparse 3-D matrix, plane-major ordering (k * n_xy + cell)."""
+        n = self.nz * self.plane.n
         return (sp.kron(sp.identity(self.nz), self.plane.A) + sp.kron(sp.csr_matrix(self.Dzz),
-                                                                        sp.identity(self.plane.n))).tocsr()
+                                                                        sp.identity(self.plane.n))
+                + self.shift * sp.identity(n)).tocsr()
 
     def residual(self, f, p):
         """r = f - A p in the caller's layout."""

@@ -37,12 +37,12 @@ def _compatibility(g: Grid, F: np.ndarray):
     return tot / float(g.vol.sum())
 
 
-def solve(blocks, f, rtol_mode=1e-13, nu1=2, nu2=2, max_cycles=100, modes=None, mg=None):
-    """Solve A p = f. Returns (p in the caller layout, info dict).
+def solve(blocks, f, rtol_mode=1e-13, nu1=2, nu2=2, max_cycles=100, modes=None, mg=None, shift=0.0):
+    """Solve (A + shift I) p = f (shift = 0: Eq. 8). Returns (p in the caller layout, info dict).
 
     ``modes`` restricts the per-wavenumber solves to a subset (the others are left zero): used to
     time a bounded sample of a large problem. ``mg`` reuses a prepared Multigrid hierarchy."""
-    g = Grid(blocks)
+    g = Grid(blocks, shift)
     F = g.to_planes(f)
     info = {"removed_mean": 0.0, "singular": g.singular, "kind": g.kind}
     if g.singular:
@@ -58,7 +58,7 @@ def solve(blocks, f, rtol_mode=1e-13, nu1=2, nu2=2, max_cycles=100, modes=None, 
     mode_res = np.zeros(g.nz)
     # Algorithm 1, second loop: one reduced 2-D solve per wavenumber
     for q in (range(g.nz) if modes is None else modes):
-        sigma = lam[q] / (g.dz * g.dz)
+        sigma = lam[q] / (g.dz * g.dz) + g.shift
         Ph[q], cycles[q], mode_res[q] = mg.solve(sigma, Fh[q], singular=(g.singular and lam[q] == 0.0),
                                                  rtol=rtol_mode, max_cycles=max_cycles)
     # Algorithm 1, third loop: backward transform
@@ -75,9 +75,9 @@ def solve(blocks, f, rtol_mode=1e-13, nu1=2, nu2=2, max_cycles=100, modes=None, 
     return p, info
 
 
-def solve_dense(blocks, f):
+def solve_dense(blocks, f, shift=0.0):
     """Dense direct solve of the assembled 3-D system (tiny grids only)."""
-    g = Grid(blocks)
+    g = Grid(blocks, shift)
     F = g.to_planes(f)
     A = g.matrix().toarray()
     n = A.shape[0]
@@ -94,15 +94,15 @@ def solve_dense(blocks, f):
     return g.from_planes(x.reshape(g.nz, g.plane.n))
 
 
-def apply_operator(blocks, p):
-    """A p (Eq. 8) in the caller's layout."""
-    g = Grid(blocks)
+def apply_operator(blocks, p, shift=0.0):
+    """(A + shift I) p (Eq. 8) in the caller's layout."""
+    g = Grid(blocks, shift)
     return g.from_planes(g.apply(g.to_planes(p)))
 
 
-def rel_residual(blocks, f, p):
-    """||f - A p|| / ||f|| (2-norm over all cells, rows per unit volume)."""
-    g = Grid(blocks)
+def rel_residual(blocks, f, p, shift=0.0):
+    """||f - (A + shift I) p|| / ||f|| (2-norm over all cells, rows per unit volume)."""
+    g = Grid(blocks, shift)
     F = g.to_planes(f)
     r = F - g.apply(g.to_planes(p))
     return float(np.linalg.norm(r) / max(np.linalg.norm(F), 1e-300))

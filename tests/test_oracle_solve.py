@@ -158,3 +158,51 @@ def test_planted_mistakes_are_caught(monkeypatch):
     from test_oracle_operator import staggered_div_grad
     p = np.random.default_rng(0).standard_normal(f.size)
     assert not np.allclose(osv.apply_operator(blocks, p), staggered_div_grad(blocks, p), rtol=1e-6)
+
+
+@pytest.mark.parametrize("zpair", ZPAIRS)
+def test_manufactured_eigenfunction_helmholtz(zpair):
+    """Helmholtz form (A + s I) p = f (Sec. 3.3, footnote): the same eigenfunctions, with every
+    eigenvalue shifted by s."""
+    nx, ny, nz = 16, 8, 8
+    dx, dy, dz = 1.0 / nx, 2.0 / ny, 0.5 / nz
+    xf, yf, zf = np.arange(nx + 1) * dx, np.arange(ny + 1) * dy, np.arange(nz + 1) * dz
+    blocks = inputs.make_blocks(xf, yf, zf, [(0, nx, 0, ny)], {"x-": "N", "x+": "N", "y-": "N", "y+": "N"},
+                                make.__globals__["Z_PAIRS"][zpair])
+    s = -37.5
+    for (a, b, q) in [(0, 0, 0), (3, 5, 1), (nx - 1, ny - 1, nz - 1)]:
+        X = T.basis_vector("NN", nx, a)
+        Y = T.basis_vector("NN", ny, b)
+        Z = T.basis_vector(zpair, nz, q)
+        lam = (T.eigenvalues("NN", nx)[a] / dx ** 2 + T.eigenvalues("NN", ny)[b] / dy ** 2
+               + T.eigenvalues(zpair, nz)[q] / dz ** 2 + s)
+        ph = (Z[:, None, None] * Y[None, :, None] * X[None, None, :]).ravel()
+        p, info = osv.solve(blocks, lam * ph, shift=s)
+        assert not info["singular"]
+        assert np.linalg.norm(p - ph) <= 1e-11 * np.linalg.norm(ph)
+
+
+@pytest.mark.parametrize("layout", ["1", "L", "2x2"])
+@pytest.mark.parametrize("zpair", ["PP", "NN", "DD", "DN"])
+def test_helmholtz_matches_dense_lu(layout, zpair):
+    """All-Neumann walls with a periodic or Neumann z would be singular; with a shift the problem is
+    regular, any right-hand side is admissible, and the solve equals the dense solution."""
+    blocks = make(layout, n=4, nz=6, zpair=zpair, walls=("N", "N", "N", "N"), stretched=True)
+    f = inputs.uniform_rhs(blocks, 5, remove_mean=False) + 0.5
+    for s in (-1.0, -250.0):
+        p, info = osv.solve(blocks, f, shift=s)
+        pd = osv.solve_dense(blocks, f, shift=s)
+        assert info["removed_mean"] == 0.0
+        assert np.linalg.norm(p - pd) <= 1e-11 * np.linalg.norm(pd)
+        assert osv.rel_residual(blocks, f, p, shift=s) <= 1e-12
+
+
+def test_helmholtz_shift_sign():
+    blocks = make("1", n=4, nz=6, zpair="NN", walls=("N", "N", "N", "N"))
+    f = inputs.uniform_rhs(blocks, 1, remove_mean=True)
+    with pytest.raises(ValueError):
+        osv.solve(blocks, f, shift=1.0)
+    # shift 0 is Eq. 8 itself
+    p0, _ = osv.solve(blocks, f)
+    p1, _ = osv.solve(blocks, f, shift=0.0)
+    assert np.array_equal(p0, p1)
