@@ -95,6 +95,10 @@ typedef struct {
   double inner_reduction; /* mixed plans: residual reduction asked of the FP32 multigrid in each
                              defect-correction step, in (0, 1) (1e-3); FP64 plans solve each step to
                              the tolerance directly                                                  */
+  double shift;        /* Helmholtz shift s <= 0 (0): solve (A + s I) p = f, the Helmholtz form the
+                          method applies to unchanged (Sec. 3.3, footnote); every reduced equation
+                          (Eq. 9) gets the extra diagonal s, and s < 0 removes the null space of the
+                          periodic / all-Neumann case (no mean is removed then)                     */
 } snac_options;
 
 /* Result of the last solve of a plan. */

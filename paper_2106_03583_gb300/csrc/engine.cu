@@ -90,6 +90,7 @@ std::string problem_key(const Request& r) {
     put(k, r.opt.max_coarse);
     put(k, r.opt.fused);
     put(k, r.opt.inner_reduction);
+    put(k, r.opt.shift);
   }
   return k;
 }

@@ -610,7 +610,8 @@ int create(snac_plan** out, int32_t nblocks, const snac_block* blocks, int32_t h
     P->max_coarse = opt->max_coarse;
     P->inner_reduction = opt->inner_reduction;
     P->fused = opt->fused;
-    if (!(P->inner_reduction > 0.0 && P->inner_reduction < 1.0) || (P->precision != SNAC_FP64 && P->precision != SNAC_MIXED) || P->nu1 < 0 || P->nu2 < 0 ||
+    P->shift = opt->shift;
+    if (!(P->inner_reduction > 0.0 && P->inner_reduction < 1.0) || !(P->shift <= 0.0) || !std::isfinite(P->shift) || (P->precision != SNAC_FP64 && P->precision != SNAC_MIXED) || P->nu1 < 0 || P->nu2 < 0 ||
         P->nu1 + P->nu2 < 1 || P->nu1 > 16 || P->nu2 > 16 || P->max_outer < 1 || P->max_cycles < 1 ||
         P->max_coarse < 1 || P->max_coarse > MAX_COARSE) {
       delete P;
@@ -636,7 +637,7 @@ int create(snac_plan** out, int32_t nblocks, const snac_block* blocks, int32_t h
   for (const HBlock& h : hb)
     for (int a = 0; a < 2; ++a)
       for (int sd = 0; sd < 2; ++sd) dirichlet_xy |= h.bc[a][sd] == SNAC_BC_DIRICHLET;
-  P->singular = (P->kind == KIND_PP || P->kind == KIND_NN) && !dirichlet_xy;
+  P->singular = (P->kind == KIND_PP || P->kind == KIND_NN) && !dirichlet_xy && P->shift == 0.0;
   const size_t inner = P->precision == SNAC_FP64 ? sizeof(double) : sizeof(float);
   long long off3 = 0;
   P->vol_total = 0.0;
@@ -659,18 +660,18 @@ int create(snac_plan** out, int32_t nblocks, const snac_block* blocks, int32_t h
     if (st) break;
     // z operator pieces (uniform spacing). The ends are written as a mirrored ghost on the cell
     // itself: Neumann ghost = p_0 (coefficient +1/dz^2), Dirichlet ghost = -p_0 (-1/dz^2); the
-    // diagonal is then -2/dz^2 on every plane.
+    // diagonal is then -2/dz^2 on every plane, and carries the Helmholtz shift.
     const double iz2 = 1.0 / (P->dz * P->dz);
     for (int k = 0; k < P->nz; ++k) {
       const bool per = P->kind == KIND_PP;
-      Coef<double> c{iz2, iz2, -2.0 * iz2, P->dz};
+      Coef<double> c{iz2, iz2, -2.0 * iz2 + P->shift, P->dz};
       if (!per && k == 0) c.lo = zl == SNAC_BC_DIRICHLET ? -iz2 : iz2;
       if (!per && k == P->nz - 1) c.hi = zh == SNAC_BC_DIRICHLET ? -iz2 : iz2;
       P->cz.push_back(c);
     }
     if ((st = upload(P, &P->d_cz, P->cz))) break;
     for (int q = 0; q < P->nz; ++q) {
-      P->sigma.push_back(mode_lambda(P->kind, P->nz, q) * iz2);
+      P->sigma.push_back(mode_lambda(P->kind, P->nz, q) * iz2 + P->shift);
       P->pweight.push_back(parseval_weight(P->kind, P->nz, q));
     }
     if ((st = upload(P, &P->d_sigma64, P->sigma)) || (st = upload(P, &P->d_sigma32, to32(P->sigma)))) break;

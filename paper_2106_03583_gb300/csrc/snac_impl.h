@@ -143,6 +143,7 @@ struct snac_plan {
   int precision = SNAC_FP64;
   int nu1 = 2, nu2 = 2, max_outer = 20, max_cycles = 40, max_coarse = 64;
   double inner_reduction = 1e-3;
+  double shift = 0.0;  // Helmholtz shift (<= 0), included in sigma and in the residual's diagonal
   int fused = -1;
   int nblk = 0;
   int nz = 0;

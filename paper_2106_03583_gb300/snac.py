@@ -49,7 +49,7 @@ class _Block(ctypes.Structure):
 class _Options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("nu1", ctypes.c_int32), ("nu2", ctypes.c_int32),
                 ("max_outer", ctypes.c_int32), ("max_cycles", ctypes.c_int32), ("max_coarse", ctypes.c_int32),
-                ("fused", ctypes.c_int32), ("inner_reduction", ctypes.c_double)]
+                ("fused", ctypes.c_int32), ("inner_reduction", ctypes.c_double), ("shift", ctypes.c_double)]
 
 
 class _KStat(ctypes.Structure):
@@ -176,7 +176,7 @@ class Plan:
 
     def __init__(self, blocks, homog_axis: int = 2, precision: str = "fp64", nu1: int = 2, nu2: int = 2,
                  max_outer: int = 20, max_cycles: int = 40, max_coarse: int = 64, inner_reduction: float = 1e-3,
-                 fused: int = -1):
+                 fused: int = -1, shift: float = 0.0):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("snac.Plan needs a CUDA device")
@@ -188,7 +188,7 @@ class Plan:
         self.precision = precision
         self.inner_dtype = torch.float64 if precision == "fp64" else torch.float32
         arr, keep = _marshal_blocks(blocks)
-        opt = _Options(_PREC[precision], nu1, nu2, max_outer, max_cycles, max_coarse, fused, inner_reduction)
+        opt = _Options(_PREC[precision], nu1, nu2, max_outer, max_cycles, max_coarse, fused, inner_reduction, shift)
         h = ctypes.c_void_p()
         _check(lib().snac_plan_create(ctypes.byref(h), len(blocks), arr, homog_axis, ctypes.byref(opt)))
         del keep
@@ -327,7 +327,7 @@ class Engine:
 
     def submit(self, blocks, rhs, tol: float = 1e-10, precision: str = "fp64", homog_axis: int = 2, nu1: int = 2,
                nu2: int = 2, max_outer: int = 20, max_cycles: int = 40, max_coarse: int = 64,
-               inner_reduction: float = 1e-3, fused: int = -1) -> int:
+               inner_reduction: float = 1e-3, fused: int = -1, shift: float = 0.0) -> int:
         if precision not in _PREC:
             raise ValueError(f"precision must be one of {list(_PREC)}")
         n3 = int(sum(np.prod([b["hi"][a] - b["lo"][a] + 1 for a in range(3)]) for b in blocks))
@@ -336,7 +336,7 @@ class Engine:
             raise ValueError(f"rhs must be a float64 array of {n3} elements")
         p = np.empty(n3, dtype=np.float64)
         arr, keep = _marshal_blocks(blocks)
-        opt = _Options(_PREC[precision], nu1, nu2, max_outer, max_cycles, max_coarse, fused, inner_reduction)
+        opt = _Options(_PREC[precision], nu1, nu2, max_outer, max_cycles, max_coarse, fused, inner_reduction, shift)
         t = ctypes.c_int64()
         _check(lib().snac_engine_submit(self._h, len(blocks), arr, homog_axis, ctypes.byref(opt),
                                         ctypes.c_void_p(rhs.ctypes.data), ctypes.c_void_p(p.ctypes.data),

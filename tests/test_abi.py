@@ -100,3 +100,17 @@ def test_engine_argument_checks(lib):
     assert lib.snac_engine_get_stats(None, None) == -1
     assert lib.snac_engine_destroy(None) == 0
     assert lib.snac_engine_clock() >= 0.0
+
+
+def test_option_validation(lib):
+    """Bad options are refused before any device work (including a positive Helmholtz shift)."""
+    blocks = make("1", n=4, nz=8, zpair="NN")
+    for kw in ({"shift": 1.0}, {"shift": float("nan")}, {"inner_reduction": 1.5}, {"nu1": 0, "nu2": 0},
+               {"max_coarse": 1000}):
+        o = dict(precision=0, nu1=2, nu2=2, max_outer=20, max_cycles=40, max_coarse=64, fused=-1,
+                 inner_reduction=1e-3, shift=0.0)
+        o.update(kw)
+        opt = snac._Options(o["precision"], o["nu1"], o["nu2"], o["max_outer"], o["max_cycles"], o["max_coarse"],
+                            o["fused"], o["inner_reduction"], o["shift"])
+        st, msg = _create(lib, blocks, opt=ctypes.byref(opt))
+        assert st == -1 and "options" in msg, (kw, st, msg)

@@ -118,6 +118,26 @@ def test_zero_guess_shortcut_matches_residual_path(precision, zpair, walls):
     assert info2["outer_iters"] == info0["outer_iters"] and rel(host(p), p0) <= 1e-15
 
 
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("layout,zpair,walls", [("2x2", "NN", ("N", "N", "N", "N")), ("L", "PP", ("N", "N", "N", "N")),
+                                                ("1x2", "DD", ("D", "N", "N", "N")), ("1", "ND", ("D", "D", "N", "N"))])
+def test_helmholtz_vs_oracle(precision, layout, zpair, walls):
+    """(A + s I) p = f, s < 0 (the Helmholtz form of Sec. 3.3): regular even where s = 0 would be
+    singular, so a right-hand side with a nonzero mean is solved as it is."""
+    import torch
+    blocks = make(layout, n=16, nz=8, zpair=zpair, walls=walls, stretched=True)
+    f = inputs.uniform_rhs(blocks, 9, remove_mean=False) + 0.25
+    s = -40.0
+    po, _ = osv.solve(blocks, f, shift=s)
+    p, info, pl = gpu_solve(blocks, f, precision, shift=s)
+    assert info["status"] == 0 and info["rel_res"] <= TOL and info["removed_mean"] == 0.0
+    assert osv.rel_residual(blocks, f, p, shift=s) <= 1.01 * TOL
+    assert rel(p, po) <= PARITY
+    out = torch.empty(len(f), dtype=torch.float64, device="cuda")
+    pl.apply_operator(dev(p), out)
+    assert rel(host(out), osv.apply_operator(blocks, p, shift=s)) <= 1e-13
+
+
 def test_errors():
     import torch
     blocks = make("2x2", n=8, nz=8, zpair="NN", walls=("N", "N", "N", "N"))
