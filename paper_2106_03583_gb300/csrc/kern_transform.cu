@@ -181,22 +181,36 @@ __global__ void __launch_bounds__(256) k_forward(const ChunkDev* __restrict__ ch
   }
   __syncthreads();
   const Cx<T>* R = cfft<T, TC>(A, Bf, m, tw.fft, false);
-  for (int idx = threadIdx.x; idx < n * TC; idx += blockDim.x) {
-    const int q = idx / TC, c = idx % TC;
-    T y;
-    if (kind == KIND_PP) {
-      const int k = q <= m ? q : n - q;
+  // F(x - shift0) = F(x) - shift0 F(1); F(1) is zero outside mode 0
+  auto put = [&](int q, int c, T y) {
+    if (q == 0) y -= sub0;
+    if (c < ch.ncol) out[(long long)q * ncell + B.off + ch.c0 + c] = y;
+  };
+  if (kind == KIND_PP || kind == KIND_NN || kind == KIND_DD) {
+    // each half-spectrum bin k = 0..m once; it gives output k and its mirror n - k
+    for (int idx = threadIdx.x; idx < (m + 1) * TC; idx += blockDim.x) {
+      const int k = idx / TC, c = idx % TC;
       const Cx<T> X = rdft_bin<T, TC>(R, k, m, c, tw);
-      y = q <= m ? X.re : X.im;
-    } else if (kind == KIND_NN || kind == KIND_DD) {
-      const int qq = kind == KIND_DD ? n - 1 - q : q;
-      const int k = qq <= m ? qq : n - qq;
-      Cx<T> V = rdft_bin<T, TC>(R, k, m, c, tw);
-      if (qq > m) V = conj(V);
-      const Cx<T> w = tw.tw2n[qq];
-      y = (T)2 * (w.re * V.re - w.im * V.im);
-    } else {
+      const bool mirror = k > 0 && k < m;
+      if (kind == KIND_PP) {
+        put(k, c, X.re);
+        if (mirror) put(n - k, c, X.im);
+      } else {
+        const Cx<T> w = tw.tw2n[k];
+        const T y = (T)2 * (w.re * X.re - w.im * X.im);
+        put(kind == KIND_DD ? n - 1 - k : k, c, y);
+        if (mirror) {  // bin n - k is conj(X_k)
+          const Cx<T> wm = tw.tw2n[n - k];
+          const T ym = (T)2 * (wm.re * X.re + wm.im * X.im);
+          put(kind == KIND_DD ? k - 1 : n - k, c, ym);
+        }
+      }
+    }
+  } else {
+    for (int idx = threadIdx.x; idx < n * TC; idx += blockDim.x) {
+      const int q = idx / TC, c = idx % TC;
       const int qq = kind == KIND_DN ? n - 1 - q : q;
+      T y;
       if ((qq & 1) == 0) {
         const int k = qq / 2;
         y = (T)2 * cmul(R[k * TC + c], tw.tw4b[k]).re;
@@ -204,9 +218,8 @@ __global__ void __launch_bounds__(256) k_forward(const ChunkDev* __restrict__ ch
         const int k = (n - 1 - qq) / 2;
         y = (T)-2 * cmul(R[k * TC + c], tw.tw4b[k]).im;
       }
+      put(q, c, y);
     }
-    if (q == 0) y -= sub0;  // F(x - shift0) = F(x) - shift0 F(1); F(1) is zero outside mode 0
-    if (c < ch.ncol) out[(long long)q * ncell + B.off + ch.c0 + c] = y;
   }
 }
 
@@ -235,26 +248,27 @@ __global__ void __launch_bounds__(256) k_backward(const ChunkDev* __restrict__ c
     const T v = xs[kk * TC + c];
     return (flip && (k & 1)) ? -v : v;
   };
-  for (int idx = threadIdx.x; idx < m * TC; idx += blockDim.x) {
-    const int k = idx / TC, c = idx % TC;
-    Cx<T> z;
-    if (kind == KIND_PP) {
-      const Cx<T> xk = k == 0 ? Cx<T>{X(0, c), 0} : Cx<T>{X(k, c), X(n - k, c)};
-      const int mk = m - k;
-      const Cx<T> xmk = mk == m ? Cx<T>{X(m, c), 0} : (mk == 0 ? Cx<T>{X(0, c), 0} : Cx<T>{X(mk, c), X(n - mk, c)});
-      z = irdft_pre(xk, xmk, tw.twn[k]);
-    } else if (kind == KIND_NN || kind == KIND_DD) {
-      // V_k = e^{+i pi k/2n} (X_k - i X_{n-k}), the real DFT of the reordered sequence
-      auto V = [&](int kk) -> Cx<T> {
-        Cx<T> v = cmul(conj(tw.tw2n[kk]), Cx<T>{X(kk, c), -X(n - kk, c)});
-        if (kk == 0 || kk == m) v.im = 0;
-        return v;
-      };
-      z = irdft_pre(V(k), V(m - k), tw.twn[k]);
-    } else {
-      z = cmul(Cx<T>{X(2 * k, c), X(n - 1 - 2 * k, c)}, tw.tw4a[k]);
+  if (kind == KIND_PP || kind == KIND_NN || kind == KIND_DD) {
+    // half-spectrum bin j of the real DFT being inverted: PP the stored bins (X_j, X_{n-j}),
+    // NN/DD V_j = e^{+i pi j/2n} (X_j - i X_{n-j}) (the real DFT of the reordered sequence)
+    auto bin = [&](int j, int c) -> Cx<T> {
+      if (kind == KIND_PP) return (j == 0 || j == m) ? Cx<T>{X(j, c), 0} : Cx<T>{X(j, c), X(n - j, c)};
+      Cx<T> v = cmul(conj(tw.tw2n[j]), Cx<T>{X(j, c), -X(n - j, c)});
+      if (j == 0 || j == m) v.im = 0;
+      return v;
+    };
+    // z_k needs bins k and m - k: each pair once, giving z_k and z_{m-k}
+    for (int idx = threadIdx.x; idx < (m / 2 + 1) * TC; idx += blockDim.x) {
+      const int k = idx / TC, c = idx % TC;
+      const Cx<T> b1 = bin(k, c), b2 = bin(m - k, c);
+      A[k * TC + c] = irdft_pre(b1, b2, tw.twn[k]);
+      if (k > 0 && m - k != k) A[(m - k) * TC + c] = irdft_pre(b2, b1, tw.twn[m - k]);
     }
-    A[idx] = z;
+  } else {
+    for (int idx = threadIdx.x; idx < m * TC; idx += blockDim.x) {
+      const int k = idx / TC, c = idx % TC;
+      A[idx] = cmul(Cx<T>{X(2 * k, c), X(n - 1 - 2 * k, c)}, tw.tw4a[k]);
+    }
   }
   __syncthreads();
   const bool inv = kind == KIND_PP || kind == KIND_NN || kind == KIND_DD;

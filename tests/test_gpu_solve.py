@@ -54,6 +54,38 @@ def test_workloads_vs_oracle(precision, name, scale):
     assert rel(p, po) <= PARITY, (rel(p, po), info)
 
 
+def _table2_blocks(refine, nz, z_bc):
+    """The four-block layout of Table 2 (its index-space corners, from the golden fixture), refined."""
+    import os
+    rows = []
+    with open(os.path.join(os.path.dirname(__file__), "golden", "table2_blocks.txt")) as fh:
+        for line in fh:
+            if line.strip() and not line.startswith("#"):
+                c = [t.split() for t in line.split("|")]
+                rows.append((tuple(map(int, c[1])), tuple(map(int, c[2]))))
+    x0, y0 = min(lo[0] for lo, _ in rows), min(lo[1] for lo, _ in rows)
+    rects = [((lo[0] - x0) * refine, (hi[0] - x0 + 1) * refine, (lo[1] - y0) * refine, (hi[1] - y0 + 1) * refine)
+             for lo, hi in rows]
+    NX, NY = max(r[1] for r in rects), max(r[3] for r in rects)
+    return inputs.make_blocks(inputs.tanh_faces(NX, 0, 1.0, 0.0, 4.0), inputs.tanh_faces(NY, 0, 1.0, 0.0, 2.0),
+                              np.linspace(0.0, 0.1 * nz / 2, nz + 1), rects,
+                              {"x-": "D", "x+": "N", "y-": "N", "y+": "N"}, z_bc)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("z_bc", [("N", "N"), ("P", "P")])
+def test_table2_layout_vs_oracle(precision, z_bc):
+    """The paper's four-block T-shaped example (Table 2, Fig. 1) refined 4x (blocks 80x40 and three
+    40x40, n_z = 16): fused levels across the T junction, a coarsest level with odd block sizes."""
+    blocks = _table2_blocks(4, 16, z_bc)
+    f = inputs.divergence_rhs(blocks, 4)
+    po, _ = osv.solve(blocks, f)
+    p, info, _ = gpu_solve(blocks, f, precision)
+    assert info["status"] == 0 and info["rel_res"] <= TOL
+    assert osv.rel_residual(blocks, f, p) <= 1.01 * TOL
+    assert rel(p, po) <= PARITY
+
+
 def test_ragged_tiles_and_periodic_xy():
     """Blocks whose sizes are not multiples of the 32x8 tile, periodic in x and y (singular)."""
     xf = inputs.tanh_faces(40, 0, 1.2, 0.0, 1.0)
