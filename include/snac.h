@@ -13,10 +13,11 @@
  * --------------------------------
  *  Layout.    A 3-D field (right-hand side, solution, residual) is one contiguous float64 buffer:
  *             blocks concatenated in id order, each block stored [z][y][x] with x fastest.
- *             A mode-space field ("modes") is [q][cell] with q the wavenumber (0..n_z-1) and cell
- *             running over the x-y cells of all blocks, block by block, [y][x] within a block;
- *             its element type is the plan's inner type (double for SNAC_FP64, float for
- *             SNAC_MIXED).
+ *             A mode-space field ("modes") is [q][cell] with q the wavenumber (0..n-1 along the
+ *             homogeneous axis) and cell running over the cells of the two other axes of all
+ *             blocks, block by block, [b][a] within a block with a < b the two non-homogeneous
+ *             axes (a fastest; [y][x] when z is homogeneous); its element type is the plan's
+ *             inner type (double for SNAC_FP64, float for SNAC_MIXED).
  *  Memory.    Pointers named d_* are device pointers on the current CUDA device; h_* are host
  *             pointers. The caller owns every buffer it passes; the library never frees them, never
  *             writes an input, and keeps no pointer to them after the call returns.
@@ -117,8 +118,13 @@ typedef struct {
 typedef struct snac_plan snac_plan;
 
 /* Build a plan for the multi-block problem (Sec. 3.1 setup; Table 1 for the homogeneous pair).
- * homog_axis must be 2 (z). On success *out receives a plan owning its device workspace, allocated
- * on the current CUDA device. */
+ * homog_axis (0 = x, 1 = y, 2 = z) names the homogeneous direction of Sec. 2 (the paper writes
+ * Eq. 9 with the synthesis along x2): uniform, one boundary pair shared by all blocks, not split into
+ * blocks (SNAC_ERR_LAYOUT otherwise). The caller's arrays keep the [z][y][x] layout whatever the
+ * axis; the transforms run along homog_axis and the multigrid on the planes of the other two.
+ * z is the fastest choice: with x, the outer residual walks the arrays across their contiguous
+ * axis. On success *out receives a plan owning its device workspace, allocated on the current CUDA
+ * device. */
 int snac_plan_create(snac_plan **out, int32_t nblocks, const snac_block *blocks, int32_t homog_axis,
                      const snac_options *opt);
 

@@ -34,12 +34,21 @@ __device__ __forceinline__ void block_sum(double (&v)[NV], double* sh /* [NV][32
 // per column. Only the sums a caller needs are formed: the kernel is bound by the FP64 pipe.
 // MODE 0: r = (f - fshift) - A p; partial {||r||^2, ||f - fshift||^2 (NEED_F2), sum V p (NEED_VP)}
 // MODE 1: r = A p
+// Caller-array offset (at k = 0) of plane cell l of block b, and that block's homogeneous stride.
+__device__ __forceinline__ long long caller_cell(const CallerBlk* __restrict__ cb, const BlockDev* __restrict__ blk,
+                                                int b, long long l, long long& sk) {
+  const CallerBlk c = cb[b];
+  const int nx = blk[b].nx;
+  sk = c.s[2];
+  return c.off3 + (l % nx) * c.s[0] + (l / nx) * c.s[1];
+}
+
 template <int MODE, bool SHIFT, bool NEED_F2, bool NEED_VP>
-__global__ void __launch_bounds__(TILE_THREADS) k_field3d(LevelView<double> L, const Coef<double>* __restrict__ cz,
-                                                           int nz, int periodic_z, double zd, double dz,
-                                                           const double* __restrict__ f, const double* __restrict__ p,
-                                                           double* __restrict__ r, double fshift,
-                                                           double* __restrict__ partial) {
+__global__ void __launch_bounds__(TILE_THREADS) k_field3d(LevelView<double> L, const CallerBlk* __restrict__ cb,
+                                                           const Coef<double>* __restrict__ cz, int nz, int periodic_z,
+                                                           double zd, double dz, const double* __restrict__ f,
+                                                           const double* __restrict__ p, double* __restrict__ r,
+                                                           double fshift, double* __restrict__ partial) {
   __shared__ double sh[4 * 32];
   const TileDev t = L.tiles[blockIdx.x];
   const BlockDev B = L.blk[t.b];
@@ -47,30 +56,29 @@ __global__ void __launch_bounds__(TILE_THREADS) k_field3d(LevelView<double> L, c
   double acc[3] = {0.0, 0.0, 0.0};
   if (i < B.nx && j < B.ny) {
     const Coef<double> cx = L.cx[B.xo + i], cy = L.cy[B.yo + j];
-    const long long plane = (long long)B.nx * B.ny;
-    const long long base = (long long)nz * B.off + (long long)j * B.nx + i;  // (k = 0)
-    // neighbours in x-y: block and in-plane index (self on a physical face, where the weight is 0)
+    // caller offsets at k = 0 of the cell and its four plane neighbours (self on a physical face,
+    // where the weight is 0), and the stride along the homogeneous axis of each one's block
+    long long sc, sw, se, ss, sn;
+    const long long base = caller_cell(cb, L.blk, t.b, (long long)j * B.nx + i, sc);
     int bw, be, bs, bn;
     long long lw, le, ls, ln;
     nbr_cells(L.blk, B, t.b, i, j, bw, lw, be, le, bs, ls, bn, ln);
-    const long long pw = nz * L.blk[bw].off + lw, pe = nz * L.blk[be].off + le;
-    const long long ps = nz * L.blk[bs].off + ls, pn = nz * L.blk[bn].off + ln;
-    const long long plw = (long long)L.blk[bw].nx * L.blk[bw].ny, ple = (long long)L.blk[be].nx * L.blk[be].ny;
-    const long long pls = (long long)L.blk[bs].nx * L.blk[bs].ny, pln = (long long)L.blk[bn].nx * L.blk[bn].ny;
+    const long long pw = caller_cell(cb, L.blk, bw, lw, sw), pe = caller_cell(cb, L.blk, be, le, se);
+    const long long ps = caller_cell(cb, L.blk, bs, ls, ss), pn = caller_cell(cb, L.blk, bn, ln, sn);
     const double dg = cx.d + cy.d + zd;
     const double va = cx.w * cy.w * dz;
     for (int k = blockIdx.y; k < nz; k += gridDim.y) {
-      const long long c = base + k * plane;
+      const long long c = base + k * sc;
       const Coef<double> z = cz[k];
       const int kd = k > 0 ? k - 1 : (periodic_z ? nz - 1 : k);
       const int ku = k < nz - 1 ? k + 1 : (periodic_z ? 0 : k);
       const double pc = p[c];
-      double ap = cx.lo * p[pw + k * plw];
-      ap = fma(cx.hi, p[pe + k * ple], ap);
-      ap = fma(cy.lo, p[ps + k * pls], ap);
-      ap = fma(cy.hi, p[pn + k * pln], ap);
-      ap = fma(z.lo, p[base + kd * plane], ap);
-      ap = fma(z.hi, p[base + ku * plane], ap);
+      double ap = cx.lo * p[pw + k * sw];
+      ap = fma(cx.hi, p[pe + k * se], ap);
+      ap = fma(cy.lo, p[ps + k * ss], ap);
+      ap = fma(cy.hi, p[pn + k * sn], ap);
+      ap = fma(z.lo, p[base + kd * sc], ap);
+      ap = fma(z.hi, p[base + ku * sc], ap);
       ap = fma(dg, pc, ap);
       if (MODE == 1) {
         r[c] = ap;
@@ -99,9 +107,10 @@ __global__ void __launch_bounds__(TILE_THREADS) k_field3d(LevelView<double> L, c
 // zero. partial {sum V f, sum V |f|, ||f||^2, sum f} (the first two and the last only for singular
 // problems); *nonzero = 1 if any p has a bit set other than its sign.
 template <bool SING>
-__global__ void __launch_bounds__(TILE_THREADS) k_prepass(LevelView<double> L, int nz, double dz,
-                                                           const double* __restrict__ f, const double* __restrict__ p,
-                                                           double* __restrict__ partial, int* __restrict__ nonzero) {
+__global__ void __launch_bounds__(TILE_THREADS) k_prepass(LevelView<double> L, const CallerBlk* __restrict__ cb, int nz,
+                                                           double dz, const double* __restrict__ f,
+                                                           const double* __restrict__ p, double* __restrict__ partial,
+                                                           int* __restrict__ nonzero) {
   __shared__ double sh[4 * 32];
   const TileDev t = L.tiles[blockIdx.x];
   const BlockDev B = L.blk[t.b];
@@ -110,10 +119,10 @@ __global__ void __launch_bounds__(TILE_THREADS) k_prepass(LevelView<double> L, i
   unsigned long long bits = 0;
   if (i < B.nx && j < B.ny) {
     const double va = L.cx[B.xo + i].w * L.cy[B.yo + j].w * dz;
-    const long long plane = (long long)B.nx * B.ny;
-    const long long base = (long long)nz * B.off + (long long)j * B.nx + i;
+    long long sk;
+    const long long base = caller_cell(cb, L.blk, t.b, (long long)j * B.nx + i, sk);
     for (int k = blockIdx.y; k < nz; k += gridDim.y) {
-      const long long c = base + k * plane;
+      const long long c = base + k * sk;
       const double fv = f[c];
       bits |= (unsigned long long)__double_as_longlong(p[c]);
       if (SING) {
@@ -192,8 +201,8 @@ __global__ void k_mean_of_p(double* sums, double vol_total) { sums[3] = sums[2] 
 template <int MODE, bool SH, bool F2, bool VP>
 void field3d_t(const LevelView<double>& L, dim3 grid, snac_plan* P, const double* f, const double* p, double* r,
                double fshift, cudaStream_t s) {
-  k_field3d<MODE, SH, F2, VP><<<grid, TILE_THREADS, 0, s>>>(L, P->d_cz, P->nz, P->kind == KIND_PP, P->cz[0].d, P->dz, f,
-                                                             p, r, fshift, P->d_partial);
+  k_field3d<MODE, SH, F2, VP><<<grid, TILE_THREADS, 0, s>>>(L, P->d_cblk, P->d_cz, P->nz, P->kind == KIND_PP, P->cz[0].d,
+                                                             P->dz, f, p, r, fshift, P->d_partial);
 }
 
 template <bool SH>
@@ -240,9 +249,9 @@ cudaError_t launch_prepass(snac_plan* P, const double* f, const double* p, cudaS
     // read f and p
     LaunchScope ls(P, K_FIELD3D, 16.0 * n3, (P->singular ? 7.0 : 2.0) * n3, s);
     if (P->singular)
-      k_prepass<true><<<grid, TILE_THREADS, 0, s>>>(L, P->nz, P->dz, f, p, P->d_partial, P->d_flag);
+      k_prepass<true><<<grid, TILE_THREADS, 0, s>>>(L, P->d_cblk, P->nz, P->dz, f, p, P->d_partial, P->d_flag);
     else
-      k_prepass<false><<<grid, TILE_THREADS, 0, s>>>(L, P->nz, P->dz, f, p, P->d_partial, P->d_flag);
+      k_prepass<false><<<grid, TILE_THREADS, 0, s>>>(L, P->d_cblk, P->nz, P->dz, f, p, P->d_partial, P->d_flag);
   }
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   const int npart = (int)(grid.x * grid.y);

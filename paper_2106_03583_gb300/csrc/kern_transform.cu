@@ -142,23 +142,44 @@ __device__ __forceinline__ Cx<T> irdft_pre(Cx<T> xk, Cx<T> xmk, const Cx<T>& twn
   return {E.re - O.im, E.im + O.re};  // E + i O
 }
 
+// Caller offsets (at k = 0) of the chunk's columns, and the caller stride along the homogeneous axis.
+template <int TC>
+__device__ __forceinline__ long long chunk_columns(const ChunkDev& ch, const BlockDev& B, const CallerBlk* __restrict__ cb,
+                                                   long long (&coff)[TC]) {
+  const CallerBlk C = cb[ch.b];
+  if (threadIdx.x < TC) {
+    const long long pc = (long long)ch.c0 + threadIdx.x;  // plane cell of the block
+    coff[threadIdx.x] = C.off3 + (pc % B.nx) * C.s[0] + (pc / B.nx) * C.s[1];
+  }
+  __syncthreads();
+  return C.s[2];
+}
+
 template <typename T, int TC, int KIND>
 __global__ void __launch_bounds__(256) k_forward(const ChunkDev* __restrict__ chunks, const BlockDev* __restrict__ blk,
-                                                 int n, Tw<T> tw, const double* __restrict__ in3,
-                                                 T* __restrict__ out, long long ncell, T sub0) {
+                                                 const CallerBlk* __restrict__ cb, int n, Tw<T> tw,
+                                                 const double* __restrict__ in3, T* __restrict__ out, long long ncell,
+                                                 T sub0) {
   constexpr int kind = KIND;
   extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ long long coff[TC];
   const int m = n / 2;
   Cx<T>* A = reinterpret_cast<Cx<T>*>(smem);
   Cx<T>* Bf = A + m * TC;
   T* xs = reinterpret_cast<T*>(Bf);  // n x TC reals, aliases Bf
   const ChunkDev ch = chunks[blockIdx.x];
   const BlockDev B = blk[ch.b];
-  const long long plane = (long long)B.nx * B.ny;
-  const long long base3 = (long long)n * B.off + ch.c0;
-  for (int idx = threadIdx.x; idx < n * TC; idx += blockDim.x) {
-    const int k = idx / TC, c = idx % TC;
-    xs[idx] = c < ch.ncol ? (T)in3[base3 + k * plane + c] : (T)0;
+  const long long sk = chunk_columns<TC>(ch, B, cb, coff);
+  if (sk == 1) {  // the homogeneous axis is the caller's contiguous one: consecutive threads along it
+    for (int idx = threadIdx.x; idx < n * TC; idx += blockDim.x) {
+      const int k = idx % n, c = idx / n;
+      xs[k * TC + c] = c < ch.ncol ? (T)in3[coff[c] + k] : (T)0;
+    }
+  } else {
+    for (int idx = threadIdx.x; idx < n * TC; idx += blockDim.x) {
+      const int k = idx / TC, c = idx % TC;
+      xs[idx] = c < ch.ncol ? (T)in3[coff[c] + k * sk] : (T)0;
+    }
   }
   __syncthreads();
   const bool flip = kind == KIND_DD || kind == KIND_DN;
@@ -225,8 +246,9 @@ __global__ void __launch_bounds__(256) k_forward(const ChunkDev* __restrict__ ch
 
 template <typename T, int TC, int KIND>
 __global__ void __launch_bounds__(256) k_backward(const ChunkDev* __restrict__ chunks, const BlockDev* __restrict__ blk,
-                                                  int n, Tw<T> tw, const T* __restrict__ modes,
-                                                  double* __restrict__ p3, long long ncell, double inv_theta) {
+                                                  const CallerBlk* __restrict__ cb, int n, Tw<T> tw,
+                                                  const T* __restrict__ modes, double* __restrict__ p3, long long ncell,
+                                                  double inv_theta) {
   constexpr int kind = KIND;
   extern __shared__ __align__(16) unsigned char smem[];
   const int m = n / 2;
@@ -273,10 +295,11 @@ __global__ void __launch_bounds__(256) k_backward(const ChunkDev* __restrict__ c
   __syncthreads();
   const bool inv = kind == KIND_PP || kind == KIND_NN || kind == KIND_DD;
   const Cx<T>* R = cfft<T, TC>(A, Bf, m, tw.fft, inv);
-  const long long plane = (long long)B.nx * B.ny;
-  const long long base3 = (long long)n * B.off + ch.c0;
+  __shared__ long long coff[TC];
+  const long long sk = chunk_columns<TC>(ch, B, cb, coff);
+  const bool along = sk == 1;  // consecutive threads along the homogeneous axis when it is contiguous
   for (int idx = threadIdx.x; idx < n * TC; idx += blockDim.x) {
-    const int j = idx / TC, c = idx % TC;
+    const int j = along ? idx % n : idx / TC, c = along ? idx / n : idx % TC;
     T y;
     if (kind == KIND_PP) {
       const Cx<T> z = R[(j >> 1) * TC + c];
@@ -297,7 +320,7 @@ __global__ void __launch_bounds__(256) k_backward(const ChunkDev* __restrict__ c
       }
     }
     if (c < ch.ncol) {
-      double* dst = p3 + base3 + j * plane + c;
+      double* dst = p3 + coff[c] + j * sk;
       *dst = fma((double)y, inv_theta, *dst);
     }
   }
@@ -322,8 +345,8 @@ cudaError_t fwd_t(snac_plan* P, const std::vector<ChunkDev>& ch, const ChunkDev*
   LaunchScope ls(P, K_FORWARD, (8.0 + sizeof(T)) * n3, (2.5 * std::log2((double)P->nz) + 8.0) * n3, s);
   auto go = [&](auto kern) {
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    kern<<<(unsigned)ch.size(), 256, smem, s>>>(dch, P->lev[0].d_blk, P->nz, make_tw<T>(P, twb), in3, (T*)modes,
-                                                P->lev[0].ncell, sub0);
+    kern<<<(unsigned)ch.size(), 256, smem, s>>>(dch, P->lev[0].d_blk, P->d_cblk, P->nz, make_tw<T>(P, twb), in3,
+                                                (T*)modes, P->lev[0].ncell, sub0);
   };
   switch (P->kind) {
     case KIND_PP: go(k_forward<T, TC, KIND_PP>); break;
@@ -344,8 +367,8 @@ cudaError_t bwd_t(snac_plan* P, const std::vector<ChunkDev>& ch, const ChunkDev*
   LaunchScope ls(P, K_BACKWARD, (16.0 + sizeof(T)) * n3, (2.5 * std::log2((double)P->nz) + 10.0) * n3, s);
   auto go = [&](auto kern) {
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    kern<<<(unsigned)ch.size(), 256, smem, s>>>(dch, P->lev[0].d_blk, P->nz, make_tw<T>(P, twb), (const T*)modes, p3,
-                                                P->lev[0].ncell, 1.0 / P->theta);
+    kern<<<(unsigned)ch.size(), 256, smem, s>>>(dch, P->lev[0].d_blk, P->d_cblk, P->nz, make_tw<T>(P, twb),
+                                                (const T*)modes, p3, P->lev[0].ncell, 1.0 / P->theta);
   };
   switch (P->kind) {
     case KIND_PP: go(k_backward<T, TC, KIND_PP>); break;

@@ -592,10 +592,40 @@ int upload_fused_tabs(snac_plan* P, HostLevel& lv, const HostLevel& lc) {
   return st;
 }
 
-int create(snac_plan** out, int32_t nblocks, const snac_block* blocks, int32_t homog_axis, const snac_options* opt) {
-  if (!out || !blocks || nblocks < 1) return fail(SNAC_ERR_INVALID_ARG, "out/blocks NULL or nblocks < 1");
+// Caller axis of each internal axis: the two non-homogeneous axes in increasing order, then the
+// homogeneous one (the plan works on internal (i, j) planes and transforms along internal k).
+void axis_order(int homog, int (&perm)[3]) {
+  int k = 0;
+  for (int a = 0; a < 3; ++a)
+    if (a != homog) perm[k++] = a;
+  perm[2] = homog;
+}
+
+// The blocks with their axes in internal order (the cell-width arrays are shared, not copied).
+std::vector<snac_block> internal_blocks(int nblocks, const snac_block* blocks, int homog) {
+  int perm[3];
+  axis_order(homog, perm);
+  std::vector<snac_block> out(blocks, blocks + nblocks);
+  for (int b = 0; b < nblocks; ++b)
+    for (int a = 0; a < 3; ++a) {
+      const int c = perm[a];
+      out[b].lo[a] = blocks[b].lo[c];
+      out[b].hi[a] = blocks[b].hi[c];
+      out[b].h_dx[a] = blocks[b].h_dx[c];
+      for (int sd = 0; sd < 2; ++sd) {
+        out[b].bc[a][sd] = blocks[b].bc[c][sd];
+        out[b].nbr[a][sd] = blocks[b].nbr[c][sd];
+      }
+    }
+  return out;
+}
+
+int create(snac_plan** out, int32_t nblocks, const snac_block* blocks_in, int32_t homog_axis, const snac_options* opt) {
+  if (!out || !blocks_in || nblocks < 1) return fail(SNAC_ERR_INVALID_ARG, "out/blocks NULL or nblocks < 1");
   *out = nullptr;
-  if (homog_axis != 2) return fail(SNAC_ERR_INVALID_ARG, "only homog_axis = 2 (z) is supported");
+  if (homog_axis < 0 || homog_axis > 2) return fail(SNAC_ERR_INVALID_ARG, "homog_axis must be 0, 1 or 2");
+  const std::vector<snac_block> iblocks = internal_blocks(nblocks, blocks_in, homog_axis);
+  const snac_block* blocks = iblocks.data();
   std::vector<HBlock> hb;
   int st = validate(nblocks, blocks, hb);
   if (st) return st;
@@ -644,6 +674,17 @@ int create(snac_plan** out, int32_t nblocks, const snac_block* blocks, int32_t h
   P->area_total = 0.0;
   for (const HBlock& h : hb) {
     P->blk_off3.push_back(off3);
+    {
+      // caller strides of the internal axes: the caller block is [z][y][x], x fastest
+      int perm[3];
+      axis_order(homog_axis, perm);
+      long long n_caller[3], s_caller[3];
+      for (int a = 0; a < 3; ++a) n_caller[perm[a]] = h.n[a];
+      s_caller[0] = 1;
+      s_caller[1] = n_caller[0];
+      s_caller[2] = n_caller[0] * n_caller[1];
+      P->cblk.push_back({off3, {s_caller[perm[0]], s_caller[perm[1]], s_caller[perm[2]]}});
+    }
     off3 += (long long)h.n[0] * h.n[1] * h.n[2];
     double ax = 0, ay = 0;
     for (double w : h.w[0]) ax += w;
@@ -669,7 +710,7 @@ int create(snac_plan** out, int32_t nblocks, const snac_block* blocks, int32_t h
       if (!per && k == P->nz - 1) c.hi = zh == SNAC_BC_DIRICHLET ? -iz2 : iz2;
       P->cz.push_back(c);
     }
-    if ((st = upload(P, &P->d_cz, P->cz))) break;
+    if ((st = upload(P, &P->d_cz, P->cz)) || (st = upload(P, &P->d_cblk, P->cblk))) break;
     for (int q = 0; q < P->nz; ++q) {
       P->sigma.push_back(mode_lambda(P->kind, P->nz, q) * iz2 + P->shift);
       P->pweight.push_back(parseval_weight(P->kind, P->nz, q));
@@ -758,10 +799,12 @@ int create(snac_plan** out, int32_t nblocks, const snac_block* blocks, int32_t h
 namespace snac {
 int plan_inner_size(const snac_plan* P) { return P->precision == SNAC_FP64 ? 8 : 4; }
 
-int check_layout(int nblocks, const snac_block* blocks) {
+int check_layout(int nblocks, const snac_block* blocks, int homog_axis) {
   if (!blocks || nblocks < 1) return fail(SNAC_ERR_INVALID_ARG, "blocks NULL or nblocks < 1");
+  if (homog_axis < 0 || homog_axis > 2) return fail(SNAC_ERR_INVALID_ARG, "homog_axis must be 0, 1 or 2");
+  const std::vector<snac_block> ib = internal_blocks(nblocks, blocks, homog_axis);
   std::vector<HBlock> hb;
-  return validate(nblocks, blocks, hb);
+  return validate(nblocks, ib.data(), hb);
 }
 }  // namespace snac
 

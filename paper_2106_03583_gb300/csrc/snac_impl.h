@@ -45,6 +45,14 @@ struct BlockDev {
   int pad;
 };
 
+// Where a block's cells sit in the caller's 3-D arrays ([z][y][x] per block, blocks concatenated):
+// cell (i, j, k) of the internal axes (plane axes i, j; homogeneous axis k) is at off3 + i s[0] +
+// j s[1] + k s[2].
+struct CallerBlk {
+  long long off3;
+  long long s[3];
+};
+
 struct TileDev {
   int b, x0, y0, pad;
 };
@@ -155,6 +163,8 @@ struct snac_plan {
   double vol_total = 0.0;
   double area_total = 0.0;
   std::vector<long long> blk_off3;  // 3-D offset of each block
+  std::vector<snac::CallerBlk> cblk;  // caller offset and strides of each block's internal axes
+  snac::CallerBlk* d_cblk = nullptr;
   std::vector<snac::HostLevel> lev;
   // z direction
   std::vector<snac::Coef<double>> cz;
@@ -242,7 +252,7 @@ cudaError_t launch_fused_up(snac_plan* P, int l, int nact, bool norms, cudaStrea
 
 int plan_inner_size(const snac_plan* P);  // bytes of the inner type
 // the block-layout checks of plan creation (sizes, widths, face kinds, z pair, connectivity)
-int check_layout(int nblocks, const snac_block* blocks);
+int check_layout(int nblocks, const snac_block* blocks, int homog_axis);
 
 // Counts one launch of `kind` with its algorithmic bytes / flops; with profiling on, brackets it
 // with a CUDA event pair on stream s (construct just before the launch, destroy just after).

@@ -9,7 +9,7 @@ import pytest
 
 from paper_2106_03583_gb300 import build, inputs, snac
 
-from layouts import make
+from layouts import homogeneous_along, make
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
@@ -70,8 +70,8 @@ def test_layout_validation(lib):
     cong[1] = dict(cong[1], dx=(cong[1]["dx"][0], wy, cong[1]["dx"][2]))
     st, msg = _create(lib, cong)
     assert st == -2 and "congruent" in msg
-    st, _ = _create(lib, good, homog=0)
-    assert st == -1
+    st, _ = _create(lib, good, homog=0)     # split into blocks along x: x cannot be the homogeneous axis
+    assert st == -2
     neg = [dict(good[0], dx=(-good[0]["dx"][0], good[0]["dx"][1], good[0]["dx"][2]))] + good[1:]
     st, _ = _create(lib, neg)
     assert st == -1
@@ -114,3 +114,16 @@ def test_option_validation(lib):
                             o["fused"], o["inner_reduction"], o["shift"])
         st, msg = _create(lib, blocks, opt=ctypes.byref(opt))
         assert st == -1 and "options" in msg, (kw, st, msg)
+
+
+def test_homogeneous_axis_validation(lib):
+    """homog_axis is 0, 1 or 2; the chosen axis must be the one the blocks are not split along."""
+    blocks = make("L", n=4, nz=6, zpair="DN", walls=("D", "N", "N", "N"))
+    f = np.zeros(inputs.total_cells(blocks))
+    st, msg = _create(lib, blocks, homog=3)
+    assert st == -1 and "homog_axis" in msg
+    relabelled, _, _ = homogeneous_along(blocks, f, 0)     # homogeneous direction now along caller x
+    st, msg = _create(lib, relabelled, homog=2)             # caller z is split into blocks
+    assert st == -2
+    st, msg = _create(lib, relabelled, homog=1)
+    assert st == -2
