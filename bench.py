@@ -439,7 +439,12 @@ def _latency_summary(res):
     t0 = min(t["t_submit"] for _, t in res)
     t1 = max(t["t_done"] for _, t in res)
     ok = sum(1 for i, _ in res if i["status"] == 0)
-    return {"requests": len(res), "ok": ok, "solves_per_s": len(res) / (t1 - t0), "p50_ms": float(np.median(lat)),
+    failed = {}
+    for k, (i, _) in enumerate(res):
+        if i["status"] != 0:
+            failed.setdefault(i["status_name"], []).append(k)
+    return {"requests": len(res), "ok": ok, "failed": failed, "solves_per_s": len(res) / (t1 - t0),
+            "p50_ms": float(np.median(lat)),
             "p99_ms": float(np.percentile(lat, 99)), "mean_ms": float(lat.mean()),
             "plan_reuse": sum(t["plan_reused"] for _, t in res) / len(res)}
 
@@ -527,21 +532,26 @@ def run_batch(args):
     for pl in plans:
         pl.close()
     del fd, ps
-    with snac.Engine(workers=args.workers, hbm_budget=150e9) as eng:
-        work = [(b, f, 1e-10, "mixed") for b, f, _ in probs]
-        _engine_solve_all(eng, work)          # builds and caches the 64 plans
-        reps = []
-        for _ in range(3):
-            res = _engine_solve_all(eng, work)
-            reps.append(_latency_summary(res))
-    best = max(reps, key=lambda r: r["solves_per_s"])
+    work = [(b, f, 1e-10, "mixed") for b, f, _ in probs]
+
+    def engine_rate(autotune):
+        with snac.Engine(workers=args.workers, hbm_budget=150e9, autotune=autotune) as eng:
+            t0 = time.time()
+            _engine_solve_all(eng, work)      # builds (and, with autotune, tunes) and caches the 64 plans
+            setup_s = time.time() - t0
+            reps = [_latency_summary(_engine_solve_all(eng, work)) for _ in range(3)]
+        return max(reps, key=lambda r: r["solves_per_s"]), setup_s
+
+    best, setup_s = engine_rate(False)
+    tuned, tune_s = engine_rate(True)
     line = {"metric": "batch of 64 independent problems: solves/s", "mode": "batch", "unit": "solves/s",
             "n_gpus": 1, "data": "synthetic",
             "config": {"workload": "64 seeded problems 32^3..256x256x128 (log-uniform per axis), 1-4 blocks, random "
                                    "walls and z pair, f ~ U[-1,1]; mixed precision, tol 1e-10",
                        "workers": args.workers, "cells": int(sum(len(f) for _, f, _ in probs))},
-            "value": best["solves_per_s"], "host_inputs_in_timed_region": True,
-            "one_at_a_time_device_resident_solves_per_s": seq, "engine": best}
+            "value": max(best["solves_per_s"], tuned["solves_per_s"]), "host_inputs_in_timed_region": True,
+            "one_at_a_time_device_resident_solves_per_s": seq, "engine": best,
+            "engine_autotuned": dict(tuned, first_pass_s=tune_s), "engine_first_pass_s": setup_s}
     print(json.dumps(line), flush=True)
 
 

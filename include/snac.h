@@ -154,6 +154,27 @@ const char *snac_status_string(int status);
 /* Detail of the last error raised by plan creation on this thread (empty if none). */
 const char *snac_last_error_message(void);
 
+/* ---- Schedule autotuning ---- */
+
+typedef struct {
+  int32_t trials;      /* configurations timed (each: plan creation, one warm solve, timed solves)  */
+  int32_t improved;    /* 1 if the chosen options differ from the ones passed in                  */
+  double base_ms;      /* mean solve time with the options passed in                              */
+  double best_ms;      /* mean solve time with the chosen options                                 */
+} snac_tune_report;
+
+/* Choose the multigrid schedule for one problem by timing complete solves (snac_poisson_solve from
+ * p = 0) of a representative right-hand side d_rhs (device float64 field, caller layout) at tol.
+ * Starting from *base (NULL = defaults), coordinate descent over: (nu1, nu2) in {(2,2), (2,1),
+ * (1,2), (1,1)}; max_coarse in {16, 64, 256}; and for SNAC_MIXED, inner_reduction in {1e-3, 3e-3,
+ * 3e-4} and fused in {auto, off}. A candidate counts only if its solve succeeds at tol. *best
+ * receives the fastest options (precision, max_outer, max_cycles and shift are kept from *base).
+ * The paper has no counterpart (its multigrid is hypre's); this is the schedule choice of a serving
+ * system. Allocates and frees plans and an 8-byte-per-cell scratch field on the current device;
+ * runs on `stream` and returns when done. report may be NULL. */
+int snac_autotune(int32_t nblocks, const snac_block *blocks, int32_t homog_axis, const snac_options *base,
+                  const double *d_rhs, double tol, snac_options *best, snac_tune_report *report, void *stream);
+
 /* ---- Kernel statistics (tracing) ---- */
 
 /* Per-kernel counters of a plan: launches (always counted), and with profiling enabled the summed

@@ -28,6 +28,10 @@
  *             scanned in arrival order and the first request that fits is admitted (first fit), so a
  *             small request is not held behind a large one. A request that can never fit is refused
  *             at submission (SNAC_ERR_OOM).
+ *  Tuning.    With autotune, a problem's first request also times candidate schedules
+ *             (snac_autotune) before its solve; the tuner's scratch field (8 bytes per cell) is
+ *             counted in that request's admission. Results stay those of snac_poisson_solve with the
+ *             chosen options.
  *  Times.     Each request records, on the engine's monotonic clock (seconds): submission, admission,
  *             start on a worker, and completion (solution on the host).
  *
@@ -56,12 +60,16 @@ typedef struct {
   int32_t workers;          /* worker threads / CUDA streams, 1..64 (4)                                  */
   int32_t max_cached_plans; /* idle plans kept resident, 0..4096 (64)                                     */
   uint64_t hbm_budget;      /* device bytes the engine may hold (150e9); must cover the largest request  */
+  int32_t autotune;         /* 1: the first request of each problem runs snac_autotune on its own
+                               right-hand side (from its submitted options) and later requests of that
+                               problem reuse the chosen schedule; 0: options as submitted (0)         */
 } snac_engine_options;
 
 typedef struct {
   double t_submit, t_admit, t_start, t_done; /* engine clock, seconds                                 */
   int32_t worker;                            /* worker that ran the request                           */
   int32_t plan_reused;                       /* 1 if a cached plan served it, 0 if one was built      */
+  int32_t tuned;                             /* 1 if this request ran the autotuner                   */
 } snac_request_times;
 
 typedef struct {

@@ -49,6 +49,8 @@ struct Request {
   std::string key;
   uint64_t buf_bytes = 0;      // device copies of f and p
   uint64_t plan_estimate = 0;  // reservation while its plan is built
+  uint64_t tune_bytes = 0;     // the autotuner's scratch field, while it runs
+  bool tune = false;           // this request runs the autotuner
   // progress
   State state = State::Queued;
   PlanSlot* slot = nullptr;
@@ -114,6 +116,7 @@ struct snac_engine {
   std::deque<Request*> ready;  // admitted, waiting for a worker
   std::map<int64_t, Request*> tickets;
   std::list<PlanSlot*> plans;
+  std::map<std::string, snac_options> tuned;  // problem key -> chosen schedule (autotune)
   uint64_t used = 0, peak = 0, use_clock = 0;
   int running = 0;
   int64_t completed = 0, built = 0, evicted = 0, next_ticket = 1;
@@ -153,7 +156,8 @@ struct snac_engine {
       PlanSlot* idle = nullptr;
       for (PlanSlot* s : plans)
         if (!s->busy && s->key == r->key && (!idle || s->last_use > idle->last_use)) idle = s;
-      const uint64_t need = r->buf_bytes + (idle ? 0 : r->plan_estimate);
+      r->tune = !idle && opt.autotune && tuned.find(r->key) == tuned.end();
+      const uint64_t need = r->buf_bytes + (idle ? 0 : r->plan_estimate) + (r->tune ? r->tune_bytes : 0);
       while (used + need > opt.hbm_budget && evict_one(idle, dead)) {
       }
       if (used + need > opt.hbm_budget) {
@@ -190,19 +194,56 @@ void destroy_plans(const std::vector<snac_plan*>& dead) {
 // One request on stream s: build its plan if needed, copy f in, solve from zero, copy p out.
 int snac_engine::run(Request* r, cudaStream_t s) {
   int st = SNAC_OK;
+  const size_t nb = (size_t)r->n3 * sizeof(double);
+  double *d_f = nullptr, *d_p = nullptr;
+  if (cudaMallocAsync((void**)&d_f, nb, s) != cudaSuccess || cudaMallocAsync((void**)&d_p, nb, s) != cudaSuccess) {
+    cudaGetLastError();
+    if (d_f) cudaFreeAsync(d_f, s);
+    cudaStreamSynchronize(s);
+    std::lock_guard<std::mutex> lk(mu);
+    if (r->build_plan) account(-(int64_t)r->plan_estimate);
+    if (r->tune) account(-(int64_t)r->tune_bytes);
+    return SNAC_ERR_OOM;
+  }
+  bool ok = cudaMemcpyAsync(d_f, r->h_rhs, nb, cudaMemcpyHostToDevice, s) == cudaSuccess;
   if (r->build_plan) {
+    snac_options use = r->has_opt ? r->opt : snac_options{};
+    bool have_opt = r->has_opt;
+    if (r->tune && ok) {  // choose the schedule on this request's right-hand side
+      snac_options chosen{};
+      if (snac_autotune((int32_t)r->blocks.size(), r->blocks.data(), r->homog_axis, r->has_opt ? &r->opt : nullptr,
+                        d_f, r->tol, &chosen, nullptr, s) == SNAC_OK) {
+        use = chosen;
+        have_opt = true;
+        std::lock_guard<std::mutex> lk(mu);
+        tuned[r->key] = chosen;
+      }
+      r->times.tuned = 1;
+    } else {
+      std::lock_guard<std::mutex> lk(mu);
+      auto it = tuned.find(r->key);
+      if (it != tuned.end()) {
+        use = it->second;
+        have_opt = true;
+      }
+    }
     snac_plan* pl = nullptr;
-    st = snac_plan_create(&pl, (int32_t)r->blocks.size(), r->blocks.data(), r->homog_axis,
-                          r->has_opt ? &r->opt : nullptr);
+    st = snac_plan_create(&pl, (int32_t)r->blocks.size(), r->blocks.data(), r->homog_axis, have_opt ? &use : nullptr);
     size_t bytes = 0;
     if (st == SNAC_OK) snac_plan_workspace_bytes(pl, &bytes);
     std::lock_guard<std::mutex> lk(mu);
     account(-(int64_t)r->plan_estimate);
-    if (st != SNAC_OK) return st;
-    PlanSlot* slot = new (std::nothrow) PlanSlot{r->key, pl, (uint64_t)bytes, true, 0};
-    if (!slot) {
+    if (r->tune) account(-(int64_t)r->tune_bytes);
+    PlanSlot* slot = st == SNAC_OK ? new (std::nothrow) PlanSlot{r->key, pl, (uint64_t)bytes, true, 0} : nullptr;
+    if (st == SNAC_OK && !slot) {
       snac_plan_destroy(pl);
-      return SNAC_ERR_OOM;
+      st = SNAC_ERR_OOM;
+    }
+    if (st != SNAC_OK) {
+      cudaFreeAsync(d_f, s);
+      cudaFreeAsync(d_p, s);
+      cudaStreamSynchronize(s);
+      return st;
     }
     account((int64_t)bytes);
     plans.push_back(slot);
@@ -210,16 +251,7 @@ int snac_engine::run(Request* r, cudaStream_t s) {
     ++built;
   }
   r->times.plan_reused = r->build_plan ? 0 : 1;
-  const size_t nb = (size_t)r->n3 * sizeof(double);
-  double *d_f = nullptr, *d_p = nullptr;
-  if (cudaMallocAsync((void**)&d_f, nb, s) != cudaSuccess || cudaMallocAsync((void**)&d_p, nb, s) != cudaSuccess) {
-    cudaGetLastError();
-    if (d_f) cudaFreeAsync(d_f, s);
-    cudaStreamSynchronize(s);
-    return SNAC_ERR_OOM;
-  }
-  bool ok = cudaMemcpyAsync(d_f, r->h_rhs, nb, cudaMemcpyHostToDevice, s) == cudaSuccess &&
-            cudaMemsetAsync(d_p, 0, nb, s) == cudaSuccess;
+  ok = ok && cudaMemsetAsync(d_p, 0, nb, s) == cudaSuccess;
   if (ok) {
     st = snac_poisson_solve(r->slot->plan, d_f, d_p, r->tol, s);
     snac_plan_info(r->slot->plan, &r->info);
@@ -283,9 +315,10 @@ double snac_engine_clock(void) { return now_s(); }
 int snac_engine_create(snac_engine** out, const snac_engine_options* opt) {
   if (!out) return SNAC_ERR_INVALID_ARG;
   *out = nullptr;
-  snac_engine_options o{4, 64, 150000000000ull};
+  snac_engine_options o{4, 64, 150000000000ull, 0};
   if (opt) o = *opt;
-  if (o.workers < 1 || o.workers > 64 || o.max_cached_plans < 0 || o.max_cached_plans > 4096 || o.hbm_budget == 0)
+  if (o.workers < 1 || o.workers > 64 || o.max_cached_plans < 0 || o.max_cached_plans > 4096 || o.hbm_budget == 0 ||
+      (o.autotune != 0 && o.autotune != 1))
     return SNAC_ERR_INVALID_ARG;
   snac_engine* e = new (std::nothrow) snac_engine();
   if (!e) return SNAC_ERR_OOM;
@@ -342,7 +375,8 @@ int snac_engine_submit(snac_engine* e, int32_t nblocks, const snac_block* blocks
   r->key = problem_key(*r);
   r->buf_bytes = 16ull * (uint64_t)n3;
   r->plan_estimate = plan_estimate(n3, !(opt && opt->precision == SNAC_MIXED));
-  if (r->buf_bytes + r->plan_estimate > e->opt.hbm_budget) {
+  r->tune_bytes = e->opt.autotune ? 8ull * (uint64_t)n3 : 0;
+  if (r->buf_bytes + r->plan_estimate + r->tune_bytes > e->opt.hbm_budget) {
     delete r;
     return SNAC_ERR_OOM;
   }

@@ -31,7 +31,7 @@ EXPORTS = ("snac_plan_create", "snac_plan_workspace_bytes", "snac_poisson_solve"
            "snac_mode_operator", "snac_mode_vcycles", "snac_plan_set_profiling", "snac_plan_kernel_stats",
            "snac_plan_reset_stats", "snac_residual_noalloc",
            "snac_engine_create", "snac_engine_submit", "snac_engine_wait", "snac_engine_get_stats",
-           "snac_engine_clock", "snac_engine_destroy")
+           "snac_engine_clock", "snac_engine_destroy", "snac_autotune")
 
 
 class SnacError(RuntimeError):
@@ -64,12 +64,19 @@ class _Info(ctypes.Structure):
 
 
 class _EngineOptions(ctypes.Structure):
-    _fields_ = [("workers", ctypes.c_int32), ("max_cached_plans", ctypes.c_int32), ("hbm_budget", ctypes.c_uint64)]
+    _fields_ = [("workers", ctypes.c_int32), ("max_cached_plans", ctypes.c_int32), ("hbm_budget", ctypes.c_uint64),
+                ("autotune", ctypes.c_int32)]
 
 
 class _Times(ctypes.Structure):
     _fields_ = [("t_submit", ctypes.c_double), ("t_admit", ctypes.c_double), ("t_start", ctypes.c_double),
-                ("t_done", ctypes.c_double), ("worker", ctypes.c_int32), ("plan_reused", ctypes.c_int32)]
+                ("t_done", ctypes.c_double), ("worker", ctypes.c_int32), ("plan_reused", ctypes.c_int32),
+                ("tuned", ctypes.c_int32)]
+
+
+class _TuneReport(ctypes.Structure):
+    _fields_ = [("trials", ctypes.c_int32), ("improved", ctypes.c_int32), ("base_ms", ctypes.c_double),
+                ("best_ms", ctypes.c_double)]
 
 
 class _EngineStats(ctypes.Structure):
@@ -119,6 +126,8 @@ def lib() -> ctypes.CDLL:
             "snac_engine_get_stats": [vp, ctypes.POINTER(_EngineStats)],
             "snac_engine_clock": [],
             "snac_engine_destroy": [vp],
+            "snac_autotune": [i32, ctypes.POINTER(_Block), i32, ctypes.POINTER(_Options), vp, f64,
+                              ctypes.POINTER(_Options), ctypes.POINTER(_TuneReport), vp],
         }
         for name, args in sig.items():
             fn = getattr(L, name)
@@ -314,12 +323,13 @@ class Engine:
         p, info, times = eng.wait(t)
     """
 
-    def __init__(self, workers: int = 4, hbm_budget: float = 150e9, max_cached_plans: int = 64):
+    def __init__(self, workers: int = 4, hbm_budget: float = 150e9, max_cached_plans: int = 64,
+                 autotune: bool = False):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("snac.Engine needs a CUDA device")
         torch.cuda.init()
-        opt = _EngineOptions(int(workers), int(max_cached_plans), int(hbm_budget))
+        opt = _EngineOptions(int(workers), int(max_cached_plans), int(hbm_budget), 1 if autotune else 0)
         h = ctypes.c_void_p()
         _check(lib().snac_engine_create(ctypes.byref(h), ctypes.byref(opt)))
         self._h = h
@@ -383,3 +393,34 @@ class Engine:
 
     def __exit__(self, *exc):
         self.close()
+
+
+_OPTION_NAMES = ("nu1", "nu2", "max_outer", "max_cycles", "max_coarse", "fused", "inner_reduction", "shift")
+
+
+def autotune(blocks, rhs, tol: float = 1e-10, precision: str = "fp64", homog_axis: int = 2, **base):
+    """``snac_autotune``: the fastest multigrid schedule for this problem, found by timing complete
+    solves of ``rhs`` (a CUDA float64 tensor in the caller layout) on the current stream.
+    ``base`` overrides the starting options (Plan's keywords). Returns (options for Plan, report)."""
+    import torch
+    if precision not in _PREC:
+        raise ValueError(f"precision must be one of {list(_PREC)}")
+    n3 = int(sum(np.prod([b["hi"][a] - b["lo"][a] + 1 for a in range(3)]) for b in blocks))
+    if not isinstance(rhs, torch.Tensor) or not rhs.is_cuda or rhs.dtype != torch.float64 or \
+            not rhs.is_contiguous() or rhs.numel() != n3:
+        raise ValueError(f"rhs must be a contiguous CUDA float64 tensor with {n3} elements")
+    d = dict(nu1=2, nu2=2, max_outer=20, max_cycles=40, max_coarse=64, fused=-1, inner_reduction=1e-3, shift=0.0)
+    unknown = set(base) - set(d)
+    if unknown:
+        raise ValueError(f"unknown options {sorted(unknown)}")
+    d.update(base)
+    opt = _Options(_PREC[precision], *(d[k] for k in _OPTION_NAMES))
+    best, rep = _Options(), _TuneReport()
+    arr, keep = _marshal_blocks(blocks)
+    stream = ctypes.c_void_p(torch.cuda.current_stream(rhs.device).cuda_stream)
+    _check(lib().snac_autotune(len(blocks), arr, homog_axis, ctypes.byref(opt), ctypes.c_void_p(rhs.data_ptr()),
+                               float(tol), ctypes.byref(best), ctypes.byref(rep), stream))
+    del keep
+    chosen = {k: getattr(best, k) for k in _OPTION_NAMES}
+    chosen["precision"] = precision
+    return chosen, {k: getattr(rep, k) for k, _ in _TuneReport._fields_}

@@ -127,3 +127,13 @@ def test_homogeneous_axis_validation(lib):
     assert st == -2
     st, msg = _create(lib, relabelled, homog=1)
     assert st == -2
+
+
+def test_autotune_argument_checks(lib):
+    blocks = make("1", n=4, nz=8, zpair="NN")
+    arr, keep = snac._marshal_blocks(blocks)
+    best = snac._Options()
+    assert lib.snac_autotune(0, arr, 2, None, ctypes.c_void_p(8), 1e-10, ctypes.byref(best), None, None) == -1
+    assert lib.snac_autotune(1, arr, 2, None, None, 1e-10, ctypes.byref(best), None, None) == -1
+    assert lib.snac_autotune(1, arr, 2, None, ctypes.c_void_p(8), 0.0, ctypes.byref(best), None, None) == -1
+    assert lib.snac_autotune(1, arr, 5, None, ctypes.c_void_p(8), 1e-10, ctypes.byref(best), None, None) == -1

@@ -106,3 +106,35 @@ def test_plan_reuse_and_errors():
         with pytest.raises(snac.SnacError) as e:
             small.wait(12345)
         assert e.value.name == "INVALID_ARG"
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_autotune_picks_a_converging_schedule(precision):
+    """snac_autotune times candidate schedules on the problem itself; the chosen one is no slower
+    than the starting options and solves to the tolerance."""
+    import torch
+    ensure_built()
+    blocks = make("2x2", n=32, nz=16, zpair="NN", walls=("N", "N", "N", "N"), stretched=True)
+    f = inputs.divergence_rhs(blocks, 2)
+    chosen, rep = snac.autotune(blocks, dev(f), tol=TOL, precision=precision)
+    assert rep["trials"] >= 6 and rep["best_ms"] <= rep["base_ms"]
+    pl = snac.Plan(blocks, **chosen)
+    p = torch.zeros(len(f), dtype=torch.float64, device="cuda")
+    info = pl.solve(dev(f), p, tol=TOL)
+    assert info["status"] == 0 and info["rel_res"] <= TOL
+    po, _ = osv.solve(blocks, f)
+    assert rel(host(p), po) <= 1e-9
+
+
+def test_engine_autotune_once_per_problem():
+    blocks = make("L", n=16, nz=8, zpair="DD", walls=("N", "D", "D", "N"), stretched=True)
+    f = inputs.divergence_rhs(blocks, 3)
+    po, _ = osv.solve(blocks, f)
+    with snac.Engine(workers=2, hbm_budget=4e9, autotune=True) as eng:
+        res = [eng.wait(eng.submit(blocks, f, tol=TOL, precision="mixed")) for _ in range(3)]
+    (p1, i1, t1), (p2, i2, t2), (p3, i3, t3) = res
+    assert t1["tuned"] == 1 and t2["tuned"] == 0 and t3["tuned"] == 0
+    assert t2["plan_reused"] == 1 and t3["plan_reused"] == 1
+    assert np.array_equal(p2, p3)                 # the same tuned plan, the same result
+    for p, info in ((p1, i1), (p2, i2)):
+        assert info["status"] == 0 and info["rel_res"] <= TOL and rel(p, po) <= 1e-9
