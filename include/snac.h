@@ -113,6 +113,7 @@ typedef struct {
   double rel_res;        /* final ||f - A p||_2 / ||f||_2 (f after mean removal)                     */
   double rhs_norm;       /* ||f||_2                                                                  */
   double removed_mean;   /* volume-weighted mean removed from f (singular problems), else 0         */
+  int32_t graph_rounds;  /* V-cycle rounds of the solve replayed from captured CUDA graphs          */
 } snac_solve_info;
 
 typedef struct snac_plan snac_plan;

@@ -479,6 +479,9 @@ int upload_level(snac_plan* P, HostLevel& lv, size_t inner) {
 void free_plan(snac_plan* P) {
   if (!P) return;
   profile_release(P);
+  for (auto& kv : P->round_graphs)
+    if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+  if (P->capture_stream) cudaStreamDestroy(P->capture_stream);
   for (void* p : P->allocs) cudaFree(p);
   if (P->h_sums) cudaFreeHost(P->h_sums);
   if (P->h_mode_norm2) cudaFreeHost(P->h_mode_norm2);

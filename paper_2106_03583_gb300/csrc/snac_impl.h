@@ -14,6 +14,7 @@
 
 #include <cstddef>
 #include <cstdint>
+#include <map>
 #include <string>
 #include <vector>
 
@@ -207,6 +208,15 @@ struct snac_plan {
   std::vector<int32_t> mode_cycles;
   // tracing
   bool profiling = false;
+  // One V-cycle round (all levels + the per-mode norms) captured as a CUDA graph per number of active
+  // modes, replayed on the solve's stream; `delta` = the launch statistics of one round.
+  struct RoundGraph {
+    cudaGraphExec_t exec = nullptr;
+    snac::KernelStat delta[snac::K_COUNT];
+  };
+  std::map<int, RoundGraph> round_graphs;
+  bool graphs = true;                   // off after a failed capture
+  cudaStream_t capture_stream = nullptr;  // private stream the rounds are captured on
   snac::KernelStat kstats[snac::K_COUNT];
   std::vector<snac::PendingEvent> pending;
   std::vector<cudaEvent_t> event_pool;

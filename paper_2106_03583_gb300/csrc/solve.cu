@@ -53,6 +53,53 @@ int set_active_all(snac_plan* P, cudaStream_t s) {
 }
 
 // V-cycles of every mode until its share of `target` is met, it stagnates, or max_cycles.
+// One V-cycle round of the active modes and their norms. Without profiling the round is replayed from
+// a CUDA graph captured (on the plan's private stream) the first time this number of modes is active;
+// the graph's kernels read the active list from device memory, which the caller updates before.
+cudaError_t run_round(snac_plan* P, int nact, cudaStream_t s, int* replayed) {
+  if (!P->graphs || P->profiling) {
+    cudaError_t e = launch_vcycle(P, nact, s);
+    return e != cudaSuccess ? e : launch_mode_norms(P, nact, true, s);
+  }
+  auto it = P->round_graphs.find(nact);
+  if (it == P->round_graphs.end()) {
+    snac_plan::RoundGraph rg;
+    KernelStat before[K_COUNT];
+    for (int k = 0; k < K_COUNT; ++k) before[k] = P->kstats[k];
+    cudaError_t e = cudaSuccess;
+    if (!P->capture_stream) e = cudaStreamCreateWithFlags(&P->capture_stream, cudaStreamNonBlocking);
+    cudaGraph_t g = nullptr;
+    if (e == cudaSuccess) e = cudaStreamBeginCapture(P->capture_stream, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+      cudaError_t el = launch_vcycle(P, nact, P->capture_stream);
+      if (el == cudaSuccess) el = launch_mode_norms(P, nact, true, P->capture_stream);
+      e = cudaStreamEndCapture(P->capture_stream, &g);
+      if (el != cudaSuccess) e = el;
+    }
+    for (int k = 0; k < K_COUNT; ++k) {  // counted once at capture; added again at every replay
+      rg.delta[k].launches = P->kstats[k].launches - before[k].launches;
+      rg.delta[k].bytes = P->kstats[k].bytes - before[k].bytes;
+      rg.delta[k].flops = P->kstats[k].flops - before[k].flops;
+      P->kstats[k] = before[k];
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&rg.exec, g, 0);
+    if (g) cudaGraphDestroy(g);
+    if (e != cudaSuccess) {  // capture not possible here: launch the kernels directly from now on
+      cudaGetLastError();
+      P->graphs = false;
+      return run_round(P, nact, s, replayed);
+    }
+    it = P->round_graphs.emplace(nact, rg).first;
+  }
+  for (int k = 0; k < K_COUNT; ++k) {
+    P->kstats[k].launches += it->second.delta[k].launches;
+    P->kstats[k].bytes += it->second.delta[k].bytes;
+    P->kstats[k].flops += it->second.delta[k].flops;
+  }
+  ++*replayed;
+  return cudaGraphLaunch(it->second.exec, s);
+}
+
 int mode_solves(snac_plan* P, double target, cudaStream_t s, int* cycles_out) {
   const int nz = P->nz;
   CK(cudaMemsetAsync(P->lev[0].d_u, 0, (size_t)nz * P->lev[0].ncell * plan_inner_size(P), s));
@@ -77,8 +124,7 @@ int mode_solves(snac_plan* P, double target, cudaStream_t s, int* cycles_out) {
     const int nact = (int)list.size();
     std::copy(list.begin(), list.end(), P->h_active);
     CK(cudaMemcpyAsync(P->d_active, P->h_active, nact * sizeof(int), cudaMemcpyHostToDevice, s));
-    CK(launch_vcycle(P, nact, s));
-    CK(launch_mode_norms(P, nact, true, s));
+    CK(run_round(P, nact, s, &P->info.graph_rounds));
     CK(cudaMemcpyAsync(P->h_mode_norm2, P->d_mode_norm2, nz * sizeof(double), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     profile_resolve(P);

@@ -60,7 +60,8 @@ class _KStat(ctypes.Structure):
 class _Info(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int32), ("outer_iters", ctypes.c_int32), ("total_cycles", ctypes.c_int32),
                 ("max_mode_cycles", ctypes.c_int32), ("levels", ctypes.c_int32), ("n_modes", ctypes.c_int32),
-                ("rel_res", ctypes.c_double), ("rhs_norm", ctypes.c_double), ("removed_mean", ctypes.c_double)]
+                ("rel_res", ctypes.c_double), ("rhs_norm", ctypes.c_double), ("removed_mean", ctypes.c_double),
+                ("graph_rounds", ctypes.c_int32)]
 
 
 class _EngineOptions(ctypes.Structure):

@@ -193,6 +193,31 @@ def test_homogeneous_axis_x_or_y(homog, precision, layout, zpair, walls):
     assert rel(back(host(out)), osv.apply_operator(blocks, q)) <= 1e-13
 
 
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_graph_replay_matches_direct_launches(precision):
+    """Without profiling the V-cycle rounds are replayed from captured CUDA graphs; with profiling
+    they are launched one by one. Same kernels, same order: bitwise identical solutions and the same
+    launch counts."""
+    import torch
+    blocks, f = inputs.config("mb2x2", seed=1, scale=8)
+    pl = plan(blocks, precision=precision)
+    fd = dev(f)
+    out = {}
+    for prof in (True, False, False):
+        pl.set_profiling(prof)
+        pl.reset_stats()
+        p = torch.zeros_like(fd)
+        info = pl.solve(fd, p, tol=TOL)
+        launches = sum(v["launches"] for v in pl.kernel_stats().values())
+        out.setdefault(prof, []).append((host(p), info, launches))
+    pl.set_profiling(False)
+    (pd, idirect, ld), = out[True]
+    assert idirect["graph_rounds"] == 0
+    for pg, igraph, lg in out[False]:
+        assert np.array_equal(pg, pd) and lg == ld
+        assert igraph["graph_rounds"] > 0 and igraph["rel_res"] == idirect["rel_res"]
+
+
 def test_errors():
     import torch
     blocks = make("2x2", n=8, nz=8, zpair="NN", walls=("N", "N", "N", "N"))
