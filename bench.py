@@ -440,9 +440,9 @@ def _latency_summary(res):
     t1 = max(t["t_done"] for _, t in res)
     ok = sum(1 for i, _ in res if i["status"] == 0)
     failed = {}
-    for k, (i, _) in enumerate(res):
+    for k, (i, t) in enumerate(res):
         if i["status"] != 0:
-            failed.setdefault(i["status_name"], []).append(k)
+            failed.setdefault(i["status_name"], []).append((k, t.get("error", "")))
     return {"requests": len(res), "ok": ok, "failed": failed, "solves_per_s": len(res) / (t1 - t0),
             "p50_ms": float(np.median(lat)),
             "p99_ms": float(np.percentile(lat, 99)), "mean_ms": float(lat.mean()),

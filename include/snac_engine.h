@@ -70,6 +70,7 @@ typedef struct {
   int32_t worker;                            /* worker that ran the request                           */
   int32_t plan_reused;                       /* 1 if a cached plan served it, 0 if one was built      */
   int32_t tuned;                             /* 1 if this request ran the autotuner                   */
+  char error[160];                           /* detail of a failed request (empty if it succeeded)    */
 } snac_request_times;
 
 typedef struct {

@@ -18,6 +18,10 @@
 #include "snac_engine.h"
 #include "snac_impl.h"
 
+namespace snac {
+void set_error(const std::string& s);
+}
+
 namespace {
 
 using Clock = std::chrono::steady_clock;
@@ -205,7 +209,9 @@ int snac_engine::run(Request* r, cudaStream_t s) {
     if (r->tune) account(-(int64_t)r->tune_bytes);
     return SNAC_ERR_OOM;
   }
-  bool ok = cudaMemcpyAsync(d_f, r->h_rhs, nb, cudaMemcpyHostToDevice, s) == cudaSuccess;
+  cudaError_t ce = cudaMemcpyAsync(d_f, r->h_rhs, nb, cudaMemcpyHostToDevice, s);
+  bool ok = ce == cudaSuccess;
+  if (!ok) snac::set_error(std::string("engine: copy of the right-hand side: ") + cudaGetErrorString(ce));
   if (r->build_plan) {
     snac_options use = r->has_opt ? r->opt : snac_options{};
     bool have_opt = r->has_opt;
@@ -251,19 +257,27 @@ int snac_engine::run(Request* r, cudaStream_t s) {
     ++built;
   }
   r->times.plan_reused = r->build_plan ? 0 : 1;
-  ok = ok && cudaMemsetAsync(d_p, 0, nb, s) == cudaSuccess;
+  if (ok && (ce = cudaMemsetAsync(d_p, 0, nb, s)) != cudaSuccess) {
+    ok = false;
+    snac::set_error(std::string("engine: zeroing the solution: ") + cudaGetErrorString(ce));
+  }
   if (ok) {
     st = snac_poisson_solve(r->slot->plan, d_f, d_p, r->tol, s);
     snac_plan_info(r->slot->plan, &r->info);
     if ((st == SNAC_OK || st == SNAC_ERR_NOT_CONVERGED) &&
-        cudaMemcpyAsync(r->h_p, d_p, nb, cudaMemcpyDeviceToHost, s) != cudaSuccess)
+        (ce = cudaMemcpyAsync(r->h_p, d_p, nb, cudaMemcpyDeviceToHost, s)) != cudaSuccess) {
       st = SNAC_ERR_CUDA;
+      snac::set_error(std::string("engine: copy of the solution: ") + cudaGetErrorString(ce));
+    }
   } else {
     st = SNAC_ERR_CUDA;
   }
   cudaFreeAsync(d_f, s);
   cudaFreeAsync(d_p, s);
-  if (cudaStreamSynchronize(s) != cudaSuccess && st == SNAC_OK) st = SNAC_ERR_CUDA;
+  if ((ce = cudaStreamSynchronize(s)) != cudaSuccess && st == SNAC_OK) {
+    st = SNAC_ERR_CUDA;
+    snac::set_error(std::string("engine: stream synchronisation: ") + cudaGetErrorString(ce));
+  }
   return st;
 }
 
@@ -284,8 +298,13 @@ void snac_engine::worker(int id) {
     }
     r->times.t_start = now_s();
     r->times.worker = id;
+    snac::set_error("");
     const int st = s ? run(r, s) : SNAC_ERR_CUDA;
     r->times.t_done = now_s();
+    if (st != SNAC_OK) {  // the detail this worker thread recorded (plan creation, solve or copies)
+      std::strncpy(r->times.error, snac_last_error_message(), sizeof(r->times.error) - 1);
+      r->times.error[sizeof(r->times.error) - 1] = '\0';
+    }
     std::vector<snac_plan*> dead;
     {
       std::lock_guard<std::mutex> lk(mu);

@@ -326,6 +326,13 @@ __global__ void __launch_bounds__(256) k_backward(const ChunkDev* __restrict__ c
   }
 }
 
+// Dynamic shared memory of a transform launch: two half-length complex buffers of TC columns. The
+// kernel's maximum is a function-wide attribute shared by every plan and thread, so it is always set
+// to the largest need (n_z = MAX_NZ): a plan with a shorter axis never lowers it under a concurrent
+// launch of a plan with a longer one.
+template <typename T, int TC>
+constexpr int kMaxSmem = 2 * (MAX_NZ / 2) * TC * (int)sizeof(Cx<T>);
+
 template <typename T>
 Tw<T> make_tw(const snac_plan* P, const void* base) {
   const Cx<T>* t = reinterpret_cast<const Cx<T>*>(base);
@@ -344,7 +351,7 @@ cudaError_t fwd_t(snac_plan* P, const std::vector<ChunkDev>& ch, const ChunkDev*
   // read the FP64 field, write the modes; FFT model 2.5 log2(n) flops per point plus pre/post-processing
   LaunchScope ls(P, K_FORWARD, (8.0 + sizeof(T)) * n3, (2.5 * std::log2((double)P->nz) + 8.0) * n3, s);
   auto go = [&](auto kern) {
-    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem<T, TC>);
     kern<<<(unsigned)ch.size(), 256, smem, s>>>(dch, P->lev[0].d_blk, P->d_cblk, P->nz, make_tw<T>(P, twb), in3,
                                                 (T*)modes, P->lev[0].ncell, sub0);
   };
@@ -366,7 +373,7 @@ cudaError_t bwd_t(snac_plan* P, const std::vector<ChunkDev>& ch, const ChunkDev*
   // read the modes, read and write the FP64 field
   LaunchScope ls(P, K_BACKWARD, (16.0 + sizeof(T)) * n3, (2.5 * std::log2((double)P->nz) + 10.0) * n3, s);
   auto go = [&](auto kern) {
-    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem<T, TC>);
     kern<<<(unsigned)ch.size(), 256, smem, s>>>(dch, P->lev[0].d_blk, P->d_cblk, P->nz, make_tw<T>(P, twb),
                                                 (const T*)modes, p3, P->lev[0].ncell, 1.0 / P->theta);
   };

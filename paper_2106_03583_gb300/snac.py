@@ -72,7 +72,7 @@ class _EngineOptions(ctypes.Structure):
 class _Times(ctypes.Structure):
     _fields_ = [("t_submit", ctypes.c_double), ("t_admit", ctypes.c_double), ("t_start", ctypes.c_double),
                 ("t_done", ctypes.c_double), ("worker", ctypes.c_int32), ("plan_reused", ctypes.c_int32),
-                ("tuned", ctypes.c_int32)]
+                ("tuned", ctypes.c_int32), ("error", ctypes.c_char * 160)]
 
 
 class _TuneReport(ctypes.Structure):
@@ -366,7 +366,9 @@ class Engine:
         info = {k: getattr(inf, k) for k, _ in _Info._fields_}
         info["status"] = st
         info["status_name"] = STATUS.get(st, str(st))
-        return p, info, {k: getattr(tm, k) for k, _ in _Times._fields_}
+        times = {k: getattr(tm, k) for k, _ in _Times._fields_}
+        times["error"] = tm.error.decode(errors="replace")
+        return p, info, times
 
     def stats(self) -> dict:
         s = _EngineStats()

@@ -138,3 +138,21 @@ def test_engine_autotune_once_per_problem():
     assert np.array_equal(p2, p3)                 # the same tuned plan, the same result
     for p, info in ((p1, i1), (p2, i2)):
         assert info["status"] == 0 and info["rel_res"] <= TOL and rel(p, po) <= 1e-9
+
+
+def test_concurrent_plans_with_different_transform_lengths():
+    """Plans whose transforms have different lengths share the same transform kernels; their
+    launches interleave on the engine's streams. Every request must still succeed (the kernels'
+    shared-memory limit is a function-wide attribute, never lowered by a shorter plan)."""
+    probs = []
+    for nz, seed in ((8, 1), (512, 2)):
+        blocks = make("1", n=8, nz=nz, zpair="NN", walls=("D", "D", "N", "N"))
+        probs.append((blocks, inputs.uniform_rhs(blocks, seed, remove_mean=False)))
+    fails = []
+    with snac.Engine(workers=4, hbm_budget=8e9) as eng:
+        tickets = [eng.submit(*probs[k % 2], tol=TOL, precision="mixed" if k % 4 < 2 else "fp64") for k in range(400)]
+        for k, t in enumerate(tickets):
+            _, info, times = eng.wait(t, raise_on_error=False)
+            if info["status"] != 0:
+                fails.append((k, info["status_name"], times["error"]))
+    assert not fails, fails[:5]
