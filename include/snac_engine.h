@@ -18,7 +18,8 @@
  *  Plans.     Plans are cached by problem (blocks, spacings, boundary conditions, homogeneous axis,
  *             options) and reused by later requests of the same problem: the level hierarchy,
  *             coefficients, shifts, twiddles and coarse factors stay resident. A cached plan serves one
- *             request at a time; a second concurrent request of the same problem gets its own plan.
+ *             request at a time; a concurrent request of the same problem gets its own plan, up to
+ *             `workers` plans per problem, after which it waits for one of them.
  *             Idle plans are evicted least-recently-used when the cache holds more than
  *             `max_cached_plans` or when their memory is needed to admit a request.
  *  Admission. The engine accounts every device byte it holds: cached plans (idle or busy), plans being

@@ -121,6 +121,7 @@ struct snac_engine {
   std::map<int64_t, Request*> tickets;
   std::list<PlanSlot*> plans;
   std::map<std::string, snac_options> tuned;  // problem key -> chosen schedule (autotune)
+  std::map<std::string, int> building;        // problem key -> plans being built
   uint64_t used = 0, peak = 0, use_clock = 0;
   int running = 0;
   int64_t completed = 0, built = 0, evicted = 0, next_ticket = 1;
@@ -158,8 +159,18 @@ struct snac_engine {
     for (auto it = queue.begin(); it != queue.end();) {
       Request* r = *it;
       PlanSlot* idle = nullptr;
-      for (PlanSlot* s : plans)
-        if (!s->busy && s->key == r->key && (!idle || s->last_use > idle->last_use)) idle = s;
+      int have = 0;  // plans of this problem, resident or being built
+      for (PlanSlot* s : plans) {
+        if (s->key != r->key) continue;
+        ++have;
+        if (!s->busy && (!idle || s->last_use > idle->last_use)) idle = s;
+      }
+      auto bit = building.find(r->key);
+      if (bit != building.end()) have += bit->second;
+      if (!idle && have >= opt.workers) {  // enough plans of this problem: wait for one of them
+        ++it;
+        continue;
+      }
       r->tune = !idle && opt.autotune && tuned.find(r->key) == tuned.end();
       const uint64_t need = r->buf_bytes + (idle ? 0 : r->plan_estimate) + (r->tune ? r->tune_bytes : 0);
       while (used + need > opt.hbm_budget && evict_one(idle, dead)) {
@@ -174,6 +185,7 @@ struct snac_engine {
         r->slot = idle;
       } else {
         r->build_plan = true;
+        ++building[r->key];
       }
       r->state = State::Ready;
       r->times.t_admit = now_s();
@@ -205,7 +217,10 @@ int snac_engine::run(Request* r, cudaStream_t s) {
     if (d_f) cudaFreeAsync(d_f, s);
     cudaStreamSynchronize(s);
     std::lock_guard<std::mutex> lk(mu);
-    if (r->build_plan) account(-(int64_t)r->plan_estimate);
+    if (r->build_plan) {
+      account(-(int64_t)r->plan_estimate);
+      if (--building[r->key] == 0) building.erase(r->key);
+    }
     if (r->tune) account(-(int64_t)r->tune_bytes);
     return SNAC_ERR_OOM;
   }
@@ -240,6 +255,7 @@ int snac_engine::run(Request* r, cudaStream_t s) {
     std::lock_guard<std::mutex> lk(mu);
     account(-(int64_t)r->plan_estimate);
     if (r->tune) account(-(int64_t)r->tune_bytes);
+    if (--building[r->key] == 0) building.erase(r->key);
     PlanSlot* slot = st == SNAC_OK ? new (std::nothrow) PlanSlot{r->key, pl, (uint64_t)bytes, true, 0} : nullptr;
     if (st == SNAC_OK && !slot) {
       snac_plan_destroy(pl);
@@ -299,7 +315,18 @@ void snac_engine::worker(int id) {
     r->times.t_start = now_s();
     r->times.worker = id;
     snac::set_error("");
-    const int st = s ? run(r, s) : SNAC_ERR_CUDA;
+    int st = SNAC_ERR_CUDA;
+    if (s) {
+      st = run(r, s);
+    } else {  // this worker has no stream: release what the admission reserved for a plan build
+      std::lock_guard<std::mutex> lk(mu);
+      if (r->build_plan) {
+        account(-(int64_t)r->plan_estimate);
+        if (--building[r->key] == 0) building.erase(r->key);
+      }
+      if (r->tune) account(-(int64_t)r->tune_bytes);
+      snac::set_error("engine: the worker's CUDA stream could not be created");
+    }
     r->times.t_done = now_s();
     if (st != SNAC_OK) {  // the detail this worker thread recorded (plan creation, solve or copies)
       std::strncpy(r->times.error, snac_last_error_message(), sizeof(r->times.error) - 1);
