@@ -134,8 +134,8 @@ FUSED_CASES = [
 ]
 
 
-def _two_cycles(blocks, Fh, U0, precision, fused):
-    pl = plan(blocks, precision=precision, max_coarse=64, fused=fused)
+def _two_cycles(blocks, Fh, U0, precision, fused, nu=(2, 2)):
+    pl = plan(blocks, precision=precision, max_coarse=64, fused=fused, nu1=nu[0], nu2=nu[1])
     u = dev(U0.ravel(), pl.inner_dtype)
     pl.mode_vcycles(dev(Fh.ravel(), pl.inner_dtype), u, 2)
     got = host(u).reshape(U0.shape)
@@ -188,4 +188,28 @@ def test_vcycle_fused_matches_oracle(case):
     err_fused = rel(_mean_free(g, _two_cycles(blocks, Fh, Z, "mixed", 1)), ref0)
     err_colour = rel(_mean_free(g, _two_cycles(blocks, Fh, Z, "mixed", 0)), ref0)
     assert err_colour <= 2e-4
+    assert err_fused <= max(2e-5, 4.0 * err_colour), (err_fused, err_colour)
+
+
+@pytest.mark.parametrize("nu", [(1, 1), (2, 1), (1, 2)])
+@pytest.mark.parametrize("case", FUSED_CASES[:3])
+def test_vcycle_fused_other_schedules(case, nu):
+    """The fused kernels with the other sweep counts the autotuner may choose: exact (FP64, 1e-11)
+    against the oracle's V(nu1, nu2) cycles, and in FP32 as accurate as the per-colour kernels."""
+    blocks = _blocks(case)
+    g = ogrid.Grid(blocks)
+    mg = omg.Multigrid(g.plane, nu[0], nu[1], max_coarse=64)
+    lam = T.eigenvalues(g.kind, g.nz)
+    rng = np.random.default_rng(7)
+    Fh = rng.standard_normal((g.nz, g.plane.n))
+    for q in range(g.nz):
+        if g.singular and lam[q] == 0.0:
+            Fh[q] -= np.dot(g.plane.area, Fh[q]) / g.plane.area.sum()
+    U0 = rng.standard_normal((g.nz, g.plane.n))
+    ref = _mean_free(g, _oracle_two_cycles(g, mg, Fh, U0))
+    assert rel(_mean_free(g, _two_cycles(blocks, Fh, U0, "fp64", 1, nu)), ref) <= 1e-11
+    Z = np.zeros_like(U0)
+    ref0 = _mean_free(g, _oracle_two_cycles(g, mg, Fh, Z))
+    err_fused = rel(_mean_free(g, _two_cycles(blocks, Fh, Z, "mixed", 1, nu)), ref0)
+    err_colour = rel(_mean_free(g, _two_cycles(blocks, Fh, Z, "mixed", 0, nu)), ref0)
     assert err_fused <= max(2e-5, 4.0 * err_colour), (err_fused, err_colour)
