@@ -290,7 +290,7 @@ cudaError_t launch_shift(snac_plan* P, double* p, const double* d_c, cudaStream_
     k_mean_of_p<<<1, 1, 0, s>>>(P->d_sums, P->vol_total);
   }
   LaunchScope ls(P, K_SHIFT, 16.0 * P->n3, (double)P->n3, s);
-  k_shift<<<2 * 152, 512, 0, s>>>(p, P->n3, d_c);
+  k_shift<<<2 * P->sms, 512, 0, s>>>(p, P->n3, d_c);
   return cudaGetLastError();
 }
 

@@ -335,20 +335,20 @@ cudaError_t vcycle_t(snac_plan* P, int nact, cudaStream_t st) {
 }
 
 template <typename T>
-cudaError_t mode_norms_t(snac_plan* P, int nact, bool after_cycle, cudaStream_t st) {
+cudaError_t mode_norms_t(snac_plan* P, int nact, bool after_cycle, cudaStream_t st, const int* list) {
   const HostLevel& h = P->lev[0];
   if (!after_cycle) {  // zero iterate: the residual is the right-hand side itself
     {
       LaunchScope ls(P, K_MODE_RESID, (double)sizeof(T) * h.ncell * nact, 2.0 * h.ncell * nact, st);
-      k_mode_sumsq<T><<<dim3(MODE_SQ_CTAS, nact), 256, 0, st>>>((const T*)h.d_f, h.ncell, P->d_active, P->d_mode_part);
+      k_mode_sumsq<T><<<dim3(MODE_SQ_CTAS, nact), 256, 0, st>>>((const T*)h.d_f, h.ncell, list, P->d_mode_part);
     }
     LaunchScope ls(P, K_MODE_REDUCE, 8.0 * MODE_SQ_CTAS * nact, (double)MODE_SQ_CTAS * nact, st);
-    k_mode_reduce<<<nact, 256, 0, st>>>(P->d_mode_part, MODE_SQ_CTAS, P->d_active, P->d_mode_norm2);
+    k_mode_reduce<<<nact, 256, 0, st>>>(P->d_mode_part, MODE_SQ_CTAS, list, P->d_mode_norm2);
     return cudaGetLastError();
   }
   if (after_cycle && h.fused) {  // the level-0 up kernel left one partial per fused tile
     LaunchScope ls(P, K_MODE_REDUCE, 8.0 * h.ftiles.size() * nact, (double)h.ftiles.size() * nact, st);
-    k_mode_reduce<<<nact, 256, 0, st>>>(P->d_mode_part, (int)h.ftiles.size(), P->d_active, P->d_mode_norm2);
+    k_mode_reduce<<<nact, 256, 0, st>>>(P->d_mode_part, (int)h.ftiles.size(), list, P->d_mode_norm2);
     return cudaGetLastError();
   }
   dim3 g((unsigned)h.tiles.size(), (unsigned)nact);
@@ -358,14 +358,14 @@ cudaError_t mode_norms_t(snac_plan* P, int nact, bool after_cycle, cudaStream_t 
     const bool red = after_cycle && P->nu2 > 0 && P->lev.size() > 1;
     LaunchScope ls(P, K_MODE_RESID, (red ? 1.5 : 2.0) * sizeof(T) * cells, (red ? 7.0 : 14.0) * cells, st);
     if (red)
-      k_mode_resid2<T, true><<<g, COLOUR_THREADS, 0, st>>>(level_view<T>(h), P->d_active, sigma_ptr<T>(P),
+      k_mode_resid2<T, true><<<g, COLOUR_THREADS, 0, st>>>(level_view<T>(h), list, sigma_ptr<T>(P),
                                                            (const T*)h.d_u, (const T*)h.d_f, P->d_mode_part);
     else
-      k_mode_resid2<T, false><<<g, TILE_THREADS, 0, st>>>(level_view<T>(h), P->d_active, sigma_ptr<T>(P),
+      k_mode_resid2<T, false><<<g, TILE_THREADS, 0, st>>>(level_view<T>(h), list, sigma_ptr<T>(P),
                                                           (const T*)h.d_u, (const T*)h.d_f, P->d_mode_part);
   }
   LaunchScope ls(P, K_MODE_REDUCE, 8.0 * h.tiles.size() * nact, (double)h.tiles.size() * nact, st);
-  k_mode_reduce<<<nact, 256, 0, st>>>(P->d_mode_part, (int)h.tiles.size(), P->d_active, P->d_mode_norm2);
+  k_mode_reduce<<<nact, 256, 0, st>>>(P->d_mode_part, (int)h.tiles.size(), list, P->d_mode_norm2);
   return cudaGetLastError();
 }
 
@@ -395,10 +395,11 @@ cudaError_t launch_vcycle(snac_plan* P, int nact, cudaStream_t s) {
   return P->precision == SNAC_FP64 ? vcycle_t<double>(P, nact, s) : vcycle_t<float>(P, nact, s);
 }
 
-cudaError_t launch_mode_norms(snac_plan* P, int nact, bool after_cycle, cudaStream_t s) {
+cudaError_t launch_mode_norms(snac_plan* P, int nact, bool after_cycle, cudaStream_t s, const int* d_list) {
   if (nact <= 0) return cudaSuccess;
-  return P->precision == SNAC_FP64 ? mode_norms_t<double>(P, nact, after_cycle, s)
-                                   : mode_norms_t<float>(P, nact, after_cycle, s);
+  const int* list = d_list ? d_list : P->d_active;
+  return P->precision == SNAC_FP64 ? mode_norms_t<double>(P, nact, after_cycle, s, list)
+                                   : mode_norms_t<float>(P, nact, after_cycle, s, list);
 }
 
 // Requires d_active = 0..n_z-1.

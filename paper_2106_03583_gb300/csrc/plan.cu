@@ -486,6 +486,7 @@ void free_plan(snac_plan* P) {
   if (P->h_sums) cudaFreeHost(P->h_sums);
   if (P->h_mode_norm2) cudaFreeHost(P->h_mode_norm2);
   if (P->h_active) cudaFreeHost(P->h_active);
+  if (P->h_check) cudaFreeHost(P->h_check);
   delete P;
 }
 
@@ -778,10 +779,11 @@ int create(snac_plan** out, int32_t nblocks, const snac_block* blocks_in, int32_
     // per-mode, per-tile partial sums (basic tiles; the fused tiles are fewer)
     if ((st = dmalloc(P, &P->d_mode_part, (size_t)P->nz * std::max<size_t>(P->lev[0].tiles.size(), 64)))) break;
     if ((st = dmalloc(P, &P->d_mode_norm2, (size_t)P->nz))) break;
-    if ((st = dmalloc(P, &P->d_active, (size_t)P->nz))) break;
+    if ((st = dmalloc(P, &P->d_active, (size_t)P->nz)) || (st = dmalloc(P, &P->d_check, (size_t)P->nz))) break;
     if (cudaMallocHost(&P->h_sums, SUM_SLOTS * sizeof(double)) != cudaSuccess ||
         cudaMallocHost(&P->h_mode_norm2, P->nz * sizeof(double)) != cudaSuccess ||
-        cudaMallocHost(&P->h_active, P->nz * sizeof(int)) != cudaSuccess) {
+        cudaMallocHost(&P->h_active, P->nz * sizeof(int)) != cudaSuccess ||
+        cudaMallocHost(&P->h_check, P->nz * sizeof(int)) != cudaSuccess) {
       st = fail(SNAC_ERR_OOM, "pinned host allocation");
       break;
     }

@@ -29,7 +29,7 @@ constexpr int TILE_Y = 8;
 constexpr int TILE_THREADS = TILE_X * TILE_Y;
 constexpr int MAX_NZ = 1024;
 constexpr int MAX_COARSE = 256;
-constexpr int MEAN_CTAS = 2 * 152;
+constexpr int MEAN_CTAS = 2 * 152;  // CTAs (so partials) of the grid-stride plane reductions: fixed, for a fixed summation order
 constexpr int SUM_SLOTS = 16;     // d_sums / h_sums: [0..3] residual or pre-pass, [4..7] mean fix
 constexpr int SUM_NONZERO = 8;    // d_sums slot of the pre-pass's nonzero-guess flag  // CTAs of the grid-stride reductions over one mode plane
 constexpr int FTILE_X = 52;         // tile of the fused multigrid kernels (64x64 window with the halo)
@@ -201,6 +201,8 @@ struct snac_plan {
   double* h_sums = nullptr;       // pinned
   double* h_mode_norm2 = nullptr; // pinned
   int* h_active = nullptr;        // pinned
+  int* d_check = nullptr;         // modes whose residual norm is due after a round (predictive checks)
+  int* h_check = nullptr;         // pinned
   std::vector<void*> allocs;
   size_t bytes = 0;
   // results
@@ -253,7 +255,7 @@ cudaError_t launch_vcycle(snac_plan* P, int nactive, cudaStream_t s);
 // per-mode ||f - A u||^2 at level 0 for the active modes -> d_mode_norm2[q]; after_cycle: u is the
 // result of a V-cycle (post-smoothing ended on black, so only red cells carry a residual); otherwise
 // u is zero and the norm is that of f
-cudaError_t launch_mode_norms(snac_plan* P, int nactive, bool after_cycle, cudaStream_t s);
+cudaError_t launch_mode_norms(snac_plan* P, int nactive, bool after_cycle, cudaStream_t s, const int* d_list = nullptr);
 
 // fused FP32 levels: smoothing + residual + restriction (down), prolongation + smoothing (+ level-0
 // residual norm partials into d_mode_part) (up)

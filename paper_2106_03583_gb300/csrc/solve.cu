@@ -56,10 +56,10 @@ int set_active_all(snac_plan* P, cudaStream_t s) {
 // One V-cycle round of the active modes and their norms. Without profiling the round is replayed from
 // a CUDA graph captured (on the plan's private stream) the first time this number of modes is active;
 // the graph's kernels read the active list from device memory, which the caller updates before.
-cudaError_t run_round(snac_plan* P, int nact, cudaStream_t s, int* replayed) {
+cudaError_t run_round(snac_plan* P, int nact, bool norms, cudaStream_t s, int* replayed) {
   if (!P->graphs || P->profiling) {
     cudaError_t e = launch_vcycle(P, nact, s);
-    return e != cudaSuccess ? e : launch_mode_norms(P, nact, true, s);
+    return e != cudaSuccess || !norms ? e : launch_mode_norms(P, nact, true, s);
   }
   auto it = P->round_graphs.find(nact);
   if (it == P->round_graphs.end()) {
@@ -72,7 +72,7 @@ cudaError_t run_round(snac_plan* P, int nact, cudaStream_t s, int* replayed) {
     if (e == cudaSuccess) e = cudaStreamBeginCapture(P->capture_stream, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
       cudaError_t el = launch_vcycle(P, nact, P->capture_stream);
-      if (el == cudaSuccess) el = launch_mode_norms(P, nact, true, P->capture_stream);
+      if (el == cudaSuccess && norms) el = launch_mode_norms(P, nact, true, P->capture_stream);
       e = cudaStreamEndCapture(P->capture_stream, &g);
       if (el != cudaSuccess) e = el;
     }
@@ -87,7 +87,7 @@ cudaError_t run_round(snac_plan* P, int nact, cudaStream_t s, int* replayed) {
     if (e != cudaSuccess) {  // capture not possible here: launch the kernels directly from now on
       cudaGetLastError();
       P->graphs = false;
-      return run_round(P, nact, s, replayed);
+      return run_round(P, nact, norms, s, replayed);
     }
     it = P->round_graphs.emplace(nact, rg).first;
   }
@@ -109,8 +109,8 @@ int mode_solves(snac_plan* P, double target, cudaStream_t s, int* cycles_out) {
   CK(cudaMemcpyAsync(P->h_mode_norm2, P->d_mode_norm2, nz * sizeof(double), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
     profile_resolve(P);
-  std::vector<double> thr2(nz), prev(nz);
-  std::vector<int> list;
+  std::vector<double> thr2(nz), prev(nz);  // prev: norm^2 at the mode's last check
+  std::vector<int> list, prev_cycle(nz, 0), next_check(nz, 1);
   for (int q = 0; q < nz; ++q) {
     thr2[q] = target * target / (nz * P->pweight[q]);
     prev[q] = P->h_mode_norm2[q];
@@ -118,26 +118,58 @@ int mode_solves(snac_plan* P, double target, cudaStream_t s, int* cycles_out) {
     if (!std::isfinite(prev[q])) return SNAC_ERR_NONFINITE;
     if (prev[q] > thr2[q]) list.push_back(q);
   }
-  const double stag2 = 0.6 * 0.6;
+  // Where the level-0 norms need a pass of their own (the fused up kernel gives them for free), a
+  // mode is checked only when its observed per-cycle reduction says it should have reached its
+  // share, at most 3 cycles after its last check; rounds without a check need no synchronisation.
+  // A mode stops only at a check, so at worst it runs one cycle more than needed.
+  const bool predictive = !P->lev[0].fused;
+  const double stag2 = 0.6 * 0.6;  // a cycle that reduces the norm less than 0.6x: the precision floor
   int total = 0;
+  bool list_changed = true;
+  std::vector<char> checked(nz, 0);
   for (int c = 0; c < P->max_cycles && !list.empty(); ++c) {
     const int nact = (int)list.size();
-    std::copy(list.begin(), list.end(), P->h_active);
-    CK(cudaMemcpyAsync(P->d_active, P->h_active, nact * sizeof(int), cudaMemcpyHostToDevice, s));
-    CK(run_round(P, nact, s, &P->info.graph_rounds));
+    if (list_changed) {  // the previous upload has completed: every list change follows a synchronisation
+      std::copy(list.begin(), list.end(), P->h_active);
+      CK(cudaMemcpyAsync(P->d_active, P->h_active, nact * sizeof(int), cudaMemcpyHostToDevice, s));
+      list_changed = false;
+    }
+    CK(run_round(P, nact, !predictive, s, &P->info.graph_rounds));
+    int ncheck = 0;
+    for (int q : list) {
+      ++cycles_out[q];
+      ++total;
+      checked[q] = !predictive || cycles_out[q] >= next_check[q];
+      if (checked[q]) P->h_check[ncheck++] = q;
+    }
+    if (ncheck == 0) continue;
+    if (predictive) {
+      CK(cudaMemcpyAsync(P->d_check, P->h_check, ncheck * sizeof(int), cudaMemcpyHostToDevice, s));
+      CK(launch_mode_norms(P, ncheck, true, s, P->d_check));
+    }
     CK(cudaMemcpyAsync(P->h_mode_norm2, P->d_mode_norm2, nz * sizeof(double), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     profile_resolve(P);
     std::vector<int> next;
     for (int q : list) {
-      ++cycles_out[q];
-      ++total;
+      if (!checked[q]) {
+        next.push_back(q);
+        continue;
+      }
       const double r2 = P->h_mode_norm2[q];
       if (!std::isfinite(r2)) return SNAC_ERR_NONFINITE;
-      const bool done = r2 <= thr2[q] || r2 > stag2 * prev[q];
+      const int dc = cycles_out[q] - prev_cycle[q];
+      const bool done = r2 <= thr2[q] || r2 > std::pow(stag2, dc) * prev[q];
+      if (!done && predictive) {
+        const double rho2 = std::pow(r2 / prev[q], 1.0 / dc);  // per-cycle factor of the norm^2, < 1
+        const double need = std::log(thr2[q] / r2) / std::log(rho2);
+        next_check[q] = cycles_out[q] + std::max(1, std::min(3, (int)std::ceil(need - 0.25)));
+      }
       prev[q] = r2;
+      prev_cycle[q] = cycles_out[q];
       if (!done) next.push_back(q);
     }
+    list_changed = next.size() != list.size();
     list.swap(next);
   }
   P->info.total_cycles += total;
