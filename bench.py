@@ -46,16 +46,19 @@ _FUSED = {"src": "paper_2106_03583_gb300/csrc/kern_fused.cu",
           "sha256": "77084ceec5df844310d568fabd7f986f99d05ca61a7637f6bd6cdb5b96b45305",
           "capture": "profiles/k_fdown_k_fup_mixed_mb2x2_z64.md"}
 _FIELD = {"src": "paper_2106_03583_gb300/csrc/kern_field.cu",
-          "sha256": "871328280ff874a297663f07866e7d4cb7d6d83cfff8ea5c962959bc66b408d7",
-          "capture": "profiles/k_field3d_transforms_mixed_mb2x2_z64.md", "ratio": 400.707 / 402.653}
+          "sha256": "e654f5d465b615b7eea1c3fc11db5354d230ebc6d6d24f032965592655d56853",
+          "capture": "profiles/k_field3d_transforms_mixed_mb2x2_z64.md", "ratio": 401.097 / 402.653}
+_MG = {"src": "paper_2106_03583_gb300/csrc/kern_mg.cu",
+       "sha256": "d4291991e922866afda21591cde9a4e6f7198df939028c4bfeb4d2a42416d25d",
+       "capture": "profiles/k_smooth_fp64_mb2x2_z64.md"}
 TRAFFIC = {
-    ("fused_up", "mixed"): dict(_FUSED, ratio=196.475 / 218.104),     # level-0 up kernel, 64 modes
-    ("fused_down", "mixed"): dict(_FUSED, ratio=188.596 / 218.104),   # level-0 down kernel, 64 modes
+    ("fused_up", "mixed"): dict(_FUSED, ratio=196.023 / 218.104),     # level-0 up kernel, 64 modes
+    ("fused_down", "mixed"): dict(_FUSED, ratio=188.312 / 218.104),   # level-0 down kernel, 64 modes
     ("field3d", "mixed"): _FIELD,
     ("field3d", "fp64"): _FIELD,
-    ("smooth", "fp64"): {"src": "paper_2106_03583_gb300/csrc/kern_mg.cu",
-                         "sha256": "b4fac5f3080c517ed35652afcea4b97090178c56bb29b40695452a804e3f9462",
-                         "capture": "profiles/k_smooth_fp64_mb2x2_z64.md", "ratio": 507.089 / 201.327},
+    ("smooth", "fp64"): dict(_MG, ratio=506.936 / 201.327),           # level 0, mean of four launches
+    ("restrict", "fp64"): dict(_MG, ratio=320.484 / 335.544),
+    ("prolong", "fp64"): dict(_MG, ratio=244.183 / 301.990),
 }
 
 

@@ -122,9 +122,11 @@ __global__ void __launch_bounds__(TILE_THREADS) k_prolong(LevelView<T> F, LevelV
   const T eX = uc[bc + ((i & 1) ? e : w)];
   const T eY = uc[bc + ((j & 1) ? n : s)];
   const PW<T> px = F.px[Bf.xo + i], py = F.py[Bf.yo + j];
-  const T ef = fma(eC, (T)1 + px.self + py.self, fma(px.nbr, eX, py.nbr * eY));
   const long long c = (long long)q * F.ncell + Bf.off + (long long)j * Bf.nx + i;
-  uf[c] += ef;
+  // accumulated into u directly: three FMAs (the FP64 pipe bounds this kernel in FP64 plans)
+  T u = fma(eC, (T)1 + px.self + py.self, uf[c]);
+  u = fma(px.nbr, eX, u);
+  uf[c] = fma(py.nbr, eY, u);
 }
 
 // Direct solve of the coarsest plane: with V the cell areas, S = V^1/2 A V^-1/2 = Q Lam Q^T, so
