@@ -73,7 +73,9 @@ __global__ void __launch_bounds__(TILE_THREADS) k_field3d(LevelView<double> L, c
       const int kd = k > 0 ? k - 1 : (periodic_z ? nz - 1 : k);
       const int ku = k < nz - 1 ? k + 1 : (periodic_z ? 0 : k);
       const double pc = p[c];
-      double ap = cx.lo * p[pw + k * sw];
+      // with the shift and no ||f - fshift||^2 wanted, fshift enters the chain: r = f - (fshift + A p)
+      constexpr bool FOLD = MODE == 0 && SHIFT && !NEED_F2;
+      double ap = FOLD ? fma(cx.lo, p[pw + k * sw], fshift) : cx.lo * p[pw + k * sw];
       ap = fma(cx.hi, p[pe + k * se], ap);
       ap = fma(cy.lo, p[ps + k * ss], ap);
       ap = fma(cy.hi, p[pn + k * sn], ap);
@@ -83,7 +85,7 @@ __global__ void __launch_bounds__(TILE_THREADS) k_field3d(LevelView<double> L, c
       if (MODE == 1) {
         r[c] = ap;
       } else {
-        const double fv = SHIFT ? f[c] - fshift : f[c];
+        const double fv = SHIFT && !FOLD ? f[c] - fshift : f[c];
         const double rv = fv - ap;
         r[c] = rv;
         acc[0] = fma(rv, rv, acc[0]);

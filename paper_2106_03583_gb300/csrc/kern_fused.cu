@@ -10,8 +10,9 @@
 //            per-mode sums of squared residuals).
 //
 // A CTA copies its tile's tables once (FusedTab: coefficients, weights and the plane offsets of
-// every window row and column, built on the host) and then runs the tile for a run of consecutive
-// active modes. While it smooths one mode, the next mode's cells (and, going up, its coarse
+// every window row and column, built on the host), derives from them each thread's own cell table
+// (plane offsets of its cells and their diagonals without the shift), and then runs the tile for a
+// run of consecutive active modes. While it smooths one mode, the next mode's cells (and, going up, its coarse
 // correction window) stream into shared memory with per-thread asynchronous copies (cp.async), so
 // the global-load latency of a mode is hidden behind the previous mode's sweeps.
 //
@@ -20,8 +21,8 @@
 // all have the same column parity, so a colour update of a row is one cell per lane: the west/east
 // neighbours come from the thread itself or from one warp shuffle, the south/north neighbours from
 // the thread's own registers; only the first and last row of each strip pass through shared memory
-// (once per half-sweep). Coarse cells are exactly (row pair) x (column pair): restriction and
-// prolongation stay in registers too.
+// (once per half-sweep, only the colour that changed). Coarse cells are exactly (row pair) x
+// (column pair): restriction and prolongation stay in registers too.
 //
 // Exactness. Every interior window cell is updated in every half-sweep; the window's edge is never
 // updated, so stale values enter from the edge one cell per half-sweep. After 2 nu <= FUSED_HALO - 2
@@ -61,11 +62,15 @@ struct alignas(2 * sizeof(T)) Pair {
 template <typename T>
 struct Shared {
   FusedTab<T> tab;
-  Pair<T> stage[RPW][2][FTHREADS];  // next mode's u, f column pairs, each thread's own slots
-  T halo[2][FWARPS][2][2][HW];      // [buffer][warp][first/last row][parity][lane]
+  Pair<T> stage[RPW][2][FTHREADS];  // next mode's u, f column pairs, each thread's own slots (0: no owner)
+  Pair<T> diag[RPW][FTHREADS];      // diagonal of the thread's cells without the shift (+inf: no owner)
+  int4 goff[FTHREADS];              // plane offset of the thread's column pair in each of its rows (-1: none)
+  int coff[CW * CW];                // plane offset of each coarse window cell (-1: no owner; k_fup)
+  T halo[FWARPS][2][2][HW];         // [warp][first/last row][parity][lane]
   T e[2][CW][CW];                   // coarse correction around the tile, this mode and the next (k_fup)
   double wsum[FWARPS];
 };
+static_assert(2 * sizeof(Shared<float>) + 2048 <= 228 * 1024, "two FP32 CTAs per multiprocessor");
 
 // Per-thread asynchronous global -> shared copies (completion is tracked by the issuing thread).
 template <int BYTES>
@@ -94,20 +99,67 @@ __device__ __forceinline__ void copy_tab(Shared<T>& S, const FusedTab<T>* __rest
   for (int i = threadIdx.x; i < (int)(sizeof(FusedTab<T>) / 16); i += FTHREADS) dst[i] = src[i];
 }
 
-// Start the copies of the thread's cells of one mode (u unless it is zero, and f) into its own
-// staging slots. Cells with no owner are not copied.
+// Reciprocal of the diagonal: FP32 levels use the hardware approximation (relative error below
+// 2^-22; the FP32 smoother only needs to converge, the FP64 outer iteration fixes the rest), FP64
+// levels the exact quotient.
+__device__ __forceinline__ float recip(float x) {
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ double recip(double x) { return 1.0 / x; }
+
+// Each thread's own table, derived once per CTA from the tile's: plane offsets of its column pair
+// in its RPW rows, and the shift-free diagonals of its cells. Cells with no owner get offset -1,
+// diagonal +inf (so 1/diag = 0) and zero staging slots, which no copy ever overwrites. With
+// `coarse`, also the offsets of the coarse window, whose unowned cells are zeroed in both buffers.
 template <typename T>
-__device__ __forceinline__ void prefetch_cells(Shared<T>& S, long long base, const T* __restrict__ u,
-                                               const T* __restrict__ f, bool load_u) {
+__device__ __forceinline__ void thread_tables(Shared<T>& S, bool coarse) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const FusedTab<T>& tb = S.tab;
   const int col = tb.col[lane], rx = tb.colrx[lane];
-  if (col == FUSED_NONE) return;
+  int off[RPW];
 #pragma unroll
   for (int r = 0; r < RPW; ++r) {
-    const int ro = tb.rowoff[rx][RPW * warp + r];
-    if (ro == FUSED_NONE) continue;
-    const long long a = base + ro + col;  // even: block sizes and offsets are even
+    const int wj = RPW * warp + r;
+    const int ro = tb.rowoff[rx][wj];
+    off[r] = -1;
+    if (col != FUSED_NONE && ro != FUSED_NONE) {
+      off[r] = ro + col;  // even: block sizes and offsets are even
+      const int ry = tb.rowry[wj];
+      const T yd = tb.yd[rx][wj];
+      S.diag[r][threadIdx.x] = Pair<T>{tb.xd[ry][0][lane] + yd, tb.xd[ry][1][lane] + yd};
+    } else {
+      S.diag[r][threadIdx.x] = Pair<T>{(T)INFINITY, (T)INFINITY};
+      S.stage[r][0][threadIdx.x] = Pair<T>{0, 0};
+      S.stage[r][1][threadIdx.x] = Pair<T>{0, 0};
+    }
+  }
+  S.goff[threadIdx.x] = make_int4(off[0], off[1], off[2], off[3]);
+  static_assert(RPW == 4, "goff holds four rows");
+  if (coarse) {
+    for (int idx = threadIdx.x; idx < CW * CW; idx += FTHREADS) {
+      const int cj = idx / CW, ci = idx % CW;
+      const int cc = tb.ccol[ci];
+      const int ro = tb.crowoff[tb.ccolrx[ci]][cj];
+      const bool own = cc != FUSED_NONE && ro != FUSED_NONE;
+      S.coff[idx] = own ? ro + cc : -1;
+      if (!own) S.e[0][cj][ci] = S.e[1][cj][ci] = (T)0;
+    }
+  }
+}
+
+// Start the copies of the thread's owned cells of one mode (u if asked, and f) into its own
+// staging slots.
+template <typename T>
+__device__ __forceinline__ void prefetch_cells(Shared<T>& S, long long base, const T* __restrict__ u,
+                                               const T* __restrict__ f, bool load_u) {
+  const int4 o = S.goff[threadIdx.x];
+  const int off[RPW] = {o.x, o.y, o.z, o.w};
+#pragma unroll
+  for (int r = 0; r < RPW; ++r) {
+    if (off[r] < 0) continue;
+    const long long a = base + off[r];
     if (load_u) cp_async<2 * sizeof(T)>(&S.stage[r][0][threadIdx.x], u + a);
     cp_async<2 * sizeof(T)>(&S.stage[r][1][threadIdx.x], f + a);
   }
@@ -116,69 +168,61 @@ __device__ __forceinline__ void prefetch_cells(Shared<T>& S, long long base, con
 // The thread's 2 RPW cells of u (zero if asked), f and 1/diag, from its completed staging slots.
 template <typename T>
 __device__ __forceinline__ void take_cells(Cells<T>& C, const Shared<T>& S, bool zero_u, T sg) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const FusedTab<T>& tb = S.tab;
-  const int col = tb.col[lane], rx = tb.colrx[lane];
 #pragma unroll
   for (int r = 0; r < RPW; ++r) {
-    const int wj = RPW * warp + r;
-    const int ro = tb.rowoff[rx][wj];
-    T u0 = 0, u1 = 0, f0 = 0, f1 = 0, i0 = 0, i1 = 0;
-    if (col != FUSED_NONE && ro != FUSED_NONE) {
-      if (!zero_u) {
-        const Pair<T> v = S.stage[r][0][threadIdx.x];
-        u0 = v.a;
-        u1 = v.b;
-      }
-      const Pair<T> g = S.stage[r][1][threadIdx.x];
-      f0 = g.a;
-      f1 = g.b;
-      const int ry = tb.rowry[wj];
-      const T yd = tb.yd[rx][wj] + sg;
-      i0 = (T)1 / (tb.xd[ry][0][lane] + yd);
-      i1 = (T)1 / (tb.xd[ry][1][lane] + yd);
-    }
-    C.u[r][0] = u0;
-    C.u[r][1] = u1;
-    C.f[r][0] = f0;
-    C.f[r][1] = f1;
-    C.inv[r][0] = i0;
-    C.inv[r][1] = i1;
+    const Pair<T> v = zero_u ? Pair<T>{0, 0} : S.stage[r][0][threadIdx.x];
+    const Pair<T> g = S.stage[r][1][threadIdx.x];
+    const Pair<T> d = S.diag[r][threadIdx.x];
+    C.u[r][0] = v.a;
+    C.u[r][1] = v.b;
+    C.f[r][0] = g.a;
+    C.f[r][1] = g.b;
+    C.inv[r][0] = recip(d.a + sg);
+    C.inv[r][1] = recip(d.b + sg);
   }
 }
 
-// Start the copies of one mode's coarse correction window into S.e[buf] (zero where no owner).
+// Start the copies of one mode's coarse correction window into S.e[buf] (its unowned cells stay 0).
 template <typename T>
 __device__ __forceinline__ void prefetch_coarse(Shared<T>& S, int buf, long long cbase, const T* __restrict__ uc) {
-  const FusedTab<T>& tb = S.tab;
+  T* e = &S.e[buf][0][0];
   for (int idx = threadIdx.x; idx < CW * CW; idx += FTHREADS) {
-    const int cj = idx / CW, ci = idx % CW;
-    const int cc = tb.ccol[ci];
-    const int ro = tb.crowoff[tb.ccolrx[ci]][cj];
-    if (cc != FUSED_NONE && ro != FUSED_NONE) cp_async<sizeof(T)>(&S.e[buf][cj][ci], uc + cbase + ro + cc);
-    else S.e[buf][cj][ci] = (T)0;
+    const int o = S.coff[idx];
+    if (o >= 0) cp_async<sizeof(T)>(e + idx, uc + cbase + o);
   }
 }
 
+// The strip's first and last rows, both parities.
 template <typename T>
-__device__ __forceinline__ void write_halo(Shared<T>& S, const Cells<T>& C, int buf) {
+__device__ __forceinline__ void write_halo(Shared<T>& S, const Cells<T>& C) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  S.halo[buf][warp][0][0][lane] = C.u[0][0];
-  S.halo[buf][warp][0][1][lane] = C.u[0][1];
-  S.halo[buf][warp][1][0][lane] = C.u[RPW - 1][0];
-  S.halo[buf][warp][1][1][lane] = C.u[RPW - 1][1];
+  S.halo[warp][0][0][lane] = C.u[0][0];
+  S.halo[warp][0][1][lane] = C.u[0][1];
+  S.halo[warp][1][0][lane] = C.u[RPW - 1][0];
+  S.halo[warp][1][1][lane] = C.u[RPW - 1][1];
 }
 
 static_assert(RPW % 2 == 0, "a strip's last row has the parity of its second row");
+
+// After a half-sweep whose first row updated parity PA: only the cells of that colour changed, the
+// first row's at parity PA and the last row's at parity PA ^ 1. The next half-sweep reads only
+// entries of this colour (the neighbours of the other colour), and this half-sweep read only the
+// other colour's entries, so one buffer serves both with a barrier between half-sweeps.
+template <typename T, int PA>
+__device__ __forceinline__ void write_halo_colour(Shared<T>& S, const Cells<T>& C) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  S.halo[warp][0][PA][lane] = C.u[0][PA];
+  S.halo[warp][1][PA ^ 1][lane] = C.u[RPW - 1][PA ^ 1];
+}
 
 // The strip-edge neighbours a pass over the strip uses when its first row has colour parity PA:
 // row 0 reads the south strip's last row at parity PA, row RPW - 1 the north strip's first row at
 // parity PA ^ 1 (zero beyond the window).
 template <typename T, int PA>
-__device__ __forceinline__ void edge_values(const Shared<T>& S, int buf, T& south, T& north) {
+__device__ __forceinline__ void edge_values(const Shared<T>& S, T& south, T& north) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  south = warp > 0 ? S.halo[buf][warp - 1][1][PA][lane] : (T)0;
-  north = warp < FWARPS - 1 ? S.halo[buf][warp + 1][0][PA ^ 1][lane] : (T)0;
+  south = warp > 0 ? S.halo[warp - 1][1][PA][lane] : (T)0;
+  north = warp < FWARPS - 1 ? S.halo[warp + 1][0][PA ^ 1][lane] : (T)0;
 }
 
 // Gauss-Seidel update of row r of the strip, the colour's cells having column parity P.
@@ -205,12 +249,12 @@ __device__ __forceinline__ void update_row(Cells<T>& C, FP2<T> cx, FP2<T> cy, in
 // One half-sweep of the strip; P0 = column parity of the colour in the strip's first row. UNI: all
 // rows of the strip lie in one region row, so the x coefficients are one pair per parity.
 template <typename T, int P0, bool UNI>
-__device__ __forceinline__ void half_sweep(Cells<T>& C, const Shared<T>& S, int buf, const int (&ry)[RPW], int rx) {
+__device__ __forceinline__ void half_sweep(Cells<T>& C, Shared<T>& S, const int (&ry)[RPW], int rx) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   constexpr int PA = P0, PB = P0 ^ 1;
   const FusedTab<T>& tb = S.tab;
   T south, north;
-  edge_values<T, PA>(S, buf, south, north);
+  edge_values<T, PA>(S, south, north);
   FP2<T> cxa, cxb;
   if (UNI) {
     cxa = tb.xc[ry[0]][PA][lane];
@@ -230,14 +274,15 @@ __device__ __forceinline__ void half_sweep(Cells<T>& C, const Shared<T>& S, int 
       update_row<T, PB>(C, UNI ? cxb : tb.xc[ry[r]][PB][lane], cy, r, wj, sn, nn);
     }
   }
+  write_halo_colour<T, PA>(S, C);
 }
 
-// nu red-black sweeps of the whole window. On return the strip-edge rows of the final state are in
-// S.halo[buf] (for the residuals that follow).
+// nu red-black sweeps of the whole window. On return the strip-edge rows of the last colour are in
+// S.halo (the neighbours of the other colour, for the residuals that follow).
 // `after_first_barrier` runs once every thread has passed the barrier that follows the first
 // write of the halo rows (all earlier shared-memory reads of the CTA are then complete).
 template <typename T, typename Hook>
-__device__ void sweeps(Cells<T>& C, Shared<T>& S, int nu, int& buf, Hook&& after_first_barrier) {
+__device__ void sweeps(Cells<T>& C, Shared<T>& S, int nu, Hook&& after_first_barrier) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   int ry[RPW];
 #pragma unroll
@@ -245,22 +290,19 @@ __device__ void sweeps(Cells<T>& C, Shared<T>& S, int nu, int& buf, Hook&& after
   const bool uni = ry[0] == ry[RPW - 1];  // region rows are monotonic in the row
   const int rx = S.tab.colrx[lane];
   const int pbase = S.tab.pbase;
-  buf = 0;
-  write_halo(S, C, buf);
+  write_halo(S, C);
   __syncthreads();
   after_first_barrier();
   for (int s = 0; s < 2 * nu; ++s) {
     const int colour = s & 1;
     const int p0 = (colour - pbase - RPW * warp) & 1;
     if (uni) {
-      if (p0 == 0) half_sweep<T, 0, true>(C, S, buf, ry, rx);
-      else half_sweep<T, 1, true>(C, S, buf, ry, rx);
+      if (p0 == 0) half_sweep<T, 0, true>(C, S, ry, rx);
+      else half_sweep<T, 1, true>(C, S, ry, rx);
     } else {
-      if (p0 == 0) half_sweep<T, 0, false>(C, S, buf, ry, rx);
-      else half_sweep<T, 1, false>(C, S, buf, ry, rx);
+      if (p0 == 0) half_sweep<T, 0, false>(C, S, ry, rx);
+      else half_sweep<T, 1, false>(C, S, ry, rx);
     }
-    buf ^= 1;
-    write_halo(S, C, buf);
     __syncthreads();
   }
 }
@@ -287,12 +329,12 @@ __device__ __forceinline__ T resid_row(const Cells<T>& C, FP2<T> cx, T xd, FP2<T
 // rr[r] = residual of the red cell of row r (the black cells carry none after a sweep ending on
 // black); P0 = column parity of the red cells in the strip's first row.
 template <typename T, int P0>
-__device__ __forceinline__ void red_residuals(const Cells<T>& C, const Shared<T>& S, int buf, T sg, T (&rr)[RPW]) {
+__device__ __forceinline__ void red_residuals(const Cells<T>& C, const Shared<T>& S, T sg, T (&rr)[RPW]) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   constexpr int PA = P0, PB = P0 ^ 1;
   const FusedTab<T>& tb = S.tab;
   T south, north;
-  edge_values<T, PA>(S, buf, south, north);
+  edge_values<T, PA>(S, south, north);
   const FP2<T> cxa = tb.xc[1][PA][lane], cxb = tb.xc[1][PB][lane];
   const T xda = tb.xd[1][PA][lane] + sg, xdb = tb.xd[1][PB][lane] + sg;
 #pragma unroll
@@ -314,29 +356,28 @@ __device__ __forceinline__ void red_residuals(const Cells<T>& C, const Shared<T>
 
 // Red residuals of the strip; returns the column parity of the red cells in its first row.
 template <typename T>
-__device__ __forceinline__ int strip_residuals(const Cells<T>& C, const Shared<T>& S, int buf, T sg, T (&rr)[RPW]) {
+__device__ __forceinline__ int strip_residuals(const Cells<T>& C, const Shared<T>& S, T sg, T (&rr)[RPW]) {
   const int warp = threadIdx.x >> 5;
   const int p0 = (0 - S.tab.pbase - RPW * warp) & 1;
-  if (p0 == 0) red_residuals<T, 0>(C, S, buf, sg, rr);
-  else red_residuals<T, 1>(C, S, buf, sg, rr);
+  if (p0 == 0) red_residuals<T, 0>(C, S, sg, rr);
+  else red_residuals<T, 1>(C, S, sg, rr);
   return p0;
 }
 
 __device__ __forceinline__ bool in_tile(int w, int extent) { return w >= FH && w < FH + extent; }
 
-// Store the tile's u (window rows/columns FH .. FH + extent; region 1 is the tile's own block).
+// Store the tile's u (window rows/columns FH .. FH + extent, all in the tile's own block, where
+// the thread's load offsets are the block's own), one column pair per row.
 template <typename T>
-__device__ __forceinline__ void store_tile(const Cells<T>& C, const FusedTab<T>& tb, long long base, T* __restrict__ u) {
+__device__ __forceinline__ void store_tile(const Cells<T>& C, const Shared<T>& S, long long base, T* __restrict__ u) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  if (!in_tile(2 * lane, tb.tw)) return;
-  const int col = tb.col[lane];
+  if (!in_tile(2 * lane, S.tab.tw)) return;
+  const int4 o = S.goff[threadIdx.x];
+  const int off[RPW] = {o.x, o.y, o.z, o.w};
 #pragma unroll
   for (int r = 0; r < RPW; ++r) {
-    const int wj = RPW * warp + r;
-    if (!in_tile(wj, tb.th)) continue;
-    const long long a = base + tb.rowoff[1][wj] + col;
-    u[a] = C.u[r][0];
-    u[a + 1] = C.u[r][1];
+    if (!in_tile(RPW * warp + r, S.tab.th)) continue;
+    *reinterpret_cast<Pair<T>*>(u + base + off[r]) = Pair<T>{C.u[r][0], C.u[r][1]};
   }
 }
 
@@ -357,6 +398,7 @@ __global__ void __launch_bounds__(FTHREADS, 2)
   const int m0 = blockIdx.y * mpc, m1 = min(nact, m0 + mpc);
   copy_tab(S, tabs + blockIdx.x);
   __syncthreads();
+  thread_tables(S, false);
   const FusedTab<T>& tb = S.tab;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   int q = active[m0];
@@ -369,28 +411,27 @@ __global__ void __launch_bounds__(FTHREADS, 2)
     cp_async_wait_all();
     Cells<T> C;
     take_cells(C, S, zero_u != 0, sg);
-    int buf;
     T sgn = 0;
-    sweeps(C, S, nu, buf, [&] {
+    sweeps(C, S, nu, [&] {
       if (qn >= 0) {
         sgn = sigma[qn];
         prefetch_cells(S, (long long)qn * fncell, u, f, zero_u == 0);
         cp_async_commit();
       }
     });
-    store_tile(C, tb, base, u_out);
+    store_tile(C, S, base, u_out);
     // restriction: coarse cell = (column pair k, row pair (2h, 2h+1)) of the strip; its red children
     // are one per row, the black ones carry no residual after the sweep
     T rr[RPW];
-    const int p0 = strip_residuals(C, S, buf, sg, rr);
+    const int p0 = strip_residuals(C, S, sg, rr);
     if (in_tile(2 * lane, tb.tw)) {
       const long long cbase = (long long)q * cncell + tb.cout0 + lane;
-      const T wx[2] = {tb.rx[0][lane], tb.rx[1][lane]};
+      const T wa = tb.rx[p0][lane], wb = tb.rx[p0 ^ 1][lane];  // weights of the red cells of rows 2h, 2h + 1
 #pragma unroll
       for (int h = 0; h < RPW / 2; ++h) {
         const int wj = RPW * warp + 2 * h;
         if (!in_tile(wj, tb.th)) continue;
-        const T acc = fma(wx[p0 ^ 1] * tb.ry[wj + 1], rr[2 * h + 1], wx[p0] * tb.ry[wj] * rr[2 * h]);
+        const T acc = fma(wb * tb.ry[wj + 1], rr[2 * h + 1], wa * tb.ry[wj] * rr[2 * h]);
         const long long cc = cbase + (long long)(wj / 2) * tb.cnx;
         fc[cc] = acc;
         if (zero_coarse) uc[cc] = 0;
@@ -412,6 +453,7 @@ __global__ void __launch_bounds__(FTHREADS, 2)
   const int m0 = blockIdx.y * mpc, m1 = min(nact, m0 + mpc);
   copy_tab(S, tabs + blockIdx.x);
   __syncthreads();
+  thread_tables(S, true);
   const FusedTab<T>& tb = S.tab;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   int q = active[m0];
@@ -448,10 +490,9 @@ __global__ void __launch_bounds__(FTHREADS, 2)
         C.u[r][p] += fma(eC, (T)1 + wx.a + wy.a, fma(wx.b, eX, wy.b * eY));
       }
     }
-    int buf;
     T sgn = 0;
     // the next mode's window goes to the other coarse buffer, last read by the previous mode
-    sweeps(C, S, nu, buf, [&] {
+    sweeps(C, S, nu, [&] {
       if (qn >= 0) {
         sgn = sigma[qn];
         prefetch_cells(S, (long long)qn * fncell, u, f, true);
@@ -459,11 +500,11 @@ __global__ void __launch_bounds__(FTHREADS, 2)
         cp_async_commit();
       }
     });
-    store_tile(C, tb, base, u_out);
+    store_tile(C, S, base, u_out);
     if (part != nullptr) {
       // sum of squared residuals over the tile's cells (only red cells carry one after a sweep)
       T rr[RPW];
-      strip_residuals(C, S, buf, sg, rr);
+      strip_residuals(C, S, sg, rr);
       T r2 = 0;
       if (in_tile(2 * lane, tb.tw)) {
 #pragma unroll
