@@ -25,9 +25,11 @@ __device__ __forceinline__ T apply_row(const Coef<T>& cx, const Coef<T>& cy, T d
 // colour. 128 threads cover a 32x8 tile: each thread owns the one cell of its row pair that has the
 // colour, so every lane of every warp works. FP64 plans read the precomputed inverse diagonal (the
 // FP64 pipe is the bound there); FP32 plans form it on the fly.
+// SCALED: the level holds g = f / diag instead of f (FP64 plans without fused levels), and the
+// update is u_c = g_c - (sum_nbr a u_nbr) / diag_c, one FP64 operation fewer per cell.
 constexpr int COLOUR_THREADS = 128;
 
-template <typename T, bool PRE_INV>
+template <typename T, bool PRE_INV, bool SCALED>
 __global__ void __launch_bounds__(COLOUR_THREADS) k_smooth(LevelView<T> L, const int* __restrict__ active,
                                                             const T* __restrict__ sigma, const double* __restrict__ invd,
                                                             T* __restrict__ u, const T* __restrict__ f, int colour) {
@@ -52,7 +54,24 @@ __global__ void __launch_bounds__(COLOUR_THREADS) k_smooth(LevelView<T> L, const
   a = fma(cx.hi, u[base + e], a);
   a = fma(cy.lo, u[base + s], a);
   a = fma(cy.hi, u[base + n], a);
-  u[base + c] = (f[base + c] - a) * id;
+  if constexpr (SCALED) u[base + c] = fma(-a, id, f[base + c]);
+  else u[base + c] = (f[base + c] - a) * id;
+}
+
+// Residual of cell c with the off-diagonal sum a and the diagonal: f - (a + diag u) from f, or
+// diag (g - u) - a from the scaled right-hand side g = f / diag (the same number of operations).
+template <typename T, bool SCALED>
+__device__ __forceinline__ T cell_residual(const Coef<T>& cx, const Coef<T>& cy, T diag, T fc, T uc, T uw, T ue, T us,
+                                           T un) {
+  if constexpr (SCALED) {
+    T a = cx.lo * uw;
+    a = fma(cx.hi, ue, a);
+    a = fma(cy.lo, us, a);
+    a = fma(cy.hi, un, a);
+    return fma(diag, fc - uc, -a);
+  } else {
+    return fc - apply_row(cx, cy, diag, uc, uw, ue, us, un);
+  }
 }
 
 __global__ void __launch_bounds__(TILE_THREADS) k_invd(LevelView<double> L, const double* __restrict__ sigma,
@@ -70,11 +89,16 @@ __global__ void __launch_bounds__(TILE_THREADS) k_invd(LevelView<double> L, cons
 // the coarse iterate starts at zero.
 // After a red-black sweep ending on black, every black cell has zero residual (its update solved its
 // own row), so with RED_ONLY only the two red children of each coarse cell are evaluated.
-template <typename T, bool RED_ONLY>
+// SCALED: the fine level holds f / diag. With invd_c the coarse level does too (its right-hand side
+// is written times its inverse diagonal), and with first_red the coarse level's first colour-0
+// half-sweep is done here: from a zero iterate it sets each colour-0 cell to f / diag, which is the
+// value written, and the coarse smoothing starts with colour 1.
+template <typename T, bool RED_ONLY, bool SCALED>
 __global__ void __launch_bounds__(TILE_THREADS) k_restrict(LevelView<T> F, LevelView<T> C, const int* __restrict__ active,
                                                             const T* __restrict__ sigma, const T* __restrict__ uf,
                                                             const T* __restrict__ ff, T* __restrict__ fc,
-                                                            T* __restrict__ uc) {
+                                                            T* __restrict__ uc, const double* __restrict__ invd_c,
+                                                            int first_red) {
   const TileDev t = C.tiles[blockIdx.x];
   const BlockDev Bc = C.blk[t.b];
   const int I = t.x0 + (threadIdx.x % TILE_X), J = t.y0 + (threadIdx.x / TILE_X);
@@ -95,22 +119,34 @@ __global__ void __launch_bounds__(TILE_THREADS) k_restrict(LevelView<T> F, Level
       const long long c = Bf.off + (long long)j * Bf.nx + i;
       const Coef<T> cx = F.cx[Bf.xo + i], cy = F.cy[Bf.yo + j];
       const T diag = cx.d + cy.d + sg;
-      const T r = ff[bf + c] - apply_row(cx, cy, diag, uf[bf + c], uf[bf + w], uf[bf + e], uf[bf + s], uf[bf + n]);
+      const T r = cell_residual<T, SCALED>(cx, cy, diag, ff[bf + c], uf[bf + c], uf[bf + w], uf[bf + e], uf[bf + s],
+                                           uf[bf + n]);
       acc = fma(F.rx[Bf.xo + i] * F.ry[Bf.yo + j], r, acc);
     }
   }
   const long long cc = (long long)q * C.ncell + Bc.off + (long long)J * Bc.nx + I;
+  if (invd_c != nullptr) acc *= (T)invd_c[cc];
   fc[cc] = acc;
-  uc[cc] = 0;
+  uc[cc] = (first_red && ((Bc.par + I + J) & 1) == 0) ? acc : (T)0;
 }
 
 // u_f += e_C (1 + sx + sy) + nx e_X + ny e_Y: parent C, coarse neighbours X / Y on the fine cell's side.
-template <typename T>
+// With ONE_COLOUR only the cells of `colour` are corrected (COLOUR_THREADS threads per tile, as in
+// k_smooth): when a post-smoothing half-sweep of the other colour follows, it overwrites the other
+// colour's cells from their neighbours and f alone, so correcting them would be wasted work.
+template <typename T, bool ONE_COLOUR>
 __global__ void __launch_bounds__(TILE_THREADS) k_prolong(LevelView<T> F, LevelView<T> C, const int* __restrict__ active,
-                                                           T* __restrict__ uf, const T* __restrict__ uc) {
+                                                           T* __restrict__ uf, const T* __restrict__ uc, int colour) {
   const TileDev t = F.tiles[blockIdx.x];
   const BlockDev Bf = F.blk[t.b];
-  const int i = t.x0 + (threadIdx.x % TILE_X), j = t.y0 + (threadIdx.x / TILE_X);
+  int i, j;
+  if (ONE_COLOUR) {
+    j = t.y0 + (threadIdx.x >> 4);
+    i = t.x0 + 2 * (threadIdx.x & 15) + ((colour ^ Bf.par ^ j) & 1);
+  } else {
+    i = t.x0 + (threadIdx.x % TILE_X);
+    j = t.y0 + (threadIdx.x / TILE_X);
+  }
   if (i >= Bf.nx || j >= Bf.ny) return;
   const int q = active[blockIdx.y];
   const BlockDev Bc = C.blk[t.b];
@@ -121,10 +157,10 @@ __global__ void __launch_bounds__(TILE_THREADS) k_prolong(LevelView<T> F, LevelV
   const T eC = uc[bc + Bc.off + (long long)J * Bc.nx + I];
   const T eX = uc[bc + ((i & 1) ? e : w)];
   const T eY = uc[bc + ((j & 1) ? n : s)];
-  const PW<T> px = F.px[Bf.xo + i], py = F.py[Bf.yo + j];
+  const PW<T> px = F.px[Bf.xo + i], py = F.py[Bf.yo + j];  // px.self already holds 1 + self_x
   const long long c = (long long)q * F.ncell + Bf.off + (long long)j * Bf.nx + i;
   // accumulated into u directly: three FMAs (the FP64 pipe bounds this kernel in FP64 plans)
-  T u = fma(eC, (T)1 + px.self + py.self, uf[c]);
+  T u = fma(eC, px.self + py.self, uf[c]);
   u = fma(px.nbr, eX, u);
   uf[c] = fma(py.nbr, eY, u);
 }
@@ -182,7 +218,7 @@ __global__ void __launch_bounds__(TILE_THREADS) k_mode_apply(LevelView<T> L, con
 
 // Per-tile partial sums of (f - (A + sigma) u)^2 for every listed mode (FP64 accumulation). With
 // RED_ONLY (after a sweep ending on black) only the red cells carry a residual.
-template <typename T, bool RED_ONLY>
+template <typename T, bool RED_ONLY, bool SCALED>
 __global__ void __launch_bounds__(TILE_THREADS) k_mode_resid2(LevelView<T> L, const int* __restrict__ active,
                                                                const T* __restrict__ sigma, const T* __restrict__ u,
                                                                const T* __restrict__ f, double* __restrict__ part) {
@@ -206,7 +242,8 @@ __global__ void __launch_bounds__(TILE_THREADS) k_mode_resid2(LevelView<T> L, co
     const long long c = B.off + (long long)j * B.nx + i;
     const Coef<T> cx = L.cx[B.xo + i], cy = L.cy[B.yo + j];
     const T diag = cx.d + cy.d + sigma[q];
-    const T r = f[base + c] - apply_row(cx, cy, diag, u[base + c], u[base + w], u[base + e], u[base + s], u[base + n]);
+    const T r = cell_residual<T, SCALED>(cx, cy, diag, f[base + c], u[base + c], u[base + w], u[base + e], u[base + s],
+                                         u[base + n]);
     r2 = r * r;
   }
   r2 = warp_sum_t(r2);
@@ -246,6 +283,32 @@ __global__ void __launch_bounds__(256) k_mode_sumsq(const T* __restrict__ f, lon
   }
 }
 
+// The same sums for the right-hand side as the transform left it, which is then scaled in place by
+// the level's inverse diagonal (the form the SCALED kernels read).
+__global__ void __launch_bounds__(256) k_mode_sumsq_scale(double* __restrict__ f, const double* __restrict__ invd,
+                                                          long long ncell, const int* __restrict__ active,
+                                                          double* __restrict__ part) {
+  __shared__ double sh[32];
+  const int q = active[blockIdx.y];
+  double* fq = f + (long long)q * ncell;
+  const double* iq = invd + (long long)q * ncell;
+  double s = 0;
+  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < ncell; c += (long long)gridDim.x * blockDim.x) {
+    const double v = fq[c];
+    s = fma(v, v, s);
+    fq[c] = v * iq[c];
+  }
+  s = warp_sum(s);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) sh[warp] = s;
+  __syncthreads();
+  if (warp == 0) {
+    double v = lane < (int)(blockDim.x >> 5) ? sh[lane] : 0.0;
+    v = warp_sum(v);
+    if (lane == 0) part[(long long)q * MODE_SQ_CTAS + blockIdx.x] = v;
+  }
+}
+
 __global__ void __launch_bounds__(256) k_mode_reduce(const double* __restrict__ part, int ntiles,
                                                      const int* __restrict__ active, double* __restrict__ norm2) {
   __shared__ double sh[32];
@@ -277,16 +340,27 @@ cudaError_t vcycle_t(snac_plan* P, int nact, cudaStream_t st) {
   const int* act = P->d_active;
   const double w = sizeof(T);
   constexpr bool pre_inv = sizeof(T) == 8;
-  auto smooth = [&](int l, int nu) {
+  // FP64 plans without fused levels: the smoothed levels hold f / diag (see k_smooth)
+  const bool scaled = sizeof(T) == 8 && P->scaled_f;
+  auto smooth = [&](int l, int nu, bool skip_first) {
     const HostLevel& h = P->lev[l];
     const LevelView<T> V = level_view<T>(h);
     dim3 g((unsigned)h.tiles.size(), (unsigned)nact);
     const double cells = (double)h.ncell * nact;
     for (int it = 0; it < nu; ++it)
       for (int colour = 0; colour < 2; ++colour) {
+        if (skip_first && it == 0 && colour == 0) continue;  // done by the restriction
         // Gauss-Seidel half-sweep: read the other colour and f of this colour, write this colour
-        LaunchScope ls(P, K_SMOOTH, 1.5 * w * cells, (pre_inv ? 9.0 : 12.0) * 0.5 * cells, st);
-        k_smooth<T, pre_inv><<<g, COLOUR_THREADS, 0, st>>>(V, act, sg, h.d_invd, (T*)h.d_u, (const T*)h.d_f, colour);
+        LaunchScope ls(P, K_SMOOTH, 1.5 * w * cells, (pre_inv ? (scaled ? 8.0 : 9.0) : 12.0) * 0.5 * cells, st);
+        auto go = [&](auto kern) {
+          kern<<<g, COLOUR_THREADS, 0, st>>>(V, act, sg, h.d_invd, (T*)h.d_u, (const T*)h.d_f, colour);
+        };
+        if constexpr (sizeof(T) == 8) {
+          if (scaled) go(k_smooth<T, pre_inv, true>);
+          else go(k_smooth<T, pre_inv, false>);
+        } else {
+          go(k_smooth<T, pre_inv, false>);
+        }
       }
   };
   for (int l = 0; l < L; ++l) {
@@ -300,16 +374,28 @@ cudaError_t vcycle_t(snac_plan* P, int nact, cudaStream_t st) {
       if (e != cudaSuccess) return e;
       continue;
     }
-    smooth(l, P->nu1);
+    // a level below 0 starts from zero: with scaled right-hand sides its first colour-0 half-sweep
+    // is folded into the restriction that fills it
+    smooth(l, P->nu1, scaled && l > 0 && P->nu1 > 0);
     dim3 g((unsigned)hc.tiles.size(), (unsigned)nact);
     const double cells = (double)h.ncell * nact;
-    LaunchScope ls(P, K_RESTRICT, 2.5 * w * cells, (P->nu1 > 0 ? 7.5 : 15.0) * cells, st);
-    if (P->nu1 > 0)
-      k_restrict<T, true><<<g, TILE_THREADS, 0, st>>>(level_view<T>(h), level_view<T>(hc), act, sg, (const T*)h.d_u,
-                                                      (const T*)h.d_f, (T*)hc.d_f, (T*)hc.d_u);
-    else
-      k_restrict<T, false><<<g, TILE_THREADS, 0, st>>>(level_view<T>(h), level_view<T>(hc), act, sg, (const T*)h.d_u,
-                                                       (const T*)h.d_f, (T*)hc.d_f, (T*)hc.d_u);
+    const bool coarse_smoothed = l + 1 < L;
+    const double* invd_c = scaled && coarse_smoothed ? hc.d_invd : nullptr;
+    const int first_red = scaled && coarse_smoothed && P->nu1 > 0 ? 1 : 0;
+    LaunchScope ls(P, K_RESTRICT, (2.5 + (invd_c ? 0.25 : 0.0)) * w * cells, (P->nu1 > 0 ? 7.5 : 15.0) * cells, st);
+    auto restrict_k = [&](auto kern) {
+      kern<<<g, TILE_THREADS, 0, st>>>(level_view<T>(h), level_view<T>(hc), act, sg, (const T*)h.d_u,
+                                       (const T*)h.d_f, (T*)hc.d_f, (T*)hc.d_u, invd_c, first_red);
+    };
+    if constexpr (sizeof(T) == 8) {
+      if (scaled && P->nu1 > 0) restrict_k(k_restrict<T, true, true>);
+      else if (scaled) restrict_k(k_restrict<T, false, true>);
+      else if (P->nu1 > 0) restrict_k(k_restrict<T, true, false>);
+      else restrict_k(k_restrict<T, false, false>);
+    } else {
+      if (P->nu1 > 0) restrict_k(k_restrict<T, true, false>);
+      else restrict_k(k_restrict<T, false, false>);
+    }
   }
   {
     const HostLevel& h = P->lev[L];
@@ -328,10 +414,19 @@ cudaError_t vcycle_t(snac_plan* P, int nact, cudaStream_t st) {
     dim3 g((unsigned)h.tiles.size(), (unsigned)nact);
     {
       const double cells = (double)h.ncell * nact;
-      LaunchScope ls(P, K_PROLONG, 2.25 * w * cells, 8.0 * cells, st);
-      k_prolong<T><<<g, TILE_THREADS, 0, st>>>(level_view<T>(h), level_view<T>(hc), act, (T*)h.d_u, (const T*)hc.d_u);
+      if (P->nu2 > 0) {
+        // post-smoothing starts with colour 0: correct the colour-1 cells only (read and write u
+        // there, read the coarse correction)
+        LaunchScope ls(P, K_PROLONG, 1.25 * w * cells, 3.5 * cells, st);
+        k_prolong<T, true><<<g, COLOUR_THREADS, 0, st>>>(level_view<T>(h), level_view<T>(hc), act, (T*)h.d_u,
+                                                          (const T*)hc.d_u, 1);
+      } else {
+        LaunchScope ls(P, K_PROLONG, 2.25 * w * cells, 7.0 * cells, st);
+        k_prolong<T, false><<<g, TILE_THREADS, 0, st>>>(level_view<T>(h), level_view<T>(hc), act, (T*)h.d_u,
+                                                         (const T*)hc.d_u, 0);
+      }
     }
-    smooth(l, P->nu2);
+    smooth(l, P->nu2, false);
   }
   return cudaGetLastError();
 }
@@ -339,8 +434,13 @@ cudaError_t vcycle_t(snac_plan* P, int nact, cudaStream_t st) {
 template <typename T>
 cudaError_t mode_norms_t(snac_plan* P, int nact, bool after_cycle, cudaStream_t st, const int* list) {
   const HostLevel& h = P->lev[0];
+  const bool scaled = sizeof(T) == 8 && P->scaled_f;
   if (!after_cycle) {  // zero iterate: the residual is the right-hand side itself
-    {
+    if (scaled) {  // ... which is then scaled into the form the smoothed levels hold
+      LaunchScope ls(P, K_MODE_RESID, 3.0 * sizeof(T) * h.ncell * nact, 3.0 * h.ncell * nact, st);
+      k_mode_sumsq_scale<<<dim3(MODE_SQ_CTAS, nact), 256, 0, st>>>((double*)h.d_f, h.d_invd, h.ncell, list,
+                                                                   P->d_mode_part);
+    } else {
       LaunchScope ls(P, K_MODE_RESID, (double)sizeof(T) * h.ncell * nact, 2.0 * h.ncell * nact, st);
       k_mode_sumsq<T><<<dim3(MODE_SQ_CTAS, nact), 256, 0, st>>>((const T*)h.d_f, h.ncell, list, P->d_mode_part);
     }
@@ -359,12 +459,20 @@ cudaError_t mode_norms_t(snac_plan* P, int nact, bool after_cycle, cudaStream_t 
     // after post-smoothing only the red cells carry a residual (read u everywhere, f on red cells)
     const bool red = after_cycle && P->nu2 > 0 && P->lev.size() > 1;
     LaunchScope ls(P, K_MODE_RESID, (red ? 1.5 : 2.0) * sizeof(T) * cells, (red ? 7.0 : 14.0) * cells, st);
-    if (red)
-      k_mode_resid2<T, true><<<g, COLOUR_THREADS, 0, st>>>(level_view<T>(h), list, sigma_ptr<T>(P),
-                                                           (const T*)h.d_u, (const T*)h.d_f, P->d_mode_part);
-    else
-      k_mode_resid2<T, false><<<g, TILE_THREADS, 0, st>>>(level_view<T>(h), list, sigma_ptr<T>(P),
-                                                          (const T*)h.d_u, (const T*)h.d_f, P->d_mode_part);
+    auto resid = [&](auto kern, int threads) {
+      kern<<<g, threads, 0, st>>>(level_view<T>(h), list, sigma_ptr<T>(P), (const T*)h.d_u, (const T*)h.d_f,
+                                  P->d_mode_part);
+    };
+    // a single-level plan never scales (its one level is the coarsest, solved directly)
+    if constexpr (sizeof(T) == 8) {
+      if (scaled && red) resid(k_mode_resid2<T, true, true>, COLOUR_THREADS);
+      else if (scaled) resid(k_mode_resid2<T, false, true>, TILE_THREADS);
+      else if (red) resid(k_mode_resid2<T, true, false>, COLOUR_THREADS);
+      else resid(k_mode_resid2<T, false, false>, TILE_THREADS);
+    } else {
+      if (red) resid(k_mode_resid2<T, true, false>, COLOUR_THREADS);
+      else resid(k_mode_resid2<T, false, false>, TILE_THREADS);
+    }
   }
   LaunchScope ls(P, K_MODE_REDUCE, 8.0 * h.tiles.size() * nact, (double)h.tiles.size() * nact, st);
   k_mode_reduce<<<nact, 256, 0, st>>>(P->d_mode_part, (int)h.tiles.size(), list, P->d_mode_norm2);

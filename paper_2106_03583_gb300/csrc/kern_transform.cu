@@ -142,6 +142,10 @@ __device__ __forceinline__ Cx<T> irdft_pre(Cx<T> xk, Cx<T> xmk, const Cx<T>& twn
   return {E.re - O.im, E.im + O.re};  // E + i O
 }
 
+// Loads from HBM per thread in flight before their first use: the column loads of a chunk are
+// independent, and issuing them in batches keeps enough bytes in flight to cover the DRAM latency.
+constexpr int LBATCH = 8;
+
 // Caller offsets (at k = 0) of the chunk's columns, and the caller stride along the homogeneous axis.
 template <int TC>
 __device__ __forceinline__ long long chunk_columns(const ChunkDev& ch, const BlockDev& B, const CallerBlk* __restrict__ cb,
@@ -170,15 +174,20 @@ __global__ void __launch_bounds__(256) k_forward(const ChunkDev* __restrict__ ch
   const ChunkDev ch = chunks[blockIdx.x];
   const BlockDev B = blk[ch.b];
   const long long sk = chunk_columns<TC>(ch, B, cb, coff);
-  if (sk == 1) {  // the homogeneous axis is the caller's contiguous one: consecutive threads along it
-    for (int idx = threadIdx.x; idx < n * TC; idx += blockDim.x) {
-      const int k = idx % n, c = idx / n;
-      xs[k * TC + c] = c < ch.ncol ? (T)in3[coff[c] + k] : (T)0;
+  // sk == 1: the homogeneous axis is the caller's contiguous one, consecutive threads run along it
+  const bool along = sk == 1;
+  for (int i0 = threadIdx.x; i0 < n * TC; i0 += LBATCH * blockDim.x) {
+    double v[LBATCH];
+#pragma unroll
+    for (int u = 0; u < LBATCH; ++u) {
+      const int idx = i0 + u * blockDim.x;
+      const int k = along ? idx % n : idx / TC, c = along ? idx / n : idx % TC;
+      v[u] = idx < n * TC && c < ch.ncol ? in3[coff[c] + k * sk] : 0.0;
     }
-  } else {
-    for (int idx = threadIdx.x; idx < n * TC; idx += blockDim.x) {
-      const int k = idx / TC, c = idx % TC;
-      xs[idx] = c < ch.ncol ? (T)in3[coff[c] + k * sk] : (T)0;
+#pragma unroll
+    for (int u = 0; u < LBATCH; ++u) {
+      const int idx = i0 + u * blockDim.x;
+      if (idx < n * TC) xs[along ? (idx % n) * TC + idx / n : idx] = (T)v[u];
     }
   }
   __syncthreads();
@@ -257,9 +266,19 @@ __global__ void __launch_bounds__(256) k_backward(const ChunkDev* __restrict__ c
   T* xs = reinterpret_cast<T*>(Bf);
   const ChunkDev ch = chunks[blockIdx.x];
   const BlockDev B = blk[ch.b];
-  for (int idx = threadIdx.x; idx < n * TC; idx += blockDim.x) {
-    const int q = idx / TC, c = idx % TC;
-    xs[idx] = c < ch.ncol ? modes[(long long)q * ncell + B.off + ch.c0 + c] : (T)0;
+  for (int i0 = threadIdx.x; i0 < n * TC; i0 += LBATCH * blockDim.x) {
+    T v[LBATCH];
+#pragma unroll
+    for (int u = 0; u < LBATCH; ++u) {
+      const int idx = i0 + u * blockDim.x;
+      const int q = idx / TC, c = idx % TC;
+      v[u] = idx < n * TC && c < ch.ncol ? modes[(long long)q * ncell + B.off + ch.c0 + c] : (T)0;
+    }
+#pragma unroll
+    for (int u = 0; u < LBATCH; ++u) {
+      const int idx = i0 + u * blockDim.x;
+      if (idx < n * TC) xs[idx] = v[u];
+    }
   }
   __syncthreads();
   const bool rev = kind == KIND_DD;                 // DST-III reads X reversed
@@ -298,30 +317,40 @@ __global__ void __launch_bounds__(256) k_backward(const ChunkDev* __restrict__ c
   __shared__ long long coff[TC];
   const long long sk = chunk_columns<TC>(ch, B, cb, coff);
   const bool along = sk == 1;  // consecutive threads along the homogeneous axis when it is contiguous
-  for (int idx = threadIdx.x; idx < n * TC; idx += blockDim.x) {
-    const int j = along ? idx % n : idx / TC, c = along ? idx / n : idx % TC;
-    T y;
-    if (kind == KIND_PP) {
-      const Cx<T> z = R[(j >> 1) * TC + c];
-      y = (j & 1) ? z.im : z.re;
-    } else if (kind == KIND_NN || kind == KIND_DD) {
-      const int t = (j & 1) ? n - 1 - (j >> 1) : (j >> 1);  // x_2t = v_t, x_2t+1 = v_{n-1-t}
-      const Cx<T> z = R[(t >> 1) * TC + c];
-      y = (t & 1) ? z.im : z.re;
-      if (kind == KIND_DD && (j & 1)) y = -y;
-    } else {
-      const int qq = kind == KIND_DN ? n - 1 - j : j;
-      if ((qq & 1) == 0) {
-        const int k = qq / 2;
-        y = (T)2 * cmul(R[k * TC + c], tw.tw4b[k]).re;
-      } else {
-        const int k = (n - 1 - qq) / 2;
-        y = (T)-2 * cmul(R[k * TC + c], tw.tw4b[k]).im;
-      }
+  // p += y / theta: the old values of a batch are loaded before any of them is written back
+  for (int i0 = threadIdx.x; i0 < n * TC; i0 += LBATCH * blockDim.x) {
+    double old[LBATCH];
+#pragma unroll
+    for (int u = 0; u < LBATCH; ++u) {
+      const int idx = i0 + u * blockDim.x;
+      const int j = along ? idx % n : idx / TC, c = along ? idx / n : idx % TC;
+      old[u] = idx < n * TC && c < ch.ncol ? p3[coff[c] + j * sk] : 0.0;
     }
-    if (c < ch.ncol) {
-      double* dst = p3 + coff[c] + j * sk;
-      *dst = fma((double)y, inv_theta, *dst);
+#pragma unroll
+    for (int u = 0; u < LBATCH; ++u) {
+      const int idx = i0 + u * blockDim.x;
+      if (idx >= n * TC) break;
+      const int j = along ? idx % n : idx / TC, c = along ? idx / n : idx % TC;
+      T y;
+      if (kind == KIND_PP) {
+        const Cx<T> z = R[(j >> 1) * TC + c];
+        y = (j & 1) ? z.im : z.re;
+      } else if (kind == KIND_NN || kind == KIND_DD) {
+        const int t = (j & 1) ? n - 1 - (j >> 1) : (j >> 1);  // x_2t = v_t, x_2t+1 = v_{n-1-t}
+        const Cx<T> z = R[(t >> 1) * TC + c];
+        y = (t & 1) ? z.im : z.re;
+        if (kind == KIND_DD && (j & 1)) y = -y;
+      } else {
+        const int qq = kind == KIND_DN ? n - 1 - j : j;
+        if ((qq & 1) == 0) {
+          const int k = qq / 2;
+          y = (T)2 * cmul(R[k * TC + c], tw.tw4b[k]).re;
+        } else {
+          const int k = (n - 1 - qq) / 2;
+          y = (T)-2 * cmul(R[k * TC + c], tw.tw4b[k]).im;
+        }
+      }
+      if (c < ch.ncol) p3[coff[c] + j * sk] = fma((double)y, inv_theta, old[u]);
     }
   }
 }

@@ -461,8 +461,12 @@ int upload_level(snac_plan* P, HostLevel& lv, size_t inner) {
       (st = upload(P, &lv.d_cx32, to32(lv.cx))) || (st = upload(P, &lv.d_cy32, to32(lv.cy))))
     return st;
   if (!lv.px.empty()) {
-    if ((st = upload(P, &lv.d_px64, lv.px)) || (st = upload(P, &lv.d_py64, lv.py)) ||
-        (st = upload(P, &lv.d_px32, to32(lv.px))) || (st = upload(P, &lv.d_py32, to32(lv.py))) ||
+    // the device copy of the x weights carries the parent's unit weight: self_x + 1, so that the
+    // prolongation forms the parent's total weight (1 + self_x) + self_y with one addition
+    std::vector<PW<double>> px1 = lv.px;
+    for (PW<double>& w : px1) w.self += 1.0;
+    if ((st = upload(P, &lv.d_px64, px1)) || (st = upload(P, &lv.d_py64, lv.py)) ||
+        (st = upload(P, &lv.d_px32, to32(px1))) || (st = upload(P, &lv.d_py32, to32(lv.py))) ||
         (st = upload(P, &lv.d_rx64, lv.rx)) || (st = upload(P, &lv.d_ry64, lv.ry)) ||
         (st = upload(P, &lv.d_rx32, to32(lv.rx))) || (st = upload(P, &lv.d_ry32, to32(lv.ry))))
       return st;
@@ -746,6 +750,9 @@ int create(snac_plan** out, int32_t nblocks, const snac_block* blocks_in, int32_
       if (st) break;
     }
     if (P->precision == SNAC_FP64) {
+      bool any_fused = false;
+      for (const HostLevel& lv : P->lev) any_fused = any_fused || lv.fused;
+      P->scaled_f = !any_fused && P->lev.size() > 1;
       for (size_t l = 0; l + 1 < P->lev.size(); ++l)
         if ((st = dmalloc(P, &P->lev[l].d_invd, (size_t)P->nz * P->lev[l].ncell))) break;
       if (st) break;

@@ -77,7 +77,7 @@ struct LevelView {
   const TileDev* tiles;
   const Coef<T>* cx;
   const Coef<T>* cy;
-  const PW<T>* px;  // weights for prolongation into this level (fine side)
+  const PW<T>* px;  // weights for prolongation into this level (fine side); px[i].self includes the +1 of the parent
   const PW<T>* py;
   const T* rx;      // restriction weights: fine width / parent width
   const T* ry;
@@ -154,6 +154,9 @@ struct snac_plan {
   double inner_reduction = 1e-3;
   double shift = 0.0;  // Helmholtz shift (<= 0), included in sigma and in the residual's diagonal
   int fused = -1;
+  // FP64 plans without fused levels keep the right-hand side of every smoothed level (all but the
+  // coarsest) divided by the diagonal, which saves one FP64 operation per smoothing update
+  bool scaled_f = false;
   int nblk = 0;
   int nz = 0;
   double dz = 0.0;

@@ -344,6 +344,8 @@ int snac_mode_vcycles(snac_plan* plan, const void* d_f, void* d_u, int32_t ncycl
   CK(cudaMemcpyAsync(plan->lev[0].d_f, d_f, bytes, cudaMemcpyDeviceToDevice, s));
   CK(cudaMemcpyAsync(plan->lev[0].d_u, d_u, bytes, cudaMemcpyDeviceToDevice, s));
   if ((st = set_active_all(plan, s))) return st;
+  // the zero-iterate norms put the right-hand side into the form the cycles read (scaled plans)
+  if (plan->scaled_f) CK(launch_mode_norms(plan, plan->nz, false, s));
   for (int c = 0; c < ncycles; ++c) CK(launch_vcycle(plan, plan->nz, s));
   CK(cudaMemcpyAsync(d_u, plan->lev[0].d_u, bytes, cudaMemcpyDeviceToDevice, s));
   CK(cudaStreamSynchronize(s));
