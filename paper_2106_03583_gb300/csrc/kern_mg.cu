@@ -351,7 +351,7 @@ cudaError_t vcycle_t(snac_plan* P, int nact, cudaStream_t st) {
       for (int colour = 0; colour < 2; ++colour) {
         if (skip_first && it == 0 && colour == 0) continue;  // done by the restriction
         // Gauss-Seidel half-sweep: read the other colour and f of this colour, write this colour
-        LaunchScope ls(P, K_SMOOTH, 1.5 * w * cells, (pre_inv ? (scaled ? 8.0 : 9.0) : 12.0) * 0.5 * cells, st);
+        LaunchScope ls(P, K_SMOOTH, 1.5 * w * cells, (pre_inv ? 9.0 : 12.0) * 0.5 * cells, st);
         auto go = [&](auto kern) {
           kern<<<g, COLOUR_THREADS, 0, st>>>(V, act, sg, h.d_invd, (T*)h.d_u, (const T*)h.d_f, colour);
         };

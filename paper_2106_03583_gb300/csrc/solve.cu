@@ -220,8 +220,13 @@ int run_solve(snac_plan* P, const double* f, double* p, double tol, cudaStream_t
       fn = rn = fn_pre;
       if (P->singular) CK(cudaMemsetAsync(P->d_sums + 2, 0, sizeof(double), s));  // sum V p = 0
     } else {
-      // ||f|| is needed once; sum V p only for singular problems (zero-mean update)
-      CK(launch_field3d(P, 0, f, p, P->d_r3, fshift, k == 0, P->singular, s));
+      // ||f|| is needed once; sum V p only for singular problems (zero-mean update). In FP64 plans
+      // only for the caller's initial guess: an update leaves sum V p = 0 to rounding (the mean fix
+      // solves for it), so later passes take it as 0 (their partials carry 0 in that slot). Mixed
+      // plans measure it every time: the FP32 transform of the correction leaves a drift that the
+      // next mean fix removes.
+      const bool need_vp = P->singular && (k == 0 || P->precision != SNAC_FP64);
+      CK(launch_field3d(P, 0, f, p, P->d_r3, fshift, k == 0, need_vp, s));
       if ((st = read_sums(P, s))) return st;
       if (k == 0) fn = std::sqrt(P->h_sums[1]);
       rn = std::sqrt(P->h_sums[0]);
