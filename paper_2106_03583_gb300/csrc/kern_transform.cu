@@ -51,16 +51,21 @@ __device__ Cx<T>* cfft(Cx<T>* X, Cx<T>* Y, int m, const Cx<T>* __restrict__ tw, 
       for (int idx = threadIdx.x; idx < (m / 4) * TC; idx += blockDim.x) {
         const int c = idx % TC, t = idx / TC;
         const int j = t >> lg, k = t & (Ls - 1);
-        Cx<T> w1 = tw[k * r], w2 = tw[2 * k * r], w3 = tw[3 * k * r];
-        if (inverse) {
-          w1.im = -w1.im;
-          w2.im = -w2.im;
-          w3.im = -w3.im;
+        Cx<T> a0 = X[(j * Ls + k) * TC + c];
+        Cx<T> a1 = X[((j + r) * Ls + k) * TC + c];
+        Cx<T> a2 = X[((j + 2 * r) * Ls + k) * TC + c];
+        Cx<T> a3 = X[((j + 3 * r) * Ls + k) * TC + c];
+        if (Ls > 1) {  // the first stage has k = 0 only: unit twiddles
+          Cx<T> w1 = tw[k * r], w2 = tw[2 * k * r], w3 = tw[3 * k * r];
+          if (inverse) {
+            w1.im = -w1.im;
+            w2.im = -w2.im;
+            w3.im = -w3.im;
+          }
+          a1 = cmul(w1, a1);
+          a2 = cmul(w2, a2);
+          a3 = cmul(w3, a3);
         }
-        const Cx<T> a0 = X[(j * Ls + k) * TC + c];
-        const Cx<T> a1 = cmul(w1, X[((j + r) * Ls + k) * TC + c]);
-        const Cx<T> a2 = cmul(w2, X[((j + 2 * r) * Ls + k) * TC + c]);
-        const Cx<T> a3 = cmul(w3, X[((j + 3 * r) * Ls + k) * TC + c]);
         const Cx<T> s02 = {a0.re + a2.re, a0.im + a2.im}, d02 = {a0.re - a2.re, a0.im - a2.im};
         const Cx<T> s13 = {a1.re + a3.re, a1.im + a3.im}, d13 = {a1.re - a3.re, a1.im - a3.im};
         // omega_4 d13: -i d13 forward, +i d13 inverse
