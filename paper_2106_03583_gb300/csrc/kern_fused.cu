@@ -470,7 +470,9 @@ __global__ void __launch_bounds__(FTHREADS, 2)
     Cells<T> C;
     take_cells(C, S, false, sg);
     // three-point prolongation onto the thread's owned cells: parent column lane + 1 of the coarse
-    // window (both columns of the pair), parent row (RPW / 2) warp + r / 2 + 1
+    // window (both columns of the pair), parent row (RPW / 2) warp + r / 2 + 1. Only the colour-1
+    // cells: the first post-smoothing half-sweep rewrites every updated colour-0 cell from its
+    // neighbours and f alone, and the window edge, never updated, is stale either way.
     const int rxc = tb.colrx[lane];
 #pragma unroll
     for (int r = 0; r < RPW; ++r) {
@@ -479,10 +481,11 @@ __global__ void __launch_bounds__(FTHREADS, 2)
       const int cj = (RPW / 2) * warp + r / 2 + 1;
       const int cjy = (r & 1) ? cj + 1 : cj - 1;
       const int ci = lane + 1;
+      const int p1 = (1 - tb.pbase - wj) & 1;  // column parity of this row's colour-1 cell
       const FP2<T> wy = tb.py[rxc][wj];
 #pragma unroll
       for (int p = 0; p < 2; ++p) {
-        if (C.inv[r][p] == (T)0) continue;  // unowned cell
+        if (p != p1 || C.inv[r][p] == (T)0) continue;  // colour 0, or unowned
         const FP2<T> wx = tb.px[ry][p][lane];
         const T eC = S.e[eb][cj][ci];
         const T eX = S.e[eb][cj][p ? ci + 1 : ci - 1];
