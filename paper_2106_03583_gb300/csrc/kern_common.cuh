@@ -59,6 +59,15 @@ __device__ __forceinline__ void nbr_cells(const BlockDev* __restrict__ blk, cons
   }
 }
 
+// Colour-split position of cell (i, j) of block B in a plane: within each row the cells of colour 0
+// ((i + j + par) even) come first in order of i, then those of colour 1 (block widths are even).
+// FP64 plans with scaled right-hand sides keep f / diag and 1/diag of their smoothed levels in this
+// order, so that a colour kernel reads whole 32-byte sectors of both; the iterate keeps the plain
+// order.
+__device__ __forceinline__ long long split_cell(const BlockDev& B, int i, int j) {
+  return B.off + (long long)j * B.nx + (((i + j + B.par) & 1) ? (B.nx >> 1) : 0) + (i >> 1);
+}
+
 // Plane index (within one mode plane of a level) of the four neighbours of (i, j) in block b.
 __device__ __forceinline__ void nbr_plane(const BlockDev* __restrict__ blk, const BlockDev& B, int b, int i, int j,
                                           long long& w, long long& e, long long& s, long long& n) {

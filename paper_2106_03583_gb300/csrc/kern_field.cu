@@ -148,9 +148,9 @@ __global__ void __launch_bounds__(TILE_THREADS) k_prepass(LevelView<double> L, c
 }
 
 // Deterministic sum of npart x 4 partials into out[4] (one CTA, fixed order).
-// With `flag`, also out_flag = (double)*flag (read after the kernels that set it).
+// With `flag`, also out_flag = (double)*flag (read after the kernels that set it), and *flag = 0.
 __global__ void __launch_bounds__(1024) k_reduce4(const double* __restrict__ part, int npart, double* __restrict__ out,
-                                                  const int* __restrict__ flag, double* __restrict__ out_flag) {
+                                                  int* __restrict__ flag, double* __restrict__ out_flag) {
   __shared__ double sh[4 * 32];
   double acc[4] = {0, 0, 0, 0};
   for (int i = threadIdx.x; i < npart; i += blockDim.x) {
@@ -160,8 +160,22 @@ __global__ void __launch_bounds__(1024) k_reduce4(const double* __restrict__ par
   block_sum<4>(acc, sh);
   if (threadIdx.x == 0) {
     for (int k = 0; k < 4; ++k) out[k] = acc[k];
-    if (flag) *out_flag = (double)*flag;
+    if (flag) {
+      *out_flag = (double)*flag;
+      *flag = 0;  // ready for the next pre-pass
+    }
   }
+}
+
+// Control data between device memory and mapped pinned host memory (one CTA; n is small).
+__global__ void __launch_bounds__(256) k_copy_d(const double* __restrict__ src, double* __restrict__ dst, int n) {
+  for (int i = threadIdx.x; i < n; i += blockDim.x) dst[i] = src[i];
+}
+__global__ void __launch_bounds__(256) k_copy_i(const int* __restrict__ src, int* __restrict__ dst, int n) {
+  for (int i = threadIdx.x; i < n; i += blockDim.x) dst[i] = src[i];
+}
+__global__ void __launch_bounds__(256) k_fill_d(double* __restrict__ dst, int n, double v) {
+  for (int i = threadIdx.x; i < n; i += blockDim.x) dst[i] = v;
 }
 
 // The singular mode-0 correction is shifted by a constant so that the updated p has zero
@@ -245,10 +259,9 @@ cudaError_t launch_prepass(snac_plan* P, const double* f, const double* p, cudaS
   LevelView<double> L = level_view<double>(P->lev[0]);
   const dim3 grid = field_grid(P);
   const double n3 = (double)P->n3;
-  cudaError_t e = cudaMemsetAsync(P->d_flag, 0, sizeof(int), s);
-  if (e != cudaSuccess) return e;
+  cudaError_t e;
   {
-    // read f and p
+    // read f and p (the flag is zero: set at plan creation, reset by the reduction that reads it)
     LaunchScope ls(P, K_FIELD3D, 16.0 * n3, (P->singular ? 7.0 : 2.0) * n3, s);
     if (P->singular)
       k_prepass<true><<<grid, TILE_THREADS, 0, s>>>(L, P->d_cblk, P->nz, P->dz, f, p, P->d_partial, P->d_flag);
@@ -265,6 +278,24 @@ cudaError_t launch_prepass(snac_plan* P, const double* f, const double* p, cudaS
 cudaError_t launch_reduce_partials(snac_plan* P, int npart, double* out, cudaStream_t s) {
   LaunchScope ls(P, K_REDUCE, 32.0 * npart, 4.0 * npart, s);
   k_reduce4<<<1, 1024, 0, s>>>(P->d_partial, npart, out, nullptr, nullptr);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_to_host(const double* d_src, double* dh_dst, int n, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  k_copy_d<<<1, 256, 0, s>>>(d_src, dh_dst, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_from_host(const int* dh_src, int* d_dst, int n, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  k_copy_i<<<1, 256, 0, s>>>(dh_src, d_dst, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fill(double* d, int n, double v, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  k_fill_d<<<1, 256, 0, s>>>(d, n, v);
   return cudaGetLastError();
 }
 

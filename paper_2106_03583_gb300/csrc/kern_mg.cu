@@ -26,7 +26,8 @@ __device__ __forceinline__ T apply_row(const Coef<T>& cx, const Coef<T>& cy, T d
 // colour, so every lane of every warp works. FP64 plans read the precomputed inverse diagonal (the
 // FP64 pipe is the bound there); FP32 plans form it on the fly.
 // SCALED: the level holds g = f / diag instead of f (FP64 plans without fused levels), and the
-// update is u_c = g_c - (sum_nbr a u_nbr) / diag_c, one FP64 operation fewer per cell.
+// update is u_c = g_c - (sum_nbr a u_nbr) / diag_c, one FP64 operation fewer per cell; g and 1/diag
+// are in colour-split order (split_cell), so the colour's values are contiguous.
 constexpr int COLOUR_THREADS = 128;
 
 template <typename T, bool PRE_INV, bool SCALED>
@@ -43,10 +44,11 @@ __global__ void __launch_bounds__(COLOUR_THREADS) k_smooth(LevelView<T> L, const
   long long w, e, s, n;
   nbr_plane(L.blk, B, t.b, i, j, w, e, s, n);
   const long long c = B.off + (long long)j * B.nx + i;
+  const long long cg = SCALED ? split_cell(B, i, j) : c;  // position of the cell's f and 1/diag
   const Coef<T> cx = L.cx[B.xo + i], cy = L.cy[B.yo + j];
   T id;
   if constexpr (PRE_INV) {
-    id = invd[base + c];
+    id = invd[base + cg];
   } else {
     id = recip(cx.d + cy.d + sigma[q]);
   }
@@ -54,7 +56,7 @@ __global__ void __launch_bounds__(COLOUR_THREADS) k_smooth(LevelView<T> L, const
   a = fma(cx.hi, u[base + e], a);
   a = fma(cy.lo, u[base + s], a);
   a = fma(cy.hi, u[base + n], a);
-  if constexpr (SCALED) u[base + c] = fma(-a, id, f[base + c]);
+  if constexpr (SCALED) u[base + c] = fma(-a, id, f[base + cg]);
   else u[base + c] = (f[base + c] - a) * id;
 }
 
@@ -75,24 +77,36 @@ __device__ __forceinline__ T cell_residual(const Coef<T>& cx, const Coef<T>& cy,
 }
 
 __global__ void __launch_bounds__(TILE_THREADS) k_invd(LevelView<double> L, const double* __restrict__ sigma,
-                                                        double* __restrict__ invd) {
+                                                        double* __restrict__ invd, int split) {
   const TileDev t = L.tiles[blockIdx.x];
   const BlockDev B = L.blk[t.b];
   const int i = t.x0 + (threadIdx.x % TILE_X), j = t.y0 + (threadIdx.x / TILE_X);
   if (i >= B.nx || j >= B.ny) return;
   const int q = blockIdx.y;
-  const long long c = B.off + (long long)j * B.nx + i;
+  const long long c = split ? split_cell(B, i, j) : B.off + (long long)j * B.nx + i;
   invd[(long long)q * L.ncell + c] = 1.0 / (L.cx[B.xo + i].d + L.cy[B.yo + j].d + sigma[q]);
+}
+
+// Plain -> colour-split order of every mode plane of a level (the scaled FP64 levels' f).
+__global__ void __launch_bounds__(TILE_THREADS) k_to_split(LevelView<double> L, const double* __restrict__ src,
+                                                            double* __restrict__ dst) {
+  const TileDev t = L.tiles[blockIdx.x];
+  const BlockDev B = L.blk[t.b];
+  const int i = t.x0 + (threadIdx.x % TILE_X), j = t.y0 + (threadIdx.x / TILE_X);
+  if (i >= B.nx || j >= B.ny) return;
+  const long long base = (long long)blockIdx.y * L.ncell;
+  dst[base + split_cell(B, i, j)] = src[base + B.off + (long long)j * B.nx + i];
 }
 
 // Coarse right-hand side = area-weighted average of the fine residual over the four children;
 // the coarse iterate starts at zero.
 // After a red-black sweep ending on black, every black cell has zero residual (its update solved its
 // own row), so with RED_ONLY only the two red children of each coarse cell are evaluated.
-// SCALED: the fine level holds f / diag. With invd_c the coarse level does too (its right-hand side
-// is written times its inverse diagonal), and with first_red the coarse level's first colour-0
-// half-sweep is done here: from a zero iterate it sets each colour-0 cell to f / diag, which is the
-// value written, and the coarse smoothing starts with colour 1.
+// SCALED: the fine level holds f / diag (colour-split order). With invd_c the coarse level does too
+// (its right-hand side is written times its inverse diagonal, both in colour-split order), and with
+// first_red the coarse level's first colour-0 half-sweep is done here: from a zero iterate it sets
+// each colour-0 cell to f / diag, which is the value written, and the coarse smoothing starts with
+// colour 1.
 template <typename T, bool RED_ONLY, bool SCALED>
 __global__ void __launch_bounds__(TILE_THREADS) k_restrict(LevelView<T> F, LevelView<T> C, const int* __restrict__ active,
                                                             const T* __restrict__ sigma, const T* __restrict__ uf,
@@ -119,14 +133,21 @@ __global__ void __launch_bounds__(TILE_THREADS) k_restrict(LevelView<T> F, Level
       const long long c = Bf.off + (long long)j * Bf.nx + i;
       const Coef<T> cx = F.cx[Bf.xo + i], cy = F.cy[Bf.yo + j];
       const T diag = cx.d + cy.d + sg;
-      const T r = cell_residual<T, SCALED>(cx, cy, diag, ff[bf + c], uf[bf + c], uf[bf + w], uf[bf + e], uf[bf + s],
+      const long long cf = SCALED ? split_cell(Bf, i, j) : c;
+      const T r = cell_residual<T, SCALED>(cx, cy, diag, ff[bf + cf], uf[bf + c], uf[bf + w], uf[bf + e], uf[bf + s],
                                            uf[bf + n]);
       acc = fma(F.rx[Bf.xo + i] * F.ry[Bf.yo + j], r, acc);
     }
   }
-  const long long cc = (long long)q * C.ncell + Bc.off + (long long)J * Bc.nx + I;
-  if (invd_c != nullptr) acc *= (T)invd_c[cc];
-  fc[cc] = acc;
+  const long long cb = (long long)q * C.ncell;
+  const long long cc = cb + Bc.off + (long long)J * Bc.nx + I;
+  if (invd_c != nullptr) {
+    const long long cs = cb + split_cell(Bc, I, J);
+    acc *= (T)invd_c[cs];
+    fc[cs] = acc;
+  } else {
+    fc[cc] = acc;
+  }
   uc[cc] = (first_red && ((Bc.par + I + J) & 1) == 0) ? acc : (T)0;
 }
 
@@ -242,8 +263,8 @@ __global__ void __launch_bounds__(TILE_THREADS) k_mode_resid2(LevelView<T> L, co
     const long long c = B.off + (long long)j * B.nx + i;
     const Coef<T> cx = L.cx[B.xo + i], cy = L.cy[B.yo + j];
     const T diag = cx.d + cy.d + sigma[q];
-    const T r = cell_residual<T, SCALED>(cx, cy, diag, f[base + c], u[base + c], u[base + w], u[base + e], u[base + s],
-                                         u[base + n]);
+    const T r = cell_residual<T, SCALED>(cx, cy, diag, f[base + (SCALED ? split_cell(B, i, j) : c)], u[base + c],
+                                         u[base + w], u[base + e], u[base + s], u[base + n]);
     r2 = r * r;
   }
   r2 = warp_sum_t(r2);
@@ -258,19 +279,22 @@ __global__ void __launch_bounds__(TILE_THREADS) k_mode_resid2(LevelView<T> L, co
 }
 
 // Per-tile partial sums of f^2 (the residual of a zero iterate) for every listed mode: a plain
-// streaming pass over the plane, one partial per CTA-row of MODE_SQ_CTAS CTAs.
+// streaming pass over the plane, one partial per CTA-row of MODE_SQ_CTAS CTAs. With u, the listed
+// modes' iterate is set to zero in the same pass.
 constexpr int MODE_SQ_CTAS = 64;
 
 template <typename T>
 __global__ void __launch_bounds__(256) k_mode_sumsq(const T* __restrict__ f, long long ncell, const int* __restrict__ active,
-                                                    double* __restrict__ part) {
+                                                    double* __restrict__ part, T* __restrict__ u) {
   __shared__ double sh[32];
   const int q = active[blockIdx.y];
   const T* fq = f + (long long)q * ncell;
+  T* uq = u ? u + (long long)q * ncell : nullptr;
   T s = 0;
   for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < ncell; c += (long long)gridDim.x * blockDim.x) {
     const T v = fq[c];
     s = fma(v, v, s);
+    if (uq) uq[c] = 0;
   }
   s = warp_sum_t(s);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -287,16 +311,18 @@ __global__ void __launch_bounds__(256) k_mode_sumsq(const T* __restrict__ f, lon
 // the level's inverse diagonal (the form the SCALED kernels read).
 __global__ void __launch_bounds__(256) k_mode_sumsq_scale(double* __restrict__ f, const double* __restrict__ invd,
                                                           long long ncell, const int* __restrict__ active,
-                                                          double* __restrict__ part) {
+                                                          double* __restrict__ part, double* __restrict__ u) {
   __shared__ double sh[32];
   const int q = active[blockIdx.y];
   double* fq = f + (long long)q * ncell;
   const double* iq = invd + (long long)q * ncell;
+  double* uq = u ? u + (long long)q * ncell : nullptr;
   double s = 0;
   for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < ncell; c += (long long)gridDim.x * blockDim.x) {
     const double v = fq[c];
     s = fma(v, v, s);
     fq[c] = v * iq[c];
+    if (uq) uq[c] = 0.0;
   }
   s = warp_sum(s);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -432,17 +458,18 @@ cudaError_t vcycle_t(snac_plan* P, int nact, cudaStream_t st) {
 }
 
 template <typename T>
-cudaError_t mode_norms_t(snac_plan* P, int nact, bool after_cycle, cudaStream_t st, const int* list) {
+cudaError_t mode_norms_t(snac_plan* P, int nact, bool after_cycle, cudaStream_t st, const int* list, bool zero_u) {
   const HostLevel& h = P->lev[0];
   const bool scaled = sizeof(T) == 8 && P->scaled_f;
   if (!after_cycle) {  // zero iterate: the residual is the right-hand side itself
     if (scaled) {  // ... which is then scaled into the form the smoothed levels hold
-      LaunchScope ls(P, K_MODE_RESID, 3.0 * sizeof(T) * h.ncell * nact, 3.0 * h.ncell * nact, st);
+      LaunchScope ls(P, K_MODE_RESID, (zero_u ? 4.0 : 3.0) * sizeof(T) * h.ncell * nact, 3.0 * h.ncell * nact, st);
       k_mode_sumsq_scale<<<dim3(MODE_SQ_CTAS, nact), 256, 0, st>>>((double*)h.d_f, h.d_invd, h.ncell, list,
-                                                                   P->d_mode_part);
+                                                                   P->d_mode_part, zero_u ? (double*)h.d_u : nullptr);
     } else {
-      LaunchScope ls(P, K_MODE_RESID, (double)sizeof(T) * h.ncell * nact, 2.0 * h.ncell * nact, st);
-      k_mode_sumsq<T><<<dim3(MODE_SQ_CTAS, nact), 256, 0, st>>>((const T*)h.d_f, h.ncell, list, P->d_mode_part);
+      LaunchScope ls(P, K_MODE_RESID, (zero_u ? 2.0 : 1.0) * sizeof(T) * h.ncell * nact, 2.0 * h.ncell * nact, st);
+      k_mode_sumsq<T><<<dim3(MODE_SQ_CTAS, nact), 256, 0, st>>>((const T*)h.d_f, h.ncell, list, P->d_mode_part,
+                                                                zero_u ? (T*)h.d_u : nullptr);
     }
     LaunchScope ls(P, K_MODE_REDUCE, 8.0 * MODE_SQ_CTAS * nact, (double)MODE_SQ_CTAS * nact, st);
     k_mode_reduce<<<nact, 256, 0, st>>>(P->d_mode_part, MODE_SQ_CTAS, list, P->d_mode_norm2);
@@ -495,8 +522,15 @@ cudaError_t launch_inverse_diagonals(snac_plan* P, cudaStream_t s) {
   for (size_t l = 0; l + 1 < P->lev.size(); ++l) {
     const HostLevel& h = P->lev[l];
     dim3 g((unsigned)h.tiles.size(), (unsigned)P->nz);
-    k_invd<<<g, TILE_THREADS, 0, s>>>(level_view<double>(h), P->d_sigma64, h.d_invd);
+    k_invd<<<g, TILE_THREADS, 0, s>>>(level_view<double>(h), P->d_sigma64, h.d_invd, P->scaled_f ? 1 : 0);
   }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_to_split(snac_plan* P, const double* src, double* dst, cudaStream_t s) {
+  const HostLevel& h = P->lev[0];
+  dim3 g((unsigned)h.tiles.size(), (unsigned)P->nz);
+  k_to_split<<<g, TILE_THREADS, 0, s>>>(level_view<double>(h), src, dst);
   return cudaGetLastError();
 }
 
@@ -505,11 +539,12 @@ cudaError_t launch_vcycle(snac_plan* P, int nact, cudaStream_t s) {
   return P->precision == SNAC_FP64 ? vcycle_t<double>(P, nact, s) : vcycle_t<float>(P, nact, s);
 }
 
-cudaError_t launch_mode_norms(snac_plan* P, int nact, bool after_cycle, cudaStream_t s, const int* d_list) {
+cudaError_t launch_mode_norms(snac_plan* P, int nact, bool after_cycle, cudaStream_t s, const int* d_list,
+                              bool zero_u) {
   if (nact <= 0) return cudaSuccess;
   const int* list = d_list ? d_list : P->d_active;
-  return P->precision == SNAC_FP64 ? mode_norms_t<double>(P, nact, after_cycle, s, list)
-                                   : mode_norms_t<float>(P, nact, after_cycle, s, list);
+  return P->precision == SNAC_FP64 ? mode_norms_t<double>(P, nact, after_cycle, s, list, zero_u && !after_cycle)
+                                   : mode_norms_t<float>(P, nact, after_cycle, s, list, zero_u && !after_cycle);
 }
 
 // Requires d_active = 0..n_z-1.

@@ -168,17 +168,22 @@ template <typename T, int TC, int KIND>
 __global__ void __launch_bounds__(256) k_forward(const ChunkDev* __restrict__ chunks, const BlockDev* __restrict__ blk,
                                                  const CallerBlk* __restrict__ cb, int n, Tw<T> tw,
                                                  const double* __restrict__ in3, T* __restrict__ out, long long ncell,
-                                                 T sub0) {
+                                                 T sub0, int split) {
   constexpr int kind = KIND;
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ long long coff[TC];
+  __shared__ long long ooff[TC];  // position of each column in a mode plane (plain or colour-split)
   const int m = n / 2;
   Cx<T>* A = reinterpret_cast<Cx<T>*>(smem);
   Cx<T>* Bf = A + m * TC;
   T* xs = reinterpret_cast<T*>(Bf);  // n x TC reals, aliases Bf
   const ChunkDev ch = chunks[blockIdx.x];
   const BlockDev B = blk[ch.b];
-  const long long sk = chunk_columns<TC>(ch, B, cb, coff);
+  if (threadIdx.x < TC) {
+    const int pc = ch.c0 + threadIdx.x;
+    ooff[threadIdx.x] = split ? split_cell(B, pc % B.nx, pc / B.nx) : B.off + pc;
+  }
+  const long long sk = chunk_columns<TC>(ch, B, cb, coff);  // (its barrier also covers ooff)
   // sk == 1: the homogeneous axis is the caller's contiguous one, consecutive threads run along it
   const bool along = sk == 1;
   for (int i0 = threadIdx.x; i0 < n * TC; i0 += LBATCH * blockDim.x) {
@@ -219,7 +224,7 @@ __global__ void __launch_bounds__(256) k_forward(const ChunkDev* __restrict__ ch
   // F(x - shift0) = F(x) - shift0 F(1); F(1) is zero outside mode 0
   auto put = [&](int q, int c, T y) {
     if (q == 0) y -= sub0;
-    if (c < ch.ncol) out[(long long)q * ncell + B.off + ch.c0 + c] = y;
+    if (c < ch.ncol) out[(long long)q * ncell + ooff[c]] = y;
   };
   if (kind == KIND_PP || kind == KIND_NN || kind == KIND_DD) {
     // each half-spectrum bin k = 0..m once; it gives output k and its mirror n - k
@@ -375,7 +380,7 @@ Tw<T> make_tw(const snac_plan* P, const void* base) {
 
 template <typename T, int TC>
 cudaError_t fwd_t(snac_plan* P, const std::vector<ChunkDev>& ch, const ChunkDev* dch, const void* twb, const double* in3,
-                  void* modes, double shift0, cudaStream_t s) {
+                  void* modes, double shift0, bool split, cudaStream_t s) {
   // F(1) in mode 0: n for the real DFT (half-complex), 2n for the DCT-II; the other kinds have no
   // zero eigenvalue and are never shifted
   const double f1 = P->kind == KIND_PP ? (double)P->nz : 2.0 * P->nz;
@@ -387,7 +392,7 @@ cudaError_t fwd_t(snac_plan* P, const std::vector<ChunkDev>& ch, const ChunkDev*
   auto go = [&](auto kern) {
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem<T, TC>);
     kern<<<(unsigned)ch.size(), 256, smem, s>>>(dch, P->lev[0].d_blk, P->d_cblk, P->nz, make_tw<T>(P, twb), in3,
-                                                (T*)modes, P->lev[0].ncell, sub0);
+                                                (T*)modes, P->lev[0].ncell, sub0, split ? 1 : 0);
   };
   switch (P->kind) {
     case KIND_PP: go(k_forward<T, TC, KIND_PP>); break;
@@ -423,11 +428,12 @@ cudaError_t bwd_t(snac_plan* P, const std::vector<ChunkDev>& ch, const ChunkDev*
 
 }  // namespace
 
-cudaError_t launch_forward(snac_plan* P, const double* in3, void* modes, double shift0, cudaStream_t s) {
+cudaError_t launch_forward(snac_plan* P, const double* in3, void* modes, double shift0, bool split, cudaStream_t s) {
   if (shift0 != 0.0 && P->kind != KIND_PP && P->kind != KIND_NN) return cudaErrorInvalidValue;
+  if (split && P->precision != SNAC_FP64) return cudaErrorInvalidValue;
   if (P->precision == SNAC_FP64)
-    return fwd_t<double, 8>(P, P->chunks64, P->d_chunks64, P->d_tw64, in3, modes, shift0, s);
-  return fwd_t<float, 16>(P, P->chunks32, P->d_chunks32, P->d_tw32, in3, modes, shift0, s);
+    return fwd_t<double, 8>(P, P->chunks64, P->d_chunks64, P->d_tw64, in3, modes, shift0, split, s);
+  return fwd_t<float, 16>(P, P->chunks32, P->d_chunks32, P->d_tw32, in3, modes, shift0, false, s);
 }
 
 cudaError_t launch_backward_update(snac_plan* P, const void* modes, double* p3, cudaStream_t s) {

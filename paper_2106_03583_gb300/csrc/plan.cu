@@ -787,12 +787,26 @@ int create(snac_plan** out, int32_t nblocks, const snac_block* blocks_in, int32_
     if ((st = dmalloc(P, &P->d_mode_part, (size_t)P->nz * std::max<size_t>(P->lev[0].tiles.size(), 64)))) break;
     if ((st = dmalloc(P, &P->d_mode_norm2, (size_t)P->nz))) break;
     if ((st = dmalloc(P, &P->d_active, (size_t)P->nz)) || (st = dmalloc(P, &P->d_check, (size_t)P->nz))) break;
-    if (cudaMallocHost(&P->h_sums, SUM_SLOTS * sizeof(double)) != cudaSuccess ||
-        cudaMallocHost(&P->h_mode_norm2, P->nz * sizeof(double)) != cudaSuccess ||
-        cudaMallocHost(&P->h_active, P->nz * sizeof(int)) != cudaSuccess ||
-        cudaMallocHost(&P->h_check, P->nz * sizeof(int)) != cudaSuccess) {
+    auto mapped = [](auto** h, auto** dh, size_t n) {
+      return cudaHostAlloc((void**)h, n * sizeof(**h), cudaHostAllocMapped) == cudaSuccess &&
+             cudaHostGetDevicePointer((void**)dh, (void*)*h, 0) == cudaSuccess;
+    };
+    if (!mapped(&P->h_sums, &P->dh_sums, SUM_SLOTS) || !mapped(&P->h_mode_norm2, &P->dh_mode_norm2, P->nz) ||
+        !mapped(&P->h_active, &P->dh_active, P->nz) || !mapped(&P->h_check, &P->dh_check, P->nz)) {
       st = fail(SNAC_ERR_OOM, "pinned host allocation");
       break;
+    }
+    {
+      // the pre-pass flag starts at zero (its reduction resets it after each use); on a private
+      // non-blocking stream, like every other device write of plan creation
+      cudaStream_t cs = nullptr;
+      bool ok = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) == cudaSuccess &&
+                cudaMemsetAsync(P->d_flag, 0, sizeof(int), cs) == cudaSuccess && cudaStreamSynchronize(cs) == cudaSuccess;
+      if (cs) cudaStreamDestroy(cs);
+      if (!ok) {
+        st = fail(SNAC_ERR_CUDA, "initialising the pre-pass flag failed");
+        break;
+      }
     }
   } while (0);
   if (st) {

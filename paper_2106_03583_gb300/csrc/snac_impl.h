@@ -201,11 +201,18 @@ struct snac_plan {
   double* d_mode_part = nullptr;  // per-mode, per-tile partial sums of squares
   double* d_mode_norm2 = nullptr; // per-mode ||r_q||^2
   int* d_active = nullptr;
-  double* h_sums = nullptr;       // pinned
-  double* h_mode_norm2 = nullptr; // pinned
-  int* h_active = nullptr;        // pinned
+  // pinned host buffers of the solve's control data, mapped into the device address space (dh_*):
+  // kernels move them, so a solve issues no copy-engine work and never queues behind another
+  // stream's bulk host copies
+  double* h_sums = nullptr;
+  double* h_mode_norm2 = nullptr;
+  int* h_active = nullptr;
+  double* dh_sums = nullptr;
+  double* dh_mode_norm2 = nullptr;
+  int* dh_active = nullptr;
   int* d_check = nullptr;         // modes whose residual norm is due after a round (predictive checks)
-  int* h_check = nullptr;         // pinned
+  int* h_check = nullptr;
+  int* dh_check = nullptr;
   std::vector<void*> allocs;
   size_t bytes = 0;
   // results
@@ -246,7 +253,10 @@ cudaError_t launch_shift(snac_plan* P, double* p, const double* d_c, cudaStream_
 
 // ---- transforms ----
 // modes = F(in3 - shift0) along z (shift0 != 0 only for the kinds with a zero eigenvalue)
-cudaError_t launch_forward(snac_plan* P, const double* in3, void* modes, double shift0, cudaStream_t s);
+// split: write the modes in colour-split order (the plan's own level-0 f of a scaled FP64 plan).
+cudaError_t launch_forward(snac_plan* P, const double* in3, void* modes, double shift0, bool split, cudaStream_t s);
+// Level-0 mode planes from plain to colour-split order.
+cudaError_t launch_to_split(snac_plan* P, const double* src, double* dst, cudaStream_t s);
 cudaError_t launch_backward_update(snac_plan* P, const void* modes, double* p3, cudaStream_t s);
 
 // ---- multigrid ----
@@ -258,7 +268,13 @@ cudaError_t launch_vcycle(snac_plan* P, int nactive, cudaStream_t s);
 // per-mode ||f - A u||^2 at level 0 for the active modes -> d_mode_norm2[q]; after_cycle: u is the
 // result of a V-cycle (post-smoothing ended on black, so only red cells carry a residual); otherwise
 // u is zero and the norm is that of f
-cudaError_t launch_mode_norms(snac_plan* P, int nactive, bool after_cycle, cudaStream_t s, const int* d_list = nullptr);
+// zero_u (with !after_cycle): also set the listed modes' level-0 iterate to zero in the same pass.
+cudaError_t launch_mode_norms(snac_plan* P, int nactive, bool after_cycle, cudaStream_t s, const int* d_list = nullptr,
+                              bool zero_u = false);
+// Small transfers through mapped pinned memory, done by one-CTA kernels (no copy engine).
+cudaError_t launch_to_host(const double* d_src, double* dh_dst, int n, cudaStream_t s);
+cudaError_t launch_from_host(const int* dh_src, int* d_dst, int n, cudaStream_t s);
+cudaError_t launch_fill(double* d, int n, double v, cudaStream_t s);
 
 // fused FP32 levels: smoothing + residual + restriction (down), prolongation + smoothing (+ level-0
 // residual norm partials into d_mode_part) (up)

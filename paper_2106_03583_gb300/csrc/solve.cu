@@ -48,7 +48,7 @@ int check_plan(snac_plan* P) {
 
 int set_active_all(snac_plan* P, cudaStream_t s) {
   for (int q = 0; q < P->nz; ++q) P->h_active[q] = q;
-  CK(cudaMemcpyAsync(P->d_active, P->h_active, P->nz * sizeof(int), cudaMemcpyHostToDevice, s));
+  CK(launch_from_host(P->dh_active, P->d_active, P->nz, s));
   return SNAC_OK;
 }
 
@@ -102,11 +102,11 @@ cudaError_t run_round(snac_plan* P, int nact, bool norms, cudaStream_t s, int* r
 
 int mode_solves(snac_plan* P, double target, cudaStream_t s, int* cycles_out) {
   const int nz = P->nz;
-  CK(cudaMemsetAsync(P->lev[0].d_u, 0, (size_t)nz * P->lev[0].ncell * plan_inner_size(P), s));
   int st = set_active_all(P, s);
   if (st) return st;
-  CK(launch_mode_norms(P, nz, false, s));
-  CK(cudaMemcpyAsync(P->h_mode_norm2, P->d_mode_norm2, nz * sizeof(double), cudaMemcpyDeviceToHost, s));
+  // norms of the zero iterate (the right-hand side), which the same pass sets to zero
+  CK(launch_mode_norms(P, nz, false, s, nullptr, true));
+  CK(launch_to_host(P->d_mode_norm2, P->dh_mode_norm2, nz, s));
   CK(cudaStreamSynchronize(s));
     profile_resolve(P);
   std::vector<double> thr2(nz), prev(nz);  // prev: norm^2 at the mode's last check
@@ -131,7 +131,7 @@ int mode_solves(snac_plan* P, double target, cudaStream_t s, int* cycles_out) {
     const int nact = (int)list.size();
     if (list_changed) {  // the previous upload has completed: every list change follows a synchronisation
       std::copy(list.begin(), list.end(), P->h_active);
-      CK(cudaMemcpyAsync(P->d_active, P->h_active, nact * sizeof(int), cudaMemcpyHostToDevice, s));
+      CK(launch_from_host(P->dh_active, P->d_active, nact, s));
       list_changed = false;
     }
     CK(run_round(P, nact, !predictive, s, &P->info.graph_rounds));
@@ -144,10 +144,10 @@ int mode_solves(snac_plan* P, double target, cudaStream_t s, int* cycles_out) {
     }
     if (ncheck == 0) continue;
     if (predictive) {
-      CK(cudaMemcpyAsync(P->d_check, P->h_check, ncheck * sizeof(int), cudaMemcpyHostToDevice, s));
+      CK(launch_from_host(P->dh_check, P->d_check, ncheck, s));
       CK(launch_mode_norms(P, ncheck, true, s, P->d_check));
     }
-    CK(cudaMemcpyAsync(P->h_mode_norm2, P->d_mode_norm2, nz * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(launch_to_host(P->d_mode_norm2, P->dh_mode_norm2, nz, s));
     CK(cudaStreamSynchronize(s));
     profile_resolve(P);
     std::vector<int> next;
@@ -177,7 +177,7 @@ int mode_solves(snac_plan* P, double target, cudaStream_t s, int* cycles_out) {
 }
 
 int read_sums(snac_plan* P, cudaStream_t s, int n = 4) {
-  CK(cudaMemcpyAsync(P->h_sums, P->d_sums, n * sizeof(double), cudaMemcpyDeviceToHost, s));
+  CK(launch_to_host(P->d_sums, P->dh_sums, n, s));
   CK(cudaStreamSynchronize(s));
     profile_resolve(P);
   return SNAC_OK;
@@ -218,7 +218,7 @@ int run_solve(snac_plan* P, const double* f, double* p, double tol, cudaStream_t
     double rn;
     if (from_f) {
       fn = rn = fn_pre;
-      if (P->singular) CK(cudaMemsetAsync(P->d_sums + 2, 0, sizeof(double), s));  // sum V p = 0
+      if (P->singular) CK(launch_fill(P->d_sums + 2, 1, 0.0, s));  // sum V p = 0
     } else {
       // ||f|| is needed once; sum V p only for singular problems (zero-mean update). In FP64 plans
       // only for the caller's initial guess: an update leaves sum V p = 0 to rounding (the mean fix
@@ -257,8 +257,8 @@ int run_solve(snac_plan* P, const double* f, double* p, double tol, cudaStream_t
     // target of this defect-correction step
     double target = 0.5 * tol * fn;
     if (mixed) target = std::max(target, P->inner_reduction * rn);
-    if (from_f) CK(launch_forward(P, f, P->lev[0].d_f, fshift, s));
-    else CK(launch_forward(P, P->d_r3, P->lev[0].d_f, 0.0, s));
+    if (from_f) CK(launch_forward(P, f, P->lev[0].d_f, fshift, P->scaled_f, s));
+    else CK(launch_forward(P, P->d_r3, P->lev[0].d_f, 0.0, P->scaled_f, s));
     if ((st = mode_solves(P, target, s, cyc.data()))) return st;
     for (int q = 0; q < P->nz; ++q) {
       P->mode_cycles[q] = cyc[q];
@@ -311,7 +311,7 @@ int snac_forward_transform(snac_plan* plan, const double* d_in, void* d_modes, v
   if (st) return st;
   if (!d_in || !d_modes) return SNAC_ERR_INVALID_ARG;
   cudaStream_t s = (cudaStream_t)stream;
-  CK(launch_forward(plan, d_in, d_modes, 0.0, s));
+  CK(launch_forward(plan, d_in, d_modes, 0.0, false, s));
   CK(cudaStreamSynchronize(s));
   profile_resolve(plan);
   return SNAC_OK;
@@ -346,7 +346,8 @@ int snac_mode_vcycles(snac_plan* plan, const void* d_f, void* d_u, int32_t ncycl
   if (!d_f || !d_u || ncycles < 0) return SNAC_ERR_INVALID_ARG;
   cudaStream_t s = (cudaStream_t)stream;
   const size_t bytes = (size_t)plan->nz * plan->lev[0].ncell * plan_inner_size(plan);
-  CK(cudaMemcpyAsync(plan->lev[0].d_f, d_f, bytes, cudaMemcpyDeviceToDevice, s));
+  if (plan->scaled_f) CK(launch_to_split(plan, (const double*)d_f, (double*)plan->lev[0].d_f, s));
+  else CK(cudaMemcpyAsync(plan->lev[0].d_f, d_f, bytes, cudaMemcpyDeviceToDevice, s));
   CK(cudaMemcpyAsync(plan->lev[0].d_u, d_u, bytes, cudaMemcpyDeviceToDevice, s));
   if ((st = set_active_all(plan, s))) return st;
   // the zero-iterate norms put the right-hand side into the form the cycles read (scaled plans)
