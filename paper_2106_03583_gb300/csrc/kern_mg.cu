@@ -132,7 +132,7 @@ __global__ void __launch_bounds__(TILE_THREADS) k_restrict(LevelView<T> F, Level
       nbr_plane(F.blk, Bf, t.b, i, j, w, e, s, n);
       const long long c = Bf.off + (long long)j * Bf.nx + i;
       const Coef<T> cx = F.cx[Bf.xo + i], cy = F.cy[Bf.yo + j];
-      const T diag = cx.d + cy.d + sg;
+      const T diag = F.dxy[c] + sg;
       const long long cf = SCALED ? split_cell(Bf, i, j) : c;
       const T r = cell_residual<T, SCALED>(cx, cy, diag, ff[bf + cf], uf[bf + c], uf[bf + w], uf[bf + e], uf[bf + s],
                                            uf[bf + n]);
@@ -262,7 +262,7 @@ __global__ void __launch_bounds__(TILE_THREADS) k_mode_resid2(LevelView<T> L, co
     nbr_plane(L.blk, B, t.b, i, j, w, e, s, n);
     const long long c = B.off + (long long)j * B.nx + i;
     const Coef<T> cx = L.cx[B.xo + i], cy = L.cy[B.yo + j];
-    const T diag = cx.d + cy.d + sigma[q];
+    const T diag = L.dxy[c] + sigma[q];
     const T r = cell_residual<T, SCALED>(cx, cy, diag, f[base + (SCALED ? split_cell(B, i, j) : c)], u[base + c],
                                          u[base + w], u[base + e], u[base + s], u[base + n]);
     r2 = r * r;
@@ -389,7 +389,9 @@ cudaError_t vcycle_t(snac_plan* P, int nact, cudaStream_t st) {
         }
       }
   };
-  for (int l = 0; l < L; ++l) {
+  // levels from P->bottom on run as one sub-cycle launch (kern_bottom.cu); above it level by level
+  const int top = P->bottom > 0 ? P->bottom : L;
+  for (int l = 0; l < top; ++l) {
     const HostLevel& h = P->lev[l];
     const HostLevel& hc = P->lev[l + 1];
     if (h.fused) {
@@ -405,7 +407,7 @@ cudaError_t vcycle_t(snac_plan* P, int nact, cudaStream_t st) {
     smooth(l, P->nu1, scaled && l > 0 && P->nu1 > 0);
     dim3 g((unsigned)hc.tiles.size(), (unsigned)nact);
     const double cells = (double)h.ncell * nact;
-    const bool coarse_smoothed = l + 1 < L;
+    const bool coarse_smoothed = l + 1 < top;  // the sub-cycle's top level takes a plain f
     const double* invd_c = scaled && coarse_smoothed ? hc.d_invd : nullptr;
     const int first_red = scaled && coarse_smoothed && P->nu1 > 0 ? 1 : 0;
     LaunchScope ls(P, K_RESTRICT, (2.5 + (invd_c ? 0.25 : 0.0)) * w * cells, (P->nu1 > 0 ? 7.5 : 15.0) * cells, st);
@@ -423,13 +425,16 @@ cudaError_t vcycle_t(snac_plan* P, int nact, cudaStream_t st) {
       else restrict_k(k_restrict<T, false, false>);
     }
   }
-  {
+  if (top < L) {
+    cudaError_t e = launch_bottom(P, nact, st);
+    if (e != cudaSuccess) return e;
+  } else {
     const HostLevel& h = P->lev[L];
     LaunchScope ls(P, K_COARSE, 2.0 * w * P->nc * nact + 8.0 * P->nc * P->nc, 4.0 * P->nc * P->nc * nact, st);
     k_coarse<T><<<nact, 256, 0, st>>>(P->d_Q, P->d_lam, P->d_sqa, P->nc, act, P->d_sigma64, P->d_singular_mode,
                                       P->null_index, (const T*)h.d_f, (T*)h.d_u, h.ncell);
   }
-  for (int l = L - 1; l >= 0; --l) {
+  for (int l = top - 1; l >= 0; --l) {
     const HostLevel& h = P->lev[l];
     const HostLevel& hc = P->lev[l + 1];
     if (h.fused) {

@@ -14,6 +14,7 @@
 #include <new>
 
 #include "fused_tab.h"
+#include "kern_common.cuh"
 #include "snac_impl.h"
 
 using namespace snac;
@@ -460,6 +461,15 @@ int upload_level(snac_plan* P, HostLevel& lv, size_t inner) {
       (st = upload(P, &lv.d_cx64, lv.cx)) || (st = upload(P, &lv.d_cy64, lv.cy)) ||
       (st = upload(P, &lv.d_cx32, to32(lv.cx))) || (st = upload(P, &lv.d_cy32, to32(lv.cy))))
     return st;
+  {
+    // cx.d + cy.d per plane cell: the residual kernels add only the mode's shift (same rounding as
+    // forming the three-term sum in that order)
+    std::vector<double> dxy(lv.ncell);
+    for (const BlockDev& d : lv.blk)
+      for (int j = 0; j < d.ny; ++j)
+        for (int i = 0; i < d.nx; ++i) dxy[d.off + (long long)j * d.nx + i] = lv.cx[d.xo + i].d + lv.cy[d.yo + j].d;
+    if ((st = upload(P, &lv.d_dxy64, dxy)) || (st = upload(P, &lv.d_dxy32, to32(dxy)))) return st;
+  }
   if (!lv.px.empty()) {
     // the device copy of the x weights carries the parent's unit weight: self_x + 1, so that the
     // prolongation forms the parent's total weight (1 + self_x) + self_y with one addition
@@ -728,10 +738,24 @@ int create(snac_plan** out, int32_t nblocks, const snac_block* blocks_in, int32_
     for (int q = 0; q < P->nz; ++q) sm[q] = (P->singular && mode_lambda(P->kind, P->nz, q) == 0.0) ? 1 : 0;
     if ((st = upload(P, &P->d_singular_mode, sm))) break;
     if ((st = build_coarse(P))) break;
+    // the bottom of the cycle in one launch: from the first level below 0 whose planes, with all
+    // coarser ones, fit in one CTA's shared memory (at least one smoothed level above the coarsest)
+    {
+      const int L = (int)P->lev.size() - 1;
+      P->bottom = -1;
+      if (P->nu1 >= 1 && P->nu2 >= 1)
+        for (int l = std::max(1, L - BOTTOM_MAX_LEVELS + 1); l < L; ++l)
+          if (P->lev[l].ncell <= BOTTOM_MAX_CELLS && bottom_smem_bytes(P, l, inner) <= (size_t)BOTTOM_MAX_SMEM) {
+            P->bottom = l;
+            break;
+          }
+    }
     // fused FP32 tile kernels on the levels whose blocks all keep the halo inside their neighbours
+    // (above the bottom sub-cycle)
     const bool want_fused = P->fused == 1 || (P->fused < 0 && P->precision == SNAC_MIXED);
     if (want_fused && P->nu1 >= 1 && P->nu2 >= 1 && P->nu1 <= 2 && P->nu2 <= 2) {
       for (size_t l = 0; l + 1 < P->lev.size(); ++l) {
+        if (P->bottom >= 0 && (int)l >= P->bottom) break;
         HostLevel& lv = P->lev[l];
         bool ok = true;
         for (const BlockDev& d : lv.blk) ok = ok && d.nx >= FUSED_MIN_BLOCK && d.ny >= FUSED_MIN_BLOCK;
@@ -765,6 +789,27 @@ int create(snac_plan** out, int32_t nblocks, const snac_block* blocks_in, int32_
         st = fail(SNAC_ERR_CUDA, "computing the inverse diagonals failed");
         break;
       }
+    }
+    if (P->bottom > 0) {  // the bottom sub-cycle's level table (after the inverse diagonals exist)
+      const int L = (int)P->lev.size() - 1;
+      auto build_bottom = [&](auto tag) -> int {
+        using T = decltype(tag);
+        std::vector<BottomLevel<T>> tab;
+        size_t off = 0;
+        for (int l = P->bottom; l <= L; ++l) {
+          BottomLevel<T> b{};
+          b.L = level_view<T>(P->lev[l]);
+          b.invd = (sizeof(T) == 8 && l < L) ? P->lev[l].d_invd : nullptr;
+          b.soff = (int)off;
+          off += (size_t)P->lev[l].ncell * (l < L ? 3 : 2);
+          tab.push_back(b);
+        }
+        BottomLevel<T>* d = nullptr;
+        const int s2 = upload(P, &d, tab);
+        P->d_bottom = d;
+        return s2;
+      };
+      if ((st = P->precision == SNAC_FP64 ? build_bottom(double{}) : build_bottom(float{}))) break;
     }
     if ((st = build_twiddles(P))) break;
     if ((st = build_chunks(P, 8, P->chunks64, &P->d_chunks64))) break;

@@ -29,6 +29,12 @@ constexpr int TILE_Y = 8;
 constexpr int TILE_THREADS = TILE_X * TILE_Y;
 constexpr int MAX_NZ = 1024;
 constexpr int MAX_COARSE = 256;
+// The bottom of the V-cycle (kern_bottom.cu): levels from the first one (below level 0) whose
+// planes, with all coarser ones, fit in one CTA's shared memory, run in one launch per round.
+constexpr int BOTTOM_THREADS = 512;
+constexpr int BOTTOM_MAX_LEVELS = 8;
+constexpr int BOTTOM_MAX_CELLS = 8192;          // plane cells of the sub-cycle's top level
+constexpr int BOTTOM_MAX_SMEM = 200 * 1024;     // dynamic shared memory of one CTA
 constexpr int MEAN_CTAS = 2 * 152;  // CTAs (so partials) of the grid-stride plane reductions: fixed, for a fixed summation order
 constexpr int SUM_SLOTS = 16;     // d_sums / h_sums: [0..3] residual or pre-pass, [4..7] mean fix
 constexpr int SUM_NONZERO = 8;    // d_sums slot of the pre-pass's nonzero-guess flag  // CTAs of the grid-stride reductions over one mode plane
@@ -84,6 +90,16 @@ struct LevelView {
   long long ncell;
   int ntiles;
   int nblk;
+  const T* dxy;     // x-y part of the diagonal of every plane cell, cx.d + cy.d (plain order)
+};
+
+// One level of the bottom sub-cycle (kern_bottom.cu), in a device table built with the plan.
+template <typename T>
+struct BottomLevel {
+  LevelView<T> L;
+  const double* invd;  // FP64 smoothed levels: per-mode 1/diag (colour-split order if the plan is scaled)
+  int soff;            // element offset of the level's u, f [, 1/diag] in the kernel's shared memory
+  int pad;
 };
 
 // Host-side description of one level.
@@ -110,6 +126,8 @@ struct HostLevel {
   double* d_ry64 = nullptr;
   float* d_rx32 = nullptr;
   float* d_ry32 = nullptr;
+  double* d_dxy64 = nullptr;
+  float* d_dxy32 = nullptr;
   void* d_u = nullptr;  // mode-space iterate, n_z x ncell of the inner type
   void* d_f = nullptr;  // mode-space right-hand side
   double* d_invd = nullptr;  // FP64 plans, smoothed levels: 1 / (A_xy + sigma_q)_cc per mode and cell
@@ -131,7 +149,7 @@ struct TwiddleOffsets {
 // Kernel kinds counted by the tracing facility.
 enum KernelKind {
   K_FIELD3D = 0, K_REDUCE, K_FIX_MEAN, K_SHIFT, K_FORWARD, K_BACKWARD, K_SMOOTH, K_RESTRICT, K_PROLONG,
-  K_COARSE, K_MODE_RESID, K_MODE_REDUCE, K_MODE_APPLY, K_FDOWN, K_FUP, K_COUNT
+  K_COARSE, K_MODE_RESID, K_MODE_REDUCE, K_MODE_APPLY, K_FDOWN, K_FUP, K_BOTTOM, K_COUNT
 };
 
 struct KernelStat {
@@ -157,6 +175,8 @@ struct snac_plan {
   // FP64 plans without fused levels keep the right-hand side of every smoothed level (all but the
   // coarsest) divided by the diagonal, which saves one FP64 operation per smoothing update
   bool scaled_f = false;
+  int bottom = -1;  // first level of the one-launch bottom sub-cycle (kern_bottom.cu), -1: none
+  void* d_bottom = nullptr;  // its BottomLevel<inner type> table
   int nblk = 0;
   int nz = 0;
   double dz = 0.0;
@@ -271,6 +291,10 @@ cudaError_t launch_vcycle(snac_plan* P, int nactive, cudaStream_t s);
 // zero_u (with !after_cycle): also set the listed modes' level-0 iterate to zero in the same pass.
 cudaError_t launch_mode_norms(snac_plan* P, int nactive, bool after_cycle, cudaStream_t s, const int* d_list = nullptr,
                               bool zero_u = false);
+// The V-cycle from level P->bottom down to the coarsest and back, one CTA per active mode.
+cudaError_t launch_bottom(snac_plan* P, int nact, cudaStream_t s);
+// Dynamic shared memory of that kernel when it starts at level lb, for inner type width w.
+size_t bottom_smem_bytes(const snac_plan* P, int lb, size_t w);
 // Small transfers through mapped pinned memory, done by one-CTA kernels (no copy engine).
 cudaError_t launch_to_host(const double* d_src, double* dh_dst, int n, cudaStream_t s);
 cudaError_t launch_from_host(const int* dh_src, int* d_dst, int n, cudaStream_t s);

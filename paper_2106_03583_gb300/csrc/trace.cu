@@ -7,7 +7,8 @@ namespace snac {
 
 static const char* const kKernelNames[K_COUNT] = {
     "field3d", "reduce", "fix_mean", "shift", "forward_transform", "backward_update", "smooth",
-    "restrict", "prolong", "coarse_solve", "mode_resid", "mode_reduce", "mode_apply", "fused_down", "fused_up"};
+    "restrict", "prolong", "coarse_solve", "mode_resid", "mode_reduce", "mode_apply", "fused_down", "fused_up",
+    "bottom"};
 
 static cudaEvent_t take_event(snac_plan* P) {
   if (!P->event_pool.empty()) {
