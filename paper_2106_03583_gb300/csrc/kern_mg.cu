@@ -60,6 +60,68 @@ __global__ void __launch_bounds__(COLOUR_THREADS) k_smooth(LevelView<T> L, const
   else u[base + c] = (f[base + c] - a) * id;
 }
 
+// The first colour-0 half-sweep of the next V-cycle at level 0 of a scaled FP64 plan, which also
+// yields the residual norm of the state before it: after a cycle that ends on colour 1 only colour-0
+// cells carry a residual, and a colour-0 cell's residual d (g - u) - a uses the neighbour sum a that
+// its update forms anyway. Every active mode is updated; each CTA walks tiles blockIdx.x, + gridDim.x,
+// ... so that the norm's reduction is paid once per CTA, and writes one partial of r^2 for the modes
+// of the (ascending) check list.
+constexpr int CHECK_CTAS = 64;
+
+__global__ void __launch_bounds__(COLOUR_THREADS) k_smooth_check(LevelView<double> L, const int* __restrict__ active,
+                                                                  const double* __restrict__ sigma,
+                                                                  const double* __restrict__ invd, double* __restrict__ u,
+                                                                  const double* __restrict__ g,
+                                                                  const int* __restrict__ check, int ncheck,
+                                                                  double* __restrict__ part) {
+  __shared__ double sh[COLOUR_THREADS / 32];
+  __shared__ int is_checked;
+  const int q = active[blockIdx.y];
+  if (threadIdx.x == 0) {
+    int lo = 0, hi = ncheck;  // binary search of q in the ascending check list
+    while (lo < hi) {
+      const int mid = (lo + hi) >> 1;
+      if (check[mid] < q) lo = mid + 1;
+      else hi = mid;
+    }
+    is_checked = lo < ncheck && check[lo] == q;
+  }
+  const long long base = (long long)q * L.ncell;
+  const double sg = sigma[q];
+  double r2 = 0.0;
+  for (int tile = blockIdx.x; tile < L.ntiles; tile += gridDim.x) {
+    const TileDev t = L.tiles[tile];
+    const BlockDev B = L.blk[t.b];
+    const int j = t.y0 + (threadIdx.x >> 4);
+    const int i = t.x0 + 2 * (threadIdx.x & 15) + ((B.par ^ j) & 1);
+    if (i >= B.nx || j >= B.ny) continue;
+    long long w, e, s, n;
+    nbr_plane(L.blk, B, t.b, i, j, w, e, s, n);
+    const long long c = B.off + (long long)j * B.nx + i;
+    const long long cg = split_cell(B, i, j);
+    const Coef<double> cx = L.cx[B.xo + i], cy = L.cy[B.yo + j];
+    double a = cx.lo * u[base + w];
+    a = fma(cx.hi, u[base + e], a);
+    a = fma(cy.lo, u[base + s], a);
+    a = fma(cy.hi, u[base + n], a);
+    const double gv = g[base + cg], u0 = u[base + c];
+    u[base + c] = fma(-a, invd[base + cg], gv);
+    const double r = fma(L.dxy[c] + sg, gv - u0, -a);
+    r2 = fma(r, r, r2);
+  }
+  __syncthreads();
+  if (!is_checked) return;
+  r2 = warp_sum(r2);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) sh[warp] = r2;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double v = 0.0;
+    for (int k = 0; k < COLOUR_THREADS / 32; ++k) v += sh[k];
+    part[(long long)q * gridDim.x + blockIdx.x] = v;
+  }
+}
+
 // Residual of cell c with the off-diagonal sum a and the diagonal: f - (a + diag u) from f, or
 // diag (g - u) - a from the scaled right-hand side g = f / diag (the same number of operations).
 template <typename T, bool SCALED>
@@ -360,7 +422,7 @@ template <>
 const float* sigma_ptr<float>(const snac_plan* P) { return P->d_sigma32; }
 
 template <typename T>
-cudaError_t vcycle_t(snac_plan* P, int nact, cudaStream_t st) {
+cudaError_t vcycle_t(snac_plan* P, int nact, cudaStream_t st, bool skip_first0) {
   const int L = (int)P->lev.size() - 1;
   const T* sg = sigma_ptr<T>(P);
   const int* act = P->d_active;
@@ -403,8 +465,8 @@ cudaError_t vcycle_t(snac_plan* P, int nact, cudaStream_t st) {
       continue;
     }
     // a level below 0 starts from zero: with scaled right-hand sides its first colour-0 half-sweep
-    // is folded into the restriction that fills it
-    smooth(l, P->nu1, scaled && l > 0 && P->nu1 > 0);
+    // is folded into the restriction that fills it; at level 0 the norm check may have done it
+    smooth(l, P->nu1, (scaled && l > 0 && P->nu1 > 0) || (l == 0 && skip_first0));
     dim3 g((unsigned)hc.tiles.size(), (unsigned)nact);
     const double cells = (double)h.ncell * nact;
     const bool coarse_smoothed = l + 1 < top;  // the sub-cycle's top level takes a plain f
@@ -539,9 +601,29 @@ cudaError_t launch_to_split(snac_plan* P, const double* src, double* dst, cudaSt
   return cudaGetLastError();
 }
 
-cudaError_t launch_vcycle(snac_plan* P, int nact, cudaStream_t s) {
+cudaError_t launch_vcycle(snac_plan* P, int nact, cudaStream_t s, bool skip_first0) {
   if (nact <= 0) return cudaSuccess;
-  return P->precision == SNAC_FP64 ? vcycle_t<double>(P, nact, s) : vcycle_t<float>(P, nact, s);
+  return P->precision == SNAC_FP64 ? vcycle_t<double>(P, nact, s, skip_first0)
+                                   : vcycle_t<float>(P, nact, s, skip_first0);
+}
+
+cudaError_t launch_check_sweep(snac_plan* P, int nact, int ncheck, cudaStream_t s) {
+  if (nact <= 0) return cudaSuccess;
+  const HostLevel& h = P->lev[0];
+  const int ctas = std::min<int>(CHECK_CTAS, (int)h.tiles.size());
+  dim3 g((unsigned)ctas, (unsigned)nact);
+  const double cells = (double)h.ncell * nact;
+  {
+    // the half-sweep's traffic (other colour, g and 1/diag of this colour, write this colour) plus u of
+    // this colour; the update's 9 flops and the residual's 5 per colour-0 cell
+    LaunchScope ls(P, K_SMOOTH, 2.0 * 8.0 * cells, 7.0 * cells, s);
+    k_smooth_check<<<g, COLOUR_THREADS, 0, s>>>(level_view<double>(h), P->d_active, P->d_sigma64, h.d_invd,
+                                                 (double*)h.d_u, (const double*)h.d_f, P->d_check, ncheck,
+                                                 P->d_mode_part);
+  }
+  LaunchScope ls(P, K_MODE_REDUCE, 8.0 * ctas * ncheck, (double)ctas * ncheck, s);
+  k_mode_reduce<<<ncheck, 256, 0, s>>>(P->d_mode_part, ctas, P->d_check, P->d_mode_norm2);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_mode_norms(snac_plan* P, int nact, bool after_cycle, cudaStream_t s, const int* d_list,

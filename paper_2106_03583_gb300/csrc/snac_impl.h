@@ -284,7 +284,11 @@ cudaError_t launch_mode_operator(snac_plan* P, const void* u, void* out, cudaStr
 // 1 / diagonal of every mode's reduced operator on every smoothed level (FP64 plans), once per plan
 cudaError_t launch_inverse_diagonals(snac_plan* P, cudaStream_t s);
 // one V-cycle of the active modes on the plan's level buffers (level 0: d_u / d_f)
-cudaError_t launch_vcycle(snac_plan* P, int nactive, cudaStream_t s);
+// skip_first0: level 0's first colour-0 half-sweep of this cycle was done by launch_check_sweep.
+cudaError_t launch_vcycle(snac_plan* P, int nactive, cudaStream_t s, bool skip_first0 = false);
+// Scaled FP64 plans: the next cycle's first colour-0 half-sweep at level 0 for the active modes, with
+// the residual norms (before it) of the ncheck modes in d_check (ascending) into d_mode_norm2.
+cudaError_t launch_check_sweep(snac_plan* P, int nact, int ncheck, cudaStream_t s);
 // per-mode ||f - A u||^2 at level 0 for the active modes -> d_mode_norm2[q]; after_cycle: u is the
 // result of a V-cycle (post-smoothing ended on black, so only red cells carry a residual); otherwise
 // u is zero and the norm is that of f

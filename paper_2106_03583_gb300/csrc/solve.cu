@@ -56,12 +56,14 @@ int set_active_all(snac_plan* P, cudaStream_t s) {
 // One V-cycle round of the active modes and their norms. Without profiling the round is replayed from
 // a CUDA graph captured (on the plan's private stream) the first time this number of modes is active;
 // the graph's kernels read the active list from device memory, which the caller updates before.
-cudaError_t run_round(snac_plan* P, int nact, bool norms, cudaStream_t s, int* replayed) {
+// skip_first0: the cycle's first colour-0 half-sweep at level 0 was done by the last norm check.
+cudaError_t run_round(snac_plan* P, int nact, bool norms, cudaStream_t s, int* replayed, bool skip_first0) {
   if (!P->graphs || P->profiling) {
-    cudaError_t e = launch_vcycle(P, nact, s);
+    cudaError_t e = launch_vcycle(P, nact, s, skip_first0);
     return e != cudaSuccess || !norms ? e : launch_mode_norms(P, nact, true, s);
   }
-  auto it = P->round_graphs.find(nact);
+  const int key = 2 * nact + (skip_first0 ? 1 : 0);
+  auto it = P->round_graphs.find(key);
   if (it == P->round_graphs.end()) {
     snac_plan::RoundGraph rg;
     KernelStat before[K_COUNT];
@@ -71,7 +73,7 @@ cudaError_t run_round(snac_plan* P, int nact, bool norms, cudaStream_t s, int* r
     cudaGraph_t g = nullptr;
     if (e == cudaSuccess) e = cudaStreamBeginCapture(P->capture_stream, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
-      cudaError_t el = launch_vcycle(P, nact, P->capture_stream);
+      cudaError_t el = launch_vcycle(P, nact, P->capture_stream, skip_first0);
       if (el == cudaSuccess && norms) el = launch_mode_norms(P, nact, true, P->capture_stream);
       e = cudaStreamEndCapture(P->capture_stream, &g);
       if (el != cudaSuccess) e = el;
@@ -87,9 +89,9 @@ cudaError_t run_round(snac_plan* P, int nact, bool norms, cudaStream_t s, int* r
     if (e != cudaSuccess) {  // capture not possible here: launch the kernels directly from now on
       cudaGetLastError();
       P->graphs = false;
-      return run_round(P, nact, norms, s, replayed);
+      return run_round(P, nact, norms, s, replayed, skip_first0);
     }
-    it = P->round_graphs.emplace(nact, rg).first;
+    it = P->round_graphs.emplace(key, rg).first;
   }
   for (int k = 0; k < K_COUNT; ++k) {
     P->kstats[k].launches += it->second.delta[k].launches;
@@ -123,6 +125,10 @@ int mode_solves(snac_plan* P, double target, cudaStream_t s, int* cycles_out) {
   // share, at most 3 cycles after its last check; rounds without a check need no synchronisation.
   // A mode stops only at a check, so at worst it runs one cycle more than needed.
   const bool predictive = !P->lev[0].fused;
+  // scaled FP64 plans take the norms of a check from the next cycle's first colour-0 half-sweep at
+  // level 0 (done for every active mode), so the check costs no pass of its own
+  const bool sweep_checks = predictive && P->scaled_f && P->nu1 >= 1;
+  bool red_done = false;  // that half-sweep of the coming cycle is done
   const double stag2 = 0.6 * 0.6;  // a cycle that reduces the norm less than 0.6x: the precision floor
   int total = 0;
   bool list_changed = true;
@@ -134,7 +140,8 @@ int mode_solves(snac_plan* P, double target, cudaStream_t s, int* cycles_out) {
       CK(launch_from_host(P->dh_active, P->d_active, nact, s));
       list_changed = false;
     }
-    CK(run_round(P, nact, !predictive, s, &P->info.graph_rounds));
+    CK(run_round(P, nact, !predictive, s, &P->info.graph_rounds, red_done));
+    red_done = false;
     int ncheck = 0;
     for (int q : list) {
       ++cycles_out[q];
@@ -145,7 +152,12 @@ int mode_solves(snac_plan* P, double target, cudaStream_t s, int* cycles_out) {
     if (ncheck == 0) continue;
     if (predictive) {
       CK(launch_from_host(P->dh_check, P->d_check, ncheck, s));
-      CK(launch_mode_norms(P, ncheck, true, s, P->d_check));
+      if (sweep_checks) {
+        CK(launch_check_sweep(P, nact, ncheck, s));
+        red_done = true;  // for every mode that stays active
+      } else {
+        CK(launch_mode_norms(P, ncheck, true, s, P->d_check));
+      }
     }
     CK(launch_to_host(P->d_mode_norm2, P->dh_mode_norm2, nz, s));
     CK(cudaStreamSynchronize(s));
