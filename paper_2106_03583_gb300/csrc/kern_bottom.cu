@@ -126,7 +126,7 @@ __device__ void restrict_to(const LevelView<T>& F, const LevelSmem<T>& SF, const
         a = fma(cy.lo, SF.u[s], a);
         a = fma(cy.hi, SF.u[n], a);
         a = fma(F.dxy[c] + sg, SF.u[c], a);
-        acc = fma(F.rx[Bf.xo + i] * F.ry[Bf.yo + j], SF.f[c] - a, acc);
+        acc = fma(F.wr[c], SF.f[c] - a, acc);  // rx * ry
       }
     }
     SC.f[cc] = acc;
@@ -156,9 +156,9 @@ __device__ void prolong_from(const LevelView<T>& F, const LevelSmem<T>& SF, cons
     const T eC = SC.u[Bc.off + (long long)J * Bc.nx + I];
     const T eX = SC.u[(i & 1) ? e : w];
     const T eY = SC.u[(j & 1) ? n : s];
-    const PW<T> px = F.px[Bf.xo + i], py = F.py[Bf.yo + j];  // px.self already holds 1 + self_x
+    const PW<T> px = F.px[Bf.xo + i], py = F.py[Bf.yo + j];
     const int c = (int)(Bf.off + (long long)j * Bf.nx + i);
-    T u = fma(eC, px.self + py.self, SF.u[c]);
+    T u = fma(eC, F.wp[c], SF.u[c]);  // 1 + self_x + self_y
     u = fma(px.nbr, eX, u);
     SF.u[c] = fma(py.nbr, eY, u);
   }

@@ -86,13 +86,13 @@ inline LevelView<T> level_view(const HostLevel& l);
 template <>
 inline LevelView<double> level_view<double>(const HostLevel& l) {
   return LevelView<double>{l.d_blk, l.d_tiles, l.d_cx64, l.d_cy64, l.d_px64, l.d_py64, l.d_rx64, l.d_ry64,
-                           l.ncell, (int)l.tiles.size(), l.nblk, l.d_dxy64};
+                           l.ncell, (int)l.tiles.size(), l.nblk, l.d_dxy64, l.d_wr64, l.d_wp64};
 }
 
 template <>
 inline LevelView<float> level_view<float>(const HostLevel& l) {
   return LevelView<float>{l.d_blk, l.d_tiles, l.d_cx32, l.d_cy32, l.d_px32, l.d_py32, l.d_rx32, l.d_ry32,
-                          l.ncell, (int)l.tiles.size(), l.nblk, l.d_dxy32};
+                          l.ncell, (int)l.tiles.size(), l.nblk, l.d_dxy32, l.d_wr32, l.d_wp32};
 }
 
 // 1/x: the single-precision reciprocal, refined by one Newton step in double.

@@ -198,7 +198,7 @@ __global__ void __launch_bounds__(TILE_THREADS) k_restrict(LevelView<T> F, Level
       const long long cf = SCALED ? split_cell(Bf, i, j) : c;
       const T r = cell_residual<T, SCALED>(cx, cy, diag, ff[bf + cf], uf[bf + c], uf[bf + w], uf[bf + e], uf[bf + s],
                                            uf[bf + n]);
-      acc = fma(F.rx[Bf.xo + i] * F.ry[Bf.yo + j], r, acc);
+      acc = fma(F.wr[c], r, acc);  // rx * ry
     }
   }
   const long long cb = (long long)q * C.ncell;
@@ -240,10 +240,12 @@ __global__ void __launch_bounds__(TILE_THREADS) k_prolong(LevelView<T> F, LevelV
   const T eC = uc[bc + Bc.off + (long long)J * Bc.nx + I];
   const T eX = uc[bc + ((i & 1) ? e : w)];
   const T eY = uc[bc + ((j & 1) ? n : s)];
-  const PW<T> px = F.px[Bf.xo + i], py = F.py[Bf.yo + j];  // px.self already holds 1 + self_x
-  const long long c = (long long)q * F.ncell + Bf.off + (long long)j * Bf.nx + i;
-  // accumulated into u directly: three FMAs (the FP64 pipe bounds this kernel in FP64 plans)
-  T u = fma(eC, px.self + py.self, uf[c]);
+  const PW<T> px = F.px[Bf.xo + i], py = F.py[Bf.yo + j];
+  const long long cl = Bf.off + (long long)j * Bf.nx + i;
+  const long long c = (long long)q * F.ncell + cl;
+  // accumulated into u directly: three FMAs (the FP64 pipe bounds this kernel in FP64 plans); the
+  // parent's weight 1 + self_x + self_y comes from the level's table
+  T u = fma(eC, F.wp[cl], uf[c]);
   u = fma(px.nbr, eX, u);
   uf[c] = fma(py.nbr, eY, u);
 }

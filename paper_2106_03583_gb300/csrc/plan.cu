@@ -475,7 +475,19 @@ int upload_level(snac_plan* P, HostLevel& lv, size_t inner) {
     // prolongation forms the parent's total weight (1 + self_x) + self_y with one addition
     std::vector<PW<double>> px1 = lv.px;
     for (PW<double>& w : px1) w.self += 1.0;
-    if ((st = upload(P, &lv.d_px64, px1)) || (st = upload(P, &lv.d_py64, lv.py)) ||
+    // per plane cell: the restriction weight rx * ry and the parent's prolongation weight
+    // (1 + self_x) + self_y, as the kernels would form them (one FP64 operation fewer per use)
+    std::vector<double> wr(lv.ncell), wp(lv.ncell);
+    for (const BlockDev& d : lv.blk)
+      for (int j = 0; j < d.ny; ++j)
+        for (int i = 0; i < d.nx; ++i) {
+          const long long c = d.off + (long long)j * d.nx + i;
+          wr[c] = lv.rx[d.xo + i] * lv.ry[d.yo + j];
+          wp[c] = px1[d.xo + i].self + lv.py[d.yo + j].self;
+        }
+    if ((st = upload(P, &lv.d_wr64, wr)) || (st = upload(P, &lv.d_wr32, to32(wr))) ||
+        (st = upload(P, &lv.d_wp64, wp)) || (st = upload(P, &lv.d_wp32, to32(wp))) ||
+        (st = upload(P, &lv.d_px64, px1)) || (st = upload(P, &lv.d_py64, lv.py)) ||
         (st = upload(P, &lv.d_px32, to32(px1))) || (st = upload(P, &lv.d_py32, to32(lv.py))) ||
         (st = upload(P, &lv.d_rx64, lv.rx)) || (st = upload(P, &lv.d_ry64, lv.ry)) ||
         (st = upload(P, &lv.d_rx32, to32(lv.rx))) || (st = upload(P, &lv.d_ry32, to32(lv.ry))))

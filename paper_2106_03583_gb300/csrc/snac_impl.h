@@ -91,6 +91,8 @@ struct LevelView {
   int ntiles;
   int nblk;
   const T* dxy;     // x-y part of the diagonal of every plane cell, cx.d + cy.d (plain order)
+  const T* wr;      // restriction weight of every plane cell, rx * ry (levels with a coarser one)
+  const T* wp;      // prolongation weight of the parent, 1 + self_x + self_y (levels with a coarser one)
 };
 
 // One level of the bottom sub-cycle (kern_bottom.cu), in a device table built with the plan.
@@ -128,6 +130,10 @@ struct HostLevel {
   float* d_ry32 = nullptr;
   double* d_dxy64 = nullptr;
   float* d_dxy32 = nullptr;
+  double* d_wr64 = nullptr;
+  float* d_wr32 = nullptr;
+  double* d_wp64 = nullptr;
+  float* d_wp32 = nullptr;
   void* d_u = nullptr;  // mode-space iterate, n_z x ncell of the inner type
   void* d_f = nullptr;  // mode-space right-hand side
   double* d_invd = nullptr;  // FP64 plans, smoothed levels: 1 / (A_xy + sigma_q)_cc per mode and cell
