@@ -43,22 +43,22 @@ FP64_IN_FP64_PLAN = {"smooth", "restrict", "prolong", "mode_resid", "mode_apply"
 # bench scales the ratio to its own launches (traffic grows in proportion to the cells processed) and
 # reports null once the source differs from the captured one. Captures: profiles/*.md.
 _FUSED = {"src": "paper_2106_03583_gb300/csrc/kern_fused.cu",
-          "sha256": "77084ceec5df844310d568fabd7f986f99d05ca61a7637f6bd6cdb5b96b45305",
+          "sha256": "8482a9e751212f3f6a0228c49b52b8e79a5f0751fb2e1972b428e25e6573bf02",
           "capture": "profiles/k_fdown_k_fup_mixed_mb2x2_z64.md"}
 _FIELD = {"src": "paper_2106_03583_gb300/csrc/kern_field.cu",
-          "sha256": "e654f5d465b615b7eea1c3fc11db5354d230ebc6d6d24f032965592655d56853",
-          "capture": "profiles/k_field3d_transforms_mixed_mb2x2_z64.md", "ratio": 401.097 / 402.653}
+          "sha256": "38cefb3e6b6743e2be74704dc12fc9aff796eef828e27a65fcc6dcead8d6b089",
+          "capture": "profiles/k_field3d_transforms_mb2x2_z64.md", "ratio": 401.3 / 402.653}
 _MG = {"src": "paper_2106_03583_gb300/csrc/kern_mg.cu",
-       "sha256": "d4291991e922866afda21591cde9a4e6f7198df939028c4bfeb4d2a42416d25d",
+       "sha256": "7ff5bf650cac1bff272ed46562c8e0a873024af37927a04949010cce6a4b6037",
        "capture": "profiles/k_smooth_fp64_mb2x2_z64.md"}
 TRAFFIC = {
-    ("fused_up", "mixed"): dict(_FUSED, ratio=196.023 / 218.104),     # level-0 up kernel, 64 modes
-    ("fused_down", "mixed"): dict(_FUSED, ratio=188.312 / 218.104),   # level-0 down kernel, 64 modes
+    ("fused_up", "mixed"): dict(_FUSED, ratio=195.9 / 218.104),     # level-0 up kernel, 64 modes
+    ("fused_down", "mixed"): dict(_FUSED, ratio=188.0 / 218.104),   # level-0 down kernel, 64 modes
     ("field3d", "mixed"): _FIELD,
     ("field3d", "fp64"): _FIELD,
-    ("smooth", "fp64"): dict(_MG, ratio=506.936 / 201.327),           # level 0, mean of four launches
-    ("restrict", "fp64"): dict(_MG, ratio=320.484 / 335.544),
-    ("prolong", "fp64"): dict(_MG, ratio=244.183 / 301.990),
+    ("smooth", "fp64"): dict(_MG, ratio=354.2 / 201.327),           # level-0 half-sweep, mean of four
+    ("restrict", "fp64"): dict(_MG, ratio=290.6 / 369.099),
+    ("prolong", "fp64"): dict(_MG, ratio=245.4 / 167.772),
 }
 
 
