@@ -190,11 +190,20 @@ __device__ void coarse_solve(const double* __restrict__ Q, const double* __restr
   __syncthreads();
 }
 
+// The level's arrays of mode q: u and 1/diag in shared memory; f there too, or (sf < 0) the level's
+// global right-hand side. The block table is the shared-memory copy.
 template <typename T>
-__device__ __forceinline__ LevelSmem<T> level_smem(unsigned char* raw, const BottomLevel<T>& bl, bool smoothed) {
-  T* base = reinterpret_cast<T*>(raw) + bl.soff;
-  const int n = (int)bl.L.ncell;
-  return LevelSmem<T>{base, base + n, smoothed ? base + 2 * n : nullptr};
+__device__ __forceinline__ LevelSmem<T> level_smem(unsigned char* raw, const BottomLevel<T>& bl, const T* f_global) {
+  T* base = reinterpret_cast<T*>(raw);
+  return LevelSmem<T>{base + bl.su, bl.sf >= 0 ? base + bl.sf : const_cast<T*>(f_global),
+                      bl.sinv >= 0 ? base + bl.sinv : nullptr};
+}
+
+template <typename T>
+__device__ __forceinline__ BottomLevel<T> level_at(const BottomArgs<T>& A, unsigned char* raw, int l) {
+  BottomLevel<T> bl = A.lv[l];
+  bl.L.blk = reinterpret_cast<const BlockDev*>(raw + bl.sblk);
+  return bl;
 }
 
 template <typename T>
@@ -207,17 +216,27 @@ __global__ void __launch_bounds__(BT) k_bottom(const BottomArgs<T> A) {
   const T sg = A.sigma[q];
   const double sg64 = A.sigma64[q];
   const bool sing = A.singular_mode[q] != 0;
-  // the top level's right-hand side, and 1/diag of every smoothed level
+  const T* f0g = A.f_top + (long long)q * A.lv[0].L.ncell;  // the top level's right-hand side
+  // the levels' block tables, the top level's right-hand side (when it is kept on chip), and 1/diag
+  // of every smoothed level
+  for (int l = 0; l < nl; ++l) {
+    const BottomLevel<T> bl = A.lv[l];
+    const unsigned* src = reinterpret_cast<const unsigned*>(bl.L.blk);
+    unsigned* dst = reinterpret_cast<unsigned*>(smem_raw + bl.sblk);
+    const int words = bl.L.nblk * (int)(sizeof(BlockDev) / sizeof(unsigned));
+    for (int k = threadIdx.x; k < words; k += BT) dst[k] = src[k];
+  }
   {
     const BottomLevel<T> top = A.lv[0];
-    const LevelSmem<T> S = level_smem(smem_raw, top, nl > 1);
-    const int n0 = (int)top.L.ncell;
-    const T* f0 = A.f_top + (long long)q * n0;
-    for (int c = threadIdx.x; c < n0; c += BT) S.f[c] = f0[c];
+    if (top.sf >= 0) {
+      T* f0 = reinterpret_cast<T*>(smem_raw) + top.sf;
+      for (int c = threadIdx.x; c < (int)top.L.ncell; c += BT) f0[c] = f0g[c];
+    }
   }
+  __syncthreads();
   for (int l = 0; l + 1 < nl; ++l) {
-    const BottomLevel<T> bl = A.lv[l];
-    const LevelSmem<T> S = level_smem(smem_raw, bl, true);
+    const BottomLevel<T> bl = level_at(A, smem_raw, l);
+    const LevelSmem<T> S = level_smem(smem_raw, bl, f0g);
     const int n = (int)bl.L.ncell;
     for (int c = threadIdx.x; c < n; c += BT) {
       T iv;
@@ -235,8 +254,8 @@ __global__ void __launch_bounds__(BT) k_bottom(const BottomArgs<T> A) {
   __syncthreads();
   // the top level's first colour-0 half-sweep from its zero iterate
   {
-    const BottomLevel<T> top = A.lv[0];
-    const LevelSmem<T> S = level_smem(smem_raw, top, nl > 1);
+    const BottomLevel<T> top = level_at(A, smem_raw, 0);
+    const LevelSmem<T> S = level_smem(smem_raw, top, f0g);
     const int n0 = (int)top.L.ncell;
     for (int c = threadIdx.x; c < n0; c += BT) {
       int b0, i, j;
@@ -248,22 +267,22 @@ __global__ void __launch_bounds__(BT) k_bottom(const BottomArgs<T> A) {
   }
   // down: nu1 sweeps (the first colour-0 half-sweep already done), residual, restriction
   for (int l = 0; l + 1 < nl; ++l) {
-    const BottomLevel<T> F = A.lv[l], C = A.lv[l + 1];
-    const LevelSmem<T> SF = level_smem(smem_raw, F, true), SC = level_smem(smem_raw, C, l + 2 < nl);
+    const BottomLevel<T> F = level_at(A, smem_raw, l), C = level_at(A, smem_raw, l + 1);
+    const LevelSmem<T> SF = level_smem(smem_raw, F, f0g), SC = level_smem(smem_raw, C, f0g);
     for (int it = 0; it < A.nu1; ++it) {
       if (it > 0) half_sweep(F.L, SF, 0);
       half_sweep(F.L, SF, 1);
     }
-    restrict_to(F.L, SF, C.L, SC, sg, l + 2 < nl);
+    restrict_to(F.L, SF, C.L, SC, sg, l + 2 < nl);  // plans run it with nu1 >= 1
   }
   {
-    const BottomLevel<T> C = A.lv[nl - 1];
-    coarse_solve(A.Q, A.lam, A.sqa, A.nc, A.null_index, level_smem(smem_raw, C, false), sg64, sing, b, y);
+    const BottomLevel<T> C = level_at(A, smem_raw, nl - 1);
+    coarse_solve(A.Q, A.lam, A.sqa, A.nc, A.null_index, level_smem(smem_raw, C, f0g), sg64, sing, b, y);
   }
   // up: prolongation onto the colour-1 cells, nu2 sweeps
   for (int l = nl - 2; l >= 0; --l) {
-    const BottomLevel<T> F = A.lv[l], C = A.lv[l + 1];
-    const LevelSmem<T> SF = level_smem(smem_raw, F, true), SC = level_smem(smem_raw, C, l + 2 < nl);
+    const BottomLevel<T> F = level_at(A, smem_raw, l), C = level_at(A, smem_raw, l + 1);
+    const LevelSmem<T> SF = level_smem(smem_raw, F, f0g), SC = level_smem(smem_raw, C, f0g);
     prolong_from(F.L, SF, C.L, SC, true);
     for (int it = 0; it < A.nu2; ++it) {
       half_sweep(F.L, SF, 0);
@@ -273,7 +292,7 @@ __global__ void __launch_bounds__(BT) k_bottom(const BottomArgs<T> A) {
   // the top level's correction, back to the level-by-level part of the cycle
   {
     const BottomLevel<T> top = A.lv[0];
-    const LevelSmem<T> S = level_smem(smem_raw, top, nl > 1);
+    const LevelSmem<T> S = level_smem(smem_raw, top, f0g);
     const int n0 = (int)top.L.ncell;
     T* u0 = A.u_top + (long long)q * n0;
     for (int c = threadIdx.x; c < n0; c += BT) u0[c] = S.u[c];
@@ -284,15 +303,13 @@ template <typename T>
 cudaError_t bottom_t(snac_plan* P, int nact, cudaStream_t s) {
   BottomArgs<T> A{};
   const int lb = P->bottom, L = (int)P->lev.size() - 1;
+  const BottomLayout lay = bottom_layout(P, lb, sizeof(T));
   A.nlev = L - lb + 1;
   A.split = P->scaled_f ? 1 : 0;
   A.nu1 = P->nu1;
   A.nu2 = P->nu2;
   A.lv = (const BottomLevel<T>*)P->d_bottom;
-  size_t off = 0;
-  for (int l = lb; l <= L; ++l) off += (size_t)P->lev[l].ncell * (l < L ? 3 : 2);
-  A.coarse_off = (int)((off * sizeof(T) + 15) / 16 * 16);
-  const size_t smem = A.coarse_off + 2 * MAX_COARSE * sizeof(double);
+  A.coarse_off = lay.coarse_off;
   A.active = P->d_active;
   if constexpr (sizeof(T) == 8) A.sigma = (const T*)P->d_sigma64;
   else A.sigma = (const T*)P->d_sigma32;
@@ -311,17 +328,42 @@ cudaError_t bottom_t(snac_plan* P, int nact, cudaStream_t s) {
   // DRAM: the top level's right-hand side in and its correction out (tables and factors stay in L2)
   const double w = sizeof(T);
   LaunchScope ls(P, K_BOTTOM, 2.0 * w * (double)P->lev[lb].ncell * nact, flops + 4.0 * P->nc * P->nc * nact, s);
-  k_bottom<T><<<nact, BT, smem, s>>>(A);
+  k_bottom<T><<<nact, BT, lay.bytes, s>>>(A);
   return cudaGetLastError();
 }
 
 }  // namespace
 
-size_t bottom_smem_bytes(const snac_plan* P, int lb, size_t w) {
+BottomLayout bottom_layout(const snac_plan* P, int lb, size_t w) {
+  BottomLayout lay{};
   const int L = (int)P->lev.size() - 1;
-  size_t off = 0;
-  for (int l = lb; l <= L; ++l) off += (size_t)P->lev[l].ncell * (l < L ? 3 : 2);
-  return (off * w + 15) / 16 * 16 + 2 * MAX_COARSE * sizeof(double);
+  size_t el = 0;  // elements of the inner type
+  for (int l = lb; l <= L && l - lb < BOTTOM_MAX_LEVELS; ++l) {
+    const int k = l - lb;
+    const size_t n = (size_t)P->lev[l].ncell;
+    lay.su[k] = (int)el;
+    el += n;
+    if (k == 0 && w == sizeof(double)) {
+      lay.sf[k] = -1;
+    } else {
+      lay.sf[k] = (int)el;
+      el += n;
+    }
+    lay.sinv[k] = -1;
+    if (l < L) {
+      lay.sinv[k] = (int)el;
+      el += n;
+    }
+  }
+  size_t bytes = (el * w + 15) / 16 * 16;
+  lay.coarse_off = (int)bytes;
+  bytes += 2 * MAX_COARSE * sizeof(double);
+  for (int l = lb; l <= L && l - lb < BOTTOM_MAX_LEVELS; ++l) {
+    lay.sblk[l - lb] = (int)bytes;
+    bytes += (size_t)P->lev[l].nblk * sizeof(BlockDev);
+  }
+  lay.bytes = bytes;
+  return lay;
 }
 
 cudaError_t launch_bottom(snac_plan* P, int nact, cudaStream_t s) {

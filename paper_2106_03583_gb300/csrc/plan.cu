@@ -757,7 +757,8 @@ int create(snac_plan** out, int32_t nblocks, const snac_block* blocks_in, int32_
       P->bottom = -1;
       if (P->nu1 >= 1 && P->nu2 >= 1)
         for (int l = std::max(1, L - BOTTOM_MAX_LEVELS + 1); l < L; ++l)
-          if (P->lev[l].ncell <= BOTTOM_MAX_CELLS && bottom_smem_bytes(P, l, inner) <= (size_t)BOTTOM_MAX_SMEM) {
+          if (P->lev[l].ncell <= BOTTOM_MAX_CELLS && L - l < BOTTOM_MAX_LEVELS &&
+              bottom_layout(P, l, inner).bytes <= (size_t)BOTTOM_MAX_SMEM) {
             P->bottom = l;
             break;
           }
@@ -806,14 +807,17 @@ int create(snac_plan** out, int32_t nblocks, const snac_block* blocks_in, int32_
       const int L = (int)P->lev.size() - 1;
       auto build_bottom = [&](auto tag) -> int {
         using T = decltype(tag);
+        const BottomLayout lay = bottom_layout(P, P->bottom, sizeof(T));
         std::vector<BottomLevel<T>> tab;
-        size_t off = 0;
         for (int l = P->bottom; l <= L; ++l) {
+          const int k = l - P->bottom;
           BottomLevel<T> b{};
           b.L = level_view<T>(P->lev[l]);
           b.invd = (sizeof(T) == 8 && l < L) ? P->lev[l].d_invd : nullptr;
-          b.soff = (int)off;
-          off += (size_t)P->lev[l].ncell * (l < L ? 3 : 2);
+          b.su = lay.su[k];
+          b.sf = lay.sf[k];
+          b.sinv = lay.sinv[k];
+          b.sblk = lay.sblk[k];
           tab.push_back(b);
         }
         BottomLevel<T>* d = nullptr;

@@ -100,8 +100,9 @@ template <typename T>
 struct BottomLevel {
   LevelView<T> L;
   const double* invd;  // FP64 smoothed levels: per-mode 1/diag (colour-split order if the plan is scaled)
-  int soff;            // element offset of the level's u, f [, 1/diag] in the kernel's shared memory
-  int pad;
+  int su, sf, sinv;    // element offsets of u, f and 1/diag in the kernel's shared memory (-1: f read
+                       // from the level's global array, 1/diag absent on the coarsest level)
+  int sblk;            // byte offset of the level's block table copy in shared memory
 };
 
 // Host-side description of one level.
@@ -303,8 +304,16 @@ cudaError_t launch_mode_norms(snac_plan* P, int nactive, bool after_cycle, cudaS
                               bool zero_u = false);
 // The V-cycle from level P->bottom down to the coarsest and back, one CTA per active mode.
 cudaError_t launch_bottom(snac_plan* P, int nact, cudaStream_t s);
-// Dynamic shared memory of that kernel when it starts at level lb, for inner type width w.
-size_t bottom_smem_bytes(const snac_plan* P, int lb, size_t w);
+// Shared-memory layout of that kernel when it starts at level lb, for inner type width w: per level
+// the element offsets of u, f (-1: the top level's f stays in global memory, as in FP64 plans, so
+// that two CTAs fit on one multiprocessor) and 1/diag (-1 on the coarsest level), the byte offset of
+// the level's block table copy; the byte offset of the coarsest solve's vectors and the total.
+struct BottomLayout {
+  int su[BOTTOM_MAX_LEVELS], sf[BOTTOM_MAX_LEVELS], sinv[BOTTOM_MAX_LEVELS], sblk[BOTTOM_MAX_LEVELS];
+  int coarse_off;
+  size_t bytes;
+};
+BottomLayout bottom_layout(const snac_plan* P, int lb, size_t w);
 // Small transfers through mapped pinned memory, done by one-CTA kernels (no copy engine).
 cudaError_t launch_to_host(const double* d_src, double* dh_dst, int n, cudaStream_t s);
 cudaError_t launch_from_host(const int* dh_src, int* d_dst, int n, cudaStream_t s);
