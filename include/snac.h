@@ -137,7 +137,9 @@ int snac_plan_workspace_bytes(const snac_plan *plan, size_t *bytes);
  * latest solution, Sec. 3.3.1), out: solution. Singular problems (periodic or Neumann-Neumann z and
  * no Dirichlet face in x-y): a volume-weighted mean of f within 1e-12 sum(V|f|) is removed and the
  * zero-mean solution returned; a larger mean gives SNAC_ERR_INCOMPATIBLE_RHS with p untouched.
- * A zero f gives p = 0. */
+ * A zero f gives p = 0. Runs on `stream` and returns when p is complete. It issues kernels only: its
+ * small control transfers (norms read back, mode lists) go through pinned host memory mapped into the
+ * device (held by the plan), so copies that other streams run meanwhile do not delay it. */
 int snac_poisson_solve(snac_plan *plan, const double *d_rhs, double *d_p, double tol, void *stream);
 
 /* Statistics of the last solve. */
