@@ -3,7 +3,9 @@
 // CTA per active wavenumber. The coarse levels hold few cells per mode, so run level by level they
 // are many small launches that fill the GPU badly (a 16x16 block inside a 64x64 fused window, grids
 // of four tiles); here each mode's u, f and 1/diag of those levels stay on chip for the whole
-// sub-cycle, and the only DRAM traffic is the level's right-hand side in and its correction out.
+// sub-cycle (FP64 plans read the top level's f from L2, so that two CTAs share a multiprocessor),
+// the levels' block tables are copied to shared memory, and the only DRAM traffic is the top level's
+// right-hand side in and its correction out.
 //
 // The arithmetic is that of the level-by-level path: red-black Gauss-Seidel (colour = parity of the
 // global index-space position), red-only residuals after a sweep ending on black, area-weighted
@@ -44,7 +46,7 @@ struct BottomArgs {
 template <typename T>
 struct LevelSmem {
   T* u;
-  T* f;
+  T* f;    // shared memory, or the top level's global right-hand side (read only)
   T* inv;  // smoothed levels only
 };
 
