@@ -19,5 +19,8 @@ Pins (tests/test_oracle_*.py): library transforms (scipy.fft), round trips x the
 eigenvalues of every boundary-condition pair, manufactured eigenfunction solutions, a triple-transform
 closed-form solve on uniform boxes, the factorisation of the operator into the staggered divergence of
 the staggered gradient, volume-weighted symmetry, dense LU on tiny grids, the zero-mean invariant and
-partition invariance. No function here is "parity unpinned".
+partition invariance; for the multigrid pieces one at a time: restriction moments, exactness of the
+prolongation on affine fields (with the face ghosts), exact colour half-sweeps, coarse operators
+equal to the direct assembly on every other face, and a grid-independent V-cycle contraction.
+No function here is "parity unpinned".
 """
