@@ -1,6 +1,7 @@
-"""Pins of the oracle's multigrid pieces (the free choices of reading R10: cell-centred 2x2
-coarsening, red-black Gauss-Seidel, area-weighted restriction, three-point affine prolongation,
-rediscretised coarse operators) against facts of the geometry and of multigrid theory.
+"""Pins of the oracle's multigrid pieces (free choices, since the paper leaves the multigrid to hypre,
+Sec. 3.3: cell-centred 2x2 coarsening, red-black Gauss-Seidel, area-weighted restriction, three-point
+affine prolongation, rediscretised coarse operators) against facts of the geometry and of multigrid
+theory.
 
 The per-cycle GPU parity tests compare the kernels with these pieces one cycle at a time, where the
 converged-solution pins (dense LU, eigenfunctions) cannot see them: a wrong weight only slows a
