@@ -2,22 +2,30 @@
 """Benchmark of the FFT-accelerated multi-block Poisson solve: solves/s at relative residual 1e-10.
 
 Workload (one step = one complete solve from a zero initial guess, all stages on the GPU):
-  2x2 blocks of 256x256 cells (assembled 512x512; x uniform on [0,2], y two-sided tanh factor 1.5 on
-  [0,2]; Neumann walls) by n_z = 256 Neumann-Neumann (DCT-II) on [0,1]; f = D u for a seeded
-  random-phase velocity field with a k^-5/3 spectrum. 6.7e7 cells, 537 MB per float64 field.
-The headline is the FP64 solve; the mixed-precision solve (FP32 multigrid inside FP64 defect
-correction) of the same problem is reported beside it.
+  the channel-like problem: one block of 1024 x 512 cells (x uniform on [0, 2], Dirichlet walls;
+  y two-sided tanh factor 2.0 on [0, 1], Neumann walls) by n_z = 512 periodic (real DFT) on [0, 1];
+  f = D u for a seeded random-phase velocity field with a k^-5/3 spectrum. 2.7e8 cells, 2.1 GB
+  per float64 field.
+The headline is the mixed-precision solve (FP32 transforms and multigrid inside FP64 defect
+correction); the FP64 solve of the same problem is reported beside it under "fp64", each with its
+own roofline and end-to-end figure. The 2x2-block workload (6.7e7 cells) is reported as a
+secondary line under "secondary".
 
     python bench.py [--gpus N --steps K --warmup W] [--impl reference]
 
 Prints one JSON line (rank 0). With N > 1 (torchrun), every rank solves its own seeded problem
 (independent replicas, no collective on the data path): weak scaling.
+
+The CPU baseline and the reference arm (--impl reference) time the repository's FP64 CPU oracle as
+it stands, on bounded samples of the same workload: the O(n^2) transforms on a sample of the
+columns and the per-wavenumber multigrid solves on a sample of the wavenumbers, each scaled to the
+whole solve.
 """
 from __future__ import annotations
 
 import argparse
 import json
-import math
+import multiprocessing as mp
 import os
 import statistics
 import subprocess
@@ -29,37 +37,26 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "Poisson solves/s & HBM GB/s at rel-residual 1e-10, mixed vs FP64; p50/p99 lat"
-WORKLOAD = ("mb2x2: 2x2 blocks of 256x256 cells (assembled 512x512, x uniform [0,2], y tanh 1.5 on [0,2], "
-            "Neumann walls) x n_z=256 Neumann-Neumann (DCT-II) on [0,1]; f = D u, random-phase k^-5/3 "
-            "velocity; zero initial guess each solve")
+WORKLOADS = {
+    "chan": ("chan: 1 block 1024x512 (x uniform [0,2] Dirichlet-Dirichlet, y tanh 2.0 on [0,1] Neumann-Neumann) "
+             "x n_z=512 periodic (real DFT) on [0,1]; f = D u, random-phase k^-5/3 velocity; zero initial guess "
+             "each solve"),
+    "mb2x2": ("mb2x2: 2x2 blocks of 256x256 cells (assembled 512x512, x uniform [0,2], y tanh 1.5 on [0,2], "
+              "Neumann walls) x n_z=256 Neumann-Neumann (DCT-II) on [0,1]; f = D u, random-phase k^-5/3 "
+              "velocity; zero initial guess each solve"),
+}
 FP64_ALU_PEAK = 152 * 2 * 2 * 2.07e9   # SMs x FP64 FMA/clk/SM x 2 flop x max SM clock = 1.259 TFLOP/s
 # kernels whose arithmetic is FP64 in every plan, and those that are FP64 in an FP64 plan: their
 # roof is the FP64 pipe, not HBM
 FP64_ALWAYS = {"field3d"}
 FP64_IN_FP64_PLAN = {"smooth", "restrict", "prolong", "mode_resid", "mode_apply", "forward_transform",
                      "backward_update", "coarse_solve"}
-# DRAM traffic of one ncu-captured launch (dram__bytes_read.sum + dram__bytes_write.sum) divided by that
-# launch's algorithmic bytes, with the sha256 of the kernel's source file when it was captured. The
-# bench scales the ratio to its own launches (traffic grows in proportion to the cells processed) and
-# reports null once the source differs from the captured one. Captures: profiles/*.md.
-_FUSED = {"src": "paper_2106_03583_gb300/csrc/kern_fused.cu",
-          "sha256": "8482a9e751212f3f6a0228c49b52b8e79a5f0751fb2e1972b428e25e6573bf02",
-          "capture": "profiles/k_fdown_k_fup_mixed_mb2x2_z64.md"}
-_FIELD = {"src": "paper_2106_03583_gb300/csrc/kern_field.cu",
-          "sha256": "38cefb3e6b6743e2be74704dc12fc9aff796eef828e27a65fcc6dcead8d6b089",
-          "capture": "profiles/k_field3d_transforms_mb2x2_z64.md", "ratio": 401.3 / 402.653}
-_MG = {"src": "paper_2106_03583_gb300/csrc/kern_mg.cu",
-       "sha256": "7ff5bf650cac1bff272ed46562c8e0a873024af37927a04949010cce6a4b6037",
-       "capture": "profiles/k_smooth_fp64_mb2x2_z64.md"}
-TRAFFIC = {
-    ("fused_up", "mixed"): dict(_FUSED, ratio=195.9 / 218.104),     # level-0 up kernel, 64 modes
-    ("fused_down", "mixed"): dict(_FUSED, ratio=188.0 / 218.104),   # level-0 down kernel, 64 modes
-    ("field3d", "mixed"): _FIELD,
-    ("field3d", "fp64"): _FIELD,
-    ("smooth", "fp64"): dict(_MG, ratio=354.2 / 201.327),           # level-0 half-sweep, mean of four
-    ("restrict", "fp64"): dict(_MG, ratio=290.6 / 369.099),
-    ("prolong", "fp64"): dict(_MG, ratio=245.4 / 167.772),
-}
+# DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum from one ncu capture of the
+# kernel on the workload at 1/2 scale per axis), divided by that launch's algorithmic bytes, with the
+# sha256 of the kernel's source file when it was captured. The bench scales the ratio to its own
+# launches (traffic grows in proportion to the cells processed) and reports null once the source
+# differs from the captured one.
+TRAFFIC = {}
 
 
 def parse():
@@ -68,11 +65,12 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["snac", "reference"], default="snac")
-    ap.add_argument("--workload", default="mb2x2")
+    ap.add_argument("--workload", default="chan")
+    ap.add_argument("--secondary", default="mb2x2", help="second workload reported beside the headline ('none')")
     ap.add_argument("--tol", type=float, default=1e-10)
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--precisions", default="fp64,mixed")
+    ap.add_argument("--precisions", default="mixed,fp64", help="the first one is the headline")
     ap.add_argument("--serve", action="store_true",
                     help="serving stream: Poisson arrivals of mixed problems through the engine")
     ap.add_argument("--batch", action="store_true", help="64 independent mixed problems at once through the engine")
@@ -169,68 +167,232 @@ def whole_job_rate(world, steps, max_ms):
     return world * steps / (max_ms * 1e-3)
 
 
-def base_line(args, world, precision="fp64"):
-    dtype = "f64" if precision == "fp64" else "f32 multigrid and transforms, f64 residual and update"
+def _dtype(precision):
+    return "f64" if precision == "fp64" else "f32 transforms and multigrid, f64 residual and update (mixed)"
+
+
+def workload_config(name, blocks, tol, precision, world):
+    """The config dict of a bench line; identical for the GPU arm and the reference arm."""
+    from paper_2106_03583_gb300 import inputs
+    n3 = inputs.total_cells(blocks)
+    return {"workload": WORKLOADS.get(name, name), "n_cells": n3, "tol": tol, "precision": precision,
+            "parallelism": f"replicas x{world}",
+            "l2": (f"inputs larger than L2 ({8 * n3 / 1e6:.0f} MB per float64 field), no flush" if 8 * n3 > 129e6
+                   else f"{8 * n3 / 1e6:.0f} MB per float64 field: L2-resident, no flush")}
+
+
+def base_line(args, world, blocks, precision):
     return {"metric": METRIC, "unit": "solves/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": dtype, "data": "synthetic",
-            "config": {"workload": WORKLOAD if args.workload == "mb2x2" else args.workload, "tol": args.tol,
-                       "precision": precision, "parallelism": f"replicas x{world}",
-                       "l2": "inputs larger than L2 (537 MB per float64 field), no flush"}}
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": _dtype(precision),
+            "data": "synthetic", "config": workload_config(args.workload, blocks, args.tol, precision, world)}
 
 
-def _oracle_setup(blocks):
+# ---------------------------------------------------------------------------------------------
+# The CPU oracle, timed on bounded samples (cpu_baseline and the reference arm)
+# ---------------------------------------------------------------------------------------------
+
+_ORACLE_MG = None
+_BLAS_ENV = ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")
+
+
+def _oracle_worker_init(blocks):
+    """Worker process: one BLAS thread (set in the environment before the spawn) and the oracle's
+    multigrid hierarchy of the problem's plane, built once (a plan's setup, not timed)."""
+    global _ORACLE_MG
     from oracle import grid as ogrid
     from oracle import mg as omg
-    g = ogrid.Grid(blocks)
-    return g, omg.Multigrid(g.plane)
+    _ORACLE_MG = omg.Multigrid(ogrid.Grid(blocks).plane)
 
 
-def cpu_baseline(args, blocks, f, n_sample, setup=None, t_transforms=None):
-    """The oracle as it stands on a bounded sample: both full transforms plus n_sample of the n_z
-    per-wavenumber multigrid solves; the per-wavenumber time is scaled to all n_z. The transforms'
-    time is measured by a solve without wavenumbers (once, or given)."""
-    import numpy as np
-    from oracle import solve as osv
-    g, mg = setup or _oracle_setup(blocks)
-    nz = g.nz
-    sample = [int(q) for q in np.linspace(0, nz - 1, n_sample).round()]
-    if t_transforms is None:
-        t0 = time.perf_counter()
-        osv.solve(blocks, f, modes=[], mg=mg)
-        t_transforms = time.perf_counter() - t0
+def _oracle_worker_modes(tasks):
+    """The oracle's per-wavenumber multigrid solves (Algorithm 1, second loop) of the given
+    (sigma, right-hand side plane, singular) tasks; returns the seconds they took."""
+    t0 = time.perf_counter()
+    for sigma, fq, singular in tasks:
+        _ORACLE_MG.solve(sigma, fq, singular=singular, rtol=1e-13)
+    return time.perf_counter() - t0
+
+
+def _oracle_worker_ready(_):
+    time.sleep(0.05)
+    return _ORACLE_MG is not None
+
+
+def _oracle_single_thread(kind, cols, tasks):
+    """In a one-thread worker: the oracle's forward and backward transforms of a column sample and
+    the multigrid solves of a wavenumber sample; returns their seconds."""
+    from oracle import transforms as T
+    t0 = time.perf_counter()
+    X = T.forward(kind, cols)
     t1 = time.perf_counter()
-    osv.solve(blocks, f, modes=sample, mg=mg)
+    T.backward(kind, X)
     t2 = time.perf_counter()
-    t_mode = max((t2 - t1) - t_transforms, 0.0) / len(sample)
-    t_full = t_transforms + t_mode * nz
-    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
-    return {"value": 1.0 / t_full, "unit": "solves/s", "cores": cores, "kind": "oracle",
-            "sample": (f"both O(n^2) transforms in full + {len(sample)} of {nz} wavenumber multigrid solves "
-                       f"(q={sample}) at 1e-13; per-wavenumber time x{nz}; numpy/BLAS threads for transforms, "
-                       f"single-threaded sparse multigrid; {t2 - t1:.1f} s of CPU work"),
-            "seconds_per_solve_est": t_full, "t_transforms": t_transforms}
+    tm = _oracle_worker_modes(tasks)
+    return t1 - t0, t2 - t1, tm
+
+
+class OracleSampler:
+    """Bounded samples of the oracle's solve of one problem.
+
+    The oracle's solve is Algorithm 1 as written: the O(n^2) forward transform of every column, one
+    textbook multigrid solve per wavenumber (to a per-mode relative residual of 1e-13), the backward
+    transform. A sample times the transforms on a subset of the columns and the multigrid on a subset
+    of the wavenumbers (evenly spaced over q, so that slow low modes and fast high modes are both in
+    it), and scales each part to the whole problem. The multigrid hierarchy is built once per worker
+    (the oracle's counterpart of a plan; not timed)."""
+
+    def __init__(self, blocks, f):
+        import numpy as np
+        from oracle import grid as ogrid
+        from oracle import solve as osv
+        from oracle import transforms as T
+        self.blocks = blocks
+        g = ogrid.Grid(blocks)
+        F = g.to_planes(f)
+        if g.singular:
+            F = F - osv._compatibility(g, F)
+        self.F = F                                   # (n_z, cells of the plane)
+        self.kind, self.nz, self.ncell = g.kind, g.nz, F.shape[1]
+        self.lam = T.eigenvalues(g.kind, g.nz)
+        self.dz, self.shift, self.singular = g.dz, g.shift, g.singular
+        self._M = T.forward_matrix(g.kind, g.nz)
+        self._rows = {}
+        self.cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
+        self.pool = None
+        self.np = np
+
+    def columns(self, n):
+        idx = self.np.linspace(0, self.ncell - 1, min(n, self.ncell)).round().astype(int)
+        return self.np.ascontiguousarray(self.F[:, idx])
+
+    def modes(self, n, offset=0):
+        """n wavenumbers evenly spaced over 0..n_z-1 (shifted by offset, modulo n_z)."""
+        n = min(n, self.nz)
+        return sorted({(int(q) + offset) % self.nz for q in self.np.linspace(0, self.nz - 1, n).round()})
+
+    def tasks(self, modes):
+        """(sigma_q, transformed right-hand side of mode q, singular) for the given wavenumbers: the
+        rows of the oracle's forward transform that the sample needs (preparation, not timed)."""
+        need = [q for q in modes if q not in self._rows]
+        if need:
+            rows = self._M[need] @ self.F
+            for q, r in zip(need, rows):
+                self._rows[q] = r
+        return [(self.lam[q] / (self.dz * self.dz) + self.shift, self._rows[q],
+                 bool(self.singular and self.lam[q] == 0.0)) for q in modes]
+
+    def _with_one_blas_thread(self, fn):
+        old = {k: os.environ.get(k) for k in _BLAS_ENV}
+        for k in _BLAS_ENV:
+            os.environ[k] = "1"
+        try:
+            return fn()
+        finally:
+            for k, v in old.items():
+                if v is None:
+                    os.environ.pop(k, None)
+                else:
+                    os.environ[k] = v
+
+    def single_thread(self, ncols, nmodes):
+        """Seconds per solve on one core (one process, one BLAS thread)."""
+        cols = self.columns(ncols)
+        modes = self.modes(nmodes)
+        tasks = self.tasks(modes)
+        ctx = mp.get_context("spawn")
+        with self._with_one_blas_thread(lambda: ctx.Pool(1, initializer=_oracle_worker_init,
+                                                         initargs=(self.blocks,))) as pool:
+            tf, tb, tm = pool.apply(_oracle_single_thread, (self.kind, cols, tasks))
+        t = (tf + tb) * self.ncell / cols.shape[1] + tm / len(modes) * self.nz
+        return {"seconds_per_solve_est": t, "value": 1.0 / t, "cores": 1,
+                "sample": (f"one process, one BLAS thread: both O(n^2) transforms of {cols.shape[1]} of {self.ncell} "
+                           f"columns (x{self.ncell / cols.shape[1]:.0f}) and the multigrid solves of {len(modes)} of "
+                           f"{self.nz} wavenumbers (x{self.nz / len(modes):.0f}); {tf + tb + tm:.1f} s of CPU work")}
+
+    def start_pool(self):
+        if self.pool is None:
+            ctx = mp.get_context("spawn")
+            self.pool = self._with_one_blas_thread(
+                lambda: ctx.Pool(self.cores, initializer=_oracle_worker_init, initargs=(self.blocks,)))
+            self.pool.map(_oracle_worker_ready, range(4 * self.cores), chunksize=1)
+
+    def close(self):
+        if self.pool is not None:
+            self.pool.close()
+            self.pool.join()
+            self.pool = None
+
+    def all_cores(self, ncols, nmodes, offset=0):
+        """Seconds per solve on every core the process may use: the transforms with numpy's BLAS
+        threads, the wavenumbers spread over one single-threaded worker process per core."""
+        from oracle import transforms as T
+        self.start_pool()
+        cols = self.columns(ncols)
+        modes = self.modes(nmodes, offset)
+        tasks = self.tasks(modes)
+        t0 = time.perf_counter()
+        X = T.forward(self.kind, cols)
+        t1 = time.perf_counter()
+        T.backward(self.kind, X)
+        t2 = time.perf_counter()
+        self.pool.map(_oracle_worker_modes, [[t] for t in tasks], chunksize=1)
+        t3 = time.perf_counter()
+        t = (t2 - t0) * self.ncell / cols.shape[1] + (t3 - t2) / len(modes) * self.nz
+        return {"seconds_per_solve_est": t, "value": 1.0 / t, "cores": self.cores, "wall_s": t3 - t0,
+                "sample": (f"{self.cores} cores: both O(n^2) transforms of {cols.shape[1]} of {self.ncell} columns "
+                           f"(numpy BLAS threads, x{self.ncell / cols.shape[1]:.0f}) and the multigrid solves of "
+                           f"{len(modes)} of {self.nz} wavenumbers over {self.cores} single-threaded worker "
+                           f"processes (x{self.nz / len(modes):.0f}); {t3 - t0:.1f} s wall")}
+
+
+def cpu_baseline(blocks, f):
+    """The oracle on the host cores, single-threaded and on all cores (bounded samples)."""
+    s = OracleSampler(blocks, f)
+    try:
+        single = s.single_thread(max(1, s.ncell // 64), 8)
+        allc = s.all_cores(max(1, s.ncell // 8), 2 * s.cores)
+    finally:
+        s.close()
+    out = {"value": allc["value"], "unit": "solves/s", "cores": allc["cores"], "kind": "oracle",
+           "sample": allc["sample"] + "; 'cores' and 'value' refer to this all-cores timing",
+           "seconds_per_solve_est": allc["seconds_per_solve_est"],
+           "all_cores": {k: allc[k] for k in ("value", "cores", "seconds_per_solve_est", "sample")},
+           "single_thread": single}
+    return out
 
 
 def run_reference(args):
+    """The reference arm: the CPU oracle as it stands, on this workload's config and metric. Each
+    step is a bounded sample of one solve on all host cores (the transforms of 1/8 of the columns,
+    the multigrid solves of one wavenumber per core, rotating through the wavenumbers from step to
+    step); its value is that sample scaled to whole solves."""
     world, rank, _ = dist()
     if rank != 0:
         return
     from paper_2106_03583_gb300 import inputs
     blocks, f = inputs.config(args.workload, seed=args.seed)
-    setup = _oracle_setup(blocks)
-    first = cpu_baseline(args, blocks, f, 4, setup)
-    ttr = first["t_transforms"]
-    for _ in range(max(args.warmup - 1, 0)):
-        cpu_baseline(args, blocks, f, 4, setup, ttr)
-    vals = []
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        vals.append(cpu_baseline(args, blocks, f, 4, setup, ttr))
-    wall = time.perf_counter() - t0
+    s = OracleSampler(blocks, f)
+    try:
+        s.start_pool()
+        ncols = max(1, s.ncell // 8)
+        for w in range(args.warmup):
+            s.all_cores(ncols, s.cores, offset=w)
+        vals = []
+        t0 = time.perf_counter()
+        for k in range(args.steps):
+            vals.append(s.all_cores(ncols, s.cores, offset=args.warmup + k))
+        wall = time.perf_counter() - t0
+    finally:
+        s.close()
     v = statistics.median(x["value"] for x in vals)
-    line = base_line(args, 1)
-    line.update({"impl": "reference", "value": v, "ms_per_step": 1e3 / v, "n_gpus": world,
-                 "cpu_baseline": dict(vals[0], value=v),
+    line = base_line(args, world, blocks, getattr(args, "precisions", "mixed").split(",")[0])
+    line["dtype"] = "f64 (the CPU oracle)"
+    step_ms = 1e3 * wall / args.steps
+    line.update({"impl": "reference", "value": v, "ms_per_step": step_ms,
+                 "step": "a bounded sample of one solve; value = the sample scaled to whole solves",
+                 "cpu_baseline": {"value": v, "unit": "solves/s", "cores": s.cores, "kind": "oracle",
+                                  "sample": vals[0]["sample"]},
+                 "seconds_per_solve_est": statistics.median(x["seconds_per_solve_est"] for x in vals),
                  "e2e": {"value": v, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
                  "wall_s": wall})
     print(json.dumps(line), flush=True)
@@ -245,14 +407,14 @@ def _sha256(rel):
         return None
 
 
-def traffic_per_launch(name, precision, alg_bytes_per_launch):
-    t = TRAFFIC.get((name, precision))
+def traffic_per_launch(workload, name, precision, alg_bytes_per_launch):
+    t = TRAFFIC.get((workload, name, precision))
     if not t or _sha256(t["src"]) != t["sha256"]:
         return None
     return t["ratio"] * alg_bytes_per_launch
 
 
-def roofline(stats, precision, hbm_peak, hbm_kind, K):
+def roofline(stats, precision, hbm_peak, hbm_kind, K, workload):
     """The dominant kernel (largest summed CUDA-event time) against its bound."""
     name = max(stats, key=lambda k: stats[k]["ms"])
     s = stats[name]
@@ -265,7 +427,8 @@ def roofline(stats, precision, hbm_peak, hbm_kind, K):
     else:
         ach = s["bytes"] / per / dur_s / 1e9
         r = {"bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s", "peak_kind": hbm_kind}
-    r.update({"frac": r["achieved"] / r["peak"], "traffic": traffic_per_launch(name, precision, s["bytes"] / per),
+    r.update({"frac": r["achieved"] / r["peak"],
+              "traffic": traffic_per_launch(workload, name, precision, s["bytes"] / per),
               "kernel": name, "launches_per_step": per / K, "avg_launch_us": dur_s * 1e6,
               "alg_bytes_per_launch": s["bytes"] / per})
     return r
@@ -353,8 +516,92 @@ def e2e_pipelined(plan, f, f_host, K, tol, barrier, world):
     return max_over_ranks(e0.elapsed_time(e1), world, "cuda"), ok
 
 
-def run_snac(args):
+def measure(plan, f, f_np, args, world, rank, local, hbm_peak, hbm_kind, workload, with_e2e=True):
+    """W warm-up solves, then K timed solves (launch counting only), then the same K solves with a
+    CUDA-event pair around every launch for the kernel breakdown, then (with_e2e) the end-to-end
+    passes through the public API with host inputs and outputs. Returns the result dict."""
     import numpy as np
+    import torch
+    K, W = args.steps, args.warmup
+    n3 = f.numel()
+    p = torch.zeros_like(f)
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    for _ in range(W):
+        p.zero_()
+        plan.solve(f, p, tol=args.tol)
+    # timed region: K solves, launches counted by the library (no per-launch events)
+    plan.reset_stats()
+    ck = Clocks(local) if rank == 0 else None
+    barrier()
+    torch.cuda.synchronize()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(K + 1)]
+    ev[0].record()
+    infos = []
+    for k in range(K):
+        p.zero_()
+        infos.append(plan.solve(f, p, tol=args.tol))
+        ev[k + 1].record()
+    torch.cuda.synchronize()
+    barrier()
+    step_ms = [ev[k].elapsed_time(ev[k + 1]) for k in range(K)]
+    total_ms = max_over_ranks(ev[0].elapsed_time(ev[K]), world, "cuda")
+    counts = plan.kernel_stats()
+    launches = sum(s["launches"] for s in counts.values())
+    bytes_model = sum(s["bytes"] for s in counts.values()) / K
+    # second timed region for the kernel breakdown: the same K solves with a CUDA-event pair
+    # around every launch, on the stream it is launched on (adds a few % to the solve time)
+    plan.reset_stats()
+    plan.set_profiling(True)
+    barrier()
+    torch.cuda.synchronize()
+    pe0, pe1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    pe0.record()
+    for k in range(K):
+        p.zero_()
+        plan.solve(f, p, tol=args.tol)
+    pe1.record()
+    torch.cuda.synchronize()
+    barrier()
+    ck_res = ck.stop() if ck else None
+    profiled_ms = max_over_ranks(pe0.elapsed_time(pe1), world, "cuda") / K
+    stats = plan.kernel_stats()
+    plan.set_profiling(False)
+    prec = plan.precision
+    ok = all(i["status"] == 0 and i["rel_res"] <= args.tol for i in infos)
+    res = {
+        "value": whole_job_rate(world, K, total_ms), "ms_per_step": total_ms / K,
+        "p50_ms": statistics.median(step_ms), "p99_ms": float(np.percentile(step_ms, 99)),
+        "cells_per_s": whole_job_rate(world, K, total_ms) * n3,
+        "hbm_gbs_model": bytes_model / (total_ms / K * 1e-3) / 1e9,
+        "roofline": roofline(stats, prec, hbm_peak, hbm_kind, K, workload),
+        "profiled_ms_per_step": profiled_ms,
+        "gpu_launches": launches,
+        "rel_res": infos[-1]["rel_res"], "outer_iters": infos[-1]["outer_iters"],
+        "total_cycles": infos[-1]["total_cycles"], "max_mode_cycles": infos[-1]["max_mode_cycles"],
+        "all_converged": ok,
+        "kernels": {k: {"launches": v["launches"], "ms": round(v["ms"], 3),
+                        "share": round(v["ms"] / max(sum(x["ms"] for x in stats.values()), 1e-30), 4)}
+                    for k, v in stats.items() if v["launches"]},
+        "clocks": ck_res,
+    }
+    del p
+    if with_e2e:
+        # e2e through the public API: host (pinned) rhs in, solution back to host, every step
+        f_host = torch.from_numpy(f_np).pin_memory()
+        e2e_serial_ms = e2e_serial(plan, f, f_host, K, args.tol, barrier, world)
+        e2e_ms, e2e_ok = e2e_pipelined(plan, f, f_host, K, args.tol, barrier, world)
+        res["e2e"] = {"value": whole_job_rate(world, K, e2e_ms), "unit": "solves/s", "h2d_bytes_per_step": 8 * n3,
+                      "d2h_bytes_per_step": 8 * n3, "copies": "overlapped with the neighbouring solves",
+                      "serial_value": whole_job_rate(world, K, e2e_serial_ms), "all_converged": e2e_ok}
+        del f_host
+    return res
+
+
+def run_snac(args):
     import torch
     world, rank, local = dist()
     if world > 1:
@@ -364,103 +611,47 @@ def run_snac(args):
     from paper_2106_03583_gb300 import build, inputs, snac
     build.build()
     hbm_peak, hbm_kind = peaks()
+    precs = args.precisions.split(",")
     blocks, f_np = inputs.config(args.workload, seed=rank_seed(args.seed, rank))
-    n3 = len(f_np)
     f = torch.from_numpy(f_np).cuda()
-    p = torch.zeros_like(f)
-    K, W = args.steps, args.warmup
-
-    def barrier():
-        if world > 1:
-            torch.distributed.barrier()
-
     results = {}
-    clocks = None
-    for prec in args.precisions.split(","):
+    for prec in precs:
         plan = snac.Plan(blocks, precision=prec)
-        for _ in range(W):
-            p.zero_()
-            plan.solve(f, p, tol=args.tol)
-        # timed region: K solves, launches counted by the library (no per-launch events)
-        plan.reset_stats()
-        ck = Clocks(local) if rank == 0 else None
-        barrier()
-        torch.cuda.synchronize()
-        ev = [torch.cuda.Event(enable_timing=True) for _ in range(K + 1)]
-        ev[0].record()
-        infos = []
-        for k in range(K):
-            p.zero_()
-            infos.append(plan.solve(f, p, tol=args.tol))
-            ev[k + 1].record()
-        torch.cuda.synchronize()
-        barrier()
-        step_ms = [ev[k].elapsed_time(ev[k + 1]) for k in range(K)]
-        total_ms = max_over_ranks(ev[0].elapsed_time(ev[K]), world, "cuda")
-        counts = plan.kernel_stats()
-        launches = sum(s["launches"] for s in counts.values())
-        bytes_model = sum(s["bytes"] for s in counts.values()) / K
-        # second timed region for the kernel breakdown: the same K solves with a CUDA-event pair
-        # around every launch, on the stream it is launched on (adds a few % to the solve time)
-        plan.reset_stats()
-        plan.set_profiling(True)
-        barrier()
-        torch.cuda.synchronize()
-        pe0, pe1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        pe0.record()
-        for k in range(K):
-            p.zero_()
-            plan.solve(f, p, tol=args.tol)
-        pe1.record()
-        torch.cuda.synchronize()
-        barrier()
-        ck_res = ck.stop() if ck else None
-        profiled_ms = max_over_ranks(pe0.elapsed_time(pe1), world, "cuda") / K
-        stats = plan.kernel_stats()
-        plan.set_profiling(False)
-        # e2e through the public API: host (pinned) rhs in, solution back to host, every step
-        f_host = torch.from_numpy(f_np).pin_memory()
-        e2e_serial_ms = e2e_serial(plan, f, f_host, K, args.tol, barrier, world)
-        e2e_ms, e2e_ok = e2e_pipelined(plan, f, f_host, K, args.tol, barrier, world)
-        ok = all(i["status"] == 0 and i["rel_res"] <= args.tol for i in infos)
-        results[prec] = {
-            "value": whole_job_rate(world, K, total_ms), "ms_per_step": total_ms / K,
-            "p50_ms": statistics.median(step_ms), "p99_ms": float(np.percentile(step_ms, 99)),
-            "hbm_gbs_model": bytes_model / (total_ms / K * 1e-3) / 1e9,
-            "roofline": roofline(stats, prec, hbm_peak, hbm_kind, K),
-            "profiled_ms_per_step": profiled_ms,
-            "e2e": {"value": whole_job_rate(world, K, e2e_ms), "unit": "solves/s", "h2d_bytes_per_step": 8 * n3,
-                    "d2h_bytes_per_step": 8 * n3, "copies": "overlapped with the neighbouring solves",
-                    "serial_value": whole_job_rate(world, K, e2e_serial_ms), "all_converged": e2e_ok},
-            "gpu_launches": launches,
-            "rel_res": infos[-1]["rel_res"], "outer_iters": infos[-1]["outer_iters"],
-            "total_cycles": infos[-1]["total_cycles"], "max_mode_cycles": infos[-1]["max_mode_cycles"],
-            "all_converged": ok,
-            "kernels": {k: {"launches": v["launches"], "ms": round(v["ms"], 3),
-                            "share": round(v["ms"] / max(sum(x["ms"] for x in stats.values()), 1e-30), 4)}
-                        for k, v in stats.items() if v["launches"]},
-            "clocks": ck_res,
-        }
-        if clocks is None or prec == "fp64":
-            clocks = ck_res
+        results[prec] = measure(plan, f, f_np, args, world, rank, local, hbm_peak, hbm_kind, args.workload)
         plan.close()
+        torch.cuda.empty_cache()
+    del f
+    torch.cuda.empty_cache()
+    secondary = {}
+    if args.secondary and args.secondary != "none" and args.secondary != args.workload:
+        b2, f2_np = inputs.config(args.secondary, seed=rank_seed(args.seed, rank))
+        f2 = torch.from_numpy(f2_np).cuda()
+        sec = {"config": workload_config(args.secondary, b2, args.tol, "mixed and fp64", world)}
+        for prec in precs:
+            plan = snac.Plan(b2, precision=prec)
+            r = measure(plan, f2, f2_np, args, world, rank, local, hbm_peak, hbm_kind, args.secondary, with_e2e=False)
+            plan.close()
+            sec[prec] = {k: r[k] for k in ("value", "ms_per_step", "p50_ms", "p99_ms", "cells_per_s", "hbm_gbs_model",
+                                           "roofline", "gpu_launches", "rel_res", "all_converged", "clocks")}
+        secondary[args.secondary] = sec
+        del f2
+        torch.cuda.empty_cache()
     if rank != 0:
+        if world > 1:
+            torch.distributed.destroy_process_group()
         return
-    main_prec = "fp64" if "fp64" in results else next(iter(results))
+    main_prec = precs[0]
     main = results[main_prec]
-    line = base_line(args, world, main_prec)
-    line.update({"value": main["value"], "ms_per_step": main["ms_per_step"],
-                 "p50_ms": main["p50_ms"], "p99_ms": main["p99_ms"], "hbm_gbs_model": main["hbm_gbs_model"],
-                 "roofline": main["roofline"], "e2e": main["e2e"], "gpu_launches": main["gpu_launches"],
-                 "clocks": clocks, "rel_res": main["rel_res"], "all_converged": main["all_converged"],
-                 "kernels": main["kernels"]})
-    line["config"]["n_cells"] = n3
-    if "mixed" in results and main_prec != "mixed":
-        m = dict(results["mixed"])
-        m.pop("clocks", None)
-        line["mixed"] = m
+    line = base_line(args, world, blocks, main_prec)
+    line.update({k: main[k] for k in ("value", "ms_per_step", "p50_ms", "p99_ms", "cells_per_s", "hbm_gbs_model",
+                                      "roofline", "e2e", "gpu_launches", "clocks", "rel_res", "all_converged",
+                                      "outer_iters", "total_cycles", "kernels", "profiled_ms_per_step")})
+    for prec in precs[1:]:
+        line[prec] = results[prec]
+    if secondary:
+        line["secondary"] = secondary
     if not args.no_cpu_baseline and world == 1:
-        line["cpu_baseline"] = cpu_baseline(args, blocks, f_np, 32)
+        line["cpu_baseline"] = cpu_baseline(blocks, f_np)
     print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()

@@ -48,7 +48,9 @@ typedef enum {
                                      odd for a periodic z, blocks not coarsenable, ...               */
   SNAC_ERR_OOM = -3,              /* device allocation failed                                         */
   SNAC_ERR_CUDA = -4,             /* a CUDA call failed                                               */
-  SNAC_ERR_NOT_CONVERGED = -5,    /* tolerance not reached within max_outer; p holds the last iterate */
+  SNAC_ERR_NOT_CONVERGED = -5,    /* tolerance not reached within max_outer, or a defect-correction
+                                     step did not lower the residual (the floating-point floor);
+                                     p holds the iterate with the smallest residual                   */
   SNAC_ERR_NONFINITE = -6,        /* a residual norm was NaN or Inf (non-finite input)                */
   SNAC_ERR_INCOMPATIBLE_RHS = -7, /* singular problem whose right-hand side has a non-zero mean       */
   SNAC_ERR_TIMEOUT = -8           /* reserved for bounded device-side waits                           */
@@ -241,10 +243,11 @@ int snac_mode_vcycles(snac_plan *plan, const void *d_f, void *d_u, int32_t ncycl
  * block: one block, faces SNAC_BC_DIRICHLET / _NEUMANN / _PERIODIC only (no connectivity), at most
  * SNAC_NOALLOC_MAX_CELLS_PER_AXIS cells per axis (SNAC_ERR_INVALID_ARG otherwise), uniform along z
  * (SNAC_ERR_LAYOUT otherwise). d_rhs, d_p, d_r: device float64 fields [z][y][x]; h_norms: host.
- * The first call on a device looks up the scratch's device address (once per device, with that
- * device current); make that first call before any stream capture. Every call uses the same
- * scratch, so calls whose work overlaps on the GPU (other streams, other host threads) race: issue
- * them one after another. Returns after the work on `stream` is complete. */
+ * Every call looks up the scratch's address on the current device (cudaGetSymbolAddress), copies
+ * the cell widths from host memory and waits for `stream`: do not call it while `stream` is being
+ * captured into a CUDA graph. Every call uses the same scratch, so calls whose work overlaps on the
+ * GPU (other streams, other host threads) race: issue them one after another. Returns after the work
+ * on `stream` is complete. */
 int snac_residual_noalloc(const snac_block *block, const double *d_rhs, const double *d_p, double *d_r,
                           double *h_norms, void *stream);
 

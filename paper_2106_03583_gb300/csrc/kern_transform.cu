@@ -406,7 +406,7 @@ cudaError_t fwd_t(snac_plan* P, const std::vector<ChunkDev>& ch, const ChunkDev*
 
 template <typename T, int TC>
 cudaError_t bwd_t(snac_plan* P, const std::vector<ChunkDev>& ch, const ChunkDev* dch, const void* twb, const void* modes,
-                  double* p3, cudaStream_t s) {
+                  double* p3, double sign, cudaStream_t s) {
   const size_t smem = 2 * (size_t)(P->nz / 2) * TC * sizeof(Cx<T>);
   const double n3 = (double)P->n3;
   // read the modes, read and write the FP64 field
@@ -414,7 +414,7 @@ cudaError_t bwd_t(snac_plan* P, const std::vector<ChunkDev>& ch, const ChunkDev*
   auto go = [&](auto kern) {
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem<T, TC>);
     kern<<<(unsigned)ch.size(), 256, smem, s>>>(dch, P->lev[0].d_blk, P->d_cblk, P->nz, make_tw<T>(P, twb),
-                                                (const T*)modes, p3, P->lev[0].ncell, 1.0 / P->theta);
+                                                (const T*)modes, p3, P->lev[0].ncell, sign / P->theta);
   };
   switch (P->kind) {
     case KIND_PP: go(k_backward<T, TC, KIND_PP>); break;
@@ -436,9 +436,11 @@ cudaError_t launch_forward(snac_plan* P, const double* in3, void* modes, double 
   return fwd_t<float, 16>(P, P->chunks32, P->d_chunks32, P->d_tw32, in3, modes, shift0, false, s);
 }
 
-cudaError_t launch_backward_update(snac_plan* P, const void* modes, double* p3, cudaStream_t s) {
-  if (P->precision == SNAC_FP64) return bwd_t<double, 8>(P, P->chunks64, P->d_chunks64, P->d_tw64, modes, p3, s);
-  return bwd_t<float, 16>(P, P->chunks32, P->d_chunks32, P->d_tw32, modes, p3, s);
+cudaError_t launch_backward_update(snac_plan* P, const void* modes, double* p3, cudaStream_t s, bool subtract) {
+  const double sign = subtract ? -1.0 : 1.0;
+  if (P->precision == SNAC_FP64)
+    return bwd_t<double, 8>(P, P->chunks64, P->d_chunks64, P->d_tw64, modes, p3, sign, s);
+  return bwd_t<float, 16>(P, P->chunks32, P->d_chunks32, P->d_tw32, modes, p3, sign, s);
 }
 
 }  // namespace snac

@@ -9,11 +9,11 @@
 // lives in one file-scope __device__ array of fixed size, which every GPU that loads this library
 // holds until the process exits.
 //
-// The kernels below mirror the plan path's coefficient rules and the residual kernel's order of
-// floating-point operations, so r matches snac_residual bit for bit; the norms are summed in a
-// different grouping and match to rounding.
+// The kernels below follow the plan path's coefficient rules and the residual kernel's chain of
+// FMAs. The z end conditions are folded into the diagonal here (the plan keeps them as mirrored
+// ghosts on the cell itself), and the norms are summed in a different grouping, so r and the norms
+// match snac_residual to rounding, not bit for bit.
 #include <cmath>
-#include <mutex>
 
 #include "kern_common.cuh"
 #include "snac_impl.h"
@@ -38,33 +38,18 @@ constexpr size_t NA_TOTAL = NA_S + 4;
 
 static __device__ __align__(256) double g_noalloc_scratch[NA_TOTAL];
 
-constexpr int NA_MAX_DEV = 64;
-std::mutex g_na_mutex;
-double* g_na_ptr[NA_MAX_DEV] = {};
-
-// Device address of the scratch on the current device, looked up once per device.
+// Device address of the scratch in the current device's context. In host code the array's name
+// only stands for the symbol; the address it has on the GPU comes from the runtime. It is looked up
+// on every call (a host-side table lookup, small next to the launches): an address cached per device
+// would go stale after cudaDeviceReset or any other change of the device's primary context.
 int scratch_on_current_device(double** out) {
-  int dev = -1;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) {
-    set_error(std::string("cudaGetDevice: ") + cudaGetErrorString(e));
+  void* p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+  if (e != cudaSuccess || !p) {
+    set_error(std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
     return SNAC_ERR_CUDA;
   }
-  if (dev < 0 || dev >= NA_MAX_DEV) {
-    set_error("device ordinal above 63");
-    return SNAC_ERR_INVALID_ARG;
-  }
-  std::lock_guard<std::mutex> lock(g_na_mutex);
-  if (!g_na_ptr[dev]) {
-    void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (e != cudaSuccess || !p) {
-      set_error(std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
-      return SNAC_ERR_CUDA;
-    }
-    g_na_ptr[dev] = static_cast<double*>(p);
-  }
-  *out = g_na_ptr[dev];
+  *out = static_cast<double*>(p);
   return SNAC_OK;
 }
 
@@ -167,7 +152,7 @@ __global__ void __launch_bounds__(TILE_THREADS) k_na_resid(const double* __restr
       ap = fma(cz[0], p[self + kd * plane], ap);
       ap = fma(cz[1], p[self + ku * plane], ap);
       ap = fma(dxy + cz[2], pc, ap);
-      const double fv = f[c] - 0.0;
+      const double fv = f[c];
       const double rv = fv - ap;
       r[c] = rv;
       s_r = fma(rv, rv, s_r);

@@ -284,7 +284,8 @@ cudaError_t launch_shift(snac_plan* P, double* p, const double* d_c, cudaStream_
 cudaError_t launch_forward(snac_plan* P, const double* in3, void* modes, double shift0, bool split, cudaStream_t s);
 // Level-0 mode planes from plain to colour-split order.
 cudaError_t launch_to_split(snac_plan* P, const double* src, double* dst, cudaStream_t s);
-cudaError_t launch_backward_update(snac_plan* P, const void* modes, double* p3, cudaStream_t s);
+// p3 += F^-1(modes) / theta; subtract: p3 -= F^-1(modes) / theta (takes a correction back)
+cudaError_t launch_backward_update(snac_plan* P, const void* modes, double* p3, cudaStream_t s, bool subtract = false);
 
 // ---- multigrid ----
 cudaError_t launch_mode_operator(snac_plan* P, const void* u, void* out, cudaStream_t s);

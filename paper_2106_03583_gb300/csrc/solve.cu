@@ -256,12 +256,23 @@ int run_solve(snac_plan* P, const double* f, double* p, double tol, cudaStream_t
     const double rel = rn / fn;
     P->info.rel_res = rel;
     const bool done = rel <= tol;
-    const bool give_up = !done && (k >= P->max_outer || rel > 10.0 * prev_rel);
+    // a correction that did not lower the residual: the inner solve has reached the floating-point
+    // floor of the outer residual (or diverged); more steps would not help
+    const bool stalled = updated && rel >= prev_rel;
+    const bool give_up = !done && (k >= P->max_outer || stalled);
     if (done || give_up) {
       if (P->singular && !updated) {  // the initial guess was kept: return its zero-mean shift
         CK(launch_shift(P, p, P->d_sums + 3, s));
         CK(cudaStreamSynchronize(s));
         profile_resolve(P);
+      }
+      if (stalled) {
+        // return the better iterate: take the last correction back (its modes are still in the
+        // level-0 iterate) and report the residual of what is returned, re-evaluated
+        CK(launch_backward_update(P, P->lev[0].d_u, p, s, true));
+        CK(launch_field3d(P, 0, f, p, P->d_r3, fshift, false, false, s));
+        if ((st = read_sums(P, s))) return st;
+        P->info.rel_res = std::sqrt(P->h_sums[0]) / fn;
       }
       return done ? SNAC_OK : SNAC_ERR_NOT_CONVERGED;
     }

@@ -30,7 +30,9 @@ def _solve_mode(task):
 def oracle_solve(blocks, f, rtol_mode=1e-13, nu1=2, nu2=2, workers=None, modes=None):
     """The oracle's solve (as ``oracle.solve.solve``) with the per-wavenumber solves in a pool.
 
-    Returns (p in the caller layout, per-mode planes Ph, info). With ``modes`` only those
+    Returns (p in the caller layout, per-mode planes Ph, info). info holds the per-mode cycle counts
+    and relative residuals and, for a full solve, the 3-D relative residual ||f - A p|| / ||f|| of the
+    oracle's own solution (the acceptance number of its solve). With ``modes`` only those
     wavenumbers are solved (Ph is zero elsewhere and p is not formed)."""
     from oracle import grid as ogrid
     from oracle import solve as osv
@@ -49,25 +51,30 @@ def oracle_solve(blocks, f, rtol_mode=1e-13, nu1=2, nu2=2, workers=None, modes=N
     workers = workers or min(16, os.cpu_count() or 1, len(tasks))
     Ph = np.zeros_like(Fh)
     cycles = np.zeros(g.nz, dtype=np.int64)
+    mode_res = np.zeros(g.nz)
     ctx = mp.get_context("spawn")
     env = {k: os.environ.get(k) for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")}
     for k in env:
         os.environ[k] = "1"   # one BLAS thread per worker process
     try:
         with ctx.Pool(workers, initializer=_init, initargs=(blocks, nu1, nu2)) as pool:
-            for q, u, c, _ in pool.imap_unordered(_solve_mode, tasks, chunksize=1):
+            for q, u, c, res in pool.imap_unordered(_solve_mode, tasks, chunksize=1):
                 Ph[q] = u
                 cycles[q] = c
+                mode_res[q] = res
     finally:
         for k, v in env.items():
             if v is None:
                 os.environ.pop(k, None)
             else:
                 os.environ[k] = v
-    info = {"removed_mean": mean, "cycles": cycles, "singular": g.singular}
+    info = {"removed_mean": mean, "cycles": cycles, "mode_rel_res": mode_res, "singular": g.singular}
     if modes is not None:
         return None, Ph, info
     P = T.backward(g.kind, Ph)
     if g.singular:
         P = P - float((g.vol * P).sum()) / float(g.vol.sum())
-    return g.from_planes(P), Ph, info
+    p = g.from_planes(P)
+    del P
+    info["rel_res"] = osv.rel_residual(blocks, f, p)
+    return p, Ph, info

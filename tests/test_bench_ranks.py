@@ -73,3 +73,32 @@ def test_single_rank_needs_no_process_group():
     import bench
     assert bench.max_over_ranks(3.5, 1, "cpu") == 3.5
     assert bench.whole_job_rate(1, 4, 1000.0) == pytest.approx(4.0)
+
+
+def test_reference_arm_line_has_the_gpu_arms_config(capsys):
+    """The reference arm (the CPU oracle on bounded samples) prints one line on the same config dict,
+    metric and unit as the GPU arm, with its step time and the oracle's cpu_baseline record."""
+    import json
+    sys.path.insert(0, ROOT)
+    import bench
+    from paper_2106_03583_gb300 import inputs
+    args = bench.argparse.Namespace(workload="c64", seed=0, steps=2, warmup=1, tol=1e-10, precisions="mixed,fp64")
+    bench.run_reference(args)
+    line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
+    blocks, _ = inputs.config("c64", seed=0)
+    assert line["config"] == bench.workload_config("c64", blocks, 1e-10, "mixed", 1)
+    assert line["impl"] == "reference" and line["metric"] == bench.METRIC and line["unit"] == "solves/s"
+    assert line["value"] > 0 and line["ms_per_step"] > 0 and line["higher_is_better"] is True
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["value"] == line["value"]
+    assert line["e2e"]["h2d_bytes_per_step"] == 0
+
+
+def test_cpu_baseline_reports_single_thread_and_all_cores():
+    sys.path.insert(0, ROOT)
+    import bench
+    from paper_2106_03583_gb300 import inputs
+    blocks, f = inputs.config("c64", seed=0)
+    cb = bench.cpu_baseline(blocks, f)
+    assert cb["kind"] == "oracle" and cb["single_thread"]["cores"] == 1
+    assert cb["cores"] == cb["all_cores"]["cores"] >= 1 and cb["value"] == cb["all_cores"]["value"] > 0
+    assert cb["single_thread"]["value"] > 0

@@ -9,7 +9,13 @@ For each, the oracle solves the same seeded problem in full (every wavenumber to
 residual of 1e-13, spread over host processes), and the GPU solutions must match it within 1e-9
 relative L2. Independently of the oracle's solve, the GPU solution's 3-D residual is re-evaluated
 with the oracle's own operator (Eq. 8), and for the singular problem its volume-weighted mean must be
-zero (the tie-break of the singular case)."""
+zero (the tie-break of the singular case).
+
+The oracle's own convergence is asserted too: its 3-D relative residual at most 1e-11 (ten times
+below the GPU's tolerance) and no wavenumber left above 1e-12. Each wavenumber is solved to 1e-13 or
+to the floor where a V-cycle stops reducing its residual; measured on these problems: 3-D residual
+7.3e-13 (mb2x2) and 1.7e-12 (chan), the largest per-mode residual 2.8e-13 / 5.6e-13, at q = 0 (the
+smoothest mode, whose FP64 residual floor is highest)."""
 import time
 
 import numpy as np
@@ -52,6 +58,8 @@ def test_full_size_vs_oracle(name, precisions):
     t1 = time.time()
     po, _, oinfo = oracle_solve(blocks, f)
     t2 = time.time()
+    assert oinfo["rel_res"] <= 1e-11, oinfo["rel_res"]
+    assert float(np.max(oinfo["mode_rel_res"])) <= 1e-12, np.max(oinfo["mode_rel_res"])
     g = ogrid.Grid(blocks)
     report = {}
     for prec, (p, info) in sols.items():
@@ -64,5 +72,6 @@ def test_full_size_vs_oracle(name, precisions):
         if g.singular:
             vol = g.from_planes(g.vol)
             assert abs(np.dot(vol, p)) <= 1e-12 * np.dot(vol, np.abs(p))
-    print(f"\n{name}: inputs+GPU {t1 - t0:.1f} s, oracle {t2 - t1:.1f} s, checks {time.time() - t2:.1f} s; "
+    print(f"\n{name}: inputs+GPU {t1 - t0:.1f} s, oracle {t2 - t1:.1f} s (its rel_res {oinfo['rel_res']:.2e}), "
+          f"checks {time.time() - t2:.1f} s; "
           + "; ".join(f"{k}: rel_res {a:.2e} (oracle operator {b:.2e}) rel L2 {c:.2e}" for k, (a, b, c) in report.items()))

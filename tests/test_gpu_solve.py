@@ -242,3 +242,33 @@ def test_errors():
         pl.solve(dev(f).float(), p)
     with pytest.raises(ValueError):
         pl.solve(dev(f)[:-1], p)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_stalled_solve_returns_its_best_iterate(precision):
+    """A tolerance below the floating-point floor of the FP64 outer residual: the defect correction
+    stops at the first step that does not lower the residual (instead of running max_outer steps),
+    takes that step back and returns NOT_CONVERGED with the better iterate. The reported residual is
+    that of the returned solution (re-evaluated independently here), it sits at the floor, and the
+    solution still matches the oracle's."""
+    import torch
+    blocks, f = inputs.config("mb2x2", seed=3, scale=8)
+    pref, _ = osv.solve(blocks, f)
+    pl = plan(blocks, precision=precision, max_outer=20)
+    fd = dev(f)
+    p = torch.zeros_like(fd)
+    info = pl.solve(fd, p, tol=1e-19, raise_on_error=False)
+    assert info["status_name"] == "NOT_CONVERGED"
+    assert info["outer_iters"] < 20                       # stopped by the stall, not by max_outer
+    r = torch.empty_like(fd)
+    r2, f2 = pl.residual(fd, p, r)
+    # (the solve's residual is that of f minus its round-off mean, about 1e-17: hence rel=1e-3)
+    assert info["rel_res"] == pytest.approx(np.sqrt(r2 / f2), rel=1e-3)
+    assert info["rel_res"] <= 1e-12
+    assert osv.rel_residual(blocks, f, host(p)) <= 1e-12
+    assert rel(host(p), pref) <= PARITY
+    # the same solve asked for a reachable tolerance converges to it: the stall is the floor
+    p2 = torch.zeros_like(fd)
+    info2 = pl.solve(fd, p2, tol=1e-11)
+    assert info2["status"] == 0 and info2["outer_iters"] <= info["outer_iters"]
+    pl.close()
