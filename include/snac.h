@@ -102,6 +102,12 @@ typedef struct {
                           method applies to unchanged (Sec. 3.3, footnote); every reduced equation
                           (Eq. 9) gets the extra diagonal s, and s < 0 removes the null space of the
                           periodic / all-Neumann case (no mean is removed then)                     */
+  int32_t mode_begin, mode_end; /* (0, 0): every wavenumber. Otherwise 0 <= mode_begin < mode_end <= n_z
+                          gives a wavenumber-range plan: one rank's slab of wavenumbers in a solve
+                          sharded over several GPUs (App. A, Algorithm 3). Its mode-space fields hold
+                          wavenumbers mode_begin .. mode_end - 1 only (local index q - mode_begin);
+                          it has no 3-D field, so the calls on 3-D fields return
+                          SNAC_ERR_INVALID_ARG, and the pencil calls below take their place          */
 } snac_options;
 
 /* Result of the last solve of a plan. */
@@ -212,6 +218,17 @@ int snac_apply_operator(snac_plan *plan, const double *d_p, double *d_out, void 
 int snac_residual(snac_plan *plan, const double *d_rhs, const double *d_p, double *d_r, double *h_norms,
                   void *stream);
 
+/* The same residual in float-float arithmetic, rounded to FP32: the pass that mixed plans use for
+ * their intermediate defect-correction steps (Eq. 8). d_rhs, d_p: float64 3-D fields; d_r: float32
+ * 3-D field in the same layout. Each float64 operand is split into two floats (47 significant bits)
+ * and the stencil is summed in float-float arithmetic, so |r - (f - A p)| stays below a few units of
+ * 2^-47 (|f| + sum |c p|) per cell before the final rounding to FP32; no FP64 instruction runs per
+ * cell. Operands below 2^-103 in magnitude count as zero; operands beyond the FP32 range give a
+ * non-finite r. h_norms[0] = ||r||^2, h_norms[1] = ||rhs||^2, summed from FP32 squares (for fields
+ * whose values lie within about 1e-15 .. 1e15). Works on plans of either precision. */
+int snac_residual_ff(snac_plan *plan, const double *d_rhs, const double *d_p, float *d_r, double *h_norms,
+                     void *stream);
+
 /* Forward transform along z (Table 1 F, Algorithm 1 first loop): d_in float64 3-D field ->
  * d_modes mode-space field of the plan's inner type. */
 int snac_forward_transform(snac_plan *plan, const double *d_in, void *d_modes, void *stream);
@@ -227,6 +244,53 @@ int snac_mode_operator(snac_plan *plan, const void *d_u, void *d_out, void *stre
 /* ncycles V(nu1, nu2) cycles of the reduced equations (Eq. 9) for every wavenumber, in place on
  * d_u, with right-hand side d_f (mode-space fields of the plan's inner type). */
 int snac_mode_vcycles(snac_plan *plan, const void *d_f, void *d_u, int32_t ncycles, void *stream);
+
+/* ---- One rank of a solve sharded by wavenumber (App. A, Algorithm 3) ----
+ *
+ * The x-y cells of the problem are split into pencils (contiguous ranges of the level-0 plane
+ * numbering: blocks in id order, [y][x] within a block), each held by one rank with every z plane;
+ * the wavenumbers into slabs. A rank transforms its pencil (snac_pencil_forward), the slabs are
+ * exchanged (all-to-all, outside the library), each rank solves the reduced equations of its slab
+ * (snac_mode_solve on a wavenumber-range plan), the solutions are exchanged back and each rank
+ * updates its pencil (snac_pencil_backward_update). The outer FP64 residual of a pencil needs the
+ * values of p in the neighbouring columns held by other ranks (snac_pencil_setup lists them).
+ * A pencil field is [z][c] (the ncols columns fastest), float64; its mode field [q][c], of the
+ * plan's inner type, for every q of the n_z-point transform. The calls accept any plan of the
+ * problem (full or wavenumber-range) and return after their work on `stream` is complete. */
+
+/* Forward transform along z (Table 1) of ncols columns: d_in [n_z][ncols] float64 ->
+ * d_modes [n_z][ncols] of the plan's inner type (Algorithm 3, first loop). */
+int snac_pencil_forward(snac_plan *plan, int64_t ncols, const double *d_in, void *d_modes, void *stream);
+
+/* d_p [n_z][ncols] += F^-1(d_modes) / theta (Algorithm 3, last loop). */
+int snac_pencil_backward_update(snac_plan *plan, int64_t ncols, const void *d_modes, double *d_p, void *stream);
+
+/* Describe this rank's pencil: plane cells c0 .. c0 + ncols - 1. The cells of other ranks that the
+ * pencil's x-y stencil reaches (across blocks and periodic faces too) are written to h_halo in
+ * increasing order, at most max_halo of them (*nhalo receives the count; SNAC_ERR_INVALID_ARG if it
+ * exceeds max_halo). The pencil residual reads p as [z][ncols + nhalo]: the pencil's columns, then
+ * the halo columns in that order. Replaces the plan's previous pencil. */
+int snac_pencil_setup(snac_plan *plan, int64_t c0, int64_t ncols, int64_t *h_halo, int64_t max_halo,
+                      int64_t *nhalo);
+
+/* r = (f - fshift) - A p on the pencil (Eq. 8, FP64): d_f, d_r [n_z][ncols]; d_p_ext
+ * [n_z][ncols + nhalo]. h_sums[5] receives the pencil's ||r||^2, ||f - fshift||^2, sum V p,
+ * sum V (f - fshift), sum V |f - fshift| (V = cell volume). */
+int snac_pencil_residual(snac_plan *plan, const double *d_f, const double *d_p_ext, double *d_r, double fshift,
+                         double *h_sums, void *stream);
+
+/* Solve the reduced equations (Eq. 9) of the plan's wavenumbers (every one for a full plan, the
+ * range of a wavenumber-range plan): d_rhs, d_sol [local q][plane cell] of the plan's inner type.
+ * Each wavenumber runs V-cycles from zero until w_q ||r_q||^2 <= target^2 / n_z (w_q the transform's
+ * Parseval weight), it stagnates, or max_cycles: the per-mode stopping rule of snac_poisson_solve,
+ * which makes the 3-D residual after the update at most `target` over all ranks together. */
+int snac_mode_solve(snac_plan *plan, const void *d_rhs, void *d_sol, double target, void *stream);
+
+/* Singular problems (see snac_poisson_solve): shift the wavenumber-0 plane of d_sol by a constant so
+ * that the updated p keeps a zero volume-weighted mean, given sum_vp = sum V p of the current p over
+ * the whole problem (all ranks). A no-op for non-singular problems and for plans that do not hold
+ * wavenumber 0. */
+int snac_mode_fix_mean(snac_plan *plan, void *d_sol, double sum_vp, void *stream);
 
 /* ---- Allocation-free residual of one block (the paper has no counterpart) ---- */
 

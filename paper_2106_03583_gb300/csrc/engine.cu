@@ -394,6 +394,7 @@ int snac_engine_submit(snac_engine* e, int32_t nblocks, const snac_block* blocks
                        const snac_options* opt, const double* h_rhs, double* h_p, double tol, int64_t* ticket) {
   if (!e || !blocks || nblocks < 1 || !h_rhs || !h_p || !ticket || !(tol > 0.0) || !std::isfinite(tol))
     return SNAC_ERR_INVALID_ARG;
+  if (opt && (opt->mode_begin != 0 || opt->mode_end != 0)) return SNAC_ERR_INVALID_ARG;  // whole solves only
   int st = snac::check_layout(nblocks, blocks, homog_axis);
   if (st) return st;
   Request* r = new (std::nothrow) Request();

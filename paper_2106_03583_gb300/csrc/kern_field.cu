@@ -217,7 +217,7 @@ __global__ void k_mean_of_p(double* sums, double vol_total) { sums[3] = sums[2] 
 template <int MODE, bool SH, bool F2, bool VP>
 void field3d_t(const LevelView<double>& L, dim3 grid, snac_plan* P, const double* f, const double* p, double* r,
                double fshift, cudaStream_t s) {
-  k_field3d<MODE, SH, F2, VP><<<grid, TILE_THREADS, 0, s>>>(L, P->d_cblk, P->d_cz, P->nz, P->kind == KIND_PP, P->cz[0].d,
+  k_field3d<MODE, SH, F2, VP><<<grid, TILE_THREADS, 0, s>>>(L, P->d_cblk, P->d_cz, P->nzt, P->kind == KIND_PP, P->cz[0].d,
                                                              P->dz, f, p, r, fshift, P->d_partial);
 }
 
@@ -231,7 +231,7 @@ void residual_t(const LevelView<double>& L, dim3 grid, snac_plan* P, const doubl
 }
 
 dim3 field_grid(const snac_plan* P) {
-  return dim3((unsigned)P->lev[0].tiles.size(), (unsigned)std::min(P->nz, ZSPLIT));
+  return dim3((unsigned)P->lev[0].tiles.size(), (unsigned)std::min(P->nzt, ZSPLIT));
 }
 
 }  // namespace
@@ -264,9 +264,9 @@ cudaError_t launch_prepass(snac_plan* P, const double* f, const double* p, cudaS
     // read f and p (the flag is zero: set at plan creation, reset by the reduction that reads it)
     LaunchScope ls(P, K_FIELD3D, 16.0 * n3, (P->singular ? 7.0 : 2.0) * n3, s);
     if (P->singular)
-      k_prepass<true><<<grid, TILE_THREADS, 0, s>>>(L, P->d_cblk, P->nz, P->dz, f, p, P->d_partial, P->d_flag);
+      k_prepass<true><<<grid, TILE_THREADS, 0, s>>>(L, P->d_cblk, P->nzt, P->dz, f, p, P->d_partial, P->d_flag);
     else
-      k_prepass<false><<<grid, TILE_THREADS, 0, s>>>(L, P->d_cblk, P->nz, P->dz, f, p, P->d_partial, P->d_flag);
+      k_prepass<false><<<grid, TILE_THREADS, 0, s>>>(L, P->d_cblk, P->nzt, P->dz, f, p, P->d_partial, P->d_flag);
   }
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   const int npart = (int)(grid.x * grid.y);
@@ -300,7 +300,7 @@ cudaError_t launch_fill(double* d, int n, double v, cudaStream_t s) {
 }
 
 cudaError_t launch_fix_mean(snac_plan* P, void* u0, cudaStream_t s) {
-  const double alpha = P->dz * P->nz / P->theta;
+  const double alpha = P->dz * P->nzt / P->theta;
   const long long n = P->lev[0].ncell;
   const int w = plan_inner_size(P);
   const int ctas = std::min(MEAN_CTAS, P->npartial);  // one partial per CTA, d_partial holds npartial

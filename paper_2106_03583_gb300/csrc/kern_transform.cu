@@ -164,10 +164,10 @@ __device__ __forceinline__ long long chunk_columns(const ChunkDev& ch, const Blo
   return C.s[2];
 }
 
-template <typename T, int TC, int KIND>
+template <typename T, int TC, int KIND, typename TI>
 __global__ void __launch_bounds__(256) k_forward(const ChunkDev* __restrict__ chunks, const BlockDev* __restrict__ blk,
                                                  const CallerBlk* __restrict__ cb, int n, Tw<T> tw,
-                                                 const double* __restrict__ in3, T* __restrict__ out, long long ncell,
+                                                 const TI* __restrict__ in3, T* __restrict__ out, long long ncell,
                                                  T sub0, int split) {
   constexpr int kind = KIND;
   extern __shared__ __align__(16) unsigned char smem[];
@@ -187,12 +187,12 @@ __global__ void __launch_bounds__(256) k_forward(const ChunkDev* __restrict__ ch
   // sk == 1: the homogeneous axis is the caller's contiguous one, consecutive threads run along it
   const bool along = sk == 1;
   for (int i0 = threadIdx.x; i0 < n * TC; i0 += LBATCH * blockDim.x) {
-    double v[LBATCH];
+    TI v[LBATCH];
 #pragma unroll
     for (int u = 0; u < LBATCH; ++u) {
       const int idx = i0 + u * blockDim.x;
       const int k = along ? idx % n : idx / TC, c = along ? idx / n : idx % TC;
-      v[u] = idx < n * TC && c < ch.ncol ? in3[coff[c] + k * sk] : 0.0;
+      v[u] = idx < n * TC && c < ch.ncol ? in3[coff[c] + k * sk] : (TI)0;
     }
 #pragma unroll
     for (int u = 0; u < LBATCH; ++u) {
@@ -378,43 +378,55 @@ Tw<T> make_tw(const snac_plan* P, const void* base) {
   return Tw<T>{t + P->tw.fft, t + P->tw.twn, t + P->tw.tw2n, t + P->tw.tw4a, t + P->tw.tw4b};
 }
 
-template <typename T, int TC>
-cudaError_t fwd_t(snac_plan* P, const std::vector<ChunkDev>& ch, const ChunkDev* dch, const void* twb, const double* in3,
-                  void* modes, double shift0, bool split, cudaStream_t s) {
+// Where a transform's columns live: the block table and caller offsets/strides of the 3-D field,
+// the cells of one mode plane of the output, and the field's cell count. The plan's own field, or a
+// pencil of a sharded solve (one pseudo-block of ncols columns, [z][c] layout).
+struct Geom {
+  const BlockDev* blk;
+  const CallerBlk* cb;
+  long long ncell;
+  double n3;
+};
+
+Geom plan_geom(const snac_plan* P) { return Geom{P->lev[0].d_blk, P->d_cblk, P->lev[0].ncell, (double)P->n3}; }
+
+template <typename T, int TC, typename TI = double>
+cudaError_t fwd_t(snac_plan* P, const Geom& G, const std::vector<ChunkDev>& ch, const ChunkDev* dch, const void* twb,
+                  const TI* in3, void* modes, double shift0, bool split, cudaStream_t s) {
   // F(1) in mode 0: n for the real DFT (half-complex), 2n for the DCT-II; the other kinds have no
   // zero eigenvalue and are never shifted
-  const double f1 = P->kind == KIND_PP ? (double)P->nz : 2.0 * P->nz;
+  const double f1 = P->kind == KIND_PP ? (double)P->nzt : 2.0 * P->nzt;
   const T sub0 = (T)(shift0 * f1);
-  const size_t smem = 2 * (size_t)(P->nz / 2) * TC * sizeof(Cx<T>);
-  const double n3 = (double)P->n3;
-  // read the FP64 field, write the modes; FFT model 2.5 log2(n) flops per point plus pre/post-processing
-  LaunchScope ls(P, K_FORWARD, (8.0 + sizeof(T)) * n3, (2.5 * std::log2((double)P->nz) + 8.0) * n3, s);
+  const size_t smem = 2 * (size_t)(P->nzt / 2) * TC * sizeof(Cx<T>);
+  const double n3 = G.n3;
+  // read the 3-D field, write the modes; FFT model 2.5 log2(n) flops per point plus pre/post-processing
+  LaunchScope ls(P, K_FORWARD, (double)(sizeof(TI) + sizeof(T)) * n3, (2.5 * std::log2((double)P->nzt) + 8.0) * n3, s);
   auto go = [&](auto kern) {
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem<T, TC>);
-    kern<<<(unsigned)ch.size(), 256, smem, s>>>(dch, P->lev[0].d_blk, P->d_cblk, P->nz, make_tw<T>(P, twb), in3,
-                                                (T*)modes, P->lev[0].ncell, sub0, split ? 1 : 0);
+    kern<<<(unsigned)ch.size(), 256, smem, s>>>(dch, G.blk, G.cb, P->nzt, make_tw<T>(P, twb), in3, (T*)modes, G.ncell,
+                                                sub0, split ? 1 : 0);
   };
   switch (P->kind) {
-    case KIND_PP: go(k_forward<T, TC, KIND_PP>); break;
-    case KIND_NN: go(k_forward<T, TC, KIND_NN>); break;
-    case KIND_DD: go(k_forward<T, TC, KIND_DD>); break;
-    case KIND_ND: go(k_forward<T, TC, KIND_ND>); break;
-    default: go(k_forward<T, TC, KIND_DN>); break;
+    case KIND_PP: go(k_forward<T, TC, KIND_PP, TI>); break;
+    case KIND_NN: go(k_forward<T, TC, KIND_NN, TI>); break;
+    case KIND_DD: go(k_forward<T, TC, KIND_DD, TI>); break;
+    case KIND_ND: go(k_forward<T, TC, KIND_ND, TI>); break;
+    default: go(k_forward<T, TC, KIND_DN, TI>); break;
   }
   return cudaGetLastError();
 }
 
 template <typename T, int TC>
-cudaError_t bwd_t(snac_plan* P, const std::vector<ChunkDev>& ch, const ChunkDev* dch, const void* twb, const void* modes,
-                  double* p3, double sign, cudaStream_t s) {
-  const size_t smem = 2 * (size_t)(P->nz / 2) * TC * sizeof(Cx<T>);
-  const double n3 = (double)P->n3;
+cudaError_t bwd_t(snac_plan* P, const Geom& G, const std::vector<ChunkDev>& ch, const ChunkDev* dch, const void* twb,
+                  const void* modes, double* p3, double sign, cudaStream_t s) {
+  const size_t smem = 2 * (size_t)(P->nzt / 2) * TC * sizeof(Cx<T>);
+  const double n3 = G.n3;
   // read the modes, read and write the FP64 field
-  LaunchScope ls(P, K_BACKWARD, (16.0 + sizeof(T)) * n3, (2.5 * std::log2((double)P->nz) + 10.0) * n3, s);
+  LaunchScope ls(P, K_BACKWARD, (16.0 + sizeof(T)) * n3, (2.5 * std::log2((double)P->nzt) + 10.0) * n3, s);
   auto go = [&](auto kern) {
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem<T, TC>);
-    kern<<<(unsigned)ch.size(), 256, smem, s>>>(dch, P->lev[0].d_blk, P->d_cblk, P->nz, make_tw<T>(P, twb),
-                                                (const T*)modes, p3, P->lev[0].ncell, sign / P->theta);
+    kern<<<(unsigned)ch.size(), 256, smem, s>>>(dch, G.blk, G.cb, P->nzt, make_tw<T>(P, twb), (const T*)modes, p3,
+                                                G.ncell, sign / P->theta);
   };
   switch (P->kind) {
     case KIND_PP: go(k_backward<T, TC, KIND_PP>); break;
@@ -432,15 +444,71 @@ cudaError_t launch_forward(snac_plan* P, const double* in3, void* modes, double 
   if (shift0 != 0.0 && P->kind != KIND_PP && P->kind != KIND_NN) return cudaErrorInvalidValue;
   if (split && P->precision != SNAC_FP64) return cudaErrorInvalidValue;
   if (P->precision == SNAC_FP64)
-    return fwd_t<double, 8>(P, P->chunks64, P->d_chunks64, P->d_tw64, in3, modes, shift0, split, s);
-  return fwd_t<float, 16>(P, P->chunks32, P->d_chunks32, P->d_tw32, in3, modes, shift0, false, s);
+    return fwd_t<double, 8>(P, plan_geom(P), P->chunks64, P->d_chunks64, P->d_tw64, in3, modes, shift0, split, s);
+  return fwd_t<float, 16>(P, plan_geom(P), P->chunks32, P->d_chunks32, P->d_tw32, in3, modes, shift0, false, s);
+}
+
+cudaError_t launch_forward_f32(snac_plan* P, const float* in3, void* modes, cudaStream_t s) {
+  if (P->precision != SNAC_MIXED) return cudaErrorInvalidValue;
+  return fwd_t<float, 16, float>(P, plan_geom(P), P->chunks32, P->d_chunks32, P->d_tw32, in3, modes, 0.0, false, s);
 }
 
 cudaError_t launch_backward_update(snac_plan* P, const void* modes, double* p3, cudaStream_t s, bool subtract) {
   const double sign = subtract ? -1.0 : 1.0;
   if (P->precision == SNAC_FP64)
-    return bwd_t<double, 8>(P, P->chunks64, P->d_chunks64, P->d_tw64, modes, p3, sign, s);
-  return bwd_t<float, 16>(P, P->chunks32, P->d_chunks32, P->d_tw32, modes, p3, sign, s);
+    return bwd_t<double, 8>(P, plan_geom(P), P->chunks64, P->d_chunks64, P->d_tw64, modes, p3, sign, s);
+  return bwd_t<float, 16>(P, plan_geom(P), P->chunks32, P->d_chunks32, P->d_tw32, modes, p3, sign, s);
+}
+
+// Pencil of a sharded solve: ncols columns stored [z][c], one pseudo-block (nx = ncols, ny = 1,
+// caller strides 1, ncols, ncols), its chunk tables built on the first use of this width.
+static cudaError_t pencil_tables(snac_plan* P, long long ncols) {
+  if (P->pen_tcols == ncols) return cudaSuccess;
+  for (void* p : P->pen_tallocs) cudaFree(p);
+  P->pen_tallocs.clear();
+  P->pen_tcols = -1;
+  if (ncols < 1 || ncols >= (1LL << 31)) return cudaErrorInvalidValue;
+  BlockDev b{};
+  b.off = 0;
+  b.nx = (int)ncols;
+  b.ny = 1;
+  for (int f = 0; f < 4; ++f) b.nbr[f] = -1;
+  const CallerBlk c{0, {1, ncols, ncols}};
+  P->pen_ch64.clear();
+  P->pen_ch32.clear();
+  for (long long c0 = 0; c0 < ncols; c0 += 8) P->pen_ch64.push_back({0, (int)c0, (int)std::min<long long>(8, ncols - c0), 0});
+  for (long long c0 = 0; c0 < ncols; c0 += 16) P->pen_ch32.push_back({0, (int)c0, (int)std::min<long long>(16, ncols - c0), 0});
+  auto put = [&](auto** d, const void* src, size_t bytes) -> cudaError_t {
+    cudaError_t e = cudaMalloc((void**)d, bytes);
+    if (e != cudaSuccess) return e;
+    P->pen_tallocs.push_back(*d);
+    return cudaMemcpy(*d, src, bytes, cudaMemcpyHostToDevice);
+  };
+  cudaError_t e;
+  if ((e = put(&P->d_pen_tblk, &b, sizeof b)) != cudaSuccess || (e = put(&P->d_pen_tcb, &c, sizeof c)) != cudaSuccess ||
+      (e = put(&P->d_pen_ch64, P->pen_ch64.data(), P->pen_ch64.size() * sizeof(ChunkDev))) != cudaSuccess ||
+      (e = put(&P->d_pen_ch32, P->pen_ch32.data(), P->pen_ch32.size() * sizeof(ChunkDev))) != cudaSuccess)
+    return e;
+  P->pen_tcols = ncols;
+  return cudaSuccess;
+}
+
+cudaError_t launch_pencil_forward(snac_plan* P, long long ncols, const double* in, void* modes, cudaStream_t s) {
+  cudaError_t e = pencil_tables(P, ncols);
+  if (e != cudaSuccess) return e;
+  const Geom G{P->d_pen_tblk, P->d_pen_tcb, ncols, (double)ncols * P->nzt};
+  if (P->precision == SNAC_FP64)
+    return fwd_t<double, 8>(P, G, P->pen_ch64, P->d_pen_ch64, P->d_tw64, in, modes, 0.0, false, s);
+  return fwd_t<float, 16>(P, G, P->pen_ch32, P->d_pen_ch32, P->d_tw32, in, modes, 0.0, false, s);
+}
+
+cudaError_t launch_pencil_backward(snac_plan* P, long long ncols, const void* modes, double* p, cudaStream_t s) {
+  cudaError_t e = pencil_tables(P, ncols);
+  if (e != cudaSuccess) return e;
+  const Geom G{P->d_pen_tblk, P->d_pen_tcb, ncols, (double)ncols * P->nzt};
+  if (P->precision == SNAC_FP64)
+    return bwd_t<double, 8>(P, G, P->pen_ch64, P->d_pen_ch64, P->d_tw64, modes, p, 1.0, s);
+  return bwd_t<float, 16>(P, G, P->pen_ch32, P->d_pen_ch32, P->d_tw32, modes, p, 1.0, s);
 }
 
 }  // namespace snac

@@ -422,7 +422,7 @@ int build_coarse(snac_plan* P) {
 }
 
 int build_twiddles(snac_plan* P) {
-  const int n = P->nz, m = n / 2;
+  const int n = P->nzt, m = n / 2;
   TwiddleOffsets& t = P->tw;
   t.fft = 0;
   t.twn = t.fft + m;
@@ -509,6 +509,8 @@ void free_plan(snac_plan* P) {
     if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
   if (P->capture_stream) cudaStreamDestroy(P->capture_stream);
   for (void* p : P->allocs) cudaFree(p);
+  for (void* p : P->pen_tallocs) cudaFree(p);
+  for (void* p : P->pen_allocs) cudaFree(p);
   if (P->h_sums) cudaFreeHost(P->h_sums);
   if (P->h_mode_norm2) cudaFreeHost(P->h_mode_norm2);
   if (P->h_active) cudaFreeHost(P->h_active);
@@ -684,7 +686,17 @@ int create(snac_plan** out, int32_t nblocks, const snac_block* blocks_in, int32_
     P->sms = 152;
   }
   P->nblk = nblocks;
-  P->nz = hb[0].n[2];
+  P->nzt = hb[0].n[2];
+  P->nz = P->nzt;
+  if (opt && (opt->mode_begin != 0 || opt->mode_end != 0)) {
+    if (opt->mode_begin < 0 || opt->mode_end <= opt->mode_begin || opt->mode_end > P->nzt) {
+      delete P;
+      return fail(SNAC_ERR_INVALID_ARG, "mode_begin/mode_end must satisfy 0 <= mode_begin < mode_end <= n_z");
+    }
+    P->q0 = opt->mode_begin;
+    P->nz = opt->mode_end - opt->mode_begin;
+    P->ranged = true;
+  }
   P->dz = hb[0].w[2][0];
   const int zl = hb[0].bc[2][0], zh = hb[0].bc[2][1];
   if (zl == SNAC_BC_PERIODIC) P->kind = KIND_PP;
@@ -692,7 +704,7 @@ int create(snac_plan** out, int32_t nblocks, const snac_block* blocks_in, int32_
   else if (zl == SNAC_BC_DIRICHLET && zh == SNAC_BC_DIRICHLET) P->kind = KIND_DD;
   else if (zl == SNAC_BC_NEUMANN) P->kind = KIND_ND;
   else P->kind = KIND_DN;
-  P->theta = P->kind == KIND_PP ? P->nz : 2.0 * P->nz;
+  P->theta = P->kind == KIND_PP ? P->nzt : 2.0 * P->nzt;
   bool dirichlet_xy = false;
   for (const HBlock& h : hb)
     for (int a = 0; a < 2; ++a)
@@ -722,7 +734,7 @@ int create(snac_plan** out, int32_t nblocks, const snac_block* blocks_in, int32_
     P->area_total += ax * ay;
   }
   P->n3 = off3;
-  P->vol_total = P->area_total * P->dz * P->nz;
+  P->vol_total = P->area_total * P->dz * P->nzt;
 
   do {
     if ((st = build_levels(P, hb))) break;
@@ -733,21 +745,56 @@ int create(snac_plan** out, int32_t nblocks, const snac_block* blocks_in, int32_
     // itself: Neumann ghost = p_0 (coefficient +1/dz^2), Dirichlet ghost = -p_0 (-1/dz^2); the
     // diagonal is then -2/dz^2 on every plane, and carries the Helmholtz shift.
     const double iz2 = 1.0 / (P->dz * P->dz);
-    for (int k = 0; k < P->nz; ++k) {
+    for (int k = 0; k < P->nzt; ++k) {
       const bool per = P->kind == KIND_PP;
       Coef<double> c{iz2, iz2, -2.0 * iz2 + P->shift, P->dz};
       if (!per && k == 0) c.lo = zl == SNAC_BC_DIRICHLET ? -iz2 : iz2;
-      if (!per && k == P->nz - 1) c.hi = zh == SNAC_BC_DIRICHLET ? -iz2 : iz2;
+      if (!per && k == P->nzt - 1) c.hi = zh == SNAC_BC_DIRICHLET ? -iz2 : iz2;
       P->cz.push_back(c);
     }
     if ((st = upload(P, &P->d_cz, P->cz)) || (st = upload(P, &P->d_cblk, P->cblk))) break;
-    for (int q = 0; q < P->nz; ++q) {
-      P->sigma.push_back(mode_lambda(P->kind, P->nz, q) * iz2 + P->shift);
-      P->pweight.push_back(parseval_weight(P->kind, P->nz, q));
+    {
+      std::vector<float4> czff(P->nzt);
+      for (int k = 0; k < P->nzt; ++k) {
+        const float lh = (float)P->cz[k].lo, hh = (float)P->cz[k].hi;
+        czff[k] = make_float4(lh, (float)(P->cz[k].lo - (double)lh), hh, (float)(P->cz[k].hi - (double)hh));
+      }
+      if ((st = upload(P, &P->d_czff, czff))) break;
+      if (P->precision == SNAC_MIXED && !P->ranged) {
+        auto pair = [](double v, float& h, float& l) {
+          h = (float)v;
+          l = (float)(v - (double)h);
+        };
+        const HostLevel& l0 = P->lev[0];
+        std::vector<float4> cxf(l0.cx.size()), cyf(l0.cy.size());
+        for (size_t i = 0; i < l0.cx.size(); ++i) {
+          pair(l0.cx[i].lo, cxf[i].x, cxf[i].y);
+          pair(l0.cx[i].hi, cxf[i].z, cxf[i].w);
+        }
+        for (size_t j = 0; j < l0.cy.size(); ++j) {
+          pair(l0.cy[j].lo, cyf[j].x, cyf[j].y);
+          pair(l0.cy[j].hi, cyf[j].z, cyf[j].w);
+        }
+        // the diagonal in the order the FP64 residual forms it: (cx.d + cy.d) + cz.d
+        std::vector<float2> dgf(l0.ncell);
+        for (const BlockDev& d : l0.blk)
+          for (int j = 0; j < d.ny; ++j)
+            for (int i = 0; i < d.nx; ++i) {
+              const long long c = d.off + (long long)j * d.nx + i;
+              pair(l0.cx[d.xo + i].d + l0.cy[d.yo + j].d + P->cz[0].d, dgf[c].x, dgf[c].y);
+            }
+        if ((st = upload(P, &P->d_cxff, cxf)) || (st = upload(P, &P->d_cyff, cyf)) || (st = upload(P, &P->d_dgff, dgf)))
+          break;
+      }
+    }
+    // the wavenumbers the plan holds: q0 .. q0 + nz - 1 of the n_z-point transform
+    for (int l = 0; l < P->nz; ++l) {
+      P->sigma.push_back(mode_lambda(P->kind, P->nzt, P->q0 + l) * iz2 + P->shift);
+      P->pweight.push_back(parseval_weight(P->kind, P->nzt, P->q0 + l));
     }
     if ((st = upload(P, &P->d_sigma64, P->sigma)) || (st = upload(P, &P->d_sigma32, to32(P->sigma)))) break;
     std::vector<int> sm(P->nz, 0);
-    for (int q = 0; q < P->nz; ++q) sm[q] = (P->singular && mode_lambda(P->kind, P->nz, q) == 0.0) ? 1 : 0;
+    for (int l = 0; l < P->nz; ++l) sm[l] = (P->singular && mode_lambda(P->kind, P->nzt, P->q0 + l) == 0.0) ? 1 : 0;
     if ((st = upload(P, &P->d_singular_mode, sm))) break;
     if ((st = build_coarse(P))) break;
     // the bottom of the cycle in one launch: from the first level below 0 whose planes, with all
@@ -838,8 +885,8 @@ int create(snac_plan** out, int32_t nblocks, const snac_block* blocks_in, int32_
           for (int i = 0; i < d.nx; ++i) area[d.off + (long long)j * d.nx + i] = l0.cx[d.xo + i].w * l0.cy[d.yo + j].w;
       if ((st = upload(P, &P->d_area0, area))) break;
     }
-    if ((st = dmalloc(P, &P->d_r3, (size_t)P->n3))) break;
-    const int zsplit = std::min(P->nz, 16);
+    if (!P->ranged && (st = dmalloc(P, &P->d_r3, (size_t)P->n3))) break;
+    const int zsplit = std::min(P->nzt, 16);
     // per-CTA partial sums: the 3-D residual grid (tiles x z split) or a plane reduction (MEAN_CTAS)
     P->npartial = std::max((int)P->lev[0].tiles.size() * zsplit, MEAN_CTAS);
     if ((st = dmalloc(P, &P->d_partial, (size_t)P->npartial * 4))) break;

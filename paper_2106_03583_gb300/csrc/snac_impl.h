@@ -156,7 +156,7 @@ struct TwiddleOffsets {
 // Kernel kinds counted by the tracing facility.
 enum KernelKind {
   K_FIELD3D = 0, K_REDUCE, K_FIX_MEAN, K_SHIFT, K_FORWARD, K_BACKWARD, K_SMOOTH, K_RESTRICT, K_PROLONG,
-  K_COARSE, K_MODE_RESID, K_MODE_REDUCE, K_MODE_APPLY, K_FDOWN, K_FUP, K_BOTTOM, K_COUNT
+  K_COARSE, K_MODE_RESID, K_MODE_REDUCE, K_MODE_APPLY, K_FDOWN, K_FUP, K_BOTTOM, K_FIELD3D_FF, K_COUNT
 };
 
 struct KernelStat {
@@ -185,7 +185,10 @@ struct snac_plan {
   int bottom = -1;  // first level of the one-launch bottom sub-cycle (kern_bottom.cu), -1: none
   void* d_bottom = nullptr;  // its BottomLevel<inner type> table
   int nblk = 0;
-  int nz = 0;
+  int nz = 0;    // wavenumbers held in mode space (q0 .. q0 + nz - 1)
+  int nzt = 0;   // cells along the homogeneous axis: the transform length, the 3-D field's z planes
+  int q0 = 0;    // first wavenumber held (nonzero only in a wavenumber-range plan)
+  bool ranged = false;  // a wavenumber-range plan: mode space only, no 3-D field
   double dz = 0.0;
   int kind = 0;
   double theta = 1.0;
@@ -200,6 +203,12 @@ struct snac_plan {
   // z direction
   std::vector<snac::Coef<double>> cz;
   snac::Coef<double>* d_cz = nullptr;
+  float4* d_czff = nullptr;  // per plane: {lo, hi} of cz as rounded float pairs (float-float residual)
+  // level-0 coefficients of the float-float residual (mixed plans) as rounded float pairs:
+  // {lo, hi} of every x column and y row entry, and the full diagonal cx.d + cy.d + cz.d per cell
+  float4* d_cxff = nullptr;
+  float4* d_cyff = nullptr;
+  float2* d_dgff = nullptr;
   // eigenvalue shifts lambda_q / dz^2 and the Parseval weight of every mode
   std::vector<double> sigma, pweight;
   double* d_sigma64 = nullptr;
@@ -242,6 +251,20 @@ struct snac_plan {
   int* dh_check = nullptr;
   std::vector<void*> allocs;
   size_t bytes = 0;
+  // sharded solves: transform tables of a pencil of pen_tcols columns (one pseudo-block)
+  long long pen_tcols = -1;
+  snac::BlockDev* d_pen_tblk = nullptr;
+  snac::CallerBlk* d_pen_tcb = nullptr;
+  std::vector<snac::ChunkDev> pen_ch64, pen_ch32;
+  snac::ChunkDev* d_pen_ch64 = nullptr;
+  snac::ChunkDev* d_pen_ch32 = nullptr;
+  std::vector<void*> pen_tallocs;
+  // the pencil of the pencil residual: plane cells pen_c0 .. pen_c0 + pen_ncols - 1 and its halo
+  long long pen_c0 = 0, pen_ncols = 0, pen_nhalo = 0;
+  int* d_pen_cell = nullptr;      // per pencil cell: block, i, j, then the p_ext columns of W, E, S, N
+  double* d_pen_part = nullptr;   // per-CTA partial sums (8 per CTA)
+  int pen_nparts = 0;
+  std::vector<void*> pen_allocs;
   // results
   snac_solve_info info{};
   std::vector<int32_t> mode_cycles;
@@ -268,6 +291,11 @@ namespace snac {
 // mode 1: r = A p
 cudaError_t launch_field3d(snac_plan* P, int mode, const double* f, const double* p, double* r, double fshift,
                            bool need_f2, bool need_vp, cudaStream_t s);
+// The same residual (mode 0) in float-float arithmetic, written in FP32 (mixed plans' intermediate
+// defect-correction steps; kern_ffresid.cu). fscale: the RMS of f (any positive value; it sets the
+// power-of-two scaling of the FP32 squares).
+cudaError_t launch_field3d_ff(snac_plan* P, const double* f, const double* p, float* r, double fshift, double fscale,
+                              bool need_f2, bool need_vp, cudaStream_t s);
 // d_sums = {sum V f, sum V |f|, ||f||^2, sum f} (V sums only for singular plans) and
 // d_sums[SUM_NONZERO] = 1 if p has a nonzero entry, else 0
 cudaError_t launch_prepass(snac_plan* P, const double* f, const double* p, cudaStream_t s);
@@ -282,10 +310,15 @@ cudaError_t launch_shift(snac_plan* P, double* p, const double* d_c, cudaStream_
 // modes = F(in3 - shift0) along z (shift0 != 0 only for the kinds with a zero eigenvalue)
 // split: write the modes in colour-split order (the plan's own level-0 f of a scaled FP64 plan).
 cudaError_t launch_forward(snac_plan* P, const double* in3, void* modes, double shift0, bool split, cudaStream_t s);
+// The same from an FP32 3-D field in the caller layout (the float-float residual's output; mixed plans).
+cudaError_t launch_forward_f32(snac_plan* P, const float* in3, void* modes, cudaStream_t s);
 // Level-0 mode planes from plain to colour-split order.
 cudaError_t launch_to_split(snac_plan* P, const double* src, double* dst, cudaStream_t s);
 // p3 += F^-1(modes) / theta; subtract: p3 -= F^-1(modes) / theta (takes a correction back)
 cudaError_t launch_backward_update(snac_plan* P, const void* modes, double* p3, cudaStream_t s, bool subtract = false);
+// Pencils of a sharded solve ([z][c] fields of ncols columns): forward transform, backward update.
+cudaError_t launch_pencil_forward(snac_plan* P, long long ncols, const double* in, void* modes, cudaStream_t s);
+cudaError_t launch_pencil_backward(snac_plan* P, long long ncols, const void* modes, double* p, cudaStream_t s);
 
 // ---- multigrid ----
 cudaError_t launch_mode_operator(snac_plan* P, const void* u, void* out, cudaStream_t s);

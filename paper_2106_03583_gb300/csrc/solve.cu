@@ -46,6 +46,17 @@ int check_plan(snac_plan* P) {
   return SNAC_OK;
 }
 
+// Calls on 3-D fields: not on a wavenumber-range plan, which holds a slab of the mode space only.
+int check_plan3d(snac_plan* P) {
+  int st = check_plan(P);
+  if (st) return st;
+  if (P->ranged) {
+    set_error("a wavenumber-range plan has no 3-D field: use the pencil calls");
+    return SNAC_ERR_INVALID_ARG;
+  }
+  return SNAC_OK;
+}
+
 int set_active_all(snac_plan* P, cudaStream_t s) {
   for (int q = 0; q < P->nz; ++q) P->h_active[q] = q;
   CK(launch_from_host(P->dh_active, P->d_active, P->nz, s));
@@ -114,7 +125,7 @@ int mode_solves(snac_plan* P, double target, cudaStream_t s, int* cycles_out) {
   std::vector<double> thr2(nz), prev(nz);  // prev: norm^2 at the mode's last check
   std::vector<int> list, prev_cycle(nz, 0), next_check(nz, 1);
   for (int q = 0; q < nz; ++q) {
-    thr2[q] = target * target / (nz * P->pweight[q]);
+    thr2[q] = target * target / (P->nzt * P->pweight[q]);
     prev[q] = P->h_mode_norm2[q];
     cycles_out[q] = 0;
     if (!std::isfinite(prev[q])) return SNAC_ERR_NONFINITE;
@@ -224,10 +235,18 @@ int run_solve(snac_plan* P, const double* f, double* p, double tol, cudaStream_t
   const bool mixed = P->precision == SNAC_MIXED;
   double prev_rel = INFINITY, fn = 0.0;
   bool updated = false;
+  // Mixed plans compute the residual of an intermediate defect-correction step in float-float
+  // arithmetic (written in FP32, the precision the FP32 transform reads); the FP64 pass decides
+  // convergence: it runs after a correction that aimed at the tolerance itself, and whenever the
+  // float-float residual comes within 2x of the tolerance. (The float-float error, a few units of
+  // 2^-47 of |f| + |A||p| per cell, is about 1e-11 ||f|| on the 2.7e8-cell channel: it steers an
+  // intermediate correction well enough, but a convergence decision near tol takes the FP64 pass.)
+  bool aim_final = false;
   std::vector<int> cyc(P->nz);
   for (int k = 0;; ++k) {
     const bool from_f = k == 0 && p_zero;
     double rn;
+    bool r32 = false;  // the residual in d_r3 is the float-float pass's FP32 field
     if (from_f) {
       fn = rn = fn_pre;
       if (P->singular) CK(launch_fill(P->d_sums + 2, 1, 0.0, s));  // sum V p = 0
@@ -238,10 +257,19 @@ int run_solve(snac_plan* P, const double* f, double* p, double tol, cudaStream_t
       // plans measure it every time: the FP32 transform of the correction leaves a drift that the
       // next mean fix removes.
       const bool need_vp = P->singular && (k == 0 || P->precision != SNAC_FP64);
-      CK(launch_field3d(P, 0, f, p, P->d_r3, fshift, k == 0, need_vp, s));
-      if ((st = read_sums(P, s))) return st;
-      if (k == 0) fn = std::sqrt(P->h_sums[1]);
-      rn = std::sqrt(P->h_sums[0]);
+      if (mixed && k > 0 && !aim_final) {
+        CK(launch_field3d_ff(P, f, p, reinterpret_cast<float*>(P->d_r3), fshift, fn / std::sqrt((double)P->n3), false,
+                             need_vp, s));
+        if ((st = read_sums(P, s))) return st;
+        rn = std::sqrt(P->h_sums[0]);
+        r32 = !(rn <= 2.0 * tol * fn);  // (NaN stays: reported below)
+      }
+      if (!r32) {
+        CK(launch_field3d(P, 0, f, p, P->d_r3, fshift, k == 0, need_vp, s));
+        if ((st = read_sums(P, s))) return st;
+        if (k == 0) fn = std::sqrt(P->h_sums[1]);
+        rn = std::sqrt(P->h_sums[0]);
+      }
     }
     if (!std::isfinite(rn) || !std::isfinite(fn)) return SNAC_ERR_NONFINITE;
     P->info.rhs_norm = fn;
@@ -280,7 +308,9 @@ int run_solve(snac_plan* P, const double* f, double* p, double tol, cudaStream_t
     // target of this defect-correction step
     double target = 0.5 * tol * fn;
     if (mixed) target = std::max(target, P->inner_reduction * rn);
+    aim_final = target <= 0.5 * tol * fn;
     if (from_f) CK(launch_forward(P, f, P->lev[0].d_f, fshift, P->scaled_f, s));
+    else if (r32) CK(launch_forward_f32(P, reinterpret_cast<const float*>(P->d_r3), P->lev[0].d_f, s));
     else CK(launch_forward(P, P->d_r3, P->lev[0].d_f, 0.0, P->scaled_f, s));
     if ((st = mode_solves(P, target, s, cyc.data()))) return st;
     for (int q = 0; q < P->nz; ++q) {
@@ -298,7 +328,7 @@ int run_solve(snac_plan* P, const double* f, double* p, double tol, cudaStream_t
 extern "C" {
 
 int snac_poisson_solve(snac_plan* plan, const double* d_rhs, double* d_p, double tol, void* stream) {
-  int st = check_plan(plan);
+  int st = check_plan3d(plan);
   if (st) return st;
   if (!d_rhs || !d_p || !(tol > 0.0) || !std::isfinite(tol)) return SNAC_ERR_INVALID_ARG;
   st = run_solve(plan, d_rhs, d_p, tol, (cudaStream_t)stream);
@@ -307,7 +337,7 @@ int snac_poisson_solve(snac_plan* plan, const double* d_rhs, double* d_p, double
 }
 
 int snac_apply_operator(snac_plan* plan, const double* d_p, double* d_out, void* stream) {
-  int st = check_plan(plan);
+  int st = check_plan3d(plan);
   if (st) return st;
   if (!d_p || !d_out) return SNAC_ERR_INVALID_ARG;
   cudaStream_t s = (cudaStream_t)stream;
@@ -318,7 +348,7 @@ int snac_apply_operator(snac_plan* plan, const double* d_p, double* d_out, void*
 }
 
 int snac_residual(snac_plan* plan, const double* d_rhs, const double* d_p, double* d_r, double* h_norms, void* stream) {
-  int st = check_plan(plan);
+  int st = check_plan3d(plan);
   if (st) return st;
   if (!d_rhs || !d_p || !d_r || !h_norms) return SNAC_ERR_INVALID_ARG;
   cudaStream_t s = (cudaStream_t)stream;
@@ -329,8 +359,21 @@ int snac_residual(snac_plan* plan, const double* d_rhs, const double* d_p, doubl
   return SNAC_OK;
 }
 
+int snac_residual_ff(snac_plan* plan, const double* d_rhs, const double* d_p, float* d_r, double* h_norms,
+                     void* stream) {
+  int st = check_plan3d(plan);
+  if (st) return st;
+  if (!d_rhs || !d_p || !d_r || !h_norms) return SNAC_ERR_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  CK(launch_field3d_ff(plan, d_rhs, d_p, d_r, 0.0, 1.0, true, false, s));
+  if ((st = read_sums(plan, s))) return st;
+  h_norms[0] = plan->h_sums[0];
+  h_norms[1] = plan->h_sums[1];
+  return SNAC_OK;
+}
+
 int snac_forward_transform(snac_plan* plan, const double* d_in, void* d_modes, void* stream) {
-  int st = check_plan(plan);
+  int st = check_plan3d(plan);
   if (st) return st;
   if (!d_in || !d_modes) return SNAC_ERR_INVALID_ARG;
   cudaStream_t s = (cudaStream_t)stream;
@@ -341,11 +384,52 @@ int snac_forward_transform(snac_plan* plan, const double* d_in, void* d_modes, v
 }
 
 int snac_backward_update(snac_plan* plan, const void* d_modes, double* d_p, void* stream) {
-  int st = check_plan(plan);
+  int st = check_plan3d(plan);
   if (st) return st;
   if (!d_modes || !d_p) return SNAC_ERR_INVALID_ARG;
   cudaStream_t s = (cudaStream_t)stream;
   CK(launch_backward_update(plan, d_modes, d_p, s));
+  CK(cudaStreamSynchronize(s));
+  profile_resolve(plan);
+  return SNAC_OK;
+}
+
+int snac_mode_solve(snac_plan* plan, const void* d_rhs, void* d_sol, double target, void* stream) {
+  int st = check_plan(plan);
+  if (st) return st;
+  if (!d_rhs || !d_sol || !(target >= 0.0) || !std::isfinite(target)) return SNAC_ERR_INVALID_ARG;
+  snac_plan* P = plan;
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t bytes = (size_t)P->nz * P->lev[0].ncell * plan_inner_size(P);
+  // the right-hand side into the level-0 buffer, in the order the cycles read it
+  if (P->scaled_f) CK(launch_to_split(P, (const double*)d_rhs, (double*)P->lev[0].d_f, s));
+  else CK(cudaMemcpyAsync(P->lev[0].d_f, d_rhs, bytes, cudaMemcpyDeviceToDevice, s));
+  P->info = snac_solve_info{};
+  P->info.levels = (int)P->lev.size();
+  P->info.n_modes = P->nz;
+  std::vector<int> cyc(P->nz);
+  if ((st = mode_solves(P, target, s, cyc.data()))) {
+    P->info.status = st;
+    return st;
+  }
+  for (int q = 0; q < P->nz; ++q) {
+    P->mode_cycles[q] = cyc[q];
+    P->info.max_mode_cycles = std::max(P->info.max_mode_cycles, cyc[q]);
+  }
+  CK(cudaMemcpyAsync(d_sol, P->lev[0].d_u, bytes, cudaMemcpyDeviceToDevice, s));
+  CK(cudaStreamSynchronize(s));
+  profile_resolve(P);
+  return SNAC_OK;
+}
+
+int snac_mode_fix_mean(snac_plan* plan, void* d_sol, double sum_vp, void* stream) {
+  int st = check_plan(plan);
+  if (st) return st;
+  if (!d_sol || !std::isfinite(sum_vp)) return SNAC_ERR_INVALID_ARG;
+  if (!plan->singular || plan->q0 != 0) return SNAC_OK;
+  cudaStream_t s = (cudaStream_t)stream;
+  CK(launch_fill(plan->d_sums + 2, 1, sum_vp, s));  // sum V p of the current p (all ranks)
+  CK(launch_fix_mean(plan, d_sol, s));
   CK(cudaStreamSynchronize(s));
   profile_resolve(plan);
   return SNAC_OK;

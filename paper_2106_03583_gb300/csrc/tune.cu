@@ -71,6 +71,7 @@ extern "C" int snac_autotune(int32_t nblocks, const snac_block* blocks, int32_t 
                              const double* d_rhs, double tol, snac_options* best, snac_tune_report* report,
                              void* stream) {
   if (!blocks || nblocks < 1 || !d_rhs || !best || !(tol > 0.0) || !std::isfinite(tol)) return SNAC_ERR_INVALID_ARG;
+  if (base && (base->mode_begin != 0 || base->mode_end != 0)) return SNAC_ERR_INVALID_ARG;  // whole solves only
   int st = snac::check_layout(nblocks, blocks, homog_axis);
   if (st) return st;
   const snac_options b0 = base ? *base : defaults();

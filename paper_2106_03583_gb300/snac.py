@@ -27,9 +27,10 @@ _PREC = {"fp64": 0, "mixed": 1}
 
 EXPORTS = ("snac_plan_create", "snac_plan_workspace_bytes", "snac_poisson_solve", "snac_plan_info",
            "snac_plan_mode_cycles", "snac_plan_destroy", "snac_status_string", "snac_last_error_message",
-           "snac_apply_operator", "snac_residual", "snac_forward_transform", "snac_backward_update",
+           "snac_apply_operator", "snac_residual", "snac_residual_ff", "snac_forward_transform", "snac_backward_update",
            "snac_mode_operator", "snac_mode_vcycles", "snac_plan_set_profiling", "snac_plan_kernel_stats",
-           "snac_plan_reset_stats", "snac_residual_noalloc",
+           "snac_plan_reset_stats", "snac_residual_noalloc", "snac_pencil_forward", "snac_pencil_backward_update",
+           "snac_pencil_setup", "snac_pencil_residual", "snac_mode_solve", "snac_mode_fix_mean",
            "snac_engine_create", "snac_engine_submit", "snac_engine_wait", "snac_engine_get_stats",
            "snac_engine_clock", "snac_engine_destroy", "snac_autotune")
 
@@ -49,7 +50,8 @@ class _Block(ctypes.Structure):
 class _Options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("nu1", ctypes.c_int32), ("nu2", ctypes.c_int32),
                 ("max_outer", ctypes.c_int32), ("max_cycles", ctypes.c_int32), ("max_coarse", ctypes.c_int32),
-                ("fused", ctypes.c_int32), ("inner_reduction", ctypes.c_double), ("shift", ctypes.c_double)]
+                ("fused", ctypes.c_int32), ("inner_reduction", ctypes.c_double), ("shift", ctypes.c_double),
+                ("mode_begin", ctypes.c_int32), ("mode_end", ctypes.c_int32)]
 
 
 class _KStat(ctypes.Structure):
@@ -112,6 +114,14 @@ def lib() -> ctypes.CDLL:
             "snac_last_error_message": [],
             "snac_apply_operator": [vp, vp, vp, vp],
             "snac_residual": [vp, vp, vp, vp, ctypes.POINTER(f64), vp],
+            "snac_residual_ff": [vp, vp, vp, vp, ctypes.POINTER(f64), vp],
+            "snac_pencil_forward": [vp, ctypes.c_int64, vp, vp, vp],
+            "snac_pencil_backward_update": [vp, ctypes.c_int64, vp, vp, vp],
+            "snac_pencil_setup": [vp, ctypes.c_int64, ctypes.c_int64, ctypes.POINTER(ctypes.c_int64), ctypes.c_int64,
+                                  ctypes.POINTER(ctypes.c_int64)],
+            "snac_pencil_residual": [vp, vp, vp, vp, f64, ctypes.POINTER(f64), vp],
+            "snac_mode_solve": [vp, vp, vp, f64, vp],
+            "snac_mode_fix_mean": [vp, vp, f64, vp],
             "snac_forward_transform": [vp, vp, vp, vp],
             "snac_backward_update": [vp, vp, vp, vp],
             "snac_mode_operator": [vp, vp, vp, vp],
@@ -186,7 +196,7 @@ class Plan:
 
     def __init__(self, blocks, homog_axis: int = 2, precision: str = "fp64", nu1: int = 2, nu2: int = 2,
                  max_outer: int = 20, max_cycles: int = 40, max_coarse: int = 64, inner_reduction: float = 1e-3,
-                 fused: int = -1, shift: float = 0.0):
+                 fused: int = -1, shift: float = 0.0, modes=None):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("snac.Plan needs a CUDA device")
@@ -198,7 +208,9 @@ class Plan:
         self.precision = precision
         self.inner_dtype = torch.float64 if precision == "fp64" else torch.float32
         arr, keep = _marshal_blocks(blocks)
-        opt = _Options(_PREC[precision], nu1, nu2, max_outer, max_cycles, max_coarse, fused, inner_reduction, shift)
+        q0, q1 = modes if modes is not None else (0, 0)
+        opt = _Options(_PREC[precision], nu1, nu2, max_outer, max_cycles, max_coarse, fused, inner_reduction, shift,
+                       int(q0), int(q1))
         h = ctypes.c_void_p()
         _check(lib().snac_plan_create(ctypes.byref(h), len(blocks), arr, homog_axis, ctypes.byref(opt)))
         del keep
@@ -206,6 +218,9 @@ class Plan:
         self.nz = int(blocks[0]["hi"][2] - blocks[0]["lo"][2] + 1)
         self.ncell = int(sum((b["hi"][0] - b["lo"][0] + 1) * (b["hi"][1] - b["lo"][1] + 1) for b in blocks))
         self.n3 = self.ncell * self.nz
+        # wavenumbers held in mode space (all, or the range of a wavenumber-range plan)
+        self.mode_range = (int(q0), int(q1)) if modes is not None else (0, self.nz)
+        self.nmodes = self.mode_range[1] - self.mode_range[0]
 
     # ---- helpers
     def _stream(self):
@@ -238,8 +253,8 @@ class Plan:
         return d
 
     def mode_cycles(self) -> np.ndarray:
-        out = (ctypes.c_int32 * self.nz)()
-        _check(lib().snac_plan_mode_cycles(self._h, out, self.nz))
+        out = (ctypes.c_int32 * self.nmodes)()
+        _check(lib().snac_plan_mode_cycles(self._h, out, self.nmodes))
         return np.frombuffer(out, dtype=np.int32).copy()
 
     # ---- tracing
@@ -278,6 +293,60 @@ class Plan:
                                    self._ptr(r, torch.float64, self.n3, "r"), norms, self._stream()))
         return norms[0], norms[1]
 
+    def residual_ff(self, rhs, p, r):
+        """r (float32) = rhs - A p in float-float arithmetic (the mixed plans' intermediate pass);
+        returns (||r||^2, ||rhs||^2)."""
+        import torch
+        norms = (ctypes.c_double * 2)()
+        _check(lib().snac_residual_ff(self._h, self._ptr(rhs, torch.float64, self.n3, "rhs"),
+                                      self._ptr(p, torch.float64, self.n3, "p"),
+                                      self._ptr(r, torch.float32, self.n3, "r"), norms, self._stream()))
+        return norms[0], norms[1]
+
+    # ---- one rank of a wavenumber-sharded solve (pencils [z][c], slabs [local q][plane cell])
+    def pencil_forward(self, x, modes):
+        import torch
+        nc = x.numel() // self.nz
+        _check(lib().snac_pencil_forward(self._h, nc, self._ptr(x, torch.float64, nc * self.nz, "x"),
+                                         self._ptr(modes, self.inner_dtype, nc * self.nz, "modes"), self._stream()))
+
+    def pencil_backward_update(self, modes, p):
+        import torch
+        nc = p.numel() // self.nz
+        _check(lib().snac_pencil_backward_update(self._h, nc, self._ptr(modes, self.inner_dtype, nc * self.nz, "modes"),
+                                                 self._ptr(p, torch.float64, nc * self.nz, "p"), self._stream()))
+
+    def pencil_setup(self, c0: int, ncols: int) -> np.ndarray:
+        """Set this plan's pencil (plane cells c0 .. c0 + ncols - 1); returns its halo cells."""
+        cap = 4 * int(ncols) + 8
+        buf = (ctypes.c_int64 * cap)()
+        n = ctypes.c_int64()
+        _check(lib().snac_pencil_setup(self._h, int(c0), int(ncols), buf, cap, ctypes.byref(n)))
+        self._pencil = (int(c0), int(ncols), int(n.value))
+        return np.frombuffer(buf, dtype=np.int64, count=n.value).copy()
+
+    def pencil_residual(self, f, p_ext, r, fshift: float = 0.0):
+        """r = (f - fshift) - A p on the pencil; returns (||r||^2, ||f - fshift||^2, sum V p,
+        sum V (f - fshift), sum V |f - fshift|) of the pencil."""
+        import torch
+        _, nc, nh = self._pencil
+        sums = (ctypes.c_double * 5)()
+        _check(lib().snac_pencil_residual(self._h, self._ptr(f, torch.float64, nc * self.nz, "f"),
+                                          self._ptr(p_ext, torch.float64, (nc + nh) * self.nz, "p_ext"),
+                                          self._ptr(r, torch.float64, nc * self.nz, "r"), float(fshift), sums,
+                                          self._stream()))
+        return tuple(sums)
+
+    def mode_solve(self, rhs, sol, target: float) -> dict:
+        n = self.nmodes * self.ncell
+        _check(lib().snac_mode_solve(self._h, self._ptr(rhs, self.inner_dtype, n, "rhs"),
+                                     self._ptr(sol, self.inner_dtype, n, "sol"), float(target), self._stream()))
+        return self.info()
+
+    def mode_fix_mean(self, sol, sum_vp: float):
+        _check(lib().snac_mode_fix_mean(self._h, self._ptr(sol, self.inner_dtype, self.nmodes * self.ncell, "sol"),
+                                        float(sum_vp), self._stream()))
+
     def forward_transform(self, x, modes):
         import torch
         _check(lib().snac_forward_transform(self._h, self._ptr(x, torch.float64, self.n3, "x"),
@@ -289,12 +358,14 @@ class Plan:
                                           self._ptr(p, torch.float64, self.n3, "p"), self._stream()))
 
     def mode_operator(self, u, out):
-        _check(lib().snac_mode_operator(self._h, self._ptr(u, self.inner_dtype, self.n3, "u"),
-                                        self._ptr(out, self.inner_dtype, self.n3, "out"), self._stream()))
+        n = self.nmodes * self.ncell
+        _check(lib().snac_mode_operator(self._h, self._ptr(u, self.inner_dtype, n, "u"),
+                                        self._ptr(out, self.inner_dtype, n, "out"), self._stream()))
 
     def mode_vcycles(self, f, u, ncycles: int = 1):
-        _check(lib().snac_mode_vcycles(self._h, self._ptr(f, self.inner_dtype, self.n3, "f"),
-                                       self._ptr(u, self.inner_dtype, self.n3, "u"), int(ncycles), self._stream()))
+        n = self.nmodes * self.ncell
+        _check(lib().snac_mode_vcycles(self._h, self._ptr(f, self.inner_dtype, n, "f"),
+                                       self._ptr(u, self.inner_dtype, n, "u"), int(ncycles), self._stream()))
 
     def close(self):
         if getattr(self, "_h", None) is not None and self._h.value:

@@ -137,3 +137,22 @@ def test_autotune_argument_checks(lib):
     assert lib.snac_autotune(1, arr, 2, None, None, 1e-10, ctypes.byref(best), None, None) == -1
     assert lib.snac_autotune(1, arr, 2, None, ctypes.c_void_p(8), 0.0, ctypes.byref(best), None, None) == -1
     assert lib.snac_autotune(1, arr, 5, None, ctypes.c_void_p(8), 1e-10, ctypes.byref(best), None, None) == -1
+
+
+def test_wavenumber_range_validation(lib):
+    """mode_begin/mode_end outside 0 <= begin < end <= n_z are refused before any device work."""
+    blocks = make("1", n=4, nz=8, zpair="NN")
+    for rng in ((3, 3), (-1, 2), (2, 9), (5, 4)):
+        opt = snac._Options(0, 2, 2, 20, 40, 64, -1, 1e-3, 0.0, rng[0], rng[1])
+        st, msg = _create(lib, blocks, opt=ctypes.byref(opt))
+        assert st == -1 and "mode_begin" in msg, (rng, st, msg)
+
+
+def test_pencil_calls_check_their_arguments(lib):
+    assert lib.snac_pencil_forward(None, 4, None, None, None) == -1
+    assert lib.snac_pencil_backward_update(None, 4, None, None, None) == -1
+    n = ctypes.c_int64()
+    assert lib.snac_pencil_setup(None, 0, 4, None, 0, ctypes.byref(n)) == -1
+    assert lib.snac_pencil_residual(None, None, None, None, 0.0, None, None) == -1
+    assert lib.snac_mode_solve(None, None, None, 1.0, None) == -1
+    assert lib.snac_mode_fix_mean(None, None, 0.0, None) == -1

@@ -213,3 +213,100 @@ def test_vcycle_fused_other_schedules(case, nu):
     err_fused = rel(_mean_free(g, _two_cycles(blocks, Fh, Z, "mixed", 1, nu)), ref0)
     err_colour = rel(_mean_free(g, _two_cycles(blocks, Fh, Z, "mixed", 0, nu)), ref0)
     assert err_fused <= max(2e-5, 4.0 * err_colour), (err_fused, err_colour)
+
+
+def _abs_operator(g, p):
+    """|A| |p| with the oracle's assembled 3-D operator (the scale of the cancellation in f - A p)."""
+    A = g.matrix().tocsr()
+    A.data = np.abs(A.data)
+    return g.from_planes((A @ np.abs(g.to_planes(p)).ravel()).reshape(g.nz, g.plane.n))
+
+
+def _check_ff(pl, g, f, p, norms=True):
+    """The float-float residual against the oracle's FP64 residual, cell by cell, within the bound
+    2^-24 |r| (rounding to FP32) + 16 * 2^-47 (|f| + |A||p|) + |A| 2^-103 (operands below 2^-103
+    count as zero); the norms against the sums of the same values."""
+    import torch
+    N = len(f)
+    r = torch.empty(N, dtype=torch.float32, device="cuda")
+    r2, f2 = pl.residual_ff(dev(f), dev(p), r)
+    ref = f - g.from_planes(g.apply(g.to_planes(p)))
+    got = host(r)
+    bound = 2.0 ** -24 * np.abs(ref) + 16 * 2.0 ** -47 * (np.abs(f) + _abs_operator(g, p)) + \
+        _abs_operator(g, np.ones(N)) * 2.0 ** -103
+    assert np.all(np.abs(got - ref) <= bound), float(np.max(np.abs(got - ref) / bound))
+    if norms:
+        assert r2 == pytest.approx(float(np.sum(got.astype(np.float64) ** 2)), rel=1e-5)
+        assert f2 == pytest.approx(float(np.sum(f ** 2)), rel=1e-5)
+    return got, ref
+
+
+@pytest.mark.parametrize("case", CASES + PERIODIC)
+def test_float_float_residual_random(case):
+    """Random f and p of unit size on every layout and z pair (no cancellation: the bound is the
+    FP32 rounding of r)."""
+    blocks = _blocks(case)
+    N = inputs.total_cells(blocks)
+    rng = np.random.default_rng(5)
+    _check_ff(plan(blocks, precision="mixed"), ogrid.Grid(blocks), rng.standard_normal(N), rng.standard_normal(N))
+
+
+@pytest.mark.parametrize("name,scale", [("mb2x2", 4), ("chan", 8), ("c64", 2)])
+def test_float_float_residual_near_the_solution(name, scale):
+    """p within 1e-9 of the solution, where A p cancels f to nine digits and more: the residual is
+    resolved far below |A||p| (the float-float bound), and its norm matches the FP64 residual's."""
+    from oracle import solve as osv
+    blocks, f = inputs.config(name, seed=2, scale=scale)
+    ps, _ = osv.solve(blocks, f)
+    rng = np.random.default_rng(6)
+    p = ps * (1.0 + 1e-9 * rng.standard_normal(len(ps)))
+    g = ogrid.Grid(blocks)
+    got, ref = _check_ff(plan(blocks, precision="mixed"), g, f, p)
+    assert np.linalg.norm(ref) <= 1e-6 * np.linalg.norm(_abs_operator(g, p))  # the cancellation is real
+    assert rel(got, ref) <= 1e-3
+
+
+def test_float_float_residual_special_operands():
+    """Zeros, negative zeros, operands below 2^-103 (taken as zero), all-ones mantissas, large values,
+    and a NaN (which must reach the norm). Values of 1e30 stay within the elementwise bound, but their
+    squares overflow the FP32 sums of this stage call (which has no scaling), so the norms are
+    checked with values of 1e12."""
+    import torch
+    blocks = _blocks(CASES[1])
+    N = inputs.total_cells(blocks)
+    rng = np.random.default_rng(7)
+    p = rng.standard_normal(N)
+    p[::7] = 0.0
+    p[1::7] = -0.0
+    p[2::7] = 1e-200
+    p[3::7] = -3e-33
+    p[4::7] = np.nextafter(2.0, 0.0) * np.sign(rng.standard_normal(len(p[4::7])))
+    p[5::7] = 1e30 * rng.standard_normal(len(p[5::7]))
+    f = rng.standard_normal(N)
+    f[::5] = 0.0
+    pl = plan(blocks, precision="mixed")
+    g = ogrid.Grid(blocks)
+    _check_ff(pl, g, f, p, norms=False)
+    p[5::7] = 1e12 * rng.standard_normal(len(p[5::7]))
+    _check_ff(pl, g, f, p)
+    p[10] = np.nan
+    r = torch.empty(N, dtype=torch.float32, device="cuda")
+    r2, _ = pl.residual_ff(dev(f), dev(p), r)
+    assert not np.isfinite(r2)
+
+
+def test_mixed_solve_runs_float_float_passes_and_decides_in_fp64():
+    """A mixed solve from zero: the intermediate residual passes are the float-float kernel, the
+    convergence check an FP64 pass; the result still meets the tolerance under the oracle's operator."""
+    import torch
+    from oracle import solve as osv
+    blocks, f = inputs.config("chan", seed=1, scale=8)
+    pl = plan(blocks, precision="mixed")
+    p = torch.zeros(len(f), dtype=torch.float64, device="cuda")
+    pl.reset_stats()
+    info = pl.solve(dev(f), p, tol=1e-10)
+    st = pl.kernel_stats()
+    assert info["status"] == 0 and info["outer_iters"] >= 2
+    assert st["field3d_ff"]["launches"] >= 1
+    assert st["field3d"]["launches"] >= 2          # the pre-pass and at least one FP64 check
+    assert osv.rel_residual(blocks, f, host(p)) <= 1.01e-10
