@@ -108,6 +108,10 @@ typedef struct {
                           wavenumbers mode_begin .. mode_end - 1 only (local index q - mode_begin);
                           it has no 3-D field, so the calls on 3-D fields return
                           SNAC_ERR_INVALID_ARG, and the pencil calls below take their place          */
+  int32_t onchip;      /* 0 (default): when the whole multigrid hierarchy of a wavenumber, from the
+                          finest plane, fits in one CTA's shared memory, each wavenumber's solve runs
+                          on chip in one CTA and its convergence is decided on the device (one launch
+                          per defect-correction step); -1: always the level-by-level path            */
 } snac_options;
 
 /* Result of the last solve of a plan. */
@@ -149,6 +153,18 @@ int snac_plan_workspace_bytes(const snac_plan *plan, size_t *bytes);
  * small control transfers (norms read back, mode lists) go through pinned host memory mapped into the
  * device (held by the plan), so copies that other streams run meanwhile do not delay it. */
 int snac_poisson_solve(snac_plan *plan, const double *d_rhs, double *d_p, double tol, void *stream);
+
+/* Solve n problems together (each as snac_poisson_solve would): plans[k] (distinct plans, all on
+ * the current device), d_rhs[k], d_p[k] as in snac_poisson_solve, one tolerance. The problems run
+ * in lock-step: each phase's launches of all of them go out together and one synchronisation
+ * serves them all, and the wavenumber solves of every plan whose hierarchy fits on chip (see
+ * snac_options.onchip) share one persistent launch per precision -- CTAs take (problem, wavenumber)
+ * items from a device-side queue, and each wavenumber's V-cycles stop on the device. This is the
+ * batched solve of many small systems that the paper's conclusions point to (Sec. 5). h_status[n]
+ * receives each problem's status (snac_plan_info gives its statistics); returns SNAC_OK if every
+ * problem succeeded, else the first failing status. */
+int snac_poisson_solve_batch(int32_t n, snac_plan *const *plans, const double *const *d_rhs, double *const *d_p,
+                             double tol, int32_t *h_status, void *stream);
 
 /* Statistics of the last solve. */
 int snac_plan_info(const snac_plan *plan, snac_solve_info *info);

@@ -12,6 +12,9 @@
 // restriction, three-point prolongation onto the cells that the following half-sweep keeps, and the
 // coarsest plane solved through the eigen-decomposition of its symmetrised operator. From the zero
 // iterate of each level, the first colour-0 half-sweep is u = f / diag, which is written directly.
+#include <algorithm>
+#include <vector>
+
 #include "kern_common.cuh"
 #include "snac_impl.h"
 
@@ -301,6 +304,228 @@ __global__ void __launch_bounds__(BT) k_bottom(const BottomArgs<T> A) {
   }
 }
 
+// ---- whole-mode solves on chip, with their convergence decided on the device ----
+//
+// When a plan's whole hierarchy, from level 0, fits in one CTA's shared memory, a wavenumber's
+// complete multigrid solve runs in one CTA: its right-hand side comes in once, V-cycles run on chip
+// until the mode meets its share of the target (w_q ||r_q||^2 <= target^2 / n_z, the rule of the
+// level-by-level path) or stops improving (a cycle that reduces ||r_q||^2 by less than 0.36), or
+// max_cycles; its correction goes out once. There is no host round trip per cycle: the residual
+// norm after every cycle is reduced in the CTA and the loop stops on the device.
+
+// Block-wide sum of one double, returned to every thread in a fixed order (scratch: 32 doubles).
+__device__ __forceinline__ double block_sum_all(double v, double* scratch) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  v = warp_sum(v);
+  __syncthreads();  // the scratch's previous readers are done
+  if (lane == 0) scratch[warp] = v;
+  __syncthreads();
+  double t = 0.0;
+#pragma unroll
+  for (int w = 0; w < BT / 32; ++w) t += scratch[w];
+  return t;
+}
+
+// ||f - A u||^2 over the colour-0 cells of a level (after a sweep ending on colour 1 the colour-1
+// cells carry no residual).
+template <typename T>
+__device__ double colour0_resid2(const LevelView<T>& L, const LevelSmem<T>& S, T sg, double* scratch) {
+  double acc = 0.0;
+  const int ncol = (int)(L.ncell >> 1);
+  for (int idx = threadIdx.x; idx < ncol; idx += BT) {
+    int b, i, j;
+    BlockDev B;
+    if (!colour_cell(L.blk, L.nblk, idx, 0, b, B, i, j)) break;
+    long long w, e, s, n;
+    nbr_plane(L.blk, B, b, i, j, w, e, s, n);
+    const int c = (int)(B.off + (long long)j * B.nx + i);
+    const Coef<T> cx = L.cx[B.xo + i], cy = L.cy[B.yo + j];
+    T a = cx.lo * S.u[w];
+    a = fma(cx.hi, S.u[e], a);
+    a = fma(cy.lo, S.u[s], a);
+    a = fma(cy.hi, S.u[n], a);
+    a = fma(L.dxy[c] + sg, S.u[c], a);
+    const double r = (double)(S.f[c] - a);
+    acc = fma(r, r, acc);
+  }
+  return block_sum_all(acc, scratch);
+}
+
+template <typename T>
+struct OnchipArgs {
+  BottomArgs<T> B;          // the hierarchy from level 0 (f_top, u_top: the level-0 mode fields)
+  const double* pweight;    // Parseval weight of every wavenumber the plan holds
+  double t2nz;              // target^2 / n_z: mode q is done when ||r_q||^2 <= t2nz / pweight[q]
+  int max_cycles;
+  int* cycles;              // per wavenumber: V-cycles run
+  double* norm2;            // per wavenumber: ||r_q||^2 on return
+};
+
+// One wavenumber's solve, from a zero iterate, by one CTA.
+template <typename T>
+__device__ void onchip_mode(const OnchipArgs<T>& O, int q, unsigned char* smem_raw) {
+  const BottomArgs<T>& A = O.B;
+  const int nl = A.nlev;
+  double* b = reinterpret_cast<double*>(smem_raw + A.coarse_off);
+  double* y = b + MAX_COARSE;
+  const T sg = A.sigma[q];
+  const double sg64 = A.sigma64[q];
+  const bool sing = A.singular_mode[q] != 0;
+  const T* f0g = A.f_top + (long long)q * A.lv[0].L.ncell;
+  for (int l = 0; l < nl; ++l) {
+    const BottomLevel<T> bl = A.lv[l];
+    const unsigned* src = reinterpret_cast<const unsigned*>(bl.L.blk);
+    unsigned* dst = reinterpret_cast<unsigned*>(smem_raw + bl.sblk);
+    const int words = bl.L.nblk * (int)(sizeof(BlockDev) / sizeof(unsigned));
+    for (int k = threadIdx.x; k < words; k += BT) dst[k] = src[k];
+  }
+  {
+    const BottomLevel<T> top = A.lv[0];
+    if (top.sf >= 0) {
+      T* f0 = reinterpret_cast<T*>(smem_raw) + top.sf;
+      for (int c = threadIdx.x; c < (int)top.L.ncell; c += BT) f0[c] = f0g[c];
+    }
+  }
+  __syncthreads();
+  for (int l = 0; l + 1 < nl; ++l) {
+    const BottomLevel<T> bl = level_at(A, smem_raw, l);
+    const LevelSmem<T> S = level_smem(smem_raw, bl, f0g);
+    const int n = (int)bl.L.ncell;
+    for (int c = threadIdx.x; c < n; c += BT)
+      S.inv[c] = bl.invd != nullptr ? (T)bl.invd[(long long)q * n + c] : (T)1 / (bl.L.dxy[c] + sg);
+  }
+  const BottomLevel<T> top = level_at(A, smem_raw, 0);
+  const LevelSmem<T> S0 = level_smem(smem_raw, top, f0g);
+  const int n0 = (int)top.L.ncell;
+  double f2 = 0.0;
+  for (int c = threadIdx.x; c < n0; c += BT) {
+    const double v = (double)S0.f[c];
+    f2 = fma(v, v, f2);
+    S0.u[c] = (T)0;
+  }
+  double r2 = block_sum_all(f2, y);  // (its barriers also publish u and 1/diag)
+  const double thr2 = O.t2nz / O.pweight[q];
+  int cyc = 0;
+  if (r2 > thr2) {
+    double prev = r2;
+    while (cyc < O.max_cycles) {
+      // down: nu1 sweeps (on the coarse levels the first colour-0 half-sweep is done by the
+      // restriction that fills them), residual, restriction
+      for (int l = 0; l + 1 < nl; ++l) {
+        const BottomLevel<T> F = level_at(A, smem_raw, l), C = level_at(A, smem_raw, l + 1);
+        const LevelSmem<T> SF = level_smem(smem_raw, F, f0g), SC = level_smem(smem_raw, C, f0g);
+        for (int it = 0; it < A.nu1; ++it) {
+          if (it > 0 || l == 0) half_sweep(F.L, SF, 0);
+          half_sweep(F.L, SF, 1);
+        }
+        restrict_to(F.L, SF, C.L, SC, sg, l + 2 < nl);
+      }
+      {
+        const BottomLevel<T> C = level_at(A, smem_raw, nl - 1);
+        coarse_solve(A.Q, A.lam, A.sqa, A.nc, A.null_index, level_smem(smem_raw, C, f0g), sg64, sing, b, y);
+      }
+      for (int l = nl - 2; l >= 0; --l) {
+        const BottomLevel<T> F = level_at(A, smem_raw, l), C = level_at(A, smem_raw, l + 1);
+        const LevelSmem<T> SF = level_smem(smem_raw, F, f0g), SC = level_smem(smem_raw, C, f0g);
+        prolong_from(F.L, SF, C.L, SC, true);
+        for (int it = 0; it < A.nu2; ++it) {
+          half_sweep(F.L, SF, 0);
+          half_sweep(F.L, SF, 1);
+        }
+      }
+      ++cyc;
+      r2 = colour0_resid2(top.L, S0, sg, y);
+      if (!(r2 > thr2) || r2 > 0.36 * prev) break;  // done, stagnant, or not finite
+      prev = r2;
+    }
+  }
+  T* u0 = A.u_top + (long long)q * n0;
+  for (int c = threadIdx.x; c < n0; c += BT) u0[c] = S0.u[c];
+  if (threadIdx.x == 0) {
+    O.cycles[q] = cyc;
+    O.norm2[q] = r2;
+  }
+  __syncthreads();  // the shared memory is free for the next wavenumber
+}
+
+// One plan: CTA k solves wavenumber active[k].
+template <typename T>
+__global__ void __launch_bounds__(BT) k_onchip(const OnchipArgs<T> O) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  onchip_mode(O, O.B.active[blockIdx.x], smem_raw);
+}
+
+// Many plans in one persistent launch: every CTA takes (problem, wavenumber) items from a queue
+// (an atomic counter, zero at launch) until none is left; each item uses its own problem's tables.
+template <typename T>
+__global__ void __launch_bounds__(BT) k_onchip_batch(const OnchipArgs<T>* __restrict__ args, const int2* __restrict__ items,
+                                                     int nitems, int* __restrict__ next) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ int item;
+  for (;;) {
+    if (threadIdx.x == 0) item = atomicAdd(next, 1);
+    __syncthreads();
+    const int k = item;
+    __syncthreads();
+    if (k >= nitems) break;
+    const int2 w = items[k];
+    const OnchipArgs<T> O = args[w.x];
+    onchip_mode(O, w.y, smem_raw);
+  }
+}
+
+template <typename T>
+OnchipArgs<T> onchip_args(snac_plan* P, double target) {
+  OnchipArgs<T> O{};
+  BottomArgs<T>& A = O.B;
+  const int L = (int)P->lev.size() - 1;
+  const BottomLayout lay = bottom_layout(P, 0, sizeof(T));
+  A.nlev = L + 1;
+  A.split = 0;
+  A.nu1 = P->nu1;
+  A.nu2 = P->nu2;
+  A.lv = (const BottomLevel<T>*)P->d_onchip;
+  A.coarse_off = lay.coarse_off;
+  A.active = P->d_active;
+  if constexpr (sizeof(T) == 8) A.sigma = (const T*)P->d_sigma64;
+  else A.sigma = (const T*)P->d_sigma32;
+  A.sigma64 = P->d_sigma64;
+  A.singular_mode = P->d_singular_mode;
+  A.f_top = (const T*)P->lev[0].d_f;
+  A.u_top = (T*)P->lev[0].d_u;
+  A.Q = P->d_Q;
+  A.lam = P->d_lam;
+  A.sqa = P->d_sqa;
+  A.nc = P->nc;
+  A.null_index = P->null_index;
+  O.pweight = P->d_pweight;
+  O.t2nz = target * target / (double)P->nzt;
+  O.max_cycles = P->max_cycles;
+  O.cycles = P->dh_cycles;
+  O.norm2 = P->dh_mode_norm2;
+  return O;
+}
+
+// algorithmic bytes and flops of one on-chip V-cycle of one wavenumber, and of its load and store
+double onchip_cycle_flops(const snac_plan* P) {
+  double fl = 0.0;
+  const int L = (int)P->lev.size() - 1;
+  for (int l = 0; l < L; ++l) fl += (double)P->lev[l].ncell * (12.0 * (P->nu1 + P->nu2) + 15.0 + 8.0);
+  return fl + 4.0 * P->nc * P->nc + 7.0 * P->lev[0].ncell;
+}
+
+template <typename T>
+cudaError_t onchip_t(snac_plan* P, int nact, double target, cudaStream_t s) {
+  const OnchipArgs<T> O = onchip_args<T>(P, target);
+  const BottomLayout lay = bottom_layout(P, 0, sizeof(T));
+  cudaFuncSetAttribute(k_onchip<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, BOTTOM_MAX_SMEM);
+  const double w = sizeof(T);
+  // per wavenumber: f in, u out; the flops of an assumed 4 cycles (the kernel decides how many run)
+  LaunchScope ls(P, K_ONCHIP, 2.0 * w * (double)P->lev[0].ncell * nact, 4.0 * onchip_cycle_flops(P) * nact, s);
+  k_onchip<T><<<nact, BT, lay.bytes, s>>>(O);
+  return cudaGetLastError();
+}
+
 template <typename T>
 cudaError_t bottom_t(snac_plan* P, int nact, cudaStream_t s) {
   BottomArgs<T> A{};
@@ -371,6 +596,62 @@ BottomLayout bottom_layout(const snac_plan* P, int lb, size_t w) {
 cudaError_t launch_bottom(snac_plan* P, int nact, cudaStream_t s) {
   if (nact <= 0) return cudaSuccess;
   return P->precision == SNAC_FP64 ? bottom_t<double>(P, nact, s) : bottom_t<float>(P, nact, s);
+}
+
+cudaError_t launch_onchip(snac_plan* P, int nact, double target, cudaStream_t s) {
+  if (nact <= 0) return cudaSuccess;
+  if (!P->d_onchip) return cudaErrorInvalidValue;
+  return P->precision == SNAC_FP64 ? onchip_t<double>(P, nact, target, s) : onchip_t<float>(P, nact, target, s);
+}
+
+// Many plans, one launch: the items (plan index, wavenumber) of plans of the same precision, every
+// plan's level-0 right-hand side in place; targets per plan. Device scratch (args, items, counter)
+// is the caller's, `scratch_bytes` long (onchip_batch_scratch gives the size).
+size_t onchip_batch_scratch(int nplans, int nitems) {
+  return ((size_t)nplans * sizeof(OnchipArgs<double>) + 255) / 256 * 256 + ((size_t)nitems * sizeof(int2) + 255) / 256 * 256 + 256;
+}
+
+template <typename T>
+cudaError_t onchip_batch_t(snac_plan* const* plans, const double* targets, int nplans, const int2* h_items, int nitems,
+                           void* d_scratch, int sms, cudaStream_t s) {
+  std::vector<OnchipArgs<T>> args(nplans);
+  size_t smem = 0;
+  for (int k = 0; k < nplans; ++k) {
+    args[k] = onchip_args<T>(plans[k], targets[k]);
+    smem = std::max(smem, bottom_layout(plans[k], 0, sizeof(T)).bytes);
+  }
+  char* base = static_cast<char*>(d_scratch);
+  OnchipArgs<T>* d_args = reinterpret_cast<OnchipArgs<T>*>(base);
+  int2* d_items = reinterpret_cast<int2*>(base + ((size_t)nplans * sizeof(OnchipArgs<double>) + 255) / 256 * 256);
+  int* d_next = reinterpret_cast<int*>(reinterpret_cast<char*>(d_items) + ((size_t)nitems * sizeof(int2) + 255) / 256 * 256);
+  cudaError_t e;
+  if ((e = cudaMemcpyAsync(d_args, args.data(), nplans * sizeof(OnchipArgs<T>), cudaMemcpyHostToDevice, s)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(d_items, h_items, nitems * sizeof(int2), cudaMemcpyHostToDevice, s)) != cudaSuccess ||
+      (e = cudaMemsetAsync(d_next, 0, sizeof(int), s)) != cudaSuccess)
+    return e;
+  cudaFuncSetAttribute(k_onchip_batch<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, BOTTOM_MAX_SMEM);
+  int per_sm = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_onchip_batch<T>, BT, smem);
+  const int grid = std::max(1, std::min(nitems, std::max(1, per_sm) * sms));
+  for (int k = 0; k < nplans; ++k) {  // each plan counts the shared launch once, with its own items
+    snac_plan* P = plans[k];
+    double n = 0.0;
+    for (int i = 0; i < nitems; ++i) n += h_items[i].x == k ? 1.0 : 0.0;
+    KernelStat& ks = P->kstats[K_ONCHIP];
+    ++ks.launches;
+    ks.bytes += 2.0 * sizeof(T) * (double)P->lev[0].ncell * n;
+    ks.flops += 4.0 * onchip_cycle_flops(P) * n;
+  }
+  k_onchip_batch<T><<<grid, BT, smem, s>>>(d_args, d_items, nitems, d_next);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_onchip_batch(snac_plan* const* plans, const double* targets, int nplans, const int2* h_items,
+                                int nitems, void* d_scratch, int sms, cudaStream_t s) {
+  if (nplans <= 0 || nitems <= 0) return cudaSuccess;
+  if (plans[0]->precision == SNAC_FP64)
+    return onchip_batch_t<double>(plans, targets, nplans, h_items, nitems, d_scratch, sms, s);
+  return onchip_batch_t<float>(plans, targets, nplans, h_items, nitems, d_scratch, sms, s);
 }
 
 }  // namespace snac

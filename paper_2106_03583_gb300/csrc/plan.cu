@@ -515,6 +515,7 @@ void free_plan(snac_plan* P) {
   if (P->h_mode_norm2) cudaFreeHost(P->h_mode_norm2);
   if (P->h_active) cudaFreeHost(P->h_active);
   if (P->h_check) cudaFreeHost(P->h_check);
+  if (P->h_cycles) cudaFreeHost(P->h_cycles);
   delete P;
 }
 
@@ -673,6 +674,11 @@ int create(snac_plan** out, int32_t nblocks, const snac_block* blocks_in, int32_
     P->inner_reduction = opt->inner_reduction;
     P->fused = opt->fused;
     P->shift = opt->shift;
+    P->onchip_opt = opt->onchip;
+    if (opt->onchip != 0 && opt->onchip != -1) {
+      delete P;
+      return fail(SNAC_ERR_INVALID_ARG, "bad snac_options: onchip must be 0 or -1");
+    }
     if (!(P->inner_reduction > 0.0 && P->inner_reduction < 1.0) || !(P->shift <= 0.0) || !std::isfinite(P->shift) || (P->precision != SNAC_FP64 && P->precision != SNAC_MIXED) || P->nu1 < 0 || P->nu2 < 0 ||
         P->nu1 + P->nu2 < 1 || P->nu1 > 16 || P->nu2 > 16 || P->max_outer < 1 || P->max_cycles < 1 ||
         P->max_coarse < 1 || P->max_coarse > MAX_COARSE) {
@@ -793,6 +799,7 @@ int create(snac_plan** out, int32_t nblocks, const snac_block* blocks_in, int32_
       P->pweight.push_back(parseval_weight(P->kind, P->nzt, P->q0 + l));
     }
     if ((st = upload(P, &P->d_sigma64, P->sigma)) || (st = upload(P, &P->d_sigma32, to32(P->sigma)))) break;
+    if ((st = upload(P, &P->d_pweight, P->pweight))) break;
     std::vector<int> sm(P->nz, 0);
     for (int l = 0; l < P->nz; ++l) sm[l] = (P->singular && mode_lambda(P->kind, P->nzt, P->q0 + l) == 0.0) ? 1 : 0;
     if ((st = upload(P, &P->d_singular_mode, sm))) break;
@@ -810,9 +817,15 @@ int create(snac_plan** out, int32_t nblocks, const snac_block* blocks_in, int32_
             break;
           }
     }
+    // the whole hierarchy on chip: every wavenumber's complete solve in one CTA (kern_bottom.cu)
+    {
+      const int L = (int)P->lev.size() - 1;
+      P->onchip = P->onchip_opt == 0 && P->nu1 >= 1 && P->nu2 >= 1 && L >= 1 && L < BOTTOM_MAX_LEVELS &&
+                  P->lev[0].ncell <= BOTTOM_MAX_CELLS && bottom_layout(P, 0, inner).bytes <= (size_t)BOTTOM_MAX_SMEM;
+    }
     // fused FP32 tile kernels on the levels whose blocks all keep the halo inside their neighbours
-    // (above the bottom sub-cycle)
-    const bool want_fused = P->fused == 1 || (P->fused < 0 && P->precision == SNAC_MIXED);
+    // (above the bottom sub-cycle; not needed when the whole solve runs on chip)
+    const bool want_fused = !P->onchip && (P->fused == 1 || (P->fused < 0 && P->precision == SNAC_MIXED));
     if (want_fused && P->nu1 >= 1 && P->nu2 >= 1 && P->nu1 <= 2 && P->nu2 <= 2) {
       for (size_t l = 0; l + 1 < P->lev.size(); ++l) {
         if (P->bottom >= 0 && (int)l >= P->bottom) break;
@@ -836,7 +849,7 @@ int create(snac_plan** out, int32_t nblocks, const snac_block* blocks_in, int32_
     if (P->precision == SNAC_FP64) {
       bool any_fused = false;
       for (const HostLevel& lv : P->lev) any_fused = any_fused || lv.fused;
-      P->scaled_f = !any_fused && P->lev.size() > 1;
+      P->scaled_f = !any_fused && P->lev.size() > 1 && !P->onchip;
       for (size_t l = 0; l + 1 < P->lev.size(); ++l)
         if ((st = dmalloc(P, &P->lev[l].d_invd, (size_t)P->nz * P->lev[l].ncell))) break;
       if (st) break;
@@ -874,6 +887,29 @@ int create(snac_plan** out, int32_t nblocks, const snac_block* blocks_in, int32_
       };
       if ((st = P->precision == SNAC_FP64 ? build_bottom(double{}) : build_bottom(float{}))) break;
     }
+    if (P->onchip) {  // the same kind of table for the whole hierarchy, from level 0
+      const int L = (int)P->lev.size() - 1;
+      auto build_onchip = [&](auto tag) -> int {
+        using T = decltype(tag);
+        const BottomLayout lay = bottom_layout(P, 0, sizeof(T));
+        std::vector<BottomLevel<T>> tab;
+        for (int l = 0; l <= L; ++l) {
+          BottomLevel<T> b{};
+          b.L = level_view<T>(P->lev[l]);
+          b.invd = (sizeof(T) == 8 && l < L) ? P->lev[l].d_invd : nullptr;
+          b.su = lay.su[l];
+          b.sf = lay.sf[l];
+          b.sinv = lay.sinv[l];
+          b.sblk = lay.sblk[l];
+          tab.push_back(b);
+        }
+        BottomLevel<T>* d = nullptr;
+        const int s2 = upload(P, &d, tab);
+        P->d_onchip = d;
+        return s2;
+      };
+      if ((st = P->precision == SNAC_FP64 ? build_onchip(double{}) : build_onchip(float{}))) break;
+    }
     if ((st = build_twiddles(P))) break;
     if ((st = build_chunks(P, 8, P->chunks64, &P->d_chunks64))) break;
     if ((st = build_chunks(P, 16, P->chunks32, &P->d_chunks32))) break;
@@ -900,7 +936,8 @@ int create(snac_plan** out, int32_t nblocks, const snac_block* blocks_in, int32_
              cudaHostGetDevicePointer((void**)dh, (void*)*h, 0) == cudaSuccess;
     };
     if (!mapped(&P->h_sums, &P->dh_sums, SUM_SLOTS) || !mapped(&P->h_mode_norm2, &P->dh_mode_norm2, P->nz) ||
-        !mapped(&P->h_active, &P->dh_active, P->nz) || !mapped(&P->h_check, &P->dh_check, P->nz)) {
+        !mapped(&P->h_active, &P->dh_active, P->nz) || !mapped(&P->h_check, &P->dh_check, P->nz) ||
+        !mapped(&P->h_cycles, &P->dh_cycles, P->nz)) {
       st = fail(SNAC_ERR_OOM, "pinned host allocation");
       break;
     }

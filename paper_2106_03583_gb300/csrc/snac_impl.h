@@ -156,7 +156,7 @@ struct TwiddleOffsets {
 // Kernel kinds counted by the tracing facility.
 enum KernelKind {
   K_FIELD3D = 0, K_REDUCE, K_FIX_MEAN, K_SHIFT, K_FORWARD, K_BACKWARD, K_SMOOTH, K_RESTRICT, K_PROLONG,
-  K_COARSE, K_MODE_RESID, K_MODE_REDUCE, K_MODE_APPLY, K_FDOWN, K_FUP, K_BOTTOM, K_FIELD3D_FF, K_COUNT
+  K_COARSE, K_MODE_RESID, K_MODE_REDUCE, K_MODE_APPLY, K_FDOWN, K_FUP, K_BOTTOM, K_FIELD3D_FF, K_ONCHIP, K_COUNT
 };
 
 struct KernelStat {
@@ -184,6 +184,14 @@ struct snac_plan {
   bool scaled_f = false;
   int bottom = -1;  // first level of the one-launch bottom sub-cycle (kern_bottom.cu), -1: none
   void* d_bottom = nullptr;  // its BottomLevel<inner type> table
+  // the whole hierarchy fits in one CTA's shared memory: each wavenumber's solve runs on chip,
+  // its convergence decided on the device (kern_bottom.cu, k_onchip)
+  bool onchip = false;
+  int onchip_opt = 0;         // snac_options.onchip
+  void* d_onchip = nullptr;   // BottomLevel<inner type> table from level 0
+  double* d_pweight = nullptr;
+  int* h_cycles = nullptr;    // per wavenumber: V-cycles of the last on-chip solve (mapped pinned)
+  int* dh_cycles = nullptr;
   int nblk = 0;
   int nz = 0;    // wavenumbers held in mode space (q0 .. q0 + nz - 1)
   int nzt = 0;   // cells along the homogeneous axis: the transform length, the 3-D field's z planes
@@ -338,6 +346,15 @@ cudaError_t launch_mode_norms(snac_plan* P, int nactive, bool after_cycle, cudaS
                               bool zero_u = false);
 // The V-cycle from level P->bottom down to the coarsest and back, one CTA per active mode.
 cudaError_t launch_bottom(snac_plan* P, int nact, cudaStream_t s);
+// Plans whose hierarchy fits on chip: the complete solve of each active wavenumber from a zero
+// iterate, one CTA each, to ||r_q||^2 <= target^2 / (n_z w_q) (or stagnation, or max_cycles);
+// per-mode cycles into dh_cycles and final ||r_q||^2 into dh_mode_norm2.
+cudaError_t launch_onchip(snac_plan* P, int nact, double target, cudaStream_t s);
+// The same for the wavenumbers of several plans (one precision) in one persistent launch; h_items
+// (plan index, wavenumber), targets per plan; d_scratch of onchip_batch_scratch(nplans, nitems) bytes.
+size_t onchip_batch_scratch(int nplans, int nitems);
+cudaError_t launch_onchip_batch(snac_plan* const* plans, const double* targets, int nplans, const int2* h_items,
+                                int nitems, void* d_scratch, int sms, cudaStream_t s);
 // Shared-memory layout of that kernel when it starts at level lb, for inner type width w: per level
 // the element offsets of u, f (-1: the top level's f stays in global memory, as in FP64 plans, so
 // that two CTAs fit on one multiprocessor) and 1/diag (-1 on the coarsest level), the byte offset of

@@ -113,10 +113,28 @@ cudaError_t run_round(snac_plan* P, int nact, bool norms, cudaStream_t s, int* r
   return cudaGraphLaunch(it->second.exec, s);
 }
 
+// The on-chip path's results: per-mode cycles and final norms from the mapped host arrays.
+int onchip_results(snac_plan* P, int* cycles_out) {
+  int total = 0;
+  for (int q = 0; q < P->nz; ++q) {
+    cycles_out[q] = P->h_cycles[q];
+    total += cycles_out[q];
+    if (!std::isfinite(P->h_mode_norm2[q])) return SNAC_ERR_NONFINITE;
+  }
+  P->info.total_cycles += total;
+  return SNAC_OK;
+}
+
 int mode_solves(snac_plan* P, double target, cudaStream_t s, int* cycles_out) {
   const int nz = P->nz;
   int st = set_active_all(P, s);
   if (st) return st;
+  if (P->onchip) {  // every wavenumber's whole solve in one CTA; convergence decided on the device
+    CK(launch_onchip(P, nz, target, s));
+    CK(cudaStreamSynchronize(s));
+    profile_resolve(P);
+    return onchip_results(P, cycles_out);
+  }
   // norms of the zero iterate (the right-hand side), which the same pass sets to zero
   CK(launch_mode_norms(P, nz, false, s, nullptr, true));
   CK(launch_to_host(P->d_mode_norm2, P->dh_mode_norm2, nz, s));
@@ -206,121 +224,294 @@ int read_sums(snac_plan* P, cudaStream_t s, int n = 4) {
   return SNAC_OK;
 }
 
-int run_solve(snac_plan* P, const double* f, double* p, double tol, cudaStream_t s) {
+// One problem's solve as a sequence of steps, so that several problems can run in lock-step: their
+// launches of one phase go out together, one stream synchronisation serves all of them, and the
+// on-chip wavenumber solves of all of them share one persistent launch. A single solve is a batch of
+// one (the same steps, the same synchronisations as a dedicated loop would have).
+struct Job {
+  snac_plan* P = nullptr;
+  const double* f = nullptr;
+  double* p = nullptr;
+  double tol = 0.0;
+  int st = SNAC_OK;
+  bool finished = false;
+  bool p_zero = false, updated = false, aim_final = false, r32 = false, ff = false, redo = false;
+  double fshift = 0.0, fn = 0.0, fn_pre = 0.0, prev_rel = INFINITY, rn = 0.0, target = 0.0;
+  int k = 0;
+  std::vector<int> cyc;
+  void finish(int status) {
+    st = status;
+    finished = true;
+    P->info.status = status;
+  }
+};
+
+// Mixed plans compute the residual of an intermediate defect-correction step in float-float
+// arithmetic (written in FP32, the precision the FP32 transform reads); the FP64 pass decides
+// convergence: it runs after a correction that aimed at the tolerance itself, and whenever the
+// float-float residual comes within 2x of the tolerance. (The float-float error, a few units of
+// 2^-47 of |f| + |A||p| per cell, is about 1e-11 ||f|| on the 2.7e8-cell channel: it steers an
+// intermediate correction well enough, but a convergence decision near tol takes the FP64 pass.)
+
+// pre-pass: statistics of f, and whether the initial guess is zero (then r = f - fshift at k = 0
+// and the first residual pass is not needed)
+cudaError_t job_begin(Job& J, cudaStream_t s) {
+  snac_plan* P = J.P;
   P->info = snac_solve_info{};
   P->info.levels = (int)P->lev.size();
   P->info.n_modes = P->nz;
   std::fill(P->mode_cycles.begin(), P->mode_cycles.end(), 0);
-  double fshift = 0.0;
-  int st;
-  // pre-pass: statistics of f, and whether the initial guess is zero (then r = f - fshift at k = 0
-  // and the first residual pass is not needed)
-  CK(launch_prepass(P, f, p, s));
-  if ((st = read_sums(P, s, SUM_NONZERO + 1))) return st;
-  const bool p_zero = P->h_sums[SUM_NONZERO] == 0.0;
+  J.cyc.assign(P->nz, 0);
+  cudaError_t e = launch_prepass(P, J.f, J.p, s);
+  if (e == cudaSuccess) e = launch_to_host(P->d_sums, P->dh_sums, SUM_NONZERO + 1, s);
+  return e;
+}
+
+void job_begin_read(Job& J) {
+  snac_plan* P = J.P;
+  profile_resolve(P);
+  J.p_zero = P->h_sums[SUM_NONZERO] == 0.0;
   const double f2 = P->h_sums[2], sum_f = P->h_sums[3];
-  if (!std::isfinite(f2)) return SNAC_ERR_NONFINITE;
+  if (!std::isfinite(f2)) return J.finish(SNAC_ERR_NONFINITE);
   if (P->singular) {
     const double vf = P->h_sums[0], vaf = P->h_sums[1];
-    if (!std::isfinite(vf) || !std::isfinite(vaf)) return SNAC_ERR_NONFINITE;
+    if (!std::isfinite(vf) || !std::isfinite(vaf)) return J.finish(SNAC_ERR_NONFINITE);
     if (std::fabs(vf) > 1e-12 * vaf) {
       set_error("singular problem: the volume-weighted sum of the right-hand side is not zero");
-      return SNAC_ERR_INCOMPATIBLE_RHS;
+      return J.finish(SNAC_ERR_INCOMPATIBLE_RHS);
     }
-    fshift = vf / P->vol_total;
-    P->info.removed_mean = fshift;
+    J.fshift = vf / P->vol_total;
+    P->info.removed_mean = J.fshift;
   }
   // ||f - fshift||^2 = ||f||^2 - fshift (2 sum f - N fshift)
-  const double fn_pre = std::sqrt(std::max(0.0, f2 - fshift * (2.0 * sum_f - (double)P->n3 * fshift)));
-  const bool mixed = P->precision == SNAC_MIXED;
-  double prev_rel = INFINITY, fn = 0.0;
-  bool updated = false;
-  // Mixed plans compute the residual of an intermediate defect-correction step in float-float
-  // arithmetic (written in FP32, the precision the FP32 transform reads); the FP64 pass decides
-  // convergence: it runs after a correction that aimed at the tolerance itself, and whenever the
-  // float-float residual comes within 2x of the tolerance. (The float-float error, a few units of
-  // 2^-47 of |f| + |A||p| per cell, is about 1e-11 ||f|| on the 2.7e8-cell channel: it steers an
-  // intermediate correction well enough, but a convergence decision near tol takes the FP64 pass.)
-  bool aim_final = false;
-  std::vector<int> cyc(P->nz);
-  for (int k = 0;; ++k) {
-    const bool from_f = k == 0 && p_zero;
-    double rn;
-    bool r32 = false;  // the residual in d_r3 is the float-float pass's FP32 field
-    if (from_f) {
-      fn = rn = fn_pre;
-      if (P->singular) CK(launch_fill(P->d_sums + 2, 1, 0.0, s));  // sum V p = 0
-    } else {
-      // ||f|| is needed once; sum V p only for singular problems (zero-mean update). In FP64 plans
-      // only for the caller's initial guess: an update leaves sum V p = 0 to rounding (the mean fix
-      // solves for it), so later passes take it as 0 (their partials carry 0 in that slot). Mixed
-      // plans measure it every time: the FP32 transform of the correction leaves a drift that the
-      // next mean fix removes.
-      const bool need_vp = P->singular && (k == 0 || P->precision != SNAC_FP64);
-      if (mixed && k > 0 && !aim_final) {
-        CK(launch_field3d_ff(P, f, p, reinterpret_cast<float*>(P->d_r3), fshift, fn / std::sqrt((double)P->n3), false,
-                             need_vp, s));
-        if ((st = read_sums(P, s))) return st;
-        rn = std::sqrt(P->h_sums[0]);
-        r32 = !(rn <= 2.0 * tol * fn);  // (NaN stays: reported below)
-      }
-      if (!r32) {
-        CK(launch_field3d(P, 0, f, p, P->d_r3, fshift, k == 0, need_vp, s));
-        if ((st = read_sums(P, s))) return st;
-        if (k == 0) fn = std::sqrt(P->h_sums[1]);
-        rn = std::sqrt(P->h_sums[0]);
-      }
-    }
-    if (!std::isfinite(rn) || !std::isfinite(fn)) return SNAC_ERR_NONFINITE;
-    P->info.rhs_norm = fn;
-    P->info.outer_iters = k;
-    if (fn == 0.0) {  // zero right-hand side: p = 0
-      CK(cudaMemsetAsync(p, 0, (size_t)P->n3 * sizeof(double), s));
+  J.fn_pre = std::sqrt(std::max(0.0, f2 - J.fshift * (2.0 * sum_f - (double)P->n3 * J.fshift)));
+}
+
+// The residual pass of step k (none for k = 0 from a zero guess): launched, read after a sync.
+cudaError_t job_resid_launch(Job& J, cudaStream_t s) {
+  snac_plan* P = J.P;
+  J.r32 = J.ff = J.redo = false;
+  if (J.k == 0 && J.p_zero) {
+    J.fn = J.rn = J.fn_pre;
+    return P->singular ? launch_fill(P->d_sums + 2, 1, 0.0, s) : cudaSuccess;  // sum V p = 0
+  }
+  // ||f|| is needed once; sum V p only for singular problems (zero-mean update). In FP64 plans
+  // only for the caller's initial guess: an update leaves sum V p = 0 to rounding (the mean fix
+  // solves for it), so later passes take it as 0 (their partials carry 0 in that slot). Mixed
+  // plans measure it every time: the FP32 transform of the correction leaves a drift that the
+  // next mean fix removes.
+  const bool need_vp = P->singular && (J.k == 0 || P->precision != SNAC_FP64);
+  cudaError_t e;
+  if (P->precision == SNAC_MIXED && J.k > 0 && !J.aim_final) {
+    J.ff = true;
+    e = launch_field3d_ff(P, J.f, J.p, reinterpret_cast<float*>(P->d_r3), J.fshift, J.fn / std::sqrt((double)P->n3),
+                          false, need_vp, s);
+  } else {
+    e = launch_field3d(P, 0, J.f, J.p, P->d_r3, J.fshift, J.k == 0, need_vp, s);
+  }
+  if (e == cudaSuccess) e = launch_to_host(P->d_sums, P->dh_sums, 4, s);
+  return e;
+}
+
+// After the sync: read the pass. A float-float pass within 2x of the tolerance launches the FP64
+// pass instead (J.redo: read again after another sync).
+cudaError_t job_resid_read(Job& J, cudaStream_t s) {
+  snac_plan* P = J.P;
+  profile_resolve(P);
+  if (J.k == 0 && J.p_zero) return cudaSuccess;
+  if (J.ff && !J.redo) {
+    J.rn = std::sqrt(P->h_sums[0]);
+    J.r32 = !(J.rn <= 2.0 * J.tol * J.fn);  // (NaN stays: reported by the decision)
+    if (J.r32) return cudaSuccess;
+    J.redo = true;
+    const bool need_vp = P->singular;
+    cudaError_t e = launch_field3d(P, 0, J.f, J.p, P->d_r3, J.fshift, false, need_vp, s);
+    if (e == cudaSuccess) e = launch_to_host(P->d_sums, P->dh_sums, 4, s);
+    return e;
+  }
+  if (J.k == 0) J.fn = std::sqrt(P->h_sums[1]);
+  J.rn = std::sqrt(P->h_sums[0]);
+  J.redo = false;
+  return cudaSuccess;
+}
+
+// Convergence decision of step k; on continuing, the forward transform of the residual.
+int job_decide(Job& J, cudaStream_t s) {
+  snac_plan* P = J.P;
+  int st;
+  const double rn = J.rn, fn = J.fn;
+  if (!std::isfinite(rn) || !std::isfinite(fn)) {
+    J.finish(SNAC_ERR_NONFINITE);
+    return SNAC_OK;
+  }
+  P->info.rhs_norm = fn;
+  P->info.outer_iters = J.k;
+  if (fn == 0.0) {  // zero right-hand side: p = 0
+    CK(cudaMemsetAsync(J.p, 0, (size_t)P->n3 * sizeof(double), s));
+    CK(cudaStreamSynchronize(s));
+    profile_resolve(P);
+    P->info.rel_res = 0.0;
+    J.finish(SNAC_OK);
+    return SNAC_OK;
+  }
+  const double rel = rn / fn;
+  P->info.rel_res = rel;
+  const bool done = rel <= J.tol;
+  // a correction that did not lower the residual: the inner solve has reached the floating-point
+  // floor of the outer residual (or diverged); more steps would not help
+  const bool stalled = J.updated && rel >= J.prev_rel;
+  const bool give_up = !done && (J.k >= P->max_outer || stalled);
+  if (done || give_up) {
+    if (P->singular && !J.updated) {  // the initial guess was kept: return its zero-mean shift
+      CK(launch_shift(P, J.p, P->d_sums + 3, s));
       CK(cudaStreamSynchronize(s));
       profile_resolve(P);
-      P->info.rel_res = 0.0;
-      return SNAC_OK;
     }
-    const double rel = rn / fn;
-    P->info.rel_res = rel;
-    const bool done = rel <= tol;
-    // a correction that did not lower the residual: the inner solve has reached the floating-point
-    // floor of the outer residual (or diverged); more steps would not help
-    const bool stalled = updated && rel >= prev_rel;
-    const bool give_up = !done && (k >= P->max_outer || stalled);
-    if (done || give_up) {
-      if (P->singular && !updated) {  // the initial guess was kept: return its zero-mean shift
-        CK(launch_shift(P, p, P->d_sums + 3, s));
-        CK(cudaStreamSynchronize(s));
-        profile_resolve(P);
-      }
-      if (stalled) {
-        // return the better iterate: take the last correction back (its modes are still in the
-        // level-0 iterate) and report the residual of what is returned, re-evaluated
-        CK(launch_backward_update(P, P->lev[0].d_u, p, s, true));
-        CK(launch_field3d(P, 0, f, p, P->d_r3, fshift, false, false, s));
-        if ((st = read_sums(P, s))) return st;
-        P->info.rel_res = std::sqrt(P->h_sums[0]) / fn;
-      }
-      return done ? SNAC_OK : SNAC_ERR_NOT_CONVERGED;
+    if (stalled) {
+      // return the better iterate: take the last correction back (its modes are still in the
+      // level-0 iterate) and report the residual of what is returned, re-evaluated
+      CK(launch_backward_update(P, P->lev[0].d_u, J.p, s, true));
+      CK(launch_field3d(P, 0, J.f, J.p, P->d_r3, J.fshift, false, false, s));
+      if ((st = read_sums(P, s))) return st;
+      P->info.rel_res = std::sqrt(P->h_sums[0]) / fn;
     }
-    prev_rel = rel;
-    // target of this defect-correction step
-    double target = 0.5 * tol * fn;
-    if (mixed) target = std::max(target, P->inner_reduction * rn);
-    aim_final = target <= 0.5 * tol * fn;
-    if (from_f) CK(launch_forward(P, f, P->lev[0].d_f, fshift, P->scaled_f, s));
-    else if (r32) CK(launch_forward_f32(P, reinterpret_cast<const float*>(P->d_r3), P->lev[0].d_f, s));
-    else CK(launch_forward(P, P->d_r3, P->lev[0].d_f, 0.0, P->scaled_f, s));
-    if ((st = mode_solves(P, target, s, cyc.data()))) return st;
-    for (int q = 0; q < P->nz; ++q) {
-      P->mode_cycles[q] = cyc[q];
-      P->info.max_mode_cycles = std::max(P->info.max_mode_cycles, cyc[q]);
-    }
-    if (P->singular) CK(launch_fix_mean(P, P->lev[0].d_u, s));
-    CK(launch_backward_update(P, P->lev[0].d_u, p, s));
-    updated = true;
+    J.finish(done ? SNAC_OK : SNAC_ERR_NOT_CONVERGED);
+    return SNAC_OK;
   }
+  J.prev_rel = rel;
+  // target of this defect-correction step: the tolerance (with a factor 2 of margin); in mixed
+  // plans a reduction by inner_reduction while that is still above the tolerance -- once it is not,
+  // the step aims at the tolerance itself (an FP32 solve reaches it from there), which saves a step
+  J.target = 0.5 * J.tol * fn;
+  if (P->precision == SNAC_MIXED && P->inner_reduction * rn > J.tol * fn) J.target = P->inner_reduction * rn;
+  J.aim_final = J.target <= 0.5 * J.tol * fn;
+  if (J.k == 0 && J.p_zero) CK(launch_forward(P, J.f, P->lev[0].d_f, J.fshift, P->scaled_f, s));
+  else if (J.r32) CK(launch_forward_f32(P, reinterpret_cast<const float*>(P->d_r3), P->lev[0].d_f, s));
+  else CK(launch_forward(P, P->d_r3, P->lev[0].d_f, 0.0, P->scaled_f, s));
+  return SNAC_OK;
+}
+
+// After the wavenumber solves: record their cycles, fix the mean, update p.
+cudaError_t job_update(Job& J, cudaStream_t s) {
+  snac_plan* P = J.P;
+  for (int q = 0; q < P->nz; ++q) {
+    P->mode_cycles[q] = J.cyc[q];
+    P->info.max_mode_cycles = std::max(P->info.max_mode_cycles, J.cyc[q]);
+  }
+  cudaError_t e = cudaSuccess;
+  if (P->singular) e = launch_fix_mean(P, P->lev[0].d_u, s);
+  if (e == cudaSuccess) e = launch_backward_update(P, P->lev[0].d_u, J.p, s);
+  J.updated = true;
+  ++J.k;
+  return e;
+}
+
+int job_cuda(Job& J, cudaError_t e, const char* where) {
+  if (e != cudaSuccess) J.finish(cuda_fail(e, where));
+  return J.st;
+}
+
+// Run the jobs to completion on stream s (all plans on the current device).
+int run_jobs(std::vector<Job>& jobs, cudaStream_t s) {
+  auto sync = [&]() -> cudaError_t { return cudaStreamSynchronize(s); };
+  for (Job& J : jobs) job_cuda(J, job_begin(J, s), "pre-pass");
+  cudaError_t e = sync();
+  if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+  for (Job& J : jobs)
+    if (!J.finished) job_begin_read(J);
+  void* scratch = nullptr;
+  size_t scratch_bytes = 0;
+  int sms = jobs.empty() ? 152 : jobs[0].P->sms;
+  int status = SNAC_OK;
+  for (;;) {
+    bool any = false;
+    for (Job& J : jobs) any = any || !J.finished;
+    if (!any) break;
+    for (Job& J : jobs)
+      if (!J.finished) job_cuda(J, job_resid_launch(J, s), "residual");
+    if ((e = sync()) != cudaSuccess) { status = cuda_fail(e, "cudaStreamSynchronize"); break; }
+    bool redo = false;
+    for (Job& J : jobs)
+      if (!J.finished && job_cuda(J, job_resid_read(J, s), "residual") == SNAC_OK) redo = redo || J.redo;
+    if (redo) {
+      if ((e = sync()) != cudaSuccess) { status = cuda_fail(e, "cudaStreamSynchronize"); break; }
+      for (Job& J : jobs)
+        if (!J.finished && J.redo) job_cuda(J, job_resid_read(J, s), "residual");
+    }
+    for (Job& J : jobs)
+      if (!J.finished) {
+        const int st = job_decide(J, s);
+        if (st) J.finish(st);
+      }
+    // the wavenumber solves: on-chip plans together (one persistent launch per precision), the
+    // others level by level
+    std::vector<Job*> chip[2];
+    for (Job& J : jobs)
+      if (!J.finished && J.P->onchip) chip[J.P->precision == SNAC_FP64 ? 0 : 1].push_back(&J);
+    for (int g = 0; g < 2; ++g) {
+      if (chip[g].empty()) continue;
+      if (chip[g].size() == 1) {
+        Job& J = *chip[g][0];
+        job_cuda(J, set_active_all(J.P, s) == SNAC_OK ? launch_onchip(J.P, J.P->nz, J.target, s) : cudaErrorUnknown,
+                 "on-chip wavenumber solves");
+        continue;
+      }
+      std::vector<snac_plan*> plans;
+      std::vector<double> targets;
+      std::vector<int2> items;
+      for (Job* J : chip[g]) {
+        const int idx = (int)plans.size();
+        plans.push_back(J->P);
+        targets.push_back(J->target);
+        for (int q = 0; q < J->P->nz; ++q) items.push_back(make_int2(idx, q));
+      }
+      const size_t need = onchip_batch_scratch((int)plans.size(), (int)items.size());
+      if (need > scratch_bytes) {
+        if (scratch) cudaFreeAsync(scratch, s);
+        scratch = nullptr;
+        scratch_bytes = 0;
+        if ((e = cudaMallocAsync(&scratch, need, s)) != cudaSuccess) { status = cuda_fail(e, "cudaMallocAsync"); break; }
+        scratch_bytes = need;
+      }
+      e = launch_onchip_batch(plans.data(), targets.data(), (int)plans.size(), items.data(), (int)items.size(), scratch,
+                              sms, s);
+      if (e != cudaSuccess)
+        for (Job* J : chip[g]) job_cuda(*J, e, "on-chip wavenumber solves");
+    }
+    if (status) break;
+    for (Job& J : jobs)
+      if (!J.finished && !J.P->onchip) {
+        const int st = mode_solves(J.P, J.target, s, J.cyc.data());
+        if (st) J.finish(st);
+      }
+    if (!chip[0].empty() || !chip[1].empty()) {
+      if ((e = sync()) != cudaSuccess) { status = cuda_fail(e, "cudaStreamSynchronize"); break; }
+      for (int g = 0; g < 2; ++g)
+        for (Job* J : chip[g])
+          if (!J->finished) {
+            profile_resolve(J->P);
+            const int st = onchip_results(J->P, J->cyc.data());
+            if (st) J->finish(st);
+          }
+    }
+    for (Job& J : jobs)
+      if (!J.finished) job_cuda(J, job_update(J, s), "update");
+  }
+  if (scratch) {
+    cudaFreeAsync(scratch, s);
+    cudaStreamSynchronize(s);
+  }
+  return status;
+}
+
+int run_solve(snac_plan* P, const double* f, double* p, double tol, cudaStream_t s) {
+  std::vector<Job> jobs(1);
+  jobs[0].P = P;
+  jobs[0].f = f;
+  jobs[0].p = p;
+  jobs[0].tol = tol;
+  const int st = run_jobs(jobs, s);
+  return st ? st : jobs[0].st;
 }
 
 }  // namespace
@@ -334,6 +525,34 @@ int snac_poisson_solve(snac_plan* plan, const double* d_rhs, double* d_p, double
   st = run_solve(plan, d_rhs, d_p, tol, (cudaStream_t)stream);
   plan->info.status = st;
   return st;
+}
+
+int snac_poisson_solve_batch(int32_t n, snac_plan* const* plans, const double* const* d_rhs, double* const* d_p,
+                             double tol, int32_t* h_status, void* stream) {
+  if (n < 1 || !plans || !d_rhs || !d_p || !h_status || !(tol > 0.0) || !std::isfinite(tol)) return SNAC_ERR_INVALID_ARG;
+  std::vector<Job> jobs(n);
+  for (int k = 0; k < n; ++k) {
+    int st = check_plan3d(plans[k]);
+    if (st) return st;
+    if (!d_rhs[k] || !d_p[k]) return SNAC_ERR_INVALID_ARG;
+    for (int j = 0; j < k; ++j)
+      if (plans[j] == plans[k]) {
+        set_error("a plan appears twice in one batch");
+        return SNAC_ERR_INVALID_ARG;
+      }
+    jobs[k].P = plans[k];
+    jobs[k].f = d_rhs[k];
+    jobs[k].p = d_p[k];
+    jobs[k].tol = tol;
+  }
+  const int st = run_jobs(jobs, (cudaStream_t)stream);
+  int worst = st;
+  for (int k = 0; k < n; ++k) {
+    h_status[k] = st ? st : jobs[k].st;
+    plans[k]->info.status = h_status[k];
+    if (!worst && h_status[k]) worst = h_status[k];
+  }
+  return worst;
 }
 
 int snac_apply_operator(snac_plan* plan, const double* d_p, double* d_out, void* stream) {

@@ -31,6 +31,7 @@ EXPORTS = ("snac_plan_create", "snac_plan_workspace_bytes", "snac_poisson_solve"
            "snac_mode_operator", "snac_mode_vcycles", "snac_plan_set_profiling", "snac_plan_kernel_stats",
            "snac_plan_reset_stats", "snac_residual_noalloc", "snac_pencil_forward", "snac_pencil_backward_update",
            "snac_pencil_setup", "snac_pencil_residual", "snac_mode_solve", "snac_mode_fix_mean",
+           "snac_poisson_solve_batch",
            "snac_engine_create", "snac_engine_submit", "snac_engine_wait", "snac_engine_get_stats",
            "snac_engine_clock", "snac_engine_destroy", "snac_autotune")
 
@@ -51,7 +52,7 @@ class _Options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("nu1", ctypes.c_int32), ("nu2", ctypes.c_int32),
                 ("max_outer", ctypes.c_int32), ("max_cycles", ctypes.c_int32), ("max_coarse", ctypes.c_int32),
                 ("fused", ctypes.c_int32), ("inner_reduction", ctypes.c_double), ("shift", ctypes.c_double),
-                ("mode_begin", ctypes.c_int32), ("mode_end", ctypes.c_int32)]
+                ("mode_begin", ctypes.c_int32), ("mode_end", ctypes.c_int32), ("onchip", ctypes.c_int32)]
 
 
 class _KStat(ctypes.Structure):
@@ -122,6 +123,8 @@ def lib() -> ctypes.CDLL:
             "snac_pencil_residual": [vp, vp, vp, vp, f64, ctypes.POINTER(f64), vp],
             "snac_mode_solve": [vp, vp, vp, f64, vp],
             "snac_mode_fix_mean": [vp, vp, f64, vp],
+            "snac_poisson_solve_batch": [i32, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(vp), f64,
+                                         ctypes.POINTER(i32), vp],
             "snac_forward_transform": [vp, vp, vp, vp],
             "snac_backward_update": [vp, vp, vp, vp],
             "snac_mode_operator": [vp, vp, vp, vp],
@@ -196,7 +199,7 @@ class Plan:
 
     def __init__(self, blocks, homog_axis: int = 2, precision: str = "fp64", nu1: int = 2, nu2: int = 2,
                  max_outer: int = 20, max_cycles: int = 40, max_coarse: int = 64, inner_reduction: float = 1e-3,
-                 fused: int = -1, shift: float = 0.0, modes=None):
+                 fused: int = -1, shift: float = 0.0, modes=None, onchip: bool = True):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("snac.Plan needs a CUDA device")
@@ -210,7 +213,7 @@ class Plan:
         arr, keep = _marshal_blocks(blocks)
         q0, q1 = modes if modes is not None else (0, 0)
         opt = _Options(_PREC[precision], nu1, nu2, max_outer, max_cycles, max_coarse, fused, inner_reduction, shift,
-                       int(q0), int(q1))
+                       int(q0), int(q1), 0 if onchip else -1)
         h = ctypes.c_void_p()
         _check(lib().snac_plan_create(ctypes.byref(h), len(blocks), arr, homog_axis, ctypes.byref(opt)))
         del keep
@@ -383,6 +386,23 @@ class Plan:
 
     def __exit__(self, *exc):
         self.close()
+
+
+def solve_batch(plans, rhs, p, tol: float = 1e-10, raise_on_error: bool = True) -> list:
+    """Solve several problems together (snac_poisson_solve_batch): plans[k] with rhs[k] -> p[k]
+    (CUDA float64 tensors as in Plan.solve). Returns each plan's info()."""
+    import torch
+    n = len(plans)
+    if not (len(rhs) == len(p) == n) or n == 0:
+        raise ValueError("one rhs and one p per plan")
+    hs = (ctypes.c_void_p * n)(*[pl._h.value for pl in plans])
+    fs = (ctypes.c_void_p * n)(*[pl._ptr(r, torch.float64, pl.n3, "rhs").value for pl, r in zip(plans, rhs)])
+    ps = (ctypes.c_void_p * n)(*[pl._ptr(x, torch.float64, pl.n3, "p").value for pl, x in zip(plans, p)])
+    st = (ctypes.c_int32 * n)()
+    rc = lib().snac_poisson_solve_batch(n, hs, fs, ps, float(tol), st, plans[0]._stream())
+    if rc != SNAC_OK and raise_on_error:
+        _check(rc)
+    return [pl.info() for pl in plans]
 
 
 class Engine:
