@@ -193,8 +193,9 @@ typedef struct {
 /* Choose the multigrid schedule for one problem by timing complete solves (snac_poisson_solve from
  * p = 0) of a representative right-hand side d_rhs (device float64 field, caller layout) at tol.
  * Starting from *base (NULL = defaults), coordinate descent over: (nu1, nu2) in {(2,2), (2,1),
- * (1,2), (1,1)}; max_coarse in {16, 64, 256}; and for SNAC_MIXED, inner_reduction in {1e-3, 3e-3,
- * 3e-4} and fused in {auto, off}. A candidate counts only if its solve succeeds at tol. *best
+ * (1,2), (1,1)}; max_coarse in {16, 64, 256}; onchip in {auto, off} (the launch shape of the
+ * wavenumber solves: one CTA per wavenumber on chip, or level-by-level grids over all wavenumbers);
+ * and for SNAC_MIXED, inner_reduction in {1e-3, 3e-3, 3e-4} and fused in {auto, off}. A candidate counts only if its solve succeeds at tol. *best
  * receives the fastest options (precision, max_outer, max_cycles and shift are kept from *base).
  * The paper has no counterpart (its multigrid is hypre's); this is the schedule choice of a serving
  * system. Allocates and frees plans and an 8-byte-per-cell scratch field on the current device;

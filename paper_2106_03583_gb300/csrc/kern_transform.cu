@@ -1,8 +1,8 @@
 // Real-to-real transforms along the homogeneous direction (Table 1; Algorithm 1, first and third
 // loops), batched over x-y columns. One CTA transforms TC consecutive columns of one block: the
 // columns are loaded row by row (coalesced along x), reordered into a complex sequence of half
-// length m = n/2, transformed by a shared-memory complex FFT (Stockham radix-2 for a power-of-two m,
-// a direct sum otherwise), and post-processed into the real output. Twiddles come from host-built
+// length m = n/2, transformed by a shared-memory complex FFT (mixed-radix Stockham: radices 4, 2,
+// 3, 5 and any other prime factor), and post-processed into the real output. Twiddles come from host-built
 // tables; the kernels evaluate no transcendental function.
 //
 // Reductions to a half-length complex FFT (conventions of the unnormalised real-to-real
@@ -36,16 +36,82 @@ __device__ __forceinline__ Cx<T> conj(Cx<T> a) {
   return {a.re, -a.im};
 }
 
+template <typename T>
+__device__ __forceinline__ Cx<T> cadd(Cx<T> a, Cx<T> b) {
+  return {a.re + b.re, a.im + b.im};
+}
+
+// One Stockham stage of radix R on TC columns: groups of R consecutive length-Ls transforms are
+// merged into transforms of length R Ls. Input of group j, point k: a_p = x[(j + p r) Ls + k] times
+// the twiddle w^(p k r) (w = exp(-2 pi i / m), r = m / (R Ls)); outputs y_q = sum_p a_p omega_R^(p q)
+// at (R j + q) Ls + k, with omega_R^s = w^(s m / R) taken from the same table. Radices 3 and 5 are
+// unrolled; any other prime goes through the runtime-radix stage below (O(R) work per point).
+template <typename T, int TC, int R>
+__device__ void stage_r(const Cx<T>* __restrict__ X, Cx<T>* __restrict__ Y, int m, int Ls,
+                        const Cx<T>* __restrict__ tw, bool inverse) {
+  const int r = m / (R * Ls), mr = m / R;
+  for (int idx = threadIdx.x; idx < (m / R) * TC; idx += blockDim.x) {
+    const int c = idx % TC, t = idx / TC;
+    const int j = t / Ls, k = t - j * Ls;
+    Cx<T> a[R];
+#pragma unroll
+    for (int p = 0; p < R; ++p) {
+      a[p] = X[((j + p * r) * Ls + k) * TC + c];
+      if (p > 0 && k > 0) {
+        Cx<T> w = tw[p * k * r];
+        if (inverse) w.im = -w.im;
+        a[p] = cmul(w, a[p]);
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < R; ++q) {
+      Cx<T> acc = a[0];
+#pragma unroll
+      for (int p = 1; p < R; ++p) {
+        Cx<T> w = tw[((p * q) % R) * mr];
+        if (inverse) w.im = -w.im;
+        acc = cadd(acc, cmul(w, a[p]));
+      }
+      Y[((R * j + q) * Ls + k) * TC + c] = acc;
+    }
+  }
+  __syncthreads();
+}
+
+// The same stage for a radix known only at run time (a prime factor above 5): one output per
+// thread and iteration, y = sum_p w^(p k r + (p q mod R) m / R) x_p.
+template <typename T, int TC>
+__device__ void stage_any(const Cx<T>* __restrict__ X, Cx<T>* __restrict__ Y, int m, int Ls, int R,
+                          const Cx<T>* __restrict__ tw, bool inverse) {
+  const int r = m / (R * Ls), mr = m / R;
+  for (int idx = threadIdx.x; idx < m * TC; idx += blockDim.x) {
+    const int c = idx % TC, o = idx / TC;
+    const int k = o % Ls, q = (o / Ls) % R, j = o / (Ls * R);
+    Cx<T> acc = {0, 0};
+    for (int p = 0; p < R; ++p) {
+      const int e = (int)(((long long)p * k * r + (long long)((p * q) % R) * mr) % m);
+      Cx<T> w = tw[e];
+      if (inverse) w.im = -w.im;
+      acc = cadd(acc, cmul(w, X[((j + p * r) * Ls + k) * TC + c]));
+    }
+    Y[o * TC + c] = acc;
+  }
+  __syncthreads();
+}
+
 // Complex DFT of length m of TC columns held as buf[j * TC + c]. Forward: exp(-2 pi i jk/m);
 // inverse (unnormalised): exp(+2 pi i jk/m). Returns the buffer holding the result.
+// Stockham autosort, mixed radix: the factors 4 (with the exact rotations by +-i) and 2 first, while
+// the merged length Ls is a power of two; then 3, 5 and any remaining prime.
 template <typename T, int TC>
 __device__ Cx<T>* cfft(Cx<T>* X, Cx<T>* Y, int m, const Cx<T>* __restrict__ tw, bool inverse) {
   if (m == 1) return X;
-  if ((m & (m - 1)) == 0) {
-    // Stockham autosort: merge groups of four length-Ls transforms into length-4Ls transforms while
-    // four remain (radix 4: three twiddle products per four points), then pairs (radix 2) once, if
-    // log2(m) is odd. Output stage q of a group: y_q = sum_p (w^(p k) x_p) omega_4^(p q).
-    int lg = 0, Ls = 1;
+  int Ls = 1;
+  {
+    // Merge groups of four length-Ls transforms into length-4Ls transforms while four remain
+    // (radix 4: three twiddle products per four points), then pairs (radix 2) once if a factor 2
+    // is left. Output stage q of a group: y_q = sum_p (w^(p k) x_p) omega_4^(p q).
+    int lg = 0;
     for (; (m / Ls) % 4 == 0; Ls <<= 2, lg += 2) {
       const int r = m / (4 * Ls);
       for (int idx = threadIdx.x; idx < (m / 4) * TC; idx += blockDim.x) {
@@ -81,7 +147,7 @@ __device__ Cx<T>* cfft(Cx<T>* X, Cx<T>* Y, int m, const Cx<T>* __restrict__ tw, 
       X = Y;
       Y = s;
     }
-    for (; Ls < m; Ls <<= 1, ++lg) {
+    for (; (m / Ls) % 2 == 0; Ls <<= 1, ++lg) {
       const int r = m / (2 * Ls);
       for (int idx = threadIdx.x; idx < (m / 2) * TC; idx += blockDim.x) {
         const int c = idx % TC, t = idx / TC;
@@ -98,23 +164,27 @@ __device__ Cx<T>* cfft(Cx<T>* X, Cx<T>* Y, int m, const Cx<T>* __restrict__ tw, 
       X = Y;
       Y = s;
     }
-    return X;
   }
-  // direct sum for other lengths
-  for (int idx = threadIdx.x; idx < m * TC; idx += blockDim.x) {
-    const int c = idx % TC, k = idx / TC;
-    Cx<T> acc = {0, 0};
-    for (int j = 0; j < m; ++j) {
-      Cx<T> w = tw[(int)(((long long)j * k) % m)];
-      if (inverse) w.im = -w.im;
-      const Cx<T> p = cmul(w, X[j * TC + c]);
-      acc.re += p.re;
-      acc.im += p.im;
+  auto swap = [&]() {
+    Cx<T>* s = X;
+    X = Y;
+    Y = s;
+  };
+  for (; (m / Ls) % 3 == 0; Ls *= 3) {
+    stage_r<T, TC, 3>(X, Y, m, Ls, tw, inverse);
+    swap();
+  }
+  for (; (m / Ls) % 5 == 0; Ls *= 5) {
+    stage_r<T, TC, 5>(X, Y, m, Ls, tw, inverse);
+    swap();
+  }
+  for (int p = 7; Ls < m; p += 2) {
+    for (; (m / Ls) % p == 0; Ls *= p) {
+      stage_any<T, TC>(X, Y, m, Ls, p, tw, inverse);
+      swap();
     }
-    Y[k * TC + c] = acc;
   }
-  __syncthreads();
-  return Y;
+  return X;
 }
 
 template <typename T>
@@ -367,10 +437,11 @@ __global__ void __launch_bounds__(256) k_backward(const ChunkDev* __restrict__ c
 
 // Dynamic shared memory of a transform launch: two half-length complex buffers of TC columns. The
 // kernel's maximum is a function-wide attribute shared by every plan and thread, so it is always set
-// to the largest need (n_z = MAX_NZ): a plan with a shorter axis never lowers it under a concurrent
-// launch of a plan with a longer one.
+// to the largest need of any plan that uses this instantiation (128 KB: transform_columns keeps
+// n_z x TC x 2 x sizeof(T) at or below it): a plan with a shorter axis never lowers it under a
+// concurrent launch of a plan with a longer one.
 template <typename T, int TC>
-constexpr int kMaxSmem = 2 * (MAX_NZ / 2) * TC * (int)sizeof(Cx<T>);
+constexpr int kMaxSmem = 128 * 1024;
 
 template <typename T>
 Tw<T> make_tw(const snac_plan* P, const void* base) {
@@ -440,24 +511,47 @@ cudaError_t bwd_t(snac_plan* P, const Geom& G, const std::vector<ChunkDev>& ch, 
 
 }  // namespace
 
+// The transform kernels are instantiated for the chunk widths transform_columns picks.
+template <typename T, typename TI>
+cudaError_t fwd_any(snac_plan* P, const Geom& G, const std::vector<ChunkDev>& ch, const ChunkDev* dch, const void* twb,
+                    const TI* in3, void* modes, double shift0, bool split, cudaStream_t s) {
+  const int tc = sizeof(T) == 8 ? P->tc64 : P->tc32;
+  constexpr int B = sizeof(T) == 8 ? 8 : 16;
+  if (tc == B) return fwd_t<T, B, TI>(P, G, ch, dch, twb, in3, modes, shift0, split, s);
+  if (tc == B / 2) return fwd_t<T, B / 2, TI>(P, G, ch, dch, twb, in3, modes, shift0, split, s);
+  if (tc == B / 4) return fwd_t<T, B / 4, TI>(P, G, ch, dch, twb, in3, modes, shift0, split, s);
+  return cudaErrorInvalidValue;
+}
+
+template <typename T>
+cudaError_t bwd_any(snac_plan* P, const Geom& G, const std::vector<ChunkDev>& ch, const ChunkDev* dch, const void* twb,
+                    const void* modes, double* p3, double sign, cudaStream_t s) {
+  const int tc = sizeof(T) == 8 ? P->tc64 : P->tc32;
+  constexpr int B = sizeof(T) == 8 ? 8 : 16;
+  if (tc == B) return bwd_t<T, B>(P, G, ch, dch, twb, modes, p3, sign, s);
+  if (tc == B / 2) return bwd_t<T, B / 2>(P, G, ch, dch, twb, modes, p3, sign, s);
+  if (tc == B / 4) return bwd_t<T, B / 4>(P, G, ch, dch, twb, modes, p3, sign, s);
+  return cudaErrorInvalidValue;
+}
+
 cudaError_t launch_forward(snac_plan* P, const double* in3, void* modes, double shift0, bool split, cudaStream_t s) {
   if (shift0 != 0.0 && P->kind != KIND_PP && P->kind != KIND_NN) return cudaErrorInvalidValue;
   if (split && P->precision != SNAC_FP64) return cudaErrorInvalidValue;
   if (P->precision == SNAC_FP64)
-    return fwd_t<double, 8>(P, plan_geom(P), P->chunks64, P->d_chunks64, P->d_tw64, in3, modes, shift0, split, s);
-  return fwd_t<float, 16>(P, plan_geom(P), P->chunks32, P->d_chunks32, P->d_tw32, in3, modes, shift0, false, s);
+    return fwd_any<double, double>(P, plan_geom(P), P->chunks64, P->d_chunks64, P->d_tw64, in3, modes, shift0, split, s);
+  return fwd_any<float, double>(P, plan_geom(P), P->chunks32, P->d_chunks32, P->d_tw32, in3, modes, shift0, false, s);
 }
 
 cudaError_t launch_forward_f32(snac_plan* P, const float* in3, void* modes, cudaStream_t s) {
   if (P->precision != SNAC_MIXED) return cudaErrorInvalidValue;
-  return fwd_t<float, 16, float>(P, plan_geom(P), P->chunks32, P->d_chunks32, P->d_tw32, in3, modes, 0.0, false, s);
+  return fwd_any<float, float>(P, plan_geom(P), P->chunks32, P->d_chunks32, P->d_tw32, in3, modes, 0.0, false, s);
 }
 
 cudaError_t launch_backward_update(snac_plan* P, const void* modes, double* p3, cudaStream_t s, bool subtract) {
   const double sign = subtract ? -1.0 : 1.0;
   if (P->precision == SNAC_FP64)
-    return bwd_t<double, 8>(P, plan_geom(P), P->chunks64, P->d_chunks64, P->d_tw64, modes, p3, sign, s);
-  return bwd_t<float, 16>(P, plan_geom(P), P->chunks32, P->d_chunks32, P->d_tw32, modes, p3, sign, s);
+    return bwd_any<double>(P, plan_geom(P), P->chunks64, P->d_chunks64, P->d_tw64, modes, p3, sign, s);
+  return bwd_any<float>(P, plan_geom(P), P->chunks32, P->d_chunks32, P->d_tw32, modes, p3, sign, s);
 }
 
 // Pencil of a sharded solve: ncols columns stored [z][c], one pseudo-block (nx = ncols, ny = 1,
@@ -476,8 +570,9 @@ static cudaError_t pencil_tables(snac_plan* P, long long ncols) {
   const CallerBlk c{0, {1, ncols, ncols}};
   P->pen_ch64.clear();
   P->pen_ch32.clear();
-  for (long long c0 = 0; c0 < ncols; c0 += 8) P->pen_ch64.push_back({0, (int)c0, (int)std::min<long long>(8, ncols - c0), 0});
-  for (long long c0 = 0; c0 < ncols; c0 += 16) P->pen_ch32.push_back({0, (int)c0, (int)std::min<long long>(16, ncols - c0), 0});
+  const int t64 = P->tc64, t32 = P->tc32;
+  for (long long c0 = 0; c0 < ncols; c0 += t64) P->pen_ch64.push_back({0, (int)c0, (int)std::min<long long>(t64, ncols - c0), 0});
+  for (long long c0 = 0; c0 < ncols; c0 += t32) P->pen_ch32.push_back({0, (int)c0, (int)std::min<long long>(t32, ncols - c0), 0});
   auto put = [&](auto** d, const void* src, size_t bytes) -> cudaError_t {
     cudaError_t e = cudaMalloc((void**)d, bytes);
     if (e != cudaSuccess) return e;
@@ -498,8 +593,8 @@ cudaError_t launch_pencil_forward(snac_plan* P, long long ncols, const double* i
   if (e != cudaSuccess) return e;
   const Geom G{P->d_pen_tblk, P->d_pen_tcb, ncols, (double)ncols * P->nzt};
   if (P->precision == SNAC_FP64)
-    return fwd_t<double, 8>(P, G, P->pen_ch64, P->d_pen_ch64, P->d_tw64, in, modes, 0.0, false, s);
-  return fwd_t<float, 16>(P, G, P->pen_ch32, P->d_pen_ch32, P->d_tw32, in, modes, 0.0, false, s);
+    return fwd_any<double, double>(P, G, P->pen_ch64, P->d_pen_ch64, P->d_tw64, in, modes, 0.0, false, s);
+  return fwd_any<float, double>(P, G, P->pen_ch32, P->d_pen_ch32, P->d_tw32, in, modes, 0.0, false, s);
 }
 
 cudaError_t launch_pencil_backward(snac_plan* P, long long ncols, const void* modes, double* p, cudaStream_t s) {
@@ -507,8 +602,8 @@ cudaError_t launch_pencil_backward(snac_plan* P, long long ncols, const void* mo
   if (e != cudaSuccess) return e;
   const Geom G{P->d_pen_tblk, P->d_pen_tcb, ncols, (double)ncols * P->nzt};
   if (P->precision == SNAC_FP64)
-    return bwd_t<double, 8>(P, G, P->pen_ch64, P->d_pen_ch64, P->d_tw64, modes, p, 1.0, s);
-  return bwd_t<float, 16>(P, G, P->pen_ch32, P->d_pen_ch32, P->d_tw32, modes, p, 1.0, s);
+    return bwd_any<double>(P, G, P->pen_ch64, P->d_pen_ch64, P->d_tw64, modes, p, 1.0, s);
+  return bwd_any<float>(P, G, P->pen_ch32, P->d_pen_ch32, P->d_tw32, modes, p, 1.0, s);
 }
 
 }  // namespace snac

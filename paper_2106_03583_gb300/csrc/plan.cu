@@ -85,7 +85,7 @@ int validate(int nb, const snac_block* in, std::vector<HBlock>& out) {
   if ((b0.bc[2][0] == SNAC_BC_PERIODIC) != (b0.bc[2][1] == SNAC_BC_PERIODIC))
     return fail(SNAC_ERR_LAYOUT, "a periodic z needs both z faces periodic");
   if (nz % 2) return fail(SNAC_ERR_LAYOUT, "n_z must be even (Table 1)");
-  if (nz > MAX_NZ) return fail(SNAC_ERR_LAYOUT, "n_z above the supported maximum 1024");
+  if (nz > MAX_NZ) return fail(SNAC_ERR_LAYOUT, "n_z above the supported maximum 4096");
   // x-y connectivity
   for (int b = 0; b < nb; ++b) {
     const HBlock& h = out[b];
@@ -911,8 +911,10 @@ int create(snac_plan** out, int32_t nblocks, const snac_block* blocks_in, int32_
       if ((st = P->precision == SNAC_FP64 ? build_onchip(double{}) : build_onchip(float{}))) break;
     }
     if ((st = build_twiddles(P))) break;
-    if ((st = build_chunks(P, 8, P->chunks64, &P->d_chunks64))) break;
-    if ((st = build_chunks(P, 16, P->chunks32, &P->d_chunks32))) break;
+    P->tc64 = transform_columns(P->nzt, true);
+    P->tc32 = transform_columns(P->nzt, false);
+    if ((st = build_chunks(P, P->tc64, P->chunks64, &P->d_chunks64))) break;
+    if ((st = build_chunks(P, P->tc32, P->chunks32, &P->d_chunks32))) break;
     {
       const HostLevel& l0 = P->lev[0];
       std::vector<double> area(l0.ncell);

@@ -27,7 +27,13 @@ enum Kind { KIND_PP = 0, KIND_NN = 1, KIND_DD = 2, KIND_ND = 3, KIND_DN = 4 };
 constexpr int TILE_X = 32;
 constexpr int TILE_Y = 8;
 constexpr int TILE_THREADS = TILE_X * TILE_Y;
-constexpr int MAX_NZ = 1024;
+constexpr int MAX_NZ = 4096;
+// Columns per transform CTA: two half-length complex buffers of TC columns stay within 128 KB of
+// shared memory, so TC halves as n_z doubles beyond 1024 (FP64: 8, 4, 2; FP32: 16, 8, 4).
+inline int transform_columns(int nz, bool fp64) {
+  const int base = fp64 ? 8 : 16;
+  return nz <= 1024 ? base : (nz <= 2048 ? base / 2 : base / 4);
+}
 constexpr int MAX_COARSE = 256;
 // The bottom of the V-cycle (kern_bottom.cu): levels from the first one (below level 0) whose
 // planes, with all coarser ones, fit in one CTA's shared memory, run in one launch per round.
@@ -232,6 +238,7 @@ struct snac_plan {
   snac::TwiddleOffsets tw{};
   double* d_tw64 = nullptr;  // double2 table
   float* d_tw32 = nullptr;   // float2 table
+  int tc64 = 8, tc32 = 16;  // columns per transform CTA (transform_columns)
   std::vector<snac::ChunkDev> chunks64, chunks32;
   snac::ChunkDev* d_chunks64 = nullptr;
   snac::ChunkDev* d_chunks32 = nullptr;

@@ -26,7 +26,7 @@ snac_options defaults() {
 bool same(const snac_options& a, const snac_options& b) {
   return a.precision == b.precision && a.nu1 == b.nu1 && a.nu2 == b.nu2 && a.max_outer == b.max_outer &&
          a.max_cycles == b.max_cycles && a.max_coarse == b.max_coarse && a.fused == b.fused &&
-         a.inner_reduction == b.inner_reduction && a.shift == b.shift;
+         a.inner_reduction == b.inner_reduction && a.shift == b.shift && a.onchip == b.onchip;
 }
 
 struct Trial {
@@ -123,6 +123,16 @@ extern "C" int snac_autotune(int32_t nblocks, const snac_block* blocks, int32_t 
     for (int mc : {16, 64, 256}) {
       snac_options c = start;
       c.max_coarse = mc;
+      consider(c);
+    }
+  }
+  {
+    // where the whole solve of a wavenumber fits in one CTA: on chip (device-side convergence, one
+    // launch per step) or level by level (grids over all wavenumbers, host-checked rounds)
+    const snac_options start = cur;
+    for (int oc : {0, -1}) {
+      snac_options c = start;
+      c.onchip = oc;
       consider(c);
     }
   }

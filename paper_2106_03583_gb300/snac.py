@@ -516,5 +516,6 @@ def autotune(blocks, rhs, tol: float = 1e-10, precision: str = "fp64", homog_axi
                                float(tol), ctypes.byref(best), ctypes.byref(rep), stream))
     del keep
     chosen = {k: getattr(best, k) for k in _OPTION_NAMES}
+    chosen["onchip"] = best.onchip == 0
     chosen["precision"] = precision
     return chosen, {k: getattr(rep, k) for k, _ in _TuneReport._fields_}

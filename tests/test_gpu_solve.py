@@ -200,7 +200,7 @@ def test_graph_replay_matches_direct_launches(precision):
     launch counts."""
     import torch
     blocks, f = inputs.config("mb2x2", seed=1, scale=8)
-    pl = plan(blocks, precision=precision)
+    pl = plan(blocks, precision=precision, onchip=False)  # the level-by-level rounds are what is replayed
     fd = dev(f)
     out = {}
     for prof in (True, False, False):
@@ -272,3 +272,19 @@ def test_stalled_solve_returns_its_best_iterate(precision):
     info2 = pl.solve(fd, p2, tol=1e-11)
     assert info2["status"] == 0 and info2["outer_iters"] <= info["outer_iters"]
     pl.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("nz,zpair", [(96, "PP"), (150, "NN"), (194, "DN"), (2048, "DD")])
+def test_general_lengths_solve(nz, zpair, precision):
+    """Homogeneous lengths that are not powers of two (the square-cylinder case of Sec. 4.2 uses
+    n_z = 576; here 96 = 2^5 3, 150 = 2 3 5^2 and 194 = 2 97) and a long axis (2048), solved
+    end to end against the oracle."""
+    from layouts import make
+    blocks = make("1x2", n=8 if nz < 1000 else 4, nz=nz, zpair=zpair, walls=("D", "N", "N", "N"), stretched=True)
+    f = inputs.uniform_rhs(blocks, 12, remove_mean=False)
+    ref, _ = osv.solve(blocks, f)
+    p, info, _ = gpu_solve(blocks, f, precision)
+    assert info["status"] == 0 and info["rel_res"] <= TOL
+    assert osv.rel_residual(blocks, f, p) <= 1.01 * TOL
+    assert rel(p, ref) <= PARITY

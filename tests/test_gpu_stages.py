@@ -54,8 +54,11 @@ def test_operator_and_residual(case):
 
 @pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("mixed", 2e-6)])
 @pytest.mark.parametrize("zpair", ["PP", "NN", "DD", "ND", "DN"])
-@pytest.mark.parametrize("nz", [2, 4, 6, 8, 34, 64, 256, 512, 1024])
+@pytest.mark.parametrize("nz", [2, 4, 6, 8, 34, 64, 90, 150, 194, 256, 512, 576, 1024, 2048, 4096])
 def test_transforms(precision, tol, zpair, nz):
+    """Every even length: half-lengths with factors 2 and 4 (Stockham radix 4/2), 3 and 5 (90: 45 =
+    3^2 5, 150: 75 = 3 5^2, 576: 288 = 2^5 3^2) and a prime (194: 97), up to 4096 (fewer columns per
+    CTA beyond 1024)."""
     import torch
     n = 4 if nz >= 256 else 8
     blocks = make("1x2", n=n, nz=nz, zpair=zpair, walls=("N", "N", "N", "N"))
