@@ -53,7 +53,8 @@ typedef enum {
                                      p holds the iterate with the smallest residual                   */
   SNAC_ERR_NONFINITE = -6,        /* a residual norm was NaN or Inf (non-finite input)                */
   SNAC_ERR_INCOMPATIBLE_RHS = -7, /* singular problem whose right-hand side has a non-zero mean       */
-  SNAC_ERR_TIMEOUT = -8           /* reserved for bounded device-side waits                           */
+  SNAC_ERR_TIMEOUT = -8           /* a bounded device-side wait gave up (1 s); nothing was trapped and
+                                     the context stays usable                                        */
 } snac_status;
 
 /* Face kinds (Sec. 3.1: Dirichlet, Neumann, block-block connectivity; periodic = the cyclic
@@ -165,6 +166,16 @@ int snac_poisson_solve(snac_plan *plan, const double *d_rhs, double *d_p, double
  * problem succeeded, else the first failing status. */
 int snac_poisson_solve_batch(int32_t n, snac_plan *const *plans, const double *const *d_rhs, double *const *d_p,
                              double tol, int32_t *h_status, void *stream);
+
+/* Self-test of the bounded device-side wait. For plans that solve on chip, each defect-correction
+ * step runs the forward transform and the wavenumber solves in one persistent launch: a solve
+ * waits, on the device, until its plan's transform chunks are all counted, for at most 1 s, and
+ * then gives up, skips its work and sets a status the host turns into SNAC_ERR_TIMEOUT. This call
+ * runs that launch with a chunk count that nothing can reach and a limit of wait_seconds (0 <
+ * wait_seconds <= 1): it must return SNAC_ERR_TIMEOUT, with the context still usable. Only for
+ * plans of snac_options.onchip whose n_z <= 1024 (SNAC_ERR_INVALID_ARG otherwise); it overwrites the
+ * plan's internal work buffers, not the caller's arrays. */
+int snac_test_wait_timeout(snac_plan *plan, double wait_seconds, void *stream);
 
 /* Statistics of the last solve. */
 int snac_plan_info(const snac_plan *plan, snac_solve_info *info);

@@ -17,6 +17,7 @@
 
 #include "kern_common.cuh"
 #include "snac_impl.h"
+#include "transform_dev.cuh"
 
 namespace snac {
 namespace {
@@ -474,6 +475,135 @@ __global__ void __launch_bounds__(BT) k_onchip_batch(const OnchipArgs<T>* __rest
   }
 }
 
+// ---- the forward transform and the on-chip solves in one persistent launch ----
+//
+// Items: first the forward-transform chunks of every plan (TC columns each), then the wavenumber
+// solves. A CTA that finishes a chunk counts it for its plan (release); a solve item waits until all
+// of its plan's chunks are counted (acquire). Items are claimed in increasing order and a claimed
+// item runs to completion, so every chunk a solve waits for is already held by a running CTA: the
+// wait always ends. It is still bounded: past wait_ns (global timer) the item gives up, sets its
+// plan's status word and skips its work, so that the host reports SNAC_ERR_TIMEOUT and the context
+// stays usable.
+template <typename T>
+struct FwdArgs {
+  const ChunkDev* chunks;
+  const BlockDev* blk;
+  const CallerBlk* cb;
+  Tw<T> tw;
+  const void* in3;       // the 3-D field transformed: FP64 (f or the FP64 residual) or FP32
+  T* out;                // level-0 right-hand side, [q][cell]
+  long long ncell;
+  T sub0;                // F(1) x (mean removed from f), on mode 0 (k = 0 from a zero guess)
+  int n, kind, in_f32, nchunks;
+  int need;              // chunks a solve item waits for (nchunks; more only in the timeout self-test)
+  int* done;             // chunks counted so far (zero at launch)
+  int* status;           // 1 if a wait of this plan gave up
+};
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ int load_acquire(const int* p) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+template <typename T, int TC>
+__device__ void fused_chunk(const FwdArgs<T>& F, int c, unsigned char* smem) {
+  const ChunkDev ch = F.chunks[c];
+  const int sel = F.kind * 2 + F.in_f32;
+#define SNAC_FWD(KD, TI)                                                                                   \
+  forward_chunk<T, TC, KD, TI>(ch, F.blk, F.cb, F.n, F.tw, static_cast<const TI*>(F.in3), F.out, F.ncell, F.sub0, 0, smem)
+  switch (sel) {
+    case 2 * KIND_PP: SNAC_FWD(KIND_PP, double); break;
+    case 2 * KIND_PP + 1: SNAC_FWD(KIND_PP, float); break;
+    case 2 * KIND_NN: SNAC_FWD(KIND_NN, double); break;
+    case 2 * KIND_NN + 1: SNAC_FWD(KIND_NN, float); break;
+    case 2 * KIND_DD: SNAC_FWD(KIND_DD, double); break;
+    case 2 * KIND_DD + 1: SNAC_FWD(KIND_DD, float); break;
+    case 2 * KIND_ND: SNAC_FWD(KIND_ND, double); break;
+    case 2 * KIND_ND + 1: SNAC_FWD(KIND_ND, float); break;
+    case 2 * KIND_DN: SNAC_FWD(KIND_DN, double); break;
+    default: SNAC_FWD(KIND_DN, float); break;
+  }
+#undef SNAC_FWD
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    atomicAdd(F.done, 1);
+  }
+}
+
+template <typename T>
+__device__ void fused_solve(const FwdArgs<T>& F, const OnchipArgs<T>& O, int q, long long wait_ns,
+                            unsigned char* smem, int* skip) {
+  if (threadIdx.x == 0) {
+    const unsigned long long t0 = global_ns();
+    int give_up = 0;
+    while (load_acquire(F.done) < F.need) {
+      if (global_ns() - t0 > (unsigned long long)wait_ns) {
+        give_up = 1;
+        atomicOr(F.status, 1);
+        break;
+      }
+      __nanosleep(500);
+    }
+    *skip = give_up;
+  }
+  __syncthreads();
+  const int sk = *skip;
+  __syncthreads();
+  if (!sk) onchip_mode(O, q, smem);
+}
+
+// One plan: items 0 .. nchunks - 1 are its chunks, then its wavenumbers 0 .. nmodes - 1.
+template <typename T, int TC>
+__global__ void __launch_bounds__(BT) k_fwd_onchip(const FwdArgs<T> F, const OnchipArgs<T> O, int nmodes,
+                                                   int* __restrict__ next, long long wait_ns) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ int item, skip;
+  const int nitems = F.nchunks + nmodes;
+  for (;;) {
+    if (threadIdx.x == 0) item = atomicAdd(next, 1);
+    __syncthreads();
+    const int k = item;
+    __syncthreads();
+    if (k >= nitems) break;
+    if (k < F.nchunks) fused_chunk<T, TC>(F, k, smem_raw);
+    else fused_solve(F, O, k - F.nchunks, wait_ns, smem_raw, &skip);
+  }
+}
+
+// Several plans: items (type, plan, index) from a table -- every plan's chunks first, then every
+// plan's wavenumbers.
+template <typename T, int TC>
+__global__ void __launch_bounds__(BT) k_fwd_onchip_batch(const FwdArgs<T>* __restrict__ fargs,
+                                                         const OnchipArgs<T>* __restrict__ args,
+                                                         const int4* __restrict__ items, int nitems,
+                                                         int* __restrict__ next, long long wait_ns) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ int item, skip;
+  for (;;) {
+    if (threadIdx.x == 0) item = atomicAdd(next, 1);
+    __syncthreads();
+    const int k = item;
+    __syncthreads();
+    if (k >= nitems) break;
+    const int4 it = items[k];
+    const FwdArgs<T> F = fargs[it.y];
+    if (it.x == 0) {
+      fused_chunk<T, TC>(F, it.z, smem_raw);
+    } else {
+      const OnchipArgs<T> O = args[it.y];
+      fused_solve(F, O, it.z, wait_ns, smem_raw, &skip);
+    }
+  }
+}
+
 template <typename T>
 OnchipArgs<T> onchip_args(snac_plan* P, double target) {
   OnchipArgs<T> O{};
@@ -598,10 +728,147 @@ cudaError_t launch_bottom(snac_plan* P, int nact, cudaStream_t s) {
   return P->precision == SNAC_FP64 ? bottom_t<double>(P, nact, s) : bottom_t<float>(P, nact, s);
 }
 
+__global__ void k_zero_ints(int* __restrict__ p, int n) {
+  for (int i = threadIdx.x; i < n; i += blockDim.x) p[i] = 0;
+}
+
+template <typename T>
+FwdArgs<T> fwd_args(snac_plan* P, const void* in3, bool in_f32, double shift0, int* done, int* status, int extra) {
+  FwdArgs<T> F{};
+  const bool f64 = sizeof(T) == 8;
+  F.chunks = f64 ? P->d_chunks64 : P->d_chunks32;
+  F.blk = P->lev[0].d_blk;
+  F.cb = P->d_cblk;
+  const Cx<T>* t = reinterpret_cast<const Cx<T>*>(f64 ? (const void*)P->d_tw64 : (const void*)P->d_tw32);
+  F.tw = Tw<T>{t + P->tw.fft, t + P->tw.twn, t + P->tw.tw2n, t + P->tw.tw4a, t + P->tw.tw4b};
+  F.in3 = in3;
+  F.out = (T*)P->lev[0].d_f;
+  F.ncell = P->lev[0].ncell;
+  // F(1) in mode 0: n for the real DFT (half-complex), 2n for the DCT-II
+  F.sub0 = (T)(shift0 * (P->kind == KIND_PP ? (double)P->nzt : 2.0 * P->nzt));
+  F.n = P->nzt;
+  F.kind = P->kind;
+  F.in_f32 = in_f32 ? 1 : 0;
+  F.nchunks = (int)(f64 ? P->chunks64.size() : P->chunks32.size());
+  F.need = F.nchunks + extra;
+  F.done = done;
+  F.status = status;
+  return F;
+}
+
+template <typename T>
+constexpr int fused_tc() {
+  return sizeof(T) == 8 ? 8 : 16;
+}
+
+template <typename T>
+size_t fused_smem(const snac_plan* P) {
+  const size_t fft = 2 * (size_t)(P->nzt / 2) * fused_tc<T>() * sizeof(Cx<T>);
+  return std::max(fft, bottom_layout(P, 0, sizeof(T)).bytes);
+}
+
+template <typename T>
+cudaError_t fwd_onchip_t(snac_plan* P, const void* in3, bool in_f32, double shift0, double target, double wait_s,
+                         int extra, cudaStream_t s) {
+  constexpr int TC = fused_tc<T>();
+  *P->h_wait = 0;
+  k_zero_ints<<<1, 32, 0, s>>>(P->d_fused, 2);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const FwdArgs<T> F = fwd_args<T>(P, in3, in_f32, shift0, P->d_fused + 1, P->dh_wait, extra);
+  const OnchipArgs<T> O = onchip_args<T>(P, target);
+  const size_t smem = fused_smem<T>(P);
+  cudaFuncSetAttribute(k_fwd_onchip<T, TC>, cudaFuncAttributeMaxDynamicSharedMemorySize, BOTTOM_MAX_SMEM);
+  int per_sm = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fwd_onchip<T, TC>, BT, smem);
+  const int nitems = F.nchunks + P->nz;
+  const int grid = std::max(1, std::min(nitems, std::max(1, per_sm) * P->sms));
+  const double w = sizeof(T), n3 = (double)P->n3;
+  LaunchScope ls(P, K_FWD_ONCHIP, (in_f32 ? 4.0 : 8.0) * n3 + w * n3 + 2.0 * w * (double)P->lev[0].ncell * P->nz,
+                 (2.5 * std::log2((double)P->nzt) + 8.0) * n3 + 4.0 * onchip_cycle_flops(P) * P->nz, s);
+  k_fwd_onchip<T, TC><<<grid, BT, smem, s>>>(F, O, P->nz, P->d_fused, (long long)(wait_s * 1e9));
+  return cudaGetLastError();
+}
+
 cudaError_t launch_onchip(snac_plan* P, int nact, double target, cudaStream_t s) {
   if (nact <= 0) return cudaSuccess;
   if (!P->d_onchip) return cudaErrorInvalidValue;
   return P->precision == SNAC_FP64 ? onchip_t<double>(P, nact, target, s) : onchip_t<float>(P, nact, target, s);
+}
+
+bool fused_ready(const snac_plan* P) {
+  return P->onchip && P->d_fused && !P->ranged &&
+         (P->precision == SNAC_FP64 ? P->tc64 == fused_tc<double>() : P->tc32 == fused_tc<float>());
+}
+
+cudaError_t launch_fwd_onchip(snac_plan* P, const void* in3, bool in_f32, double shift0, double target, double wait_s,
+                              int extra_need, cudaStream_t s) {
+  if (!fused_ready(P) || (in_f32 && P->precision != SNAC_MIXED)) return cudaErrorInvalidValue;
+  if (P->precision == SNAC_FP64) return fwd_onchip_t<double>(P, in3, in_f32, shift0, target, wait_s, extra_need, s);
+  return fwd_onchip_t<float>(P, in3, in_f32, shift0, target, wait_s, extra_need, s);
+}
+
+size_t fwd_onchip_batch_scratch(int nplans, int nitems) {
+  auto up = [](size_t b) { return (b + 255) / 256 * 256; };
+  return up((size_t)nplans * sizeof(FwdArgs<double>)) + up((size_t)nplans * sizeof(OnchipArgs<double>)) +
+         up((size_t)nitems * sizeof(int4)) + up((size_t)(1 + nplans) * sizeof(int));
+}
+
+template <typename T>
+cudaError_t fwd_onchip_batch_t(snac_plan* const* plans, const FusedInput* inputs, const double* targets, int nplans,
+                               double wait_s, void* d_scratch, int sms, cudaStream_t s) {
+  constexpr int TC = fused_tc<T>();
+  auto up = [](size_t b) { return (b + 255) / 256 * 256; };
+  char* base = static_cast<char*>(d_scratch);
+  FwdArgs<T>* d_fargs = reinterpret_cast<FwdArgs<T>*>(base);
+  OnchipArgs<T>* d_args = reinterpret_cast<OnchipArgs<T>*>(base + up((size_t)nplans * sizeof(FwdArgs<double>)));
+  int4* d_items = reinterpret_cast<int4*>(reinterpret_cast<char*>(d_args) + up((size_t)nplans * sizeof(OnchipArgs<double>)));
+  std::vector<FwdArgs<T>> fargs(nplans);
+  std::vector<OnchipArgs<T>> args(nplans);
+  std::vector<int4> items;
+  size_t smem = 0;
+  for (int k = 0; k < nplans; ++k)
+    for (int c = 0; c < (int)(sizeof(T) == 8 ? plans[k]->chunks64.size() : plans[k]->chunks32.size()); ++c)
+      items.push_back(make_int4(0, k, c, 0));
+  for (int k = 0; k < nplans; ++k)
+    for (int q = 0; q < plans[k]->nz; ++q) items.push_back(make_int4(1, k, q, 0));
+  int* d_ctr = reinterpret_cast<int*>(reinterpret_cast<char*>(d_items) + up(items.size() * sizeof(int4)));
+  for (int k = 0; k < nplans; ++k) {
+    snac_plan* P = plans[k];
+    *P->h_wait = 0;
+    fargs[k] = fwd_args<T>(P, inputs[k].in3, inputs[k].in_f32, inputs[k].shift0, d_ctr + 1 + k, P->dh_wait, 0);
+    args[k] = onchip_args<T>(P, targets[k]);
+    smem = std::max(smem, fused_smem<T>(P));
+    KernelStat& ks = P->kstats[K_FWD_ONCHIP];  // each plan counts the shared launch once
+    ++ks.launches;
+    const double w = sizeof(T), n3 = (double)P->n3;
+    ks.bytes += (inputs[k].in_f32 ? 4.0 : 8.0) * n3 + w * n3 + 2.0 * w * (double)P->lev[0].ncell * P->nz;
+    ks.flops += (2.5 * std::log2((double)P->nzt) + 8.0) * n3 + 4.0 * onchip_cycle_flops(P) * P->nz;
+  }
+  cudaError_t e;
+  if ((e = cudaMemcpyAsync(d_fargs, fargs.data(), nplans * sizeof(FwdArgs<T>), cudaMemcpyHostToDevice, s)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(d_args, args.data(), nplans * sizeof(OnchipArgs<T>), cudaMemcpyHostToDevice, s)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(d_items, items.data(), items.size() * sizeof(int4), cudaMemcpyHostToDevice, s)) != cudaSuccess)
+    return e;
+  k_zero_ints<<<1, 256, 0, s>>>(d_ctr, 1 + nplans);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  cudaFuncSetAttribute(k_fwd_onchip_batch<T, TC>, cudaFuncAttributeMaxDynamicSharedMemorySize, BOTTOM_MAX_SMEM);
+  int per_sm = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fwd_onchip_batch<T, TC>, BT, smem);
+  const int nitems = (int)items.size();
+  const int grid = std::max(1, std::min(nitems, std::max(1, per_sm) * sms));
+  k_fwd_onchip_batch<T, TC><<<grid, BT, smem, s>>>(d_fargs, d_args, d_items, nitems, d_ctr, (long long)(wait_s * 1e9));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fwd_onchip_batch(snac_plan* const* plans, const FusedInput* inputs, const double* targets,
+                                    int nplans, double wait_s, void* d_scratch, int sms, cudaStream_t s) {
+  if (nplans <= 0) return cudaSuccess;
+  for (int k = 0; k < nplans; ++k)
+    if (!fused_ready(plans[k]) || plans[k]->precision != plans[0]->precision) return cudaErrorInvalidValue;
+  if (plans[0]->precision == SNAC_FP64)
+    return fwd_onchip_batch_t<double>(plans, inputs, targets, nplans, wait_s, d_scratch, sms, s);
+  return fwd_onchip_batch_t<float>(plans, inputs, targets, nplans, wait_s, d_scratch, sms, s);
 }
 
 // Many plans, one launch: the items (plan index, wavenumber) of plans of the same precision, every

@@ -17,320 +17,19 @@
 //   DN  DST-IV_k(x) = DCT-IV_{n-1-k}((-1)^j x_j), its own inverse (x 2n).
 #include <cmath>
 
-#include "kern_common.cuh"
-#include "snac_impl.h"
+#include "transform_dev.cuh"
 
 namespace snac {
 namespace {
 
-template <typename T>
-struct Cx {
-  T re, im;
-};
-template <typename T>
-__device__ __forceinline__ Cx<T> cmul(Cx<T> a, Cx<T> b) {
-  return {a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re};
-}
-template <typename T>
-__device__ __forceinline__ Cx<T> conj(Cx<T> a) {
-  return {a.re, -a.im};
-}
-
-template <typename T>
-__device__ __forceinline__ Cx<T> cadd(Cx<T> a, Cx<T> b) {
-  return {a.re + b.re, a.im + b.im};
-}
-
-// One Stockham stage of radix R on TC columns: groups of R consecutive length-Ls transforms are
-// merged into transforms of length R Ls. Input of group j, point k: a_p = x[(j + p r) Ls + k] times
-// the twiddle w^(p k r) (w = exp(-2 pi i / m), r = m / (R Ls)); outputs y_q = sum_p a_p omega_R^(p q)
-// at (R j + q) Ls + k, with omega_R^s = w^(s m / R) taken from the same table. Radices 3 and 5 are
-// unrolled; any other prime goes through the runtime-radix stage below (O(R) work per point).
-template <typename T, int TC, int R>
-__device__ void stage_r(const Cx<T>* __restrict__ X, Cx<T>* __restrict__ Y, int m, int Ls,
-                        const Cx<T>* __restrict__ tw, bool inverse) {
-  const int r = m / (R * Ls), mr = m / R;
-  for (int idx = threadIdx.x; idx < (m / R) * TC; idx += blockDim.x) {
-    const int c = idx % TC, t = idx / TC;
-    const int j = t / Ls, k = t - j * Ls;
-    Cx<T> a[R];
-#pragma unroll
-    for (int p = 0; p < R; ++p) {
-      a[p] = X[((j + p * r) * Ls + k) * TC + c];
-      if (p > 0 && k > 0) {
-        Cx<T> w = tw[p * k * r];
-        if (inverse) w.im = -w.im;
-        a[p] = cmul(w, a[p]);
-      }
-    }
-#pragma unroll
-    for (int q = 0; q < R; ++q) {
-      Cx<T> acc = a[0];
-#pragma unroll
-      for (int p = 1; p < R; ++p) {
-        Cx<T> w = tw[((p * q) % R) * mr];
-        if (inverse) w.im = -w.im;
-        acc = cadd(acc, cmul(w, a[p]));
-      }
-      Y[((R * j + q) * Ls + k) * TC + c] = acc;
-    }
-  }
-  __syncthreads();
-}
-
-// The same stage for a radix known only at run time (a prime factor above 5): one output per
-// thread and iteration, y = sum_p w^(p k r + (p q mod R) m / R) x_p.
-template <typename T, int TC>
-__device__ void stage_any(const Cx<T>* __restrict__ X, Cx<T>* __restrict__ Y, int m, int Ls, int R,
-                          const Cx<T>* __restrict__ tw, bool inverse) {
-  const int r = m / (R * Ls), mr = m / R;
-  for (int idx = threadIdx.x; idx < m * TC; idx += blockDim.x) {
-    const int c = idx % TC, o = idx / TC;
-    const int k = o % Ls, q = (o / Ls) % R, j = o / (Ls * R);
-    Cx<T> acc = {0, 0};
-    for (int p = 0; p < R; ++p) {
-      const int e = (int)(((long long)p * k * r + (long long)((p * q) % R) * mr) % m);
-      Cx<T> w = tw[e];
-      if (inverse) w.im = -w.im;
-      acc = cadd(acc, cmul(w, X[((j + p * r) * Ls + k) * TC + c]));
-    }
-    Y[o * TC + c] = acc;
-  }
-  __syncthreads();
-}
-
-// Complex DFT of length m of TC columns held as buf[j * TC + c]. Forward: exp(-2 pi i jk/m);
-// inverse (unnormalised): exp(+2 pi i jk/m). Returns the buffer holding the result.
-// Stockham autosort, mixed radix: the factors 4 (with the exact rotations by +-i) and 2 first, while
-// the merged length Ls is a power of two; then 3, 5 and any remaining prime.
-template <typename T, int TC>
-__device__ Cx<T>* cfft(Cx<T>* X, Cx<T>* Y, int m, const Cx<T>* __restrict__ tw, bool inverse) {
-  if (m == 1) return X;
-  int Ls = 1;
-  {
-    // Merge groups of four length-Ls transforms into length-4Ls transforms while four remain
-    // (radix 4: three twiddle products per four points), then pairs (radix 2) once if a factor 2
-    // is left. Output stage q of a group: y_q = sum_p (w^(p k) x_p) omega_4^(p q).
-    int lg = 0;
-    for (; (m / Ls) % 4 == 0; Ls <<= 2, lg += 2) {
-      const int r = m / (4 * Ls);
-      for (int idx = threadIdx.x; idx < (m / 4) * TC; idx += blockDim.x) {
-        const int c = idx % TC, t = idx / TC;
-        const int j = t >> lg, k = t & (Ls - 1);
-        Cx<T> a0 = X[(j * Ls + k) * TC + c];
-        Cx<T> a1 = X[((j + r) * Ls + k) * TC + c];
-        Cx<T> a2 = X[((j + 2 * r) * Ls + k) * TC + c];
-        Cx<T> a3 = X[((j + 3 * r) * Ls + k) * TC + c];
-        if (Ls > 1) {  // the first stage has k = 0 only: unit twiddles
-          Cx<T> w1 = tw[k * r], w2 = tw[2 * k * r], w3 = tw[3 * k * r];
-          if (inverse) {
-            w1.im = -w1.im;
-            w2.im = -w2.im;
-            w3.im = -w3.im;
-          }
-          a1 = cmul(w1, a1);
-          a2 = cmul(w2, a2);
-          a3 = cmul(w3, a3);
-        }
-        const Cx<T> s02 = {a0.re + a2.re, a0.im + a2.im}, d02 = {a0.re - a2.re, a0.im - a2.im};
-        const Cx<T> s13 = {a1.re + a3.re, a1.im + a3.im}, d13 = {a1.re - a3.re, a1.im - a3.im};
-        // omega_4 d13: -i d13 forward, +i d13 inverse
-        const Cx<T> od = inverse ? Cx<T>{-d13.im, d13.re} : Cx<T>{d13.im, -d13.re};
-        const int o = (4 * j * Ls + k) * TC + c;
-        Y[o] = {s02.re + s13.re, s02.im + s13.im};
-        Y[o + Ls * TC] = {d02.re + od.re, d02.im + od.im};
-        Y[o + 2 * Ls * TC] = {s02.re - s13.re, s02.im - s13.im};
-        Y[o + 3 * Ls * TC] = {d02.re - od.re, d02.im - od.im};
-      }
-      __syncthreads();
-      Cx<T>* s = X;
-      X = Y;
-      Y = s;
-    }
-    for (; (m / Ls) % 2 == 0; Ls <<= 1, ++lg) {
-      const int r = m / (2 * Ls);
-      for (int idx = threadIdx.x; idx < (m / 2) * TC; idx += blockDim.x) {
-        const int c = idx % TC, t = idx / TC;
-        const int j = t >> lg, k = t & (Ls - 1);
-        Cx<T> w = tw[k * r];
-        if (inverse) w.im = -w.im;
-        const Cx<T> a = X[(j * Ls + k) * TC + c];
-        const Cx<T> b = cmul(w, X[((j + r) * Ls + k) * TC + c]);
-        Y[(2 * j * Ls + k) * TC + c] = {a.re + b.re, a.im + b.im};
-        Y[(2 * j * Ls + Ls + k) * TC + c] = {a.re - b.re, a.im - b.im};
-      }
-      __syncthreads();
-      Cx<T>* s = X;
-      X = Y;
-      Y = s;
-    }
-  }
-  auto swap = [&]() {
-    Cx<T>* s = X;
-    X = Y;
-    Y = s;
-  };
-  for (; (m / Ls) % 3 == 0; Ls *= 3) {
-    stage_r<T, TC, 3>(X, Y, m, Ls, tw, inverse);
-    swap();
-  }
-  for (; (m / Ls) % 5 == 0; Ls *= 5) {
-    stage_r<T, TC, 5>(X, Y, m, Ls, tw, inverse);
-    swap();
-  }
-  for (int p = 7; Ls < m; p += 2) {
-    for (; (m / Ls) % p == 0; Ls *= p) {
-      stage_any<T, TC>(X, Y, m, Ls, p, tw, inverse);
-      swap();
-    }
-  }
-  return X;
-}
-
-template <typename T>
-struct Tw {
-  const Cx<T>* fft;
-  const Cx<T>* twn;
-  const Cx<T>* tw2n;
-  const Cx<T>* tw4a;
-  const Cx<T>* tw4b;
-};
-
-// X_k (k = 0..m) of the real DFT of the length-n sequence packed as Z = FFT_m(x_2j + i x_2j+1).
-template <typename T, int TC>
-__device__ __forceinline__ Cx<T> rdft_bin(const Cx<T>* R, int k, int m, int c, const Tw<T>& tw) {
-  const Cx<T> zk = R[(k == m ? 0 : k) * TC + c];
-  const Cx<T> zc = conj(R[(k == 0 ? 0 : m - k) * TC + c]);
-  const Cx<T> E = {(T)0.5 * (zk.re + zc.re), (T)0.5 * (zk.im + zc.im)};
-  const Cx<T> d = {zk.re - zc.re, zk.im - zc.im};
-  const Cx<T> O = {(T)0.5 * d.im, (T)-0.5 * d.re};  // d / (2i)
-  const Cx<T> wo = cmul(tw.twn[k], O);
-  return {E.re + wo.re, E.im + wo.im};
-}
-
-// Z_k (k < m) for the inverse real DFT, from half-complex bins X_k and conj(X_{m-k}).
-template <typename T>
-__device__ __forceinline__ Cx<T> irdft_pre(Cx<T> xk, Cx<T> xmk, const Cx<T>& twn_k) {
-  const Cx<T> xc = conj(xmk);
-  const Cx<T> E = {xk.re + xc.re, xk.im + xc.im};
-  const Cx<T> O = cmul({xk.re - xc.re, xk.im - xc.im}, conj(twn_k));
-  return {E.re - O.im, E.im + O.re};  // E + i O
-}
-
-// Loads from HBM per thread in flight before their first use: the column loads of a chunk are
-// independent, and issuing them in batches keeps enough bytes in flight to cover the DRAM latency.
-constexpr int LBATCH = 8;
-
-// Caller offsets (at k = 0) of the chunk's columns, and the caller stride along the homogeneous axis.
-template <int TC>
-__device__ __forceinline__ long long chunk_columns(const ChunkDev& ch, const BlockDev& B, const CallerBlk* __restrict__ cb,
-                                                   long long (&coff)[TC]) {
-  const CallerBlk C = cb[ch.b];
-  if (threadIdx.x < TC) {
-    const long long pc = (long long)ch.c0 + threadIdx.x;  // plane cell of the block
-    coff[threadIdx.x] = C.off3 + (pc % B.nx) * C.s[0] + (pc / B.nx) * C.s[1];
-  }
-  __syncthreads();
-  return C.s[2];
-}
-
+// One CTA per chunk of TC columns.
 template <typename T, int TC, int KIND, typename TI>
 __global__ void __launch_bounds__(256) k_forward(const ChunkDev* __restrict__ chunks, const BlockDev* __restrict__ blk,
                                                  const CallerBlk* __restrict__ cb, int n, Tw<T> tw,
                                                  const TI* __restrict__ in3, T* __restrict__ out, long long ncell,
                                                  T sub0, int split) {
-  constexpr int kind = KIND;
   extern __shared__ __align__(16) unsigned char smem[];
-  __shared__ long long coff[TC];
-  __shared__ long long ooff[TC];  // position of each column in a mode plane (plain or colour-split)
-  const int m = n / 2;
-  Cx<T>* A = reinterpret_cast<Cx<T>*>(smem);
-  Cx<T>* Bf = A + m * TC;
-  T* xs = reinterpret_cast<T*>(Bf);  // n x TC reals, aliases Bf
-  const ChunkDev ch = chunks[blockIdx.x];
-  const BlockDev B = blk[ch.b];
-  if (threadIdx.x < TC) {
-    const int pc = ch.c0 + threadIdx.x;
-    ooff[threadIdx.x] = split ? split_cell(B, pc % B.nx, pc / B.nx) : B.off + pc;
-  }
-  const long long sk = chunk_columns<TC>(ch, B, cb, coff);  // (its barrier also covers ooff)
-  // sk == 1: the homogeneous axis is the caller's contiguous one, consecutive threads run along it
-  const bool along = sk == 1;
-  for (int i0 = threadIdx.x; i0 < n * TC; i0 += LBATCH * blockDim.x) {
-    TI v[LBATCH];
-#pragma unroll
-    for (int u = 0; u < LBATCH; ++u) {
-      const int idx = i0 + u * blockDim.x;
-      const int k = along ? idx % n : idx / TC, c = along ? idx / n : idx % TC;
-      v[u] = idx < n * TC && c < ch.ncol ? in3[coff[c] + k * sk] : (TI)0;
-    }
-#pragma unroll
-    for (int u = 0; u < LBATCH; ++u) {
-      const int idx = i0 + u * blockDim.x;
-      if (idx < n * TC) xs[along ? (idx % n) * TC + idx / n : idx] = (T)v[u];
-    }
-  }
-  __syncthreads();
-  const bool flip = kind == KIND_DD || kind == KIND_DN;
-  auto x = [&](int k, int c) -> T {
-    const T v = xs[k * TC + c];
-    return (flip && (k & 1)) ? -v : v;
-  };
-  for (int idx = threadIdx.x; idx < m * TC; idx += blockDim.x) {
-    const int j = idx / TC, c = idx % TC;
-    Cx<T> z;
-    if (kind == KIND_PP) {
-      z = {x(2 * j, c), x(2 * j + 1, c)};
-    } else if (kind == KIND_NN || kind == KIND_DD) {
-      const int t0 = 2 * j, t1 = 2 * j + 1;  // v_t = x_2t (t < m), x_{2(n-1-t)+1} (t >= m)
-      z = {t0 < m ? x(2 * t0, c) : x(2 * (n - 1 - t0) + 1, c), t1 < m ? x(2 * t1, c) : x(2 * (n - 1 - t1) + 1, c)};
-    } else {
-      z = cmul(Cx<T>{x(2 * j, c), x(n - 1 - 2 * j, c)}, tw.tw4a[j]);
-    }
-    A[idx] = z;
-  }
-  __syncthreads();
-  const Cx<T>* R = cfft<T, TC>(A, Bf, m, tw.fft, false);
-  // F(x - shift0) = F(x) - shift0 F(1); F(1) is zero outside mode 0
-  auto put = [&](int q, int c, T y) {
-    if (q == 0) y -= sub0;
-    if (c < ch.ncol) out[(long long)q * ncell + ooff[c]] = y;
-  };
-  if (kind == KIND_PP || kind == KIND_NN || kind == KIND_DD) {
-    // each half-spectrum bin k = 0..m once; it gives output k and its mirror n - k
-    for (int idx = threadIdx.x; idx < (m + 1) * TC; idx += blockDim.x) {
-      const int k = idx / TC, c = idx % TC;
-      const Cx<T> X = rdft_bin<T, TC>(R, k, m, c, tw);
-      const bool mirror = k > 0 && k < m;
-      if (kind == KIND_PP) {
-        put(k, c, X.re);
-        if (mirror) put(n - k, c, X.im);
-      } else {
-        const Cx<T> w = tw.tw2n[k];
-        const T y = (T)2 * (w.re * X.re - w.im * X.im);
-        put(kind == KIND_DD ? n - 1 - k : k, c, y);
-        if (mirror) {  // bin n - k is conj(X_k)
-          const Cx<T> wm = tw.tw2n[n - k];
-          const T ym = (T)2 * (wm.re * X.re + wm.im * X.im);
-          put(kind == KIND_DD ? k - 1 : n - k, c, ym);
-        }
-      }
-    }
-  } else {
-    for (int idx = threadIdx.x; idx < n * TC; idx += blockDim.x) {
-      const int q = idx / TC, c = idx % TC;
-      const int qq = kind == KIND_DN ? n - 1 - q : q;
-      T y;
-      if ((qq & 1) == 0) {
-        const int k = qq / 2;
-        y = (T)2 * cmul(R[k * TC + c], tw.tw4b[k]).re;
-      } else {
-        const int k = (n - 1 - qq) / 2;
-        y = (T)-2 * cmul(R[k * TC + c], tw.tw4b[k]).im;
-      }
-      put(q, c, y);
-    }
-  }
+  forward_chunk<T, TC, KIND, TI>(chunks[blockIdx.x], blk, cb, n, tw, in3, out, ncell, sub0, split, smem);
 }
 
 template <typename T, int TC, int KIND>

@@ -516,6 +516,7 @@ void free_plan(snac_plan* P) {
   if (P->h_active) cudaFreeHost(P->h_active);
   if (P->h_check) cudaFreeHost(P->h_check);
   if (P->h_cycles) cudaFreeHost(P->h_cycles);
+  if (P->h_wait) cudaFreeHost(P->h_wait);
   delete P;
 }
 
@@ -932,6 +933,7 @@ int create(snac_plan** out, int32_t nblocks, const snac_block* blocks_in, int32_
     // per-mode, per-tile partial sums (basic tiles; the fused tiles are fewer)
     if ((st = dmalloc(P, &P->d_mode_part, (size_t)P->nz * std::max<size_t>(P->lev[0].tiles.size(), 64)))) break;
     if ((st = dmalloc(P, &P->d_mode_norm2, (size_t)P->nz))) break;
+    if (P->onchip && (st = dmalloc(P, &P->d_fused, 2))) break;
     if ((st = dmalloc(P, &P->d_active, (size_t)P->nz)) || (st = dmalloc(P, &P->d_check, (size_t)P->nz))) break;
     auto mapped = [](auto** h, auto** dh, size_t n) {
       return cudaHostAlloc((void**)h, n * sizeof(**h), cudaHostAllocMapped) == cudaSuccess &&
@@ -939,7 +941,7 @@ int create(snac_plan** out, int32_t nblocks, const snac_block* blocks_in, int32_
     };
     if (!mapped(&P->h_sums, &P->dh_sums, SUM_SLOTS) || !mapped(&P->h_mode_norm2, &P->dh_mode_norm2, P->nz) ||
         !mapped(&P->h_active, &P->dh_active, P->nz) || !mapped(&P->h_check, &P->dh_check, P->nz) ||
-        !mapped(&P->h_cycles, &P->dh_cycles, P->nz)) {
+        !mapped(&P->h_cycles, &P->dh_cycles, P->nz) || !mapped(&P->h_wait, &P->dh_wait, 1)) {
       st = fail(SNAC_ERR_OOM, "pinned host allocation");
       break;
     }

@@ -162,7 +162,7 @@ struct TwiddleOffsets {
 // Kernel kinds counted by the tracing facility.
 enum KernelKind {
   K_FIELD3D = 0, K_REDUCE, K_FIX_MEAN, K_SHIFT, K_FORWARD, K_BACKWARD, K_SMOOTH, K_RESTRICT, K_PROLONG,
-  K_COARSE, K_MODE_RESID, K_MODE_REDUCE, K_MODE_APPLY, K_FDOWN, K_FUP, K_BOTTOM, K_FIELD3D_FF, K_ONCHIP, K_COUNT
+  K_COARSE, K_MODE_RESID, K_MODE_REDUCE, K_MODE_APPLY, K_FDOWN, K_FUP, K_BOTTOM, K_FIELD3D_FF, K_ONCHIP, K_FWD_ONCHIP, K_COUNT
 };
 
 struct KernelStat {
@@ -198,6 +198,9 @@ struct snac_plan {
   double* d_pweight = nullptr;
   int* h_cycles = nullptr;    // per wavenumber: V-cycles of the last on-chip solve (mapped pinned)
   int* dh_cycles = nullptr;
+  int* d_fused = nullptr;     // the fused transform + on-chip launch's counters: next item, chunks done
+  int* h_wait = nullptr;      // set by that launch when a bounded wait gave up (mapped pinned)
+  int* dh_wait = nullptr;
   int nblk = 0;
   int nz = 0;    // wavenumbers held in mode space (q0 .. q0 + nz - 1)
   int nzt = 0;   // cells along the homogeneous axis: the transform length, the 3-D field's z planes
@@ -360,6 +363,22 @@ cudaError_t launch_onchip(snac_plan* P, int nact, double target, cudaStream_t s)
 // The same for the wavenumbers of several plans (one precision) in one persistent launch; h_items
 // (plan index, wavenumber), targets per plan; d_scratch of onchip_batch_scratch(nplans, nitems) bytes.
 size_t onchip_batch_scratch(int nplans, int nitems);
+// The forward transform of in3 (FP64, or FP32 with in_f32; shift0: mean removed from f at k = 0)
+// and the on-chip solves of every wavenumber in one persistent launch (kern_bottom.cu): a solve
+// waits for its plan's transform chunks, at most wait_s seconds (then *h_wait = 1 and the solve is
+// skipped). extra_need > 0 only for the self-test of the timeout (a count nothing reaches).
+bool fused_ready(const snac_plan* P);
+cudaError_t launch_fwd_onchip(snac_plan* P, const void* in3, bool in_f32, double shift0, double target, double wait_s,
+                              int extra_need, cudaStream_t s);
+struct FusedInput {
+  const void* in3;
+  bool in_f32;
+  double shift0;
+};
+size_t fwd_onchip_batch_scratch(int nplans, int nitems);
+cudaError_t launch_fwd_onchip_batch(snac_plan* const* plans, const FusedInput* inputs, const double* targets,
+                                    int nplans, double wait_s, void* d_scratch, int sms, cudaStream_t s);
+constexpr double WAIT_LIMIT_S = 1.0;  // bound of every device-side wait of a solve
 cudaError_t launch_onchip_batch(snac_plan* const* plans, const double* targets, int nplans, const int2* h_items,
                                 int nitems, void* d_scratch, int sms, cudaStream_t s);
 // Shared-memory layout of that kernel when it starts at level lb, for inner type width w: per level

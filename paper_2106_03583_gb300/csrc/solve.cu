@@ -236,6 +236,8 @@ struct Job {
   int st = SNAC_OK;
   bool finished = false;
   bool p_zero = false, updated = false, aim_final = false, r32 = false, ff = false, redo = false;
+  bool fused = false;  // this step's forward transform runs inside the on-chip launch
+  FusedInput fin{};
   double fshift = 0.0, fn = 0.0, fn_pre = 0.0, prev_rel = INFINITY, rn = 0.0, target = 0.0;
   int k = 0;
   std::vector<int> cyc;
@@ -385,6 +387,12 @@ int job_decide(Job& J, cudaStream_t s) {
   J.target = 0.5 * J.tol * fn;
   if (P->precision == SNAC_MIXED && P->inner_reduction * rn > J.tol * fn) J.target = P->inner_reduction * rn;
   J.aim_final = J.target <= 0.5 * J.tol * fn;
+  J.fused = fused_ready(P);
+  if (J.fused) {  // the forward transform goes into the same launch as the wavenumber solves
+    if (J.k == 0 && J.p_zero) J.fin = FusedInput{J.f, false, J.fshift};
+    else J.fin = FusedInput{P->d_r3, J.r32, 0.0};
+    return SNAC_OK;
+  }
   if (J.k == 0 && J.p_zero) CK(launch_forward(P, J.f, P->lev[0].d_f, J.fshift, P->scaled_f, s));
   else if (J.r32) CK(launch_forward_f32(P, reinterpret_cast<const float*>(P->d_r3), P->lev[0].d_f, s));
   else CK(launch_forward(P, P->d_r3, P->lev[0].d_f, 0.0, P->scaled_f, s));
@@ -445,9 +453,44 @@ int run_jobs(std::vector<Job>& jobs, cudaStream_t s) {
       }
     // the wavenumber solves: on-chip plans together (one persistent launch per precision), the
     // others level by level
-    std::vector<Job*> chip[2];
+    std::vector<Job*> chip[2], fusedj[2];
     for (Job& J : jobs)
-      if (!J.finished && J.P->onchip) chip[J.P->precision == SNAC_FP64 ? 0 : 1].push_back(&J);
+      if (!J.finished && J.P->onchip) (J.fused ? fusedj : chip)[J.P->precision == SNAC_FP64 ? 0 : 1].push_back(&J);
+    // forward transform + on-chip solves in one persistent launch per precision (bounded waits)
+    for (int g = 0; g < 2; ++g) {
+      if (fusedj[g].empty()) continue;
+      if (fusedj[g].size() == 1) {
+        Job& J = *fusedj[g][0];
+        job_cuda(J, launch_fwd_onchip(J.P, J.fin.in3, J.fin.in_f32, J.fin.shift0, J.target, WAIT_LIMIT_S, 0, s),
+                 "forward transform and on-chip wavenumber solves");
+        continue;
+      }
+      std::vector<snac_plan*> plans;
+      std::vector<FusedInput> ins;
+      std::vector<double> targets;
+      int nitems = 0;
+      for (Job* J : fusedj[g]) {
+        plans.push_back(J->P);
+        ins.push_back(J->fin);
+        targets.push_back(J->target);
+        nitems += J->P->nz + (int)(J->P->precision == SNAC_FP64 ? J->P->chunks64.size() : J->P->chunks32.size());
+      }
+      const size_t need = fwd_onchip_batch_scratch((int)plans.size(), nitems);
+      if (need > scratch_bytes) {
+        if (scratch) cudaFreeAsync(scratch, s);
+        scratch = nullptr;
+        scratch_bytes = 0;
+        if ((e = cudaMallocAsync(&scratch, need, s)) != cudaSuccess) { status = cuda_fail(e, "cudaMallocAsync"); break; }
+        scratch_bytes = need;
+      }
+      e = launch_fwd_onchip_batch(plans.data(), ins.data(), targets.data(), (int)plans.size(), WAIT_LIMIT_S, scratch,
+                                  sms, s);
+      if (e != cudaSuccess)
+        for (Job* J : fusedj[g]) job_cuda(*J, e, "forward transform and on-chip wavenumber solves");
+      // the next group reuses the scratch only after this launch has read it
+      if (g == 0 && !fusedj[1].empty() && (e = sync()) != cudaSuccess) { status = cuda_fail(e, "cudaStreamSynchronize"); break; }
+    }
+    if (status) break;
     for (int g = 0; g < 2; ++g) {
       if (chip[g].empty()) continue;
       if (chip[g].size() == 1) {
@@ -466,7 +509,8 @@ int run_jobs(std::vector<Job>& jobs, cudaStream_t s) {
         for (int q = 0; q < J->P->nz; ++q) items.push_back(make_int2(idx, q));
       }
       const size_t need = onchip_batch_scratch((int)plans.size(), (int)items.size());
-      if (need > scratch_bytes) {
+      if (need > scratch_bytes || !fusedj[0].empty() || !fusedj[1].empty()) {
+        if (scratch && (e = sync()) != cudaSuccess) { status = cuda_fail(e, "cudaStreamSynchronize"); break; }
         if (scratch) cudaFreeAsync(scratch, s);
         scratch = nullptr;
         scratch_bytes = 0;
@@ -484,15 +528,27 @@ int run_jobs(std::vector<Job>& jobs, cudaStream_t s) {
         const int st = mode_solves(J.P, J.target, s, J.cyc.data());
         if (st) J.finish(st);
       }
-    if (!chip[0].empty() || !chip[1].empty()) {
+    if (!chip[0].empty() || !chip[1].empty() || !fusedj[0].empty() || !fusedj[1].empty()) {
       if ((e = sync()) != cudaSuccess) { status = cuda_fail(e, "cudaStreamSynchronize"); break; }
-      for (int g = 0; g < 2; ++g)
+      for (int g = 0; g < 2; ++g) {
         for (Job* J : chip[g])
           if (!J->finished) {
             profile_resolve(J->P);
             const int st = onchip_results(J->P, J->cyc.data());
             if (st) J->finish(st);
           }
+        for (Job* J : fusedj[g])
+          if (!J->finished) {
+            profile_resolve(J->P);
+            if (*J->P->h_wait) {
+              set_error("a device-side wait gave up (transform chunks not counted within the limit)");
+              J->finish(SNAC_ERR_TIMEOUT);
+              continue;
+            }
+            const int st = onchip_results(J->P, J->cyc.data());
+            if (st) J->finish(st);
+          }
+      }
     }
     for (Job& J : jobs)
       if (!J.finished) job_cuda(J, job_update(J, s), "update");
@@ -553,6 +609,19 @@ int snac_poisson_solve_batch(int32_t n, snac_plan* const* plans, const double* c
     if (!worst && h_status[k]) worst = h_status[k];
   }
   return worst;
+}
+
+int snac_test_wait_timeout(snac_plan* plan, double wait_seconds, void* stream) {
+  int st = check_plan3d(plan);
+  if (st) return st;
+  if (!fused_ready(plan) || !(wait_seconds > 0.0) || wait_seconds > WAIT_LIMIT_S) return SNAC_ERR_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  // the wavenumber solves wait for one transform chunk more than the launch has: nothing ever
+  // completes the count, every wait runs out and the launch must come back with the status set
+  CK(launch_fwd_onchip(plan, plan->d_r3, false, 0.0, 1.0, wait_seconds, 1, s));
+  CK(cudaStreamSynchronize(s));
+  profile_resolve(plan);
+  return *plan->h_wait ? SNAC_ERR_TIMEOUT : SNAC_OK;
 }
 
 int snac_apply_operator(snac_plan* plan, const double* d_p, double* d_out, void* stream) {

@@ -8,7 +8,7 @@ namespace snac {
 static const char* const kKernelNames[K_COUNT] = {
     "field3d", "reduce", "fix_mean", "shift", "forward_transform", "backward_update", "smooth",
     "restrict", "prolong", "coarse_solve", "mode_resid", "mode_reduce", "mode_apply", "fused_down", "fused_up",
-    "bottom", "field3d_ff", "onchip"};
+    "bottom", "field3d_ff", "onchip", "fwd_onchip"};
 
 static cudaEvent_t take_event(snac_plan* P) {
   if (!P->event_pool.empty()) {

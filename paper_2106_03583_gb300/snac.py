@@ -31,7 +31,7 @@ EXPORTS = ("snac_plan_create", "snac_plan_workspace_bytes", "snac_poisson_solve"
            "snac_mode_operator", "snac_mode_vcycles", "snac_plan_set_profiling", "snac_plan_kernel_stats",
            "snac_plan_reset_stats", "snac_residual_noalloc", "snac_pencil_forward", "snac_pencil_backward_update",
            "snac_pencil_setup", "snac_pencil_residual", "snac_mode_solve", "snac_mode_fix_mean",
-           "snac_poisson_solve_batch",
+           "snac_poisson_solve_batch", "snac_test_wait_timeout",
            "snac_engine_create", "snac_engine_submit", "snac_engine_wait", "snac_engine_get_stats",
            "snac_engine_clock", "snac_engine_destroy", "snac_autotune")
 
@@ -125,6 +125,7 @@ def lib() -> ctypes.CDLL:
             "snac_mode_fix_mean": [vp, vp, f64, vp],
             "snac_poisson_solve_batch": [i32, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(vp), f64,
                                          ctypes.POINTER(i32), vp],
+            "snac_test_wait_timeout": [vp, f64, vp],
             "snac_forward_transform": [vp, vp, vp, vp],
             "snac_backward_update": [vp, vp, vp, vp],
             "snac_mode_operator": [vp, vp, vp, vp],
@@ -247,6 +248,10 @@ class Plan:
         if st != SNAC_OK and raise_on_error:
             _check(st)
         return self.info()
+
+    def test_wait_timeout(self, wait_seconds: float = 0.05) -> str:
+        """Run the bounded-wait self-test (snac_test_wait_timeout); returns the status name."""
+        return STATUS.get(lib().snac_test_wait_timeout(self._h, float(wait_seconds), self._stream()), "?")
 
     def info(self) -> dict:
         inf = _Info()

@@ -40,12 +40,13 @@ def test_onchip_solve_matches_oracle_and_level_path(name, precision):
         st = pl.kernel_stats()
         assert info["status"] == 0 and info["rel_res"] <= 1e-10
         if onchip:
-            # one on-chip launch per defect-correction step, no level-by-level cycle
-            assert st["onchip"]["launches"] == info["outer_iters"] >= 1
-            assert st.get("smooth", {"launches": 0})["launches"] == 0
-            assert st.get("fused_up", {"launches": 0})["launches"] == 0
+            # one launch per defect-correction step (forward transform and on-chip solves together),
+            # no level-by-level cycle and no separate forward transform
+            assert st["fwd_onchip"]["launches"] == info["outer_iters"] >= 1
+            assert st["forward_transform"]["launches"] == 0
+            assert st["smooth"]["launches"] == 0 and st["fused_up"]["launches"] == 0
         else:
-            assert st.get("onchip", {"launches": 0})["launches"] == 0
+            assert st["fwd_onchip"]["launches"] == 0 and st["onchip"]["launches"] == 0
         sols[onchip] = host(p)
         assert osv.rel_residual(blocks, f, sols[onchip]) <= 1.01e-10
         assert rel(sols[onchip], ref) <= 1e-9
@@ -83,8 +84,8 @@ def test_batch_equals_each_problem_alone(precision):
         assert np.array_equal(host(p), pa)                       # bitwise: same arithmetic
         assert info["outer_iters"] == ia["outer_iters"] and info["total_cycles"] == ia["total_cycles"]
         assert osv.rel_residual(b, f, host(p)) <= 1.01e-10
-    # the on-chip plans' wavenumber solves shared one launch per step
-    onchip = [pl for pl in plans if pl.kernel_stats().get("onchip", {"launches": 0})["launches"]]
+    # the on-chip plans' transforms and wavenumber solves shared one launch per step
+    onchip = [pl for pl in plans if pl.kernel_stats()["fwd_onchip"]["launches"]]
     assert len(onchip) >= 3
     for pl in plans:
         pl.close()
@@ -103,3 +104,26 @@ def test_batch_reports_each_problems_status():
     assert [i["status_name"] for i in infos] == ["OK", "OK", "OK", "INCOMPATIBLE_RHS"]
     for pl in plans:
         pl.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_bounded_wait_gives_up_and_the_context_stays_usable(precision):
+    """The on-chip solves wait on the device for their plan's transform chunks. The self-test makes
+    that wait impossible (one chunk more than the launch has): every wait must give up after the
+    limit and the call return TIMEOUT without trapping; the same plan then solves normally."""
+    import time
+    import torch
+    blocks, f = inputs.config("c64", seed=5)
+    pl = plan(blocks, precision=precision)
+    t0 = time.time()
+    assert pl.test_wait_timeout(0.05) == "TIMEOUT"
+    assert time.time() - t0 < 10.0
+    p = torch.zeros(len(f), dtype=torch.float64, device="cuda")
+    info = pl.solve(dev(f), p, tol=1e-10)
+    assert info["status"] == 0
+    ref, _ = osv.solve(blocks, f)
+    assert rel(host(p), ref) <= 1e-9
+    pl.close()
+    lvl = plan(blocks, precision=precision, onchip=False)   # level by level: no on-chip wait to test
+    assert lvl.test_wait_timeout(0.05) == "INVALID_ARG"
+    lvl.close()
