@@ -794,7 +794,8 @@ def run_batch(args):
     for p in ps:
         p.zero_()
     snac.solve_batch(plans, fd, ps, tol=1e-10)
-    onchip_plans = sum(1 for pl in plans if pl.kernel_stats()["onchip"]["launches"] > 0)
+    onchip_plans = sum(1 for pl in plans
+                       if pl.kernel_stats()["onchip"]["launches"] + pl.kernel_stats()["fwd_onchip"]["launches"] > 0)
     torch.cuda.synchronize()
     reps = []
     for _ in range(3):

@@ -782,7 +782,9 @@ cudaError_t fwd_onchip_t(snac_plan* P, const void* in3, bool in_f32, double shif
   int per_sm = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fwd_onchip<T, TC>, BT, smem);
   const int nitems = F.nchunks + P->nz;
-  const int grid = std::max(1, std::min(nitems, std::max(1, per_sm) * P->sms));
+  // one CTA per multiprocessor: two wavenumber solves never share one (their V-cycles are bound by
+  // the SM's own pipes), and the transform chunks still spread over every SM
+  const int grid = std::max(1, std::min(nitems, std::min(std::max(1, per_sm), 1) * P->sms));
   const double w = sizeof(T), n3 = (double)P->n3;
   LaunchScope ls(P, K_FWD_ONCHIP, (in_f32 ? 4.0 : 8.0) * n3 + w * n3 + 2.0 * w * (double)P->lev[0].ncell * P->nz,
                  (2.5 * std::log2((double)P->nzt) + 8.0) * n3 + 4.0 * onchip_cycle_flops(P) * P->nz, s);
@@ -856,7 +858,7 @@ cudaError_t fwd_onchip_batch_t(snac_plan* const* plans, const FusedInput* inputs
   int per_sm = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fwd_onchip_batch<T, TC>, BT, smem);
   const int nitems = (int)items.size();
-  const int grid = std::max(1, std::min(nitems, std::max(1, per_sm) * sms));
+  const int grid = std::max(1, std::min(nitems, std::min(std::max(1, per_sm), 1) * sms));  // one CTA per SM
   k_fwd_onchip_batch<T, TC><<<grid, BT, smem, s>>>(d_fargs, d_args, d_items, nitems, d_ctr, (long long)(wait_s * 1e9));
   return cudaGetLastError();
 }
