@@ -66,6 +66,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["snac", "reference"], default="snac")
     ap.add_argument("--workload", default="chan")
+    ap.add_argument("--scale", type=int, default=1, help="divide every cell count by this (profiling cases)")
     ap.add_argument("--secondary", default="mb2x2", help="second workload reported beside the headline ('none')")
     ap.add_argument("--tol", type=float, default=1e-10)
     ap.add_argument("--seed", type=int, default=0)
@@ -171,11 +172,12 @@ def _dtype(precision):
     return "f64" if precision == "fp64" else "f32 transforms and multigrid, f64 residual and update (mixed)"
 
 
-def workload_config(name, blocks, tol, precision, world):
+def workload_config(name, blocks, tol, precision, world, scale=1):
     """The config dict of a bench line; identical for the GPU arm and the reference arm."""
     from paper_2106_03583_gb300 import inputs
     n3 = inputs.total_cells(blocks)
-    return {"workload": WORKLOADS.get(name, name), "n_cells": n3, "tol": tol, "precision": precision,
+    wl = WORKLOADS.get(name, name) if scale == 1 else f"{name} with every cell count divided by {scale}"
+    return {"workload": wl, "n_cells": n3, "tol": tol, "precision": precision,
             "parallelism": f"replicas x{world}",
             "l2": (f"inputs larger than L2 ({8 * n3 / 1e6:.0f} MB per float64 field), no flush" if 8 * n3 > 129e6
                    else f"{8 * n3 / 1e6:.0f} MB per float64 field: L2-resident, no flush")}
@@ -184,7 +186,8 @@ def workload_config(name, blocks, tol, precision, world):
 def base_line(args, world, blocks, precision):
     return {"metric": METRIC, "unit": "solves/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": _dtype(precision),
-            "data": "synthetic", "config": workload_config(args.workload, blocks, args.tol, precision, world)}
+            "data": "synthetic",
+            "config": workload_config(args.workload, blocks, args.tol, precision, world, getattr(args, "scale", 1))}
 
 
 # ---------------------------------------------------------------------------------------------
@@ -370,7 +373,7 @@ def run_reference(args):
     if rank != 0:
         return
     from paper_2106_03583_gb300 import inputs
-    blocks, f = inputs.config(args.workload, seed=args.seed)
+    blocks, f = inputs.config(args.workload, seed=args.seed, scale=getattr(args, "scale", 1))
     s = OracleSampler(blocks, f)
     try:
         s.start_pool()
@@ -612,7 +615,7 @@ def run_snac(args):
     build.build()
     hbm_peak, hbm_kind = peaks()
     precs = args.precisions.split(",")
-    blocks, f_np = inputs.config(args.workload, seed=rank_seed(args.seed, rank))
+    blocks, f_np = inputs.config(args.workload, seed=rank_seed(args.seed, rank), scale=args.scale)
     f = torch.from_numpy(f_np).cuda()
     results = {}
     for prec in precs:
