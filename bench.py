@@ -55,8 +55,18 @@ FP64_IN_FP64_PLAN = {"smooth", "restrict", "prolong", "mode_resid", "mode_apply"
 # kernel on the workload at 1/2 scale per axis), divided by that launch's algorithmic bytes, with the
 # sha256 of the kernel's source file when it was captured. The bench scales the ratio to its own
 # launches (traffic grows in proportion to the cells processed) and reports null once the source
-# differs from the captured one.
-TRAFFIC = {}
+# differs from the captured one. Captures: `bench.py --workload chan --scale 2` (3.4e7 cells), level-0
+# launches of the first cycles (fused kernels), the first launch of the others.
+_FUSED = {"src": "paper_2106_03583_gb300/csrc/kern_fused.cu",
+          "sha256": "8482a9e751212f3f6a0228c49b52b8e79a5f0751fb2e1972b428e25e6573bf02"}
+TRAFFIC = {
+    ("chan", "fused_up", "mixed"): dict(_FUSED, ratio=412.33 / 436.21),       # 3.25 w x 131072 cells x 256 modes
+    ("chan", "fused_down", "mixed"): dict(_FUSED, ratio=335.32 / 396.36),     # 3.5 w x 131072 x 216 modes
+    ("chan", "field3d_ff", "mixed"): {"src": "paper_2106_03583_gb300/csrc/kern_ffresid.cu", "ratio": 669.33 / 671.09,
+                                      "sha256": "fcff0956e5b274b3b442417db6de471cb24f9ae983603500bb74bce020b00bcb"},
+    ("chan", "smooth", "fp64"): {"src": "paper_2106_03583_gb300/csrc/kern_mg.cu", "ratio": 755.85 / 402.65,
+                                 "sha256": "7ff5bf650cac1bff272ed46562c8e0a873024af37927a04949010cce6a4b6037"},
+}
 
 
 def parse():

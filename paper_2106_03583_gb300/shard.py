@@ -195,7 +195,7 @@ class ShardedSolver:
         info = sv.solve(f_pencil, p_pencil, tol=1e-10)     # [z][c] tensors of this rank's columns
     """
 
-    def __init__(self, blocks, stages, exchange, cols=None, modes=None, inner_reduction: float = 1e-3,
+    def __init__(self, blocks, stages, exchange, cols=None, modes=None, inner_reduction: float = 1e-4,
                  max_outer: int = 20):
         self.blocks = blocks
         self.st = stages

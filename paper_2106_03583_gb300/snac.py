@@ -199,7 +199,7 @@ class Plan:
     """A solver plan for one multi-block problem (``snac_plan_create``)."""
 
     def __init__(self, blocks, homog_axis: int = 2, precision: str = "fp64", nu1: int = 2, nu2: int = 2,
-                 max_outer: int = 20, max_cycles: int = 40, max_coarse: int = 64, inner_reduction: float = 1e-3,
+                 max_outer: int = 20, max_cycles: int = 40, max_coarse: int = 64, inner_reduction: float = 1e-4,
                  fused: int = -1, shift: float = 0.0, modes=None, onchip: bool = True):
         import torch
         if not torch.cuda.is_available():
@@ -434,7 +434,7 @@ class Engine:
 
     def submit(self, blocks, rhs, tol: float = 1e-10, precision: str = "fp64", homog_axis: int = 2, nu1: int = 2,
                nu2: int = 2, max_outer: int = 20, max_cycles: int = 40, max_coarse: int = 64,
-               inner_reduction: float = 1e-3, fused: int = -1, shift: float = 0.0) -> int:
+               inner_reduction: float = 1e-4, fused: int = -1, shift: float = 0.0) -> int:
         if precision not in _PREC:
             raise ValueError(f"precision must be one of {list(_PREC)}")
         n3 = int(sum(np.prod([b["hi"][a] - b["lo"][a] + 1 for a in range(3)]) for b in blocks))
@@ -508,7 +508,7 @@ def autotune(blocks, rhs, tol: float = 1e-10, precision: str = "fp64", homog_axi
     if not isinstance(rhs, torch.Tensor) or not rhs.is_cuda or rhs.dtype != torch.float64 or \
             not rhs.is_contiguous() or rhs.numel() != n3:
         raise ValueError(f"rhs must be a contiguous CUDA float64 tensor with {n3} elements")
-    d = dict(nu1=2, nu2=2, max_outer=20, max_cycles=40, max_coarse=64, fused=-1, inner_reduction=1e-3, shift=0.0)
+    d = dict(nu1=2, nu2=2, max_outer=20, max_cycles=40, max_coarse=64, fused=-1, inner_reduction=1e-4, shift=0.0)
     unknown = set(base) - set(d)
     if unknown:
         raise ValueError(f"unknown options {sorted(unknown)}")
