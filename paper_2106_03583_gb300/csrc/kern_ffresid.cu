@@ -92,7 +92,7 @@ __device__ __forceinline__ long long caller_cell_ff(const CallerBlk* __restrict_
 }
 
 // One thread per x-y cell of a 32 x 8 tile, marching through kchunk consecutive z planes, so that
-// the split of p at a cell serves as the centre and as both z neighbours. The coefficients come as
+// the split of p at a cell serves as the centre and as both z neighbours (loads one plane ahead). The coefficients come as
 // rounded float pairs from tables built with the plan (no FP64 instruction per cell or per thread,
 // apart from the thread's final sums). Interior z planes couple both z neighbours with the same
 // coefficient, so their sum is formed first (one product instead of two). r (FP32) is written at the
@@ -100,7 +100,7 @@ __device__ __forceinline__ long long caller_cell_ff(const CallerBlk* __restrict_
 // sum V p (NEED_VP), 0}; the squares are taken of values scaled by nscale (a power of two chosen from
 // ||f||, so that FP32 neither underflows nor overflows) and unscaled in FP64 per thread.
 template <bool SHIFT, bool NEED_F2, bool NEED_VP>
-__global__ void __launch_bounds__(TILE_THREADS, 4)
+__global__ void __launch_bounds__(TILE_THREADS, 3)
     k_field3d_ff(LevelView<double> L, const CallerBlk* __restrict__ cb, const float4* __restrict__ cxff,
                  const float4* __restrict__ cyff, const float2* __restrict__ dgff, const float4* __restrict__ czff,
                  int nz, int periodic_z, int kchunk, double dz, const double* __restrict__ f,
@@ -134,10 +134,25 @@ __global__ void __launch_bounds__(TILE_THREADS, 4)
     FF pc = split64(qc[(long long)k0 * sc]);
     const int kd0 = k0 > 0 ? k0 - 1 : (periodic_z ? nz - 1 : k0);
     FF pd = kd0 == k0 ? pc : split64(qc[(long long)kd0 * sc]);
-    for (int k = k0; k < k1; ++k) {
+    // The raw loads of a plane (f, the four x-y neighbours, and p one plane up -- the centre itself
+    // at a non-periodic top end) are issued one plane ahead, so that their DRAM latency overlaps the
+    // previous plane's arithmetic.
+    double xu, xf, xw, xe, xs, xn;
+    auto load = [&](int k) {
       const int ku = k < nz - 1 ? k + 1 : (periodic_z ? 0 : k);
-      const FF pu = ku == k ? pc : split64(qc[(long long)ku * sc]);
-      const FF fv = split64(qf[(long long)k * sc]);
+      xu = qc[(long long)ku * sc];
+      xf = qf[(long long)k * sc];
+      xw = qw[(long long)k * sw];
+      xe = qe[(long long)k * se];
+      xs = qs[(long long)k * ss];
+      xn = qn[(long long)k * sn];
+    };
+    load(k0);
+    for (int k = k0; k < k1; ++k) {
+      const double cu = xu, cf = xf, cw = xw, ce = xe, cs = xs, cn = xn;
+      if (k + 1 < k1) load(k + 1);
+      const FF pu = split64(cu);
+      const FF fv = split64(cf);
       float s_h = fv.hi, s_l = fv.lo;
       if (SHIFT) sub_prod(s_h, s_l, FF{1.0f, 0.0f}, FF{fsh.x, fsh.y});
       if (NEED_F2) {
@@ -145,10 +160,10 @@ __global__ void __launch_bounds__(TILE_THREADS, 4)
         sf = __fmaf_rn(fr, fr, sf);
       }
       const float4 z = czff[k];
-      sub_prod(s_h, s_l, cxl, split64(qw[(long long)k * sw]));
-      sub_prod(s_h, s_l, cxh, split64(qe[(long long)k * se]));
-      sub_prod(s_h, s_l, cyl, split64(qs[(long long)k * ss]));
-      sub_prod(s_h, s_l, cyh, split64(qn[(long long)k * sn]));
+      sub_prod(s_h, s_l, cxl, split64(cw));
+      sub_prod(s_h, s_l, cxh, split64(ce));
+      sub_prod(s_h, s_l, cyl, split64(cs));
+      sub_prod(s_h, s_l, cyh, split64(cn));
       if (z.x == z.z && z.y == z.w) {  // equal couplings (every plane but the ends of a non-periodic axis)
         float zh = pd.hi, zl = pd.lo;
         add_ff(zh, zl, pu);

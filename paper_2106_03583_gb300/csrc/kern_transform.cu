@@ -129,7 +129,7 @@ __global__ void __launch_bounds__(256) k_backward(const ChunkDev* __restrict__ c
           y = (T)-2 * cmul(R[k * TC + c], tw.tw4b[k]).im;
         }
       }
-      if (c < ch.ncol) p3[coff[c] + j * sk] = fma((double)y, inv_theta, old[u]);
+      if (c < ch.ncol) p3[coff[c] + j * sk] = fma(to_double(y), inv_theta, old[u]);
     }
   }
 }

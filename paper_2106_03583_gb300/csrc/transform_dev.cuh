@@ -24,6 +24,53 @@ __device__ __forceinline__ Cx<T> conj(Cx<T> a) {
   return {a.re, -a.im};
 }
 
+// FP64 <-> FP32 conversions by integer operations on the bit patterns. GB300 runs the hardware
+// conversions on its FP64 pipe (2 lanes per clock per multiprocessor), where they cost as much as
+// the transforms' FP64 arithmetic; these use the integer pipes instead.
+//   to_f32: round to nearest even; |x| below the FP32 normal range gives a signed zero, above it (and
+//           Inf) a signed infinity, NaN a NaN.
+//   to_f64: exact for normal floats and infinities/NaN; FP32 subnormals (below 1.2e-38) give a
+//           signed zero.
+__device__ __forceinline__ float to_f32(double x) {
+  const unsigned hw = (unsigned)__double2hiint(x), lw = (unsigned)__double2loint(x);
+  const unsigned sign = hw & 0x80000000u;
+  const int e11 = (int)((hw >> 20) & 0x7ffu);
+  const int e8 = e11 - 896;  // FP32 exponent field
+  // mantissa: top 23 of the 52 bits, then the round bit and whether any lower bit is set
+  unsigned m = ((hw & 0x000fffffu) << 3) | (lw >> 29);
+  const unsigned rest = lw & 0x1fffffffu;
+  const bool up = (rest > 0x10000000u) || (rest == 0x10000000u && (m & 1u));
+  unsigned bits = ((unsigned)e8 << 23) + m + (up ? 1u : 0u);  // a mantissa carry moves into the exponent
+  if (e8 <= 0) bits = 0u;                                     // below the normal range (and zero)
+  if (e8 >= 255 || bits >= 0x7f800000u) bits = 0x7f800000u;  // overflow and Inf
+  if (e11 == 0x7ff && ((hw & 0x000fffffu) | lw)) bits = 0x7fc00000u;  // NaN
+  return __uint_as_float(bits | sign);
+}
+
+__device__ __forceinline__ double to_f64(float y) {
+  const unsigned b = __float_as_uint(y);
+  const unsigned sign = b & 0x80000000u;
+  const unsigned e8 = (b >> 23) & 0xffu;
+  const unsigned m = b & 0x007fffffu;
+  unsigned hw = sign | ((e8 + 896u) << 20) | (m >> 3);
+  unsigned lw = m << 29;
+  if (e8 == 0u) hw = sign, lw = 0u;                      // zero (and subnormals)
+  if (e8 == 255u) hw = sign | 0x7ff00000u | (m >> 3);    // Inf and NaN
+  return __hiloint2double((int)hw, (int)lw);
+}
+
+template <typename T, typename TI>
+__device__ __forceinline__ T to_inner(TI v) {
+  if constexpr (sizeof(T) == 4 && sizeof(TI) == 8) return to_f32(v);
+  else return (T)v;
+}
+
+template <typename T>
+__device__ __forceinline__ double to_double(T v) {
+  if constexpr (sizeof(T) == 4) return to_f64(v);
+  else return v;
+}
+
 template <typename T>
 __device__ __forceinline__ Cx<T> cadd(Cx<T> a, Cx<T> b) {
   return {a.re + b.re, a.im + b.im};
@@ -252,7 +299,7 @@ __device__ void forward_chunk(const ChunkDev ch, const BlockDev* __restrict__ bl
 #pragma unroll
     for (int u = 0; u < LBATCH; ++u) {
       const int idx = i0 + u * blockDim.x;
-      if (idx < n * TC) xs[along ? (idx % n) * TC + idx / n : idx] = (T)v[u];
+      if (idx < n * TC) xs[along ? (idx % n) * TC + idx / n : idx] = to_inner<T, TI>(v[u]);
     }
   }
   __syncthreads();

@@ -313,3 +313,41 @@ def test_mixed_solve_runs_float_float_passes_and_decides_in_fp64():
     assert st["field3d_ff"]["launches"] >= 1
     assert st["field3d"]["launches"] >= 2          # the pre-pass and at least one FP64 check
     assert osv.rel_residual(blocks, f, host(p)) <= 1.01e-10
+
+
+@pytest.mark.parametrize("zpair", ["PP", "NN"])
+def test_fp32_transforms_of_extreme_values(zpair):
+    """The FP32 transforms convert between FP64 and FP32 with integer operations (round to nearest
+    even; exact the other way): zeros, signs, values across the FP32 range and values above it (which
+    must come out infinite, not garbage) in the 3-D field and in the modes."""
+    import torch
+    nz = 16
+    blocks = make("1x2", n=8, nz=nz, zpair=zpair, walls=("N", "N", "N", "N"))
+    N = inputs.total_cells(blocks)
+    g = ogrid.Grid(blocks)
+    rng = np.random.default_rng(9)
+    mags = 10.0 ** rng.uniform(-30, 30, N)
+    x = np.where(rng.random(N) < 0.5, -1.0, 1.0) * mags
+    x[::11] = 0.0
+    x[1::11] = -0.0
+    pl = plan(blocks, precision="mixed")
+    modes = torch.empty(N, dtype=torch.float32, device="cuda")
+    pl.forward_transform(dev(x), modes)
+    got = host(modes).reshape(nz, -1)
+    ref = T.forward(g.kind, g.to_planes(x.astype(np.float32).astype(np.float64)))
+    # column by column, relative to the column's largest input (FP32 transform accuracy)
+    scale = np.abs(g.to_planes(x)).max(axis=0) * nz
+    assert np.all(np.abs(got - ref) <= 1e-5 * scale + 1e-37)
+    # beyond the FP32 range: an infinity or NaN reaches the modes, nothing finite and wrong
+    x[5] = 1e300
+    pl.forward_transform(dev(x), modes)
+    col = int(np.argmax(np.abs(g.to_planes(x)).max(axis=0) >= 1e300))
+    assert not np.all(np.isfinite(host(modes).reshape(nz, -1)[:, col]))
+    # backward: modes of all sizes into an FP64 field, exactly converted before the update
+    X = (np.where(rng.random(N) < 0.5, -1.0, 1.0) * 10.0 ** rng.uniform(-30, 30, N)).astype(np.float32)
+    X[::7] = 0.0
+    p = torch.zeros(N, dtype=torch.float64, device="cuda")
+    pl.backward_update(dev(X.astype(np.float64), torch.float32), p)
+    upd = g.from_planes(T.backward(g.kind, X.astype(np.float64).reshape(nz, -1)))
+    scale_b = g.from_planes(np.broadcast_to(np.abs(X.astype(np.float64).reshape(nz, -1)).max(axis=0), (nz, g.plane.n)))
+    assert np.all(np.abs(host(p) - upd) <= 1e-5 * scale_b + 1e-37)
