@@ -88,6 +88,8 @@ def parse():
     ap.add_argument("--requests", type=int, default=400, help="--serve: requests per arrival rate")
     ap.add_argument("--pool", type=int, default=16, help="--serve: distinct problems the requests draw from")
     ap.add_argument("--workers", type=int, default=4, help="--serve/--batch: engine worker streams")
+    ap.add_argument("--max-group", type=int, default=16,
+                    help="--serve/--batch: most ready on-chip requests the engine solves together (1 = never merge)")
     return ap.parse_args()
 
 
@@ -718,7 +720,8 @@ def _latency_summary(res):
     return {"requests": len(res), "ok": ok, "failed": failed, "solves_per_s": len(res) / (t1 - t0),
             "p50_ms": float(np.median(lat)),
             "p99_ms": float(np.percentile(lat, 99)), "mean_ms": float(lat.mean()),
-            "plan_reuse": sum(t["plan_reused"] for _, t in res) / len(res)}
+            "plan_reuse": sum(t["plan_reused"] for _, t in res) / len(res),
+            "mean_group": sum(t["group"] for _, t in res) / len(res)}
 
 
 def run_serve(args):
@@ -745,7 +748,7 @@ def run_serve(args):
             reqs.append((b, f, tol, prec))
         return reqs
 
-    with snac.Engine(workers=args.workers, hbm_budget=150e9) as eng:
+    with snac.Engine(workers=args.workers, hbm_budget=150e9, max_group=args.max_group) as eng:
         # warm the plan cache with every pool problem in both precisions, then C: FP64, one at a time
         _engine_solve_all(eng, [(b, f, 1e-10, pr) for b, f, _ in pool for pr in ("fp64", "mixed")])
         calib = [(b, f, 1e-10, "fp64") for b, f, _ in pool]
@@ -769,7 +772,7 @@ def run_serve(args):
             "config": {"workload": f"{args.pool} seeded problems 32^3..512x512x256 (log-uniform per axis), 1-4 blocks, "
                                    "random walls and z pair, f = D u k^-5/3; tol 1e-8 (mixed) or 1e-10 "
                                    "(FP64 or mixed); each request draws one of them",
-                       "workers": args.workers, "hbm_budget_gb": 150, "pool_cells": int(sum(len(f) for _, f, _ in pool)),
+                       "workers": args.workers, "max_group": args.max_group, "hbm_budget_gb": 150, "pool_cells": int(sum(len(f) for _, f, _ in pool)),
                        "generation_s": round(t_gen, 1)},
             "fp64_one_at_a_time_solves_per_s": c_rate, "results": results,
             "engine": {"bytes_peak_gb": st["bytes_peak"] / 1e9, "plans_built": st["plans_built"],
@@ -825,8 +828,8 @@ def run_batch(args):
     del fd, ps
     work = [(b, f, 1e-10, "mixed") for b, f, _ in probs]
 
-    def engine_rate(autotune):
-        with snac.Engine(workers=args.workers, hbm_budget=150e9, autotune=autotune) as eng:
+    def engine_rate(autotune, max_group=args.max_group):
+        with snac.Engine(workers=args.workers, hbm_budget=150e9, autotune=autotune, max_group=max_group) as eng:
             t0 = time.time()
             _engine_solve_all(eng, work)      # builds (and, with autotune, tunes) and caches the 64 plans
             setup_s = time.time() - t0
@@ -834,16 +837,18 @@ def run_batch(args):
         return max(reps, key=lambda r: r["solves_per_s"]), setup_s
 
     best, setup_s = engine_rate(False)
+    unmerged, _ = engine_rate(False, 1)
     tuned, tune_s = engine_rate(True)
     line = {"metric": "batch of 64 independent problems: solves/s", "mode": "batch", "unit": "solves/s",
             "n_gpus": 1, "data": "synthetic",
             "config": {"workload": "64 seeded problems 32^3..256x256x128 (log-uniform per axis), 1-4 blocks, random "
                                    "walls and z pair, f ~ U[-1,1]; mixed precision, tol 1e-10",
-                       "workers": args.workers, "cells": int(sum(len(f) for _, f, _ in probs))},
+                       "workers": args.workers, "max_group": args.max_group,
+                       "cells": int(sum(len(f) for _, f, _ in probs))},
             "value": max(best["solves_per_s"], tuned["solves_per_s"]), "host_inputs_in_timed_region": True,
             "one_at_a_time_device_resident_solves_per_s": seq,
             "lockstep_batch_device_resident_solves_per_s": max(reps), "lockstep_batch_all_converged": batch_ok,
-            "lockstep_batch_onchip_problems": onchip_plans, "engine": best,
+            "lockstep_batch_onchip_problems": onchip_plans, "engine": best, "engine_unmerged": unmerged,
             "engine_autotuned": dict(tuned, first_pass_s=tune_s), "engine_first_pass_s": setup_s}
     print(json.dumps(line), flush=True)
 

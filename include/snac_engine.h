@@ -15,6 +15,13 @@
  *             right-hand side to the device, solves from a zero initial guess, copies the solution
  *             back and releases the request's memory. Requests on different workers overlap on the
  *             GPU.
+ *  Merging.   Small problems are batched as they arrive (continuous batching): a worker that takes a
+ *             request whose cached plan solves its wavenumbers on chip (snac_options.onchip) also
+ *             takes the other admitted requests of that kind with the same tolerance, up to
+ *             `max_group` in all, and solves them together with snac_poisson_solve_batch -- one
+ *             persistent launch per step serves every wavenumber of every request in the group. A
+ *             request that needs a plan built, or the autotuner, runs alone. The batched solve
+ *             gives each problem the result it gets alone (bitwise), so merging changes timing only.
  *  Plans.     Plans are cached by problem (blocks, spacings, boundary conditions, homogeneous axis,
  *             options) and reused by later requests of the same problem: the level hierarchy,
  *             coefficients, shifts, twiddles and coarse factors stay resident. A cached plan serves one
@@ -64,6 +71,8 @@ typedef struct {
   int32_t autotune;         /* 1: the first request of each problem runs snac_autotune on its own
                                right-hand side (from its submitted options) and later requests of that
                                problem reuse the chosen schedule; 0: options as submitted (0)         */
+  int32_t max_group;        /* most requests one worker solves together (Merging), 1..256; 1 = never
+                               merge (16)                                                              */
 } snac_engine_options;
 
 typedef struct {
@@ -71,6 +80,7 @@ typedef struct {
   int32_t worker;                            /* worker that ran the request                           */
   int32_t plan_reused;                       /* 1 if a cached plan served it, 0 if one was built      */
   int32_t tuned;                             /* 1 if this request ran the autotuner                   */
+  int32_t group;                             /* requests in the batched solve that ran it (1: alone)  */
   char error[160];                           /* detail of a failed request (empty if it succeeded)    */
 } snac_request_times;
 
@@ -85,7 +95,8 @@ typedef struct {
   int64_t plans_evicted;    /* plans released by the cache                                            */
 } snac_engine_stats;
 
-/* Create an engine on the current CUDA device (NULL options = the defaults shown above). */
+/* Create an engine on the current CUDA device (NULL options = the defaults shown above).
+ * SNAC_ERR_INVALID_ARG for a field outside its range. */
 int snac_engine_create(snac_engine **out, const snac_engine_options *opt);
 
 /* Submit one solve of A p = f to ||f - A p|| <= tol ||f|| (snac_poisson_solve) from p = 0.

@@ -1,6 +1,7 @@
 // Serving engine (include/snac_engine.h): admission under a device-memory budget, a cache of
-// resident plans, and worker threads that each drive their own CUDA stream. Host code only; every
-// step of a solve runs in the library's kernels through snac_plan_create / snac_poisson_solve.
+// resident plans, worker threads that each drive their own CUDA stream, and continuous batching of
+// small problems. Host code only; every step of a solve runs in the library's kernels through
+// snac_plan_create / snac_poisson_solve / snac_poisson_solve_batch.
 #include <algorithm>
 #include <chrono>
 #include <cmath>
@@ -97,6 +98,7 @@ std::string problem_key(const Request& r) {
     put(k, r.opt.fused);
     put(k, r.opt.inner_reduction);
     put(k, r.opt.shift);
+    put(k, r.opt.onchip);
   }
   return k;
 }
@@ -195,8 +197,32 @@ struct snac_engine {
     }
   }
 
+  // A request that may share a batched solve: its cached plan is resident and solves on chip
+  // (caller holds mu).
+  static bool mergeable(const Request* r) {
+    return r->slot && !r->build_plan && !r->tune && r->slot->plan->onchip;
+  }
+
+  // Take the next ready request and, if it is mergeable, the ready requests that can join it
+  // (caller holds mu).
+  void take(std::vector<Request*>& group) {
+    Request* r = ready.front();
+    ready.pop_front();
+    group.push_back(r);
+    if (!mergeable(r)) return;
+    for (auto it = ready.begin(); it != ready.end() && (int)group.size() < opt.max_group;) {
+      if (mergeable(*it) && (*it)->tol == r->tol) {
+        group.push_back(*it);
+        it = ready.erase(it);
+      } else {
+        ++it;
+      }
+    }
+  }
+
   void worker(int id);
   int run(Request* r, cudaStream_t s);
+  void run_group(const std::vector<Request*>& g, cudaStream_t s, std::vector<int>& st);
 };
 
 namespace {
@@ -297,54 +323,126 @@ int snac_engine::run(Request* r, cudaStream_t s) {
   return st;
 }
 
+// Requests of resident on-chip plans on stream s, solved together by snac_poisson_solve_batch:
+// one device block holds every right-hand side and solution, each copied in and out on its own.
+void snac_engine::run_group(const std::vector<Request*>& g, cudaStream_t s, std::vector<int>& st) {
+  const size_t n = g.size();
+  std::vector<size_t> off(n + 1, 0);
+  for (size_t k = 0; k < n; ++k) {  // 256-byte aligned field pairs (f, p)
+    const size_t nb = ((size_t)g[k]->n3 * sizeof(double) + 255) / 256 * 256;
+    off[k + 1] = off[k] + 2 * nb;
+  }
+  st.assign(n, SNAC_ERR_CUDA);
+  char* base = nullptr;
+  cudaError_t ce = cudaMallocAsync((void**)&base, off[n], s);
+  if (ce != cudaSuccess) {
+    cudaGetLastError();
+    st.assign(n, SNAC_ERR_OOM);
+    snac::set_error("engine: device buffers of a batched group could not be allocated");
+    return;
+  }
+  std::vector<snac_plan*> plans(n);
+  std::vector<const double*> fs(n);
+  std::vector<double*> ps(n);
+  bool ok = true;
+  for (size_t k = 0; k < n && ok; ++k) {
+    const size_t nb = (size_t)g[k]->n3 * sizeof(double);
+    plans[k] = g[k]->slot->plan;
+    double* f = reinterpret_cast<double*>(base + off[k]);
+    ps[k] = reinterpret_cast<double*>(base + off[k] + (off[k + 1] - off[k]) / 2);
+    fs[k] = f;
+    if ((ce = cudaMemcpyAsync(f, g[k]->h_rhs, nb, cudaMemcpyHostToDevice, s)) != cudaSuccess ||
+        (ce = cudaMemsetAsync(ps[k], 0, nb, s)) != cudaSuccess) {
+      ok = false;
+      snac::set_error(std::string("engine: copies into a batched group: ") + cudaGetErrorString(ce));
+    }
+  }
+  if (ok) {
+    std::vector<int32_t> hs(n, INT32_MIN);
+    const int rc = snac_poisson_solve_batch((int32_t)n, plans.data(), fs.data(), ps.data(), g[0]->tol, hs.data(), s);
+    for (size_t k = 0; k < n; ++k) {
+      st[k] = hs[k] == INT32_MIN ? (rc ? rc : SNAC_ERR_CUDA) : hs[k];  // rejected before it ran: its status
+      snac_plan_info(plans[k], &g[k]->info);
+      if ((st[k] == SNAC_OK || st[k] == SNAC_ERR_NOT_CONVERGED) &&
+          (ce = cudaMemcpyAsync(g[k]->h_p, ps[k], (size_t)g[k]->n3 * sizeof(double), cudaMemcpyDeviceToHost, s)) !=
+              cudaSuccess) {
+        st[k] = SNAC_ERR_CUDA;
+        snac::set_error(std::string("engine: copy of a solution: ") + cudaGetErrorString(ce));
+      }
+    }
+  }
+  cudaFreeAsync(base, s);
+  if ((ce = cudaStreamSynchronize(s)) != cudaSuccess) {
+    snac::set_error(std::string("engine: stream synchronisation: ") + cudaGetErrorString(ce));
+    for (int& x : st)
+      if (x == SNAC_OK) x = SNAC_ERR_CUDA;
+  }
+}
+
 void snac_engine::worker(int id) {
   cudaSetDevice(device);
   cudaStream_t s = nullptr;
   cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+  std::vector<Request*> g;
+  std::vector<int> st;
   for (;;) {
-    Request* r = nullptr;
+    g.clear();
     {
       std::unique_lock<std::mutex> lk(mu);
       cv_work.wait(lk, [&] { return stopping || !ready.empty(); });
       if (ready.empty()) break;
-      r = ready.front();
-      ready.pop_front();
-      r->state = State::Running;
-      ++running;
+      take(g);
+      for (Request* r : g) r->state = State::Running;
+      running += (int)g.size();
     }
-    r->times.t_start = now_s();
-    r->times.worker = id;
+    const double t0 = now_s();
+    for (Request* r : g) {
+      r->times.t_start = t0;
+      r->times.worker = id;
+      r->times.group = (int32_t)g.size();
+    }
     snac::set_error("");
-    int st = SNAC_ERR_CUDA;
-    if (s) {
-      st = run(r, s);
-    } else {  // this worker has no stream: release what the admission reserved for a plan build
+    st.assign(g.size(), SNAC_ERR_CUDA);
+    if (!s) {  // this worker has no stream: release what the admission reserved for a plan build
       std::lock_guard<std::mutex> lk(mu);
-      if (r->build_plan) {
-        account(-(int64_t)r->plan_estimate);
-        if (--building[r->key] == 0) building.erase(r->key);
+      for (Request* r : g) {
+        if (r->build_plan) {
+          account(-(int64_t)r->plan_estimate);
+          if (--building[r->key] == 0) building.erase(r->key);
+        }
+        if (r->tune) account(-(int64_t)r->tune_bytes);
       }
-      if (r->tune) account(-(int64_t)r->tune_bytes);
       snac::set_error("engine: the worker's CUDA stream could not be created");
+    } else if (g.size() == 1) {
+      st[0] = run(g[0], s);
+    } else {
+      run_group(g, s, st);
+      for (Request* r : g) r->times.plan_reused = 1;
     }
-    r->times.t_done = now_s();
-    if (st != SNAC_OK) {  // the detail this worker thread recorded (plan creation, solve or copies)
-      std::strncpy(r->times.error, snac_last_error_message(), sizeof(r->times.error) - 1);
-      r->times.error[sizeof(r->times.error) - 1] = '\0';
+    const double t1 = now_s();
+    for (size_t k = 0; k < g.size(); ++k) {
+      g[k]->times.t_done = t1;
+      if (st[k] != SNAC_OK) {  // the detail this worker thread recorded (plan creation, solve or copies)
+        std::strncpy(g[k]->times.error, snac_last_error_message(), sizeof(g[k]->times.error) - 1);
+        g[k]->times.error[sizeof(g[k]->times.error) - 1] = '\0';
+      }
     }
     std::vector<snac_plan*> dead;
     {
       std::lock_guard<std::mutex> lk(mu);
-      account(-(int64_t)r->buf_bytes);
-      if (r->slot) {
-        r->slot->busy = false;
-        r->slot->last_use = ++use_clock;
+      for (size_t k = 0; k < g.size(); ++k) {
+        Request* r = g[k];
+        account(-(int64_t)r->buf_bytes);
+        if (r->slot) {
+          r->slot->busy = false;
+          r->slot->last_use = ++use_clock;
+        }
+        r->status = st[k];
+        r->info.status = st[k];
+        r->state = State::Done;
+        --running;
+        ++completed;
       }
-      r->status = st;
-      r->info.status = st;
-      r->state = State::Done;
-      --running;
-      ++completed;
       trim_cache(dead);
       admit(dead);
     }
@@ -361,10 +459,10 @@ double snac_engine_clock(void) { return now_s(); }
 int snac_engine_create(snac_engine** out, const snac_engine_options* opt) {
   if (!out) return SNAC_ERR_INVALID_ARG;
   *out = nullptr;
-  snac_engine_options o{4, 64, 150000000000ull, 0};
+  snac_engine_options o{4, 64, 150000000000ull, 0, 16};
   if (opt) o = *opt;
   if (o.workers < 1 || o.workers > 64 || o.max_cached_plans < 0 || o.max_cached_plans > 4096 || o.hbm_budget == 0 ||
-      (o.autotune != 0 && o.autotune != 1))
+      (o.autotune != 0 && o.autotune != 1) || o.max_group < 1 || o.max_group > 256)
     return SNAC_ERR_INVALID_ARG;
   snac_engine* e = new (std::nothrow) snac_engine();
   if (!e) return SNAC_ERR_OOM;

@@ -69,13 +69,13 @@ class _Info(ctypes.Structure):
 
 class _EngineOptions(ctypes.Structure):
     _fields_ = [("workers", ctypes.c_int32), ("max_cached_plans", ctypes.c_int32), ("hbm_budget", ctypes.c_uint64),
-                ("autotune", ctypes.c_int32)]
+                ("autotune", ctypes.c_int32), ("max_group", ctypes.c_int32)]
 
 
 class _Times(ctypes.Structure):
     _fields_ = [("t_submit", ctypes.c_double), ("t_admit", ctypes.c_double), ("t_start", ctypes.c_double),
                 ("t_done", ctypes.c_double), ("worker", ctypes.c_int32), ("plan_reused", ctypes.c_int32),
-                ("tuned", ctypes.c_int32), ("error", ctypes.c_char * 160)]
+                ("tuned", ctypes.c_int32), ("group", ctypes.c_int32), ("error", ctypes.c_char * 160)]
 
 
 class _TuneReport(ctypes.Structure):
@@ -413,7 +413,8 @@ def solve_batch(plans, rhs, p, tol: float = 1e-10, raise_on_error: bool = True) 
 class Engine:
     """Serving engine (``include/snac_engine.h``): solves of different problems submitted at any time,
     admitted under a device-memory budget, run concurrently by ``workers`` threads / CUDA streams
-    with resident cached plans. Host arrays in, host arrays out.
+    with resident cached plans; requests of small (on-chip) problems that are ready together are
+    solved in one batched solve of up to ``max_group``. Host arrays in, host arrays out.
 
         eng = snac.Engine(workers=4, hbm_budget=150e9)
         t = eng.submit(blocks, f, tol=1e-10, precision="mixed")
@@ -421,12 +422,13 @@ class Engine:
     """
 
     def __init__(self, workers: int = 4, hbm_budget: float = 150e9, max_cached_plans: int = 64,
-                 autotune: bool = False):
+                 autotune: bool = False, max_group: int = 16):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("snac.Engine needs a CUDA device")
         torch.cuda.init()
-        opt = _EngineOptions(int(workers), int(max_cached_plans), int(hbm_budget), 1 if autotune else 0)
+        opt = _EngineOptions(int(workers), int(max_cached_plans), int(hbm_budget), 1 if autotune else 0,
+                             int(max_group))
         h = ctypes.c_void_p()
         _check(lib().snac_engine_create(ctypes.byref(h), ctypes.byref(opt)))
         self._h = h
@@ -434,7 +436,7 @@ class Engine:
 
     def submit(self, blocks, rhs, tol: float = 1e-10, precision: str = "fp64", homog_axis: int = 2, nu1: int = 2,
                nu2: int = 2, max_outer: int = 20, max_cycles: int = 40, max_coarse: int = 64,
-               inner_reduction: float = 1e-4, fused: int = -1, shift: float = 0.0) -> int:
+               inner_reduction: float = 1e-4, fused: int = -1, shift: float = 0.0, onchip: bool = True) -> int:
         if precision not in _PREC:
             raise ValueError(f"precision must be one of {list(_PREC)}")
         n3 = int(sum(np.prod([b["hi"][a] - b["lo"][a] + 1 for a in range(3)]) for b in blocks))
@@ -443,7 +445,8 @@ class Engine:
             raise ValueError(f"rhs must be a float64 array of {n3} elements")
         p = np.empty(n3, dtype=np.float64)
         arr, keep = _marshal_blocks(blocks)
-        opt = _Options(_PREC[precision], nu1, nu2, max_outer, max_cycles, max_coarse, fused, inner_reduction, shift)
+        opt = _Options(_PREC[precision], nu1, nu2, max_outer, max_cycles, max_coarse, fused, inner_reduction, shift,
+                       onchip=0 if onchip else -1)
         t = ctypes.c_int64()
         _check(lib().snac_engine_submit(self._h, len(blocks), arr, homog_axis, ctypes.byref(opt),
                                         ctypes.c_void_p(rhs.ctypes.data), ctypes.c_void_p(p.ctypes.data),

@@ -87,12 +87,10 @@ def test_null_arguments(lib):
 def test_engine_argument_checks(lib):
     """Engine calls reject bad arguments before touching a device."""
     h = ctypes.c_void_p()
-    bad = snac._EngineOptions(0, 64, 10**9)
-    assert lib.snac_engine_create(ctypes.byref(h), ctypes.byref(bad)) == -1
-    bad = snac._EngineOptions(4, -1, 10**9)
-    assert lib.snac_engine_create(ctypes.byref(h), ctypes.byref(bad)) == -1
-    bad = snac._EngineOptions(4, 8, 0)
-    assert lib.snac_engine_create(ctypes.byref(h), ctypes.byref(bad)) == -1
+    for bad in ((0, 64, 10**9, 0, 16), (4, -1, 10**9, 0, 16), (4, 8, 0, 0, 16), (4, 8, 10**9, 2, 16),
+                (4, 8, 10**9, 0, 0), (4, 8, 10**9, 0, 257)):
+        opt = snac._EngineOptions(*bad)
+        assert lib.snac_engine_create(ctypes.byref(h), ctypes.byref(opt)) == -1, bad
     assert lib.snac_engine_create(None, None) == -1
     t = ctypes.c_int64()
     assert lib.snac_engine_submit(None, 1, None, 2, None, None, None, 1e-10, ctypes.byref(t)) == -1

@@ -156,3 +156,55 @@ def test_concurrent_plans_with_different_transform_lengths():
             if info["status"] != 0:
                 fails.append((k, info["status_name"], times["error"]))
     assert not fails, fails[:5]
+
+
+def test_small_requests_merge_into_batched_solves():
+    """Requests of resident on-chip plans that are ready together are solved as one batched solve
+    (continuous batching). Each result is still the alone result, bitwise; a failing request in a
+    group fails alone; requests whose plans are not on chip never join a group."""
+    import torch
+    ensure_built()
+    specs = [("2x2", 16, 8, "NN", ("N", "N", "N", "N"), "mixed"),
+             ("L", 16, 16, "DD", ("N", "D", "D", "N"), "fp64"),
+             ("1", 32, 8, "PP", ("D", "D", "N", "N"), "mixed"),
+             ("1x2", 16, 12, "ND", ("D", "N", "N", "N"), "fp64"),
+             ("2x1", 12, 10, "DN", ("N", "N", "D", "D"), "mixed"),
+             ("1", 24, 16, "PP", ("N", "N", "N", "N"), "fp64"),
+             ("1", 16, 8, "DD", ("D", "N", "D", "N"), "mixed"),
+             ("2x2", 8, 6, "PP", ("D", "D", "D", "D"), "fp64")]
+    mix = []
+    for k, (layout, n, nz, zp, walls, prec) in enumerate(specs):
+        blocks = make(layout, n=n, nz=nz, zpair=zp, walls=walls, stretched=True)
+        mix.append((blocks, inputs.divergence_rhs(blocks, 40 + k), prec, True))
+    level = make("1", n=16, nz=8, zpair="DD", walls=("D", "D", "N", "N"), stretched=True)
+    mix.append((level, inputs.divergence_rhs(level, 60), "mixed", False))     # level-by-level plan
+    alone = []
+    for blocks, f, prec, oc in mix:
+        pl = snac.Plan(blocks, precision=prec, onchip=oc)
+        p = torch.zeros(len(f), dtype=torch.float64, device="cuda")
+        pl.solve(dev(f), p, tol=TOL)
+        ks = pl.kernel_stats()
+        assert (ks["onchip"]["launches"] + ks["fwd_onchip"]["launches"] > 0) == oc
+        alone.append(host(p))
+        pl.close()
+    # a singular problem of its own (periodic z, Neumann walls): a compatible f caches its plan, an
+    # incompatible one fails inside a group
+    sing = make("1", n=20, nz=8, zpair="PP", walls=("N", "N", "N", "N"), stretched=True)
+    f_sing = inputs.divergence_rhs(sing, 61)
+    with snac.Engine(workers=1, hbm_budget=8e9, max_group=16) as eng:
+        for blocks, f, prec, oc in mix + [(sing, f_sing, "mixed", True)]:   # build and cache every plan
+            eng.wait(eng.submit(blocks, f, tol=TOL, precision=prec, onchip=oc))
+        for _ in range(3):
+            tickets = [eng.submit(b, f, tol=TOL, precision=prec, onchip=oc) for b, f, prec, oc in mix]
+            tickets.append(eng.submit(sing, f_sing + 1.0, tol=TOL, precision="mixed"))
+            res = [eng.wait(t, raise_on_error=False) for t in tickets]
+            if res[-1][2]["group"] > 1:
+                break
+    groups = [t["group"] for _, _, t in res]
+    assert res[-1][2]["group"] > 1, groups                   # the failing request ran in a group
+    assert res[-1][1]["status_name"] == "INCOMPATIBLE_RHS"
+    assert res[len(mix) - 1][2]["group"] == 1                 # the level-by-level plan ran alone
+    for p_alone, (p, info, times) in zip(alone, res):
+        assert info["status"] == 0 and info["rel_res"] <= TOL, (info, times)
+        assert np.array_equal(p, p_alone)
+        assert times["plan_reused"] == 1
