@@ -16,16 +16,21 @@
 // correction window) stream into shared memory with per-thread asynchronous copies (cp.async), so
 // the global-load latency of a mode is hidden behind the previous mode's sweeps.
 //
-// Registers. Warp w holds window rows 4w..4w+3, lane k holds columns 2k (parity 0) and 2k+1
-// (parity 1) of those rows: u, f and 1/diag of 8 cells per thread. In a row the cells of one colour
+// Registers. Warp w (of 8, 256 threads per CTA) holds window rows 8w..8w+7, lane k holds columns
+// 2k (parity 0) and 2k+1 (parity 1) of those rows: u, f and 1/diag of 16 cells per thread, and the
+// y couplings of its rows. The rows of one colour in a half-sweep are independent, so each warp has
+// eight updates in flight (two CTAs of 8 warps per multiprocessor at up to 128 registers measured
+// faster than 16 warps of four rows at 64 registers). In a row the cells of one colour
 // all have the same column parity, so a colour update of a row is one cell per lane: the west/east
 // neighbours come from the thread itself or from one warp shuffle, the south/north neighbours from
 // the thread's own registers; only the first and last row of each strip pass through shared memory
 // (once per half-sweep, only the colour that changed). Coarse cells are exactly (row pair) x
 // (column pair): restriction and prolongation stay in registers too.
 //
-// Exactness. Every interior window cell is updated in every half-sweep; the window's edge is never
-// updated, so stale values enter from the edge one cell per half-sweep. After 2 nu <= FUSED_HALO - 2
+// Exactness. Every window cell is updated in every half-sweep of its colour. The neighbours of an
+// edge cell beyond the window are unknown (the update reads zero or the cell's own pair instead), so
+// wrong values enter from the edge one cell per half-sweep -- as stale ones would if the edge were
+// left alone, and without a per-cell test in the update. After 2 nu <= FUSED_HALO - 2
 // half-sweeps the tile and the ring around it (used by the residual) equal the global Gauss-Seidel
 // sweep. Window cells outside the tile's block belong to the connected blocks and use that block's
 // coefficients, so sweeps across block interfaces are exact too. Cells with no owner (beyond a
@@ -48,9 +53,10 @@ constexpr int FH = FUSED_HALO;
 constexpr int WN = FWN;
 constexpr int HW = FHW;
 constexpr int CW = FCW;
-constexpr int RPW = 4;  // rows per warp
-constexpr int FTHREADS = 512;
-constexpr int FWARPS = FTHREADS / 32;
+constexpr int RPW = 8;  // rows per warp
+constexpr int FWARPS = WN / RPW;
+constexpr int FTHREADS = 32 * FWARPS;
+constexpr int FMINB = 2;  // CTAs per multiprocessor
 static_assert(FTILE_X == FTILE_Y && HW == 32 && FWARPS * RPW == WN, "the fused kernels assume a 64x64 window");
 static_assert(FH % 2 == 0 && 2 * 2 <= FH - 2, "nu <= 2 sweeps must stay exact inside the halo");
 
@@ -64,7 +70,7 @@ struct Shared {
   FusedTab<T> tab;
   Pair<T> stage[RPW][2][FTHREADS];  // next mode's u, f column pairs, each thread's own slots (0: no owner)
   Pair<T> diag[RPW][FTHREADS];      // diagonal of the thread's cells without the shift (+inf: no owner)
-  int4 goff[FTHREADS];              // plane offset of the thread's column pair in each of its rows (-1: none)
+  int goff[RPW][FTHREADS];          // plane offset of the thread's column pair in each of its rows (-1: none)
   int coff[CW * CW];                // plane offset of each coarse window cell (-1: no owner; k_fup)
   T halo[FWARPS][2][2][HW];         // [warp][first/last row][parity][lane]
   T e[2][CW][CW];                   // coarse correction around the tile, this mode and the next (k_fup)
@@ -135,8 +141,8 @@ __device__ __forceinline__ void thread_tables(Shared<T>& S, bool coarse) {
       S.stage[r][1][threadIdx.x] = Pair<T>{0, 0};
     }
   }
-  S.goff[threadIdx.x] = make_int4(off[0], off[1], off[2], off[3]);
-  static_assert(RPW == 4, "goff holds four rows");
+#pragma unroll
+  for (int r = 0; r < RPW; ++r) S.goff[r][threadIdx.x] = off[r];
   if (coarse) {
     for (int idx = threadIdx.x; idx < CW * CW; idx += FTHREADS) {
       const int cj = idx / CW, ci = idx % CW;
@@ -154,8 +160,9 @@ __device__ __forceinline__ void thread_tables(Shared<T>& S, bool coarse) {
 template <typename T>
 __device__ __forceinline__ void prefetch_cells(Shared<T>& S, long long base, const T* __restrict__ u,
                                                const T* __restrict__ f, bool load_u) {
-  const int4 o = S.goff[threadIdx.x];
-  const int off[RPW] = {o.x, o.y, o.z, o.w};
+  int off[RPW];
+#pragma unroll
+  for (int r = 0; r < RPW; ++r) off[r] = S.goff[r][threadIdx.x];
 #pragma unroll
   for (int r = 0; r < RPW; ++r) {
     if (off[r] < 0) continue;
@@ -225,10 +232,10 @@ __device__ __forceinline__ void edge_values(const Shared<T>& S, T& south, T& nor
   north = warp < FWARPS - 1 ? S.halo[warp + 1][0][PA ^ 1][lane] : (T)0;
 }
 
-// Gauss-Seidel update of row r of the strip, the colour's cells having column parity P.
+// Gauss-Seidel update of row r of the strip, the colour's cells having column parity P. At the
+// window's west and east edges the shuffles return the lane's own pair (see Exactness).
 template <typename T, int P>
-__device__ __forceinline__ void update_row(Cells<T>& C, FP2<T> cx, FP2<T> cy, int r, int wj, T sn, T nn) {
-  const int lane = threadIdx.x & 31;
+__device__ __forceinline__ void update_row(Cells<T>& C, FP2<T> cx, FP2<T> cy, int r, T sn, T nn) {
   T w, e;
   if (P == 0) {
     w = __shfl_up_sync(0xffffffffu, C.u[r][1], 1);
@@ -241,16 +248,14 @@ __device__ __forceinline__ void update_row(Cells<T>& C, FP2<T> cx, FP2<T> cy, in
   a = fma(cx.b, e, a);
   a = fma(cy.a, sn, a);
   a = fma(cy.b, nn, a);
-  const T v = (C.f[r][P] - a) * C.inv[r][P];
-  const bool edge = (P == 0 && lane == 0) || (P == 1 && lane == HW - 1) || wj == 0 || wj == WN - 1;
-  if (!edge) C.u[r][P] = v;
+  C.u[r][P] = (C.f[r][P] - a) * C.inv[r][P];
 }
 
 // One half-sweep of the strip; P0 = column parity of the colour in the strip's first row. UNI: all
 // rows of the strip lie in one region row, so the x coefficients are one pair per parity.
 template <typename T, int P0, bool UNI>
-__device__ __forceinline__ void half_sweep(Cells<T>& C, Shared<T>& S, const int (&ry)[RPW], int rx) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+__device__ __forceinline__ void half_sweep(Cells<T>& C, Shared<T>& S, const int (&ry)[RPW], const FP2<T> (&cy)[RPW]) {
+  const int lane = threadIdx.x & 31;
   constexpr int PA = P0, PB = P0 ^ 1;
   const FusedTab<T>& tb = S.tab;
   T south, north;
@@ -262,16 +267,14 @@ __device__ __forceinline__ void half_sweep(Cells<T>& C, Shared<T>& S, const int 
   }
 #pragma unroll
   for (int r = 0; r < RPW; ++r) {
-    const int wj = RPW * warp + r;
-    const FP2<T> cy = tb.yc[rx][wj];
     if ((r & 1) == 0) {  // parity PA; never the last row
       const T sn = r > 0 ? C.u[r > 0 ? r - 1 : 0][PA] : south;
       const T nn = C.u[r < RPW - 1 ? r + 1 : 0][PA];
-      update_row<T, PA>(C, UNI ? cxa : tb.xc[ry[r]][PA][lane], cy, r, wj, sn, nn);
+      update_row<T, PA>(C, UNI ? cxa : tb.xc[ry[r]][PA][lane], cy[r], r, sn, nn);
     } else {             // parity PB; never the first row
       const T sn = C.u[r > 0 ? r - 1 : 0][PB];
       const T nn = r < RPW - 1 ? C.u[r < RPW - 1 ? r + 1 : 0][PB] : north;
-      update_row<T, PB>(C, UNI ? cxb : tb.xc[ry[r]][PB][lane], cy, r, wj, sn, nn);
+      update_row<T, PB>(C, UNI ? cxb : tb.xc[ry[r]][PB][lane], cy[r], r, sn, nn);
     }
   }
   write_halo_colour<T, PA>(S, C);
@@ -285,10 +288,14 @@ template <typename T, typename Hook>
 __device__ void sweeps(Cells<T>& C, Shared<T>& S, int nu, Hook&& after_first_barrier) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   int ry[RPW];
-#pragma unroll
-  for (int r = 0; r < RPW; ++r) ry[r] = S.tab.rowry[RPW * warp + r];
-  const bool uni = ry[0] == ry[RPW - 1];  // region rows are monotonic in the row
+  FP2<T> cy[RPW];  // y couplings of the thread's rows, in registers for all half-sweeps
   const int rx = S.tab.colrx[lane];
+#pragma unroll
+  for (int r = 0; r < RPW; ++r) {
+    ry[r] = S.tab.rowry[RPW * warp + r];
+    cy[r] = S.tab.yc[rx][RPW * warp + r];
+  }
+  const bool uni = ry[0] == ry[RPW - 1];  // region rows are monotonic in the row
   const int pbase = S.tab.pbase;
   write_halo(S, C);
   __syncthreads();
@@ -297,11 +304,11 @@ __device__ void sweeps(Cells<T>& C, Shared<T>& S, int nu, Hook&& after_first_bar
     const int colour = s & 1;
     const int p0 = (colour - pbase - RPW * warp) & 1;
     if (uni) {
-      if (p0 == 0) half_sweep<T, 0, true>(C, S, ry, rx);
-      else half_sweep<T, 1, true>(C, S, ry, rx);
+      if (p0 == 0) half_sweep<T, 0, true>(C, S, ry, cy);
+      else half_sweep<T, 1, true>(C, S, ry, cy);
     } else {
-      if (p0 == 0) half_sweep<T, 0, false>(C, S, ry, rx);
-      else half_sweep<T, 1, false>(C, S, ry, rx);
+      if (p0 == 0) half_sweep<T, 0, false>(C, S, ry, cy);
+      else half_sweep<T, 1, false>(C, S, ry, cy);
     }
     __syncthreads();
   }
@@ -372,8 +379,9 @@ template <typename T>
 __device__ __forceinline__ void store_tile(const Cells<T>& C, const Shared<T>& S, long long base, T* __restrict__ u) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   if (!in_tile(2 * lane, S.tab.tw)) return;
-  const int4 o = S.goff[threadIdx.x];
-  const int off[RPW] = {o.x, o.y, o.z, o.w};
+  int off[RPW];
+#pragma unroll
+  for (int r = 0; r < RPW; ++r) off[r] = S.goff[r][threadIdx.x];
 #pragma unroll
   for (int r = 0; r < RPW; ++r) {
     if (!in_tile(RPW * warp + r, S.tab.th)) continue;
@@ -389,7 +397,7 @@ inline int modes_per_cta(int sms, int ntiles, int nact) {
 
 // CTA (tile blockIdx.x, modes active[m0 .. m1)), m0 = blockIdx.y * mpc.
 template <typename T>
-__global__ void __launch_bounds__(FTHREADS, 2)
+__global__ void __launch_bounds__(FTHREADS, FMINB)
     k_fdown(const FusedTab<T>* __restrict__ tabs, long long fncell, long long cncell, const int* __restrict__ active,
             int nact, int mpc, const T* __restrict__ sigma, const T* __restrict__ u, T* __restrict__ u_out,
             const T* __restrict__ f, T* __restrict__ fc, T* __restrict__ uc, int nu, int zero_u, int zero_coarse) {
@@ -444,7 +452,7 @@ __global__ void __launch_bounds__(FTHREADS, 2)
 }
 
 template <typename T>
-__global__ void __launch_bounds__(FTHREADS, 2)
+__global__ void __launch_bounds__(FTHREADS, FMINB)
     k_fup(const FusedTab<T>* __restrict__ tabs, int nftiles, long long fncell, long long cncell,
           const int* __restrict__ active, int nact, int mpc, const T* __restrict__ sigma, const T* __restrict__ u,
           T* __restrict__ u_out, const T* __restrict__ f, const T* __restrict__ uc, int nu, double* __restrict__ part) {
@@ -472,7 +480,7 @@ __global__ void __launch_bounds__(FTHREADS, 2)
     // three-point prolongation onto the thread's owned cells: parent column lane + 1 of the coarse
     // window (both columns of the pair), parent row (RPW / 2) warp + r / 2 + 1. Only the colour-1
     // cells: the first post-smoothing half-sweep rewrites every updated colour-0 cell from its
-    // neighbours and f alone, and the window edge, never updated, is stale either way.
+    // neighbours and f alone, and the window edge is wrong either way (Exactness).
     const int rxc = tb.colrx[lane];
 #pragma unroll
     for (int r = 0; r < RPW; ++r) {
