@@ -517,7 +517,7 @@ __device__ void fused_chunk(const FwdArgs<T>& F, int c, unsigned char* smem) {
   const ChunkDev ch = F.chunks[c];
   const int sel = F.kind * 2 + F.in_f32;
 #define SNAC_FWD(KD, TI)                                                                                   \
-  forward_chunk<T, TC, KD, TI>(ch, F.blk, F.cb, F.n, F.tw, static_cast<const TI*>(F.in3), F.out, F.ncell, F.sub0, 0, smem)
+  forward_chunk<T, TC, KD, TI, BT>(ch, F.blk, F.cb, F.n, F.tw, static_cast<const TI*>(F.in3), F.out, F.ncell, F.sub0, 0, smem)
   switch (sel) {
     case 2 * KIND_PP: SNAC_FWD(KIND_PP, double); break;
     case 2 * KIND_PP + 1: SNAC_FWD(KIND_PP, float); break;
@@ -562,7 +562,7 @@ __device__ void fused_solve(const FwdArgs<T>& F, const OnchipArgs<T>& O, int q, 
 
 // One plan: items 0 .. nchunks - 1 are its chunks, then its wavenumbers 0 .. nmodes - 1.
 template <typename T, int TC>
-__global__ void __launch_bounds__(BT) k_fwd_onchip(const FwdArgs<T> F, const OnchipArgs<T> O, int nmodes,
+__global__ void __launch_bounds__(BT, 1) k_fwd_onchip(const FwdArgs<T> F, const OnchipArgs<T> O, int nmodes,
                                                    int* __restrict__ next, long long wait_ns) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int item, skip;

@@ -22,22 +22,25 @@
 namespace snac {
 namespace {
 
-// One CTA per chunk of TC columns.
+// One CTA of TNT threads per chunk of TC columns.
+constexpr int TNT = 256;
+
 template <typename T, int TC, int KIND, typename TI>
-__global__ void __launch_bounds__(256) k_forward(const ChunkDev* __restrict__ chunks, const BlockDev* __restrict__ blk,
+__global__ void __launch_bounds__(TNT, 3) k_forward(const ChunkDev* __restrict__ chunks, const BlockDev* __restrict__ blk,
                                                  const CallerBlk* __restrict__ cb, int n, Tw<T> tw,
                                                  const TI* __restrict__ in3, T* __restrict__ out, long long ncell,
                                                  T sub0, int split) {
   extern __shared__ __align__(16) unsigned char smem[];
-  forward_chunk<T, TC, KIND, TI>(chunks[blockIdx.x], blk, cb, n, tw, in3, out, ncell, sub0, split, smem);
+  forward_chunk<T, TC, KIND, TI, TNT>(chunks[blockIdx.x], blk, cb, n, tw, in3, out, ncell, sub0, split, smem);
 }
 
 template <typename T, int TC, int KIND>
-__global__ void __launch_bounds__(256) k_backward(const ChunkDev* __restrict__ chunks, const BlockDev* __restrict__ blk,
+__global__ void __launch_bounds__(TNT, 3) k_backward(const ChunkDev* __restrict__ chunks, const BlockDev* __restrict__ blk,
                                                   const CallerBlk* __restrict__ cb, int n, Tw<T> tw,
                                                   const T* __restrict__ modes, double* __restrict__ p3, long long ncell,
                                                   double inv_theta) {
   constexpr int kind = KIND;
+  constexpr int RS = TNT / TC;  // rows per pass
   extern __shared__ __align__(16) unsigned char smem[];
   const int m = n / 2;
   Cx<T>* A = reinterpret_cast<Cx<T>*>(smem);
@@ -45,24 +48,28 @@ __global__ void __launch_bounds__(256) k_backward(const ChunkDev* __restrict__ c
   T* xs = reinterpret_cast<T*>(Bf);
   const ChunkDev ch = chunks[blockIdx.x];
   const BlockDev B = blk[ch.b];
-  for (int i0 = threadIdx.x; i0 < n * TC; i0 += LBATCH * blockDim.x) {
-    T v[LBATCH];
+  const int c = my_col<TC, TNT>(), r0 = my_row<TC, TNT>();
+  const bool live = c < ch.ncol;
+  {
+    const T* src = modes + B.off + ch.c0 + (live ? c : 0);
+    for (int q0 = r0; q0 < n; q0 += LBATCH * RS) {
+      T v[LBATCH];
 #pragma unroll
-    for (int u = 0; u < LBATCH; ++u) {
-      const int idx = i0 + u * blockDim.x;
-      const int q = idx / TC, c = idx % TC;
-      v[u] = idx < n * TC && c < ch.ncol ? modes[(long long)q * ncell + B.off + ch.c0 + c] : (T)0;
-    }
+      for (int u = 0; u < LBATCH; ++u) {
+        const int q = q0 + u * RS;
+        v[u] = live && q < n ? src[(long long)q * ncell] : (T)0;
+      }
 #pragma unroll
-    for (int u = 0; u < LBATCH; ++u) {
-      const int idx = i0 + u * blockDim.x;
-      if (idx < n * TC) xs[idx] = v[u];
+      for (int u = 0; u < LBATCH; ++u) {
+        const int q = q0 + u * RS;
+        if (q < n) xs[q * TC + c] = v[u];
+      }
     }
   }
   __syncthreads();
   const bool rev = kind == KIND_DD;                 // DST-III reads X reversed
   const bool flip = kind == KIND_DN;                // DST-IV = DCT-IV of the sign-flipped input, reversed
-  auto X = [&](int k, int c) -> T {
+  auto X = [&](int k) -> T {
     if (k >= n) return (T)0;
     const int kk = rev ? n - 1 - k : k;
     const T v = xs[kk * TC + c];
@@ -71,65 +78,84 @@ __global__ void __launch_bounds__(256) k_backward(const ChunkDev* __restrict__ c
   if (kind == KIND_PP || kind == KIND_NN || kind == KIND_DD) {
     // half-spectrum bin j of the real DFT being inverted: PP the stored bins (X_j, X_{n-j}),
     // NN/DD V_j = e^{+i pi j/2n} (X_j - i X_{n-j}) (the real DFT of the reordered sequence)
-    auto bin = [&](int j, int c) -> Cx<T> {
-      if (kind == KIND_PP) return (j == 0 || j == m) ? Cx<T>{X(j, c), 0} : Cx<T>{X(j, c), X(n - j, c)};
-      Cx<T> v = cmul(conj(tw.tw2n[j]), Cx<T>{X(j, c), -X(n - j, c)});
+    auto bin = [&](int j) -> Cx<T> {
+      if (kind == KIND_PP) return (j == 0 || j == m) ? Cx<T>{X(j), 0} : Cx<T>{X(j), X(n - j)};
+      Cx<T> v = cmul(conj(tw.tw2n[j]), Cx<T>{X(j), -X(n - j)});
       if (j == 0 || j == m) v.im = 0;
       return v;
     };
     // z_k needs bins k and m - k: each pair once, giving z_k and z_{m-k}
-    for (int idx = threadIdx.x; idx < (m / 2 + 1) * TC; idx += blockDim.x) {
-      const int k = idx / TC, c = idx % TC;
-      const Cx<T> b1 = bin(k, c), b2 = bin(m - k, c);
+    for (int k = r0; k < m / 2 + 1; k += RS) {
+      const Cx<T> b1 = bin(k), b2 = bin(m - k);
       A[k * TC + c] = irdft_pre(b1, b2, tw.twn[k]);
       if (k > 0 && m - k != k) A[(m - k) * TC + c] = irdft_pre(b2, b1, tw.twn[m - k]);
     }
   } else {
-    for (int idx = threadIdx.x; idx < m * TC; idx += blockDim.x) {
-      const int k = idx / TC, c = idx % TC;
-      A[idx] = cmul(Cx<T>{X(2 * k, c), X(n - 1 - 2 * k, c)}, tw.tw4a[k]);
-    }
+    for (int k = r0; k < m; k += RS) A[k * TC + c] = cmul(Cx<T>{X(2 * k), X(n - 1 - 2 * k)}, tw.tw4a[k]);
   }
   __syncthreads();
   const bool inv = kind == KIND_PP || kind == KIND_NN || kind == KIND_DD;
-  const Cx<T>* R = cfft<T, TC>(A, Bf, m, tw.fft, inv);
+  const Cx<T>* R = cfft<T, TC, TNT>(A, Bf, m, tw.fft, inv);
   __shared__ long long coff[TC];
   const long long sk = chunk_columns<TC>(ch, B, cb, coff);
-  const bool along = sk == 1;  // consecutive threads along the homogeneous axis when it is contiguous
-  // p += y / theta: the old values of a batch are loaded before any of them is written back
-  for (int i0 = threadIdx.x; i0 < n * TC; i0 += LBATCH * blockDim.x) {
-    double old[LBATCH];
-#pragma unroll
-    for (int u = 0; u < LBATCH; ++u) {
-      const int idx = i0 + u * blockDim.x;
-      const int j = along ? idx % n : idx / TC, c = along ? idx / n : idx % TC;
-      old[u] = idx < n * TC && c < ch.ncol ? p3[coff[c] + j * sk] : 0.0;
-    }
-#pragma unroll
-    for (int u = 0; u < LBATCH; ++u) {
-      const int idx = i0 + u * blockDim.x;
-      if (idx >= n * TC) break;
-      const int j = along ? idx % n : idx / TC, c = along ? idx / n : idx % TC;
-      T y;
-      if (kind == KIND_PP) {
-        const Cx<T> z = R[(j >> 1) * TC + c];
-        y = (j & 1) ? z.im : z.re;
-      } else if (kind == KIND_NN || kind == KIND_DD) {
-        const int t = (j & 1) ? n - 1 - (j >> 1) : (j >> 1);  // x_2t = v_t, x_2t+1 = v_{n-1-t}
-        const Cx<T> z = R[(t >> 1) * TC + c];
-        y = (t & 1) ? z.im : z.re;
-        if (kind == KIND_DD && (j & 1)) y = -y;
+  // output j of column cc
+  auto y_of = [&](int j, int cc) -> T {
+    T y;
+    if (kind == KIND_PP) {
+      const Cx<T> z = R[(j >> 1) * TC + cc];
+      y = (j & 1) ? z.im : z.re;
+    } else if (kind == KIND_NN || kind == KIND_DD) {
+      const int t = (j & 1) ? n - 1 - (j >> 1) : (j >> 1);  // x_2t = v_t, x_2t+1 = v_{n-1-t}
+      const Cx<T> z = R[(t >> 1) * TC + cc];
+      y = (t & 1) ? z.im : z.re;
+      if (kind == KIND_DD && (j & 1)) y = -y;
+    } else {
+      const int qq = kind == KIND_DN ? n - 1 - j : j;
+      if ((qq & 1) == 0) {
+        const int k = qq / 2;
+        y = (T)2 * cmul(R[k * TC + cc], tw.tw4b[k]).re;
       } else {
-        const int qq = kind == KIND_DN ? n - 1 - j : j;
-        if ((qq & 1) == 0) {
-          const int k = qq / 2;
-          y = (T)2 * cmul(R[k * TC + c], tw.tw4b[k]).re;
-        } else {
-          const int k = (n - 1 - qq) / 2;
-          y = (T)-2 * cmul(R[k * TC + c], tw.tw4b[k]).im;
-        }
+        const int k = (n - 1 - qq) / 2;
+        y = (T)-2 * cmul(R[k * TC + cc], tw.tw4b[k]).im;
       }
-      if (c < ch.ncol) p3[coff[c] + j * sk] = fma(to_double(y), inv_theta, old[u]);
+    }
+    return y;
+  };
+  // p += y / theta: the old values of a batch are loaded before any of them is written back
+  if (sk != 1) {  // column c is this thread's
+    double* dst = p3 + (live ? coff[c] : 0);
+    for (int j0 = r0; j0 < n; j0 += LBATCH * RS) {
+      double old[LBATCH];
+#pragma unroll
+      for (int u = 0; u < LBATCH; ++u) {
+        const int j = j0 + u * RS;
+        old[u] = live && j < n ? dst[(long long)j * sk] : 0.0;
+      }
+#pragma unroll
+      for (int u = 0; u < LBATCH; ++u) {
+        const int j = j0 + u * RS;
+        if (j >= n) break;
+        const T y = y_of(j, c);
+        if (live) dst[(long long)j * sk] = fma(to_double(y), inv_theta, old[u]);
+      }
+    }
+  } else {  // the homogeneous axis is the caller's contiguous one: consecutive threads run along it
+    for (int i0 = threadIdx.x; i0 < n * TC; i0 += LBATCH * TNT) {
+      double old[LBATCH];
+#pragma unroll
+      for (int u = 0; u < LBATCH; ++u) {
+        const int idx = i0 + u * TNT;
+        const int j = idx % n, cc = idx / n;
+        old[u] = idx < n * TC && cc < ch.ncol ? p3[coff[cc] + j] : 0.0;
+      }
+#pragma unroll
+      for (int u = 0; u < LBATCH; ++u) {
+        const int idx = i0 + u * TNT;
+        if (idx >= n * TC) break;
+        const int j = idx % n, cc = idx / n;
+        const T y = y_of(j, cc);
+        if (cc < ch.ncol) p3[coff[cc] + j] = fma(to_double(y), inv_theta, old[u]);
+      }
     }
   }
 }
@@ -173,7 +199,7 @@ cudaError_t fwd_t(snac_plan* P, const Geom& G, const std::vector<ChunkDev>& ch, 
   LaunchScope ls(P, K_FORWARD, (double)(sizeof(TI) + sizeof(T)) * n3, (2.5 * std::log2((double)P->nzt) + 8.0) * n3, s);
   auto go = [&](auto kern) {
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem<T, TC>);
-    kern<<<(unsigned)ch.size(), 256, smem, s>>>(dch, G.blk, G.cb, P->nzt, make_tw<T>(P, twb), in3, (T*)modes, G.ncell,
+    kern<<<(unsigned)ch.size(), TNT, smem, s>>>(dch, G.blk, G.cb, P->nzt, make_tw<T>(P, twb), in3, (T*)modes, G.ncell,
                                                 sub0, split ? 1 : 0);
   };
   switch (P->kind) {
@@ -195,7 +221,7 @@ cudaError_t bwd_t(snac_plan* P, const Geom& G, const std::vector<ChunkDev>& ch, 
   LaunchScope ls(P, K_BACKWARD, (16.0 + sizeof(T)) * n3, (2.5 * std::log2((double)P->nzt) + 10.0) * n3, s);
   auto go = [&](auto kern) {
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem<T, TC>);
-    kern<<<(unsigned)ch.size(), 256, smem, s>>>(dch, G.blk, G.cb, P->nzt, make_tw<T>(P, twb), (const T*)modes, p3,
+    kern<<<(unsigned)ch.size(), TNT, smem, s>>>(dch, G.blk, G.cb, P->nzt, make_tw<T>(P, twb), (const T*)modes, p3,
                                                 G.ncell, sign / P->theta);
   };
   switch (P->kind) {

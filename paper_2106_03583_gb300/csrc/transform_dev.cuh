@@ -76,17 +76,30 @@ __device__ __forceinline__ Cx<T> cadd(Cx<T> a, Cx<T> b) {
   return {a.re + b.re, a.im + b.im};
 }
 
+// Work split of a transform CTA of NT threads over a chunk of TC columns (NT a multiple of TC):
+// thread t keeps column t % TC in every pass and takes rows t / TC, t / TC + NT / TC, ... of it,
+// so column offsets and pointers are set up once per thread, not per element.
+template <int TC, int NT>
+__device__ __forceinline__ int my_col() {
+  static_assert(NT % TC == 0, "a transform CTA covers whole rows of its chunk");
+  return threadIdx.x % TC;
+}
+template <int TC, int NT>
+__device__ __forceinline__ int my_row() {
+  return threadIdx.x / TC;
+}
+
 // One Stockham stage of radix R on TC columns: groups of R consecutive length-Ls transforms are
 // merged into transforms of length R Ls. Input of group j, point k: a_p = x[(j + p r) Ls + k] times
 // the twiddle w^(p k r) (w = exp(-2 pi i / m), r = m / (R Ls)); outputs y_q = sum_p a_p omega_R^(p q)
 // at (R j + q) Ls + k, with omega_R^s = w^(s m / R) taken from the same table. Radices 3 and 5 are
 // unrolled; any other prime goes through the runtime-radix stage below (O(R) work per point).
-template <typename T, int TC, int R>
+template <typename T, int TC, int NT, int R>
 __device__ void stage_r(const Cx<T>* __restrict__ X, Cx<T>* __restrict__ Y, int m, int Ls,
                         const Cx<T>* __restrict__ tw, bool inverse) {
   const int r = m / (R * Ls), mr = m / R;
-  for (int idx = threadIdx.x; idx < (m / R) * TC; idx += blockDim.x) {
-    const int c = idx % TC, t = idx / TC;
+  const int c = my_col<TC, NT>();
+  for (int t = my_row<TC, NT>(); t < m / R; t += NT / TC) {
     const int j = t / Ls, k = t - j * Ls;
     Cx<T> a[R];
 #pragma unroll
@@ -115,12 +128,12 @@ __device__ void stage_r(const Cx<T>* __restrict__ X, Cx<T>* __restrict__ Y, int 
 
 // The same stage for a radix known only at run time (a prime factor above 5): one output per
 // thread and iteration, y = sum_p w^(p k r + (p q mod R) m / R) x_p.
-template <typename T, int TC>
+template <typename T, int TC, int NT>
 __device__ void stage_any(const Cx<T>* __restrict__ X, Cx<T>* __restrict__ Y, int m, int Ls, int R,
                           const Cx<T>* __restrict__ tw, bool inverse) {
   const int r = m / (R * Ls), mr = m / R;
-  for (int idx = threadIdx.x; idx < m * TC; idx += blockDim.x) {
-    const int c = idx % TC, o = idx / TC;
+  const int c = my_col<TC, NT>();
+  for (int o = my_row<TC, NT>(); o < m; o += NT / TC) {
     const int k = o % Ls, q = (o / Ls) % R, j = o / (Ls * R);
     Cx<T> acc = {0, 0};
     for (int p = 0; p < R; ++p) {
@@ -138,9 +151,10 @@ __device__ void stage_any(const Cx<T>* __restrict__ X, Cx<T>* __restrict__ Y, in
 // inverse (unnormalised): exp(+2 pi i jk/m). Returns the buffer holding the result.
 // Stockham autosort, mixed radix: the factors 4 (with the exact rotations by +-i) and 2 first, while
 // the merged length Ls is a power of two; then 3, 5 and any remaining prime.
-template <typename T, int TC>
+template <typename T, int TC, int NT>
 __device__ Cx<T>* cfft(Cx<T>* X, Cx<T>* Y, int m, const Cx<T>* __restrict__ tw, bool inverse) {
   if (m == 1) return X;
+  const int c = my_col<TC, NT>();
   int Ls = 1;
   {
     // Merge groups of four length-Ls transforms into length-4Ls transforms while four remain
@@ -149,13 +163,14 @@ __device__ Cx<T>* cfft(Cx<T>* X, Cx<T>* Y, int m, const Cx<T>* __restrict__ tw, 
     int lg = 0;
     for (; (m / Ls) % 4 == 0; Ls <<= 2, lg += 2) {
       const int r = m / (4 * Ls);
-      for (int idx = threadIdx.x; idx < (m / 4) * TC; idx += blockDim.x) {
-        const int c = idx % TC, t = idx / TC;
+      for (int t = my_row<TC, NT>(); t < m / 4; t += NT / TC) {
         const int j = t >> lg, k = t & (Ls - 1);
-        Cx<T> a0 = X[(j * Ls + k) * TC + c];
-        Cx<T> a1 = X[((j + r) * Ls + k) * TC + c];
-        Cx<T> a2 = X[((j + 2 * r) * Ls + k) * TC + c];
-        Cx<T> a3 = X[((j + 3 * r) * Ls + k) * TC + c];
+        const Cx<T>* x = X + (j * Ls + k) * TC + c;
+        const int sx = r * Ls * TC;
+        Cx<T> a0 = x[0];
+        Cx<T> a1 = x[sx];
+        Cx<T> a2 = x[2 * sx];
+        Cx<T> a3 = x[3 * sx];
         if (Ls > 1) {  // the first stage has k = 0 only: unit twiddles
           Cx<T> w1 = tw[k * r], w2 = tw[2 * k * r], w3 = tw[3 * k * r];
           if (inverse) {
@@ -171,11 +186,12 @@ __device__ Cx<T>* cfft(Cx<T>* X, Cx<T>* Y, int m, const Cx<T>* __restrict__ tw, 
         const Cx<T> s13 = {a1.re + a3.re, a1.im + a3.im}, d13 = {a1.re - a3.re, a1.im - a3.im};
         // omega_4 d13: -i d13 forward, +i d13 inverse
         const Cx<T> od = inverse ? Cx<T>{-d13.im, d13.re} : Cx<T>{d13.im, -d13.re};
-        const int o = (4 * j * Ls + k) * TC + c;
-        Y[o] = {s02.re + s13.re, s02.im + s13.im};
-        Y[o + Ls * TC] = {d02.re + od.re, d02.im + od.im};
-        Y[o + 2 * Ls * TC] = {s02.re - s13.re, s02.im - s13.im};
-        Y[o + 3 * Ls * TC] = {d02.re - od.re, d02.im - od.im};
+        Cx<T>* y = Y + (4 * j * Ls + k) * TC + c;
+        const int sy = Ls * TC;
+        y[0] = {s02.re + s13.re, s02.im + s13.im};
+        y[sy] = {d02.re + od.re, d02.im + od.im};
+        y[2 * sy] = {s02.re - s13.re, s02.im - s13.im};
+        y[3 * sy] = {d02.re - od.re, d02.im - od.im};
       }
       __syncthreads();
       Cx<T>* s = X;
@@ -184,8 +200,7 @@ __device__ Cx<T>* cfft(Cx<T>* X, Cx<T>* Y, int m, const Cx<T>* __restrict__ tw, 
     }
     for (; (m / Ls) % 2 == 0; Ls <<= 1, ++lg) {
       const int r = m / (2 * Ls);
-      for (int idx = threadIdx.x; idx < (m / 2) * TC; idx += blockDim.x) {
-        const int c = idx % TC, t = idx / TC;
+      for (int t = my_row<TC, NT>(); t < m / 2; t += NT / TC) {
         const int j = t >> lg, k = t & (Ls - 1);
         Cx<T> w = tw[k * r];
         if (inverse) w.im = -w.im;
@@ -206,16 +221,16 @@ __device__ Cx<T>* cfft(Cx<T>* X, Cx<T>* Y, int m, const Cx<T>* __restrict__ tw, 
     Y = s;
   };
   for (; (m / Ls) % 3 == 0; Ls *= 3) {
-    stage_r<T, TC, 3>(X, Y, m, Ls, tw, inverse);
+    stage_r<T, TC, NT, 3>(X, Y, m, Ls, tw, inverse);
     swap();
   }
   for (; (m / Ls) % 5 == 0; Ls *= 5) {
-    stage_r<T, TC, 5>(X, Y, m, Ls, tw, inverse);
+    stage_r<T, TC, NT, 5>(X, Y, m, Ls, tw, inverse);
     swap();
   }
   for (int p = 7; Ls < m; p += 2) {
     for (; (m / Ls) % p == 0; Ls *= p) {
-      stage_any<T, TC>(X, Y, m, Ls, p, tw, inverse);
+      stage_any<T, TC, NT>(X, Y, m, Ls, p, tw, inverse);
       swap();
     }
   }
@@ -269,88 +284,109 @@ __device__ __forceinline__ long long chunk_columns(const ChunkDev& ch, const Blo
   return C.s[2];
 }
 
-template <typename T, int TC, int KIND, typename TI>
+// Forward transform of one chunk by a CTA of NT threads (dynamic shared memory: two buffers of
+// n/2 x TC complex values). The loads go straight into the half-length FFT's input for the kinds
+// whose reordering is a pure permutation (PP, NN, DD: z_j = v_2j + i v_2j+1 with v = x (PP) or
+// Makhoul's v_t = x_2t (t < m), x_2(n-1-t)+1 (t >= m)); DCT-IV / DST-IV need a twiddled pre-pass.
+// The sign flip of the DST kinds ((-1)^k x_k) is applied as the values arrive.
+template <typename T, int TC, int KIND, typename TI, int NT>
 __device__ void forward_chunk(const ChunkDev ch, const BlockDev* __restrict__ blk, const CallerBlk* __restrict__ cb,
                               int n, const Tw<T>& tw, const TI* __restrict__ in3, T* __restrict__ out, long long ncell,
                               T sub0, int split, unsigned char* smem) {
   constexpr int kind = KIND;
+  constexpr int RS = NT / TC;  // rows per pass
+  constexpr bool direct = kind == KIND_PP || kind == KIND_NN || kind == KIND_DD;
+  constexpr bool flip = kind == KIND_DD || kind == KIND_DN;
   __shared__ long long coff[TC];
   __shared__ long long ooff[TC];  // position of each column in a mode plane (plain or colour-split)
   const int m = n / 2;
   Cx<T>* A = reinterpret_cast<Cx<T>*>(smem);
   Cx<T>* Bf = A + m * TC;
-  T* xs = reinterpret_cast<T*>(Bf);  // n x TC reals, aliases Bf
+  T* xs = reinterpret_cast<T*>(Bf);  // n x TC reals, aliases Bf (DCT-IV / DST-IV only)
+  T* Af = reinterpret_cast<T*>(A);
   const BlockDev B = blk[ch.b];
   if (threadIdx.x < TC) {
     const int pc = ch.c0 + threadIdx.x;
     ooff[threadIdx.x] = split ? split_cell(B, pc % B.nx, pc / B.nx) : B.off + pc;
   }
   const long long sk = chunk_columns<TC>(ch, B, cb, coff);  // (its barrier also covers ooff)
-  // sk == 1: the homogeneous axis is the caller's contiguous one, consecutive threads run along it
-  const bool along = sk == 1;
-  for (int i0 = threadIdx.x; i0 < n * TC; i0 += LBATCH * blockDim.x) {
-    TI v[LBATCH];
-#pragma unroll
-    for (int u = 0; u < LBATCH; ++u) {
-      const int idx = i0 + u * blockDim.x;
-      const int k = along ? idx % n : idx / TC, c = along ? idx / n : idx % TC;
-      v[u] = idx < n * TC && c < ch.ncol ? in3[coff[c] + k * sk] : (TI)0;
-    }
-#pragma unroll
-    for (int u = 0; u < LBATCH; ++u) {
-      const int idx = i0 + u * blockDim.x;
-      if (idx < n * TC) xs[along ? (idx % n) * TC + idx / n : idx] = to_inner<T, TI>(v[u]);
-    }
-  }
-  __syncthreads();
-  const bool flip = kind == KIND_DD || kind == KIND_DN;
-  auto x = [&](int k, int c) -> T {
-    const T v = xs[k * TC + c];
-    return (flip && (k & 1)) ? -v : v;
-  };
-  for (int idx = threadIdx.x; idx < m * TC; idx += blockDim.x) {
-    const int j = idx / TC, c = idx % TC;
-    Cx<T> z;
-    if (kind == KIND_PP) {
-      z = {x(2 * j, c), x(2 * j + 1, c)};
-    } else if (kind == KIND_NN || kind == KIND_DD) {
-      const int t0 = 2 * j, t1 = 2 * j + 1;  // v_t = x_2t (t < m), x_{2(n-1-t)+1} (t >= m)
-      z = {t0 < m ? x(2 * t0, c) : x(2 * (n - 1 - t0) + 1, c), t1 < m ? x(2 * t1, c) : x(2 * (n - 1 - t1) + 1, c)};
+  const int c = my_col<TC, NT>(), r0 = my_row<TC, NT>();
+  const bool live = c < ch.ncol;
+  // x_k of column cc, as it arrives
+  auto store = [&](int k, int cc, TI v) {
+    T x = to_inner<T, TI>(v);
+    if (flip && (k & 1)) x = -x;
+    if constexpr (direct) {
+      const int t = kind == KIND_PP ? k : ((k & 1) ? n - 1 - (k >> 1) : (k >> 1));
+      Af[(((t >> 1) * TC + cc) << 1) + (t & 1)] = x;
     } else {
-      z = cmul(Cx<T>{x(2 * j, c), x(n - 1 - 2 * j, c)}, tw.tw4a[j]);
+      xs[k * TC + cc] = x;
     }
-    A[idx] = z;
+  };
+  if (sk != 1) {  // rows of the chunk are TC consecutive cells (coalesced); column c is this thread's
+    const TI* src = in3 + (live ? coff[c] : 0);
+    for (int k0 = r0; k0 < n; k0 += LBATCH * RS) {
+      TI v[LBATCH];
+#pragma unroll
+      for (int u = 0; u < LBATCH; ++u) {
+        const int k = k0 + u * RS;
+        v[u] = live && k < n ? src[(long long)k * sk] : (TI)0;
+      }
+#pragma unroll
+      for (int u = 0; u < LBATCH; ++u) {
+        const int k = k0 + u * RS;
+        if (k < n) store(k, c, v[u]);
+      }
+    }
+  } else {  // the homogeneous axis is the caller's contiguous one: consecutive threads run along it
+    for (int i0 = threadIdx.x; i0 < n * TC; i0 += LBATCH * NT) {
+      TI v[LBATCH];
+#pragma unroll
+      for (int u = 0; u < LBATCH; ++u) {
+        const int idx = i0 + u * NT;
+        const int k = idx % n, cc = idx / n;
+        v[u] = idx < n * TC && cc < ch.ncol ? in3[coff[cc] + k] : (TI)0;
+      }
+#pragma unroll
+      for (int u = 0; u < LBATCH; ++u) {
+        const int idx = i0 + u * NT;
+        if (idx < n * TC) store(idx % n, idx / n, v[u]);
+      }
+    }
   }
   __syncthreads();
-  const Cx<T>* R = cfft<T, TC>(A, Bf, m, tw.fft, false);
+  if constexpr (!direct) {  // t_j = (x_2j + i x_{n-1-2j}) e^{-i pi (4j+1)/4n}
+    for (int j = r0; j < m; j += RS) A[j * TC + c] = cmul(Cx<T>{xs[2 * j * TC + c], xs[(n - 1 - 2 * j) * TC + c]}, tw.tw4a[j]);
+    __syncthreads();
+  }
+  const Cx<T>* R = cfft<T, TC, NT>(A, Bf, m, tw.fft, false);
   // F(x - shift0) = F(x) - shift0 F(1); F(1) is zero outside mode 0
-  auto put = [&](int q, int c, T y) {
+  T* ob = out + (live ? ooff[c] : 0);
+  auto put = [&](int q, T y) {
     if (q == 0) y -= sub0;
-    if (c < ch.ncol) out[(long long)q * ncell + ooff[c]] = y;
+    if (live) ob[(long long)q * ncell] = y;
   };
-  if (kind == KIND_PP || kind == KIND_NN || kind == KIND_DD) {
+  if constexpr (direct) {
     // each half-spectrum bin k = 0..m once; it gives output k and its mirror n - k
-    for (int idx = threadIdx.x; idx < (m + 1) * TC; idx += blockDim.x) {
-      const int k = idx / TC, c = idx % TC;
+    for (int k = r0; k <= m; k += RS) {
       const Cx<T> X = rdft_bin<T, TC>(R, k, m, c, tw);
       const bool mirror = k > 0 && k < m;
       if (kind == KIND_PP) {
-        put(k, c, X.re);
-        if (mirror) put(n - k, c, X.im);
+        put(k, X.re);
+        if (mirror) put(n - k, X.im);
       } else {
         const Cx<T> w = tw.tw2n[k];
         const T y = (T)2 * (w.re * X.re - w.im * X.im);
-        put(kind == KIND_DD ? n - 1 - k : k, c, y);
+        put(kind == KIND_DD ? n - 1 - k : k, y);
         if (mirror) {  // bin n - k is conj(X_k)
           const Cx<T> wm = tw.tw2n[n - k];
           const T ym = (T)2 * (wm.re * X.re + wm.im * X.im);
-          put(kind == KIND_DD ? k - 1 : n - k, c, ym);
+          put(kind == KIND_DD ? k - 1 : n - k, ym);
         }
       }
     }
   } else {
-    for (int idx = threadIdx.x; idx < n * TC; idx += blockDim.x) {
-      const int q = idx / TC, c = idx % TC;
+    for (int q = r0; q < n; q += RS) {
       const int qq = kind == KIND_DN ? n - 1 - q : q;
       T y;
       if ((qq & 1) == 0) {
@@ -360,7 +396,7 @@ __device__ void forward_chunk(const ChunkDev ch, const BlockDev* __restrict__ bl
         const int k = (n - 1 - qq) / 2;
         y = (T)-2 * cmul(R[k * TC + c], tw.tw4b[k]).im;
       }
-      put(q, c, y);
+      put(q, y);
     }
   }
 }
