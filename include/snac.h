@@ -113,6 +113,11 @@ typedef struct {
                           finest plane, fits in one CTA's shared memory, each wavenumber's solve runs
                           on chip in one CTA and its convergence is decided on the device (one launch
                           per defect-correction step); -1: always the level-by-level path            */
+  int32_t bottom_cells;  /* where the bottom sub-cycle starts (the coarse levels that run in one CTA's
+                          shared memory per wavenumber, one launch per cycle): at the finest level below
+                          level 0 whose plane has at most this many cells and whose hierarchy fits;
+                          0 (default) = 8192; 16 .. 8192; -1 = none (every level level by level, a
+                          dense solve at the coarsest). Changes the launch shape only, not the method */
 } snac_options;
 
 /* Result of the last solve of a plan. */

@@ -99,6 +99,7 @@ std::string problem_key(const Request& r) {
     put(k, r.opt.inner_reduction);
     put(k, r.opt.shift);
     put(k, r.opt.onchip);
+    put(k, r.opt.bottom_cells);
   }
   return k;
 }

@@ -680,6 +680,12 @@ int create(snac_plan** out, int32_t nblocks, const snac_block* blocks_in, int32_
       delete P;
       return fail(SNAC_ERR_INVALID_ARG, "bad snac_options: onchip must be 0 or -1");
     }
+    P->bottom_cells = opt->bottom_cells;
+    if (opt->bottom_cells != 0 && opt->bottom_cells != -1 &&
+        (opt->bottom_cells < 16 || opt->bottom_cells > BOTTOM_MAX_CELLS)) {
+      delete P;
+      return fail(SNAC_ERR_INVALID_ARG, "bad snac_options: bottom_cells must be 0, -1 or 16 .. 8192");
+    }
     if (!(P->inner_reduction > 0.0 && P->inner_reduction < 1.0) || !(P->shift <= 0.0) || !std::isfinite(P->shift) || (P->precision != SNAC_FP64 && P->precision != SNAC_MIXED) || P->nu1 < 0 || P->nu2 < 0 ||
         P->nu1 + P->nu2 < 1 || P->nu1 > 16 || P->nu2 > 16 || P->max_outer < 1 || P->max_cycles < 1 ||
         P->max_coarse < 1 || P->max_coarse > MAX_COARSE) {
@@ -807,12 +813,14 @@ int create(snac_plan** out, int32_t nblocks, const snac_block* blocks_in, int32_
     if ((st = build_coarse(P))) break;
     // the bottom of the cycle in one launch: from the first level below 0 whose planes, with all
     // coarser ones, fit in one CTA's shared memory (at least one smoothed level above the coarsest)
+    // and whose plane has at most bottom_cells cells
     {
       const int L = (int)P->lev.size() - 1;
+      const long long cap = P->bottom_cells > 0 ? P->bottom_cells : BOTTOM_MAX_CELLS;
       P->bottom = -1;
-      if (P->nu1 >= 1 && P->nu2 >= 1)
+      if (P->nu1 >= 1 && P->nu2 >= 1 && P->bottom_cells != -1)
         for (int l = std::max(1, L - BOTTOM_MAX_LEVELS + 1); l < L; ++l)
-          if (P->lev[l].ncell <= BOTTOM_MAX_CELLS && L - l < BOTTOM_MAX_LEVELS &&
+          if (P->lev[l].ncell <= cap && L - l < BOTTOM_MAX_LEVELS &&
               bottom_layout(P, l, inner).bytes <= (size_t)BOTTOM_MAX_SMEM) {
             P->bottom = l;
             break;

@@ -194,6 +194,7 @@ struct snac_plan {
   // its convergence decided on the device (kern_bottom.cu, k_onchip)
   bool onchip = false;
   int onchip_opt = 0;         // snac_options.onchip
+  int bottom_cells = 0;       // snac_options.bottom_cells
   void* d_onchip = nullptr;   // BottomLevel<inner type> table from level 0
   double* d_pweight = nullptr;
   int* h_cycles = nullptr;    // per wavenumber: V-cycles of the last on-chip solve (mapped pinned)

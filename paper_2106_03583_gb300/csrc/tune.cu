@@ -20,13 +20,15 @@ snac_options defaults() {
   o.fused = d.fused;
   o.inner_reduction = d.inner_reduction;
   o.shift = d.shift;
+  o.bottom_cells = d.bottom_cells;
   return o;
 }
 
 bool same(const snac_options& a, const snac_options& b) {
   return a.precision == b.precision && a.nu1 == b.nu1 && a.nu2 == b.nu2 && a.max_outer == b.max_outer &&
          a.max_cycles == b.max_cycles && a.max_coarse == b.max_coarse && a.fused == b.fused &&
-         a.inner_reduction == b.inner_reduction && a.shift == b.shift && a.onchip == b.onchip;
+         a.inner_reduction == b.inner_reduction && a.shift == b.shift && a.onchip == b.onchip &&
+         a.bottom_cells == b.bottom_cells;
 }
 
 struct Trial {
@@ -133,6 +135,16 @@ extern "C" int snac_autotune(int32_t nblocks, const snac_block* blocks, int32_t 
     for (int oc : {0, -1}) {
       snac_options c = start;
       c.onchip = oc;
+      consider(c);
+    }
+  }
+  {
+    // where the coarse levels move into one CTA's shared memory per wavenumber: a smaller top
+    // level means more, lighter CTAs for the bottom launch and one more level on the grid-wide path
+    const snac_options start = cur;
+    for (int bc : {0, 2048, 512}) {
+      snac_options c = start;
+      c.bottom_cells = bc;
       consider(c);
     }
   }

@@ -52,7 +52,8 @@ class _Options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("nu1", ctypes.c_int32), ("nu2", ctypes.c_int32),
                 ("max_outer", ctypes.c_int32), ("max_cycles", ctypes.c_int32), ("max_coarse", ctypes.c_int32),
                 ("fused", ctypes.c_int32), ("inner_reduction", ctypes.c_double), ("shift", ctypes.c_double),
-                ("mode_begin", ctypes.c_int32), ("mode_end", ctypes.c_int32), ("onchip", ctypes.c_int32)]
+                ("mode_begin", ctypes.c_int32), ("mode_end", ctypes.c_int32), ("onchip", ctypes.c_int32),
+                ("bottom_cells", ctypes.c_int32)]
 
 
 class _KStat(ctypes.Structure):
@@ -200,7 +201,7 @@ class Plan:
 
     def __init__(self, blocks, homog_axis: int = 2, precision: str = "fp64", nu1: int = 2, nu2: int = 2,
                  max_outer: int = 20, max_cycles: int = 40, max_coarse: int = 64, inner_reduction: float = 1e-4,
-                 fused: int = -1, shift: float = 0.0, modes=None, onchip: bool = True):
+                 fused: int = -1, shift: float = 0.0, modes=None, onchip: bool = True, bottom_cells: int = 0):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("snac.Plan needs a CUDA device")
@@ -214,7 +215,7 @@ class Plan:
         arr, keep = _marshal_blocks(blocks)
         q0, q1 = modes if modes is not None else (0, 0)
         opt = _Options(_PREC[precision], nu1, nu2, max_outer, max_cycles, max_coarse, fused, inner_reduction, shift,
-                       int(q0), int(q1), 0 if onchip else -1)
+                       int(q0), int(q1), 0 if onchip else -1, int(bottom_cells))
         h = ctypes.c_void_p()
         _check(lib().snac_plan_create(ctypes.byref(h), len(blocks), arr, homog_axis, ctypes.byref(opt)))
         del keep
@@ -436,7 +437,8 @@ class Engine:
 
     def submit(self, blocks, rhs, tol: float = 1e-10, precision: str = "fp64", homog_axis: int = 2, nu1: int = 2,
                nu2: int = 2, max_outer: int = 20, max_cycles: int = 40, max_coarse: int = 64,
-               inner_reduction: float = 1e-4, fused: int = -1, shift: float = 0.0, onchip: bool = True) -> int:
+               inner_reduction: float = 1e-4, fused: int = -1, shift: float = 0.0, onchip: bool = True,
+               bottom_cells: int = 0) -> int:
         if precision not in _PREC:
             raise ValueError(f"precision must be one of {list(_PREC)}")
         n3 = int(sum(np.prod([b["hi"][a] - b["lo"][a] + 1 for a in range(3)]) for b in blocks))
@@ -446,7 +448,7 @@ class Engine:
         p = np.empty(n3, dtype=np.float64)
         arr, keep = _marshal_blocks(blocks)
         opt = _Options(_PREC[precision], nu1, nu2, max_outer, max_cycles, max_coarse, fused, inner_reduction, shift,
-                       onchip=0 if onchip else -1)
+                       onchip=0 if onchip else -1, bottom_cells=int(bottom_cells))
         t = ctypes.c_int64()
         _check(lib().snac_engine_submit(self._h, len(blocks), arr, homog_axis, ctypes.byref(opt),
                                         ctypes.c_void_p(rhs.ctypes.data), ctypes.c_void_p(p.ctypes.data),
@@ -498,6 +500,7 @@ class Engine:
 
 
 _OPTION_NAMES = ("nu1", "nu2", "max_outer", "max_cycles", "max_coarse", "fused", "inner_reduction", "shift")
+_TUNED_EXTRA = ("bottom_cells",)
 
 
 def autotune(blocks, rhs, tol: float = 1e-10, precision: str = "fp64", homog_axis: int = 2, **base):
@@ -511,19 +514,20 @@ def autotune(blocks, rhs, tol: float = 1e-10, precision: str = "fp64", homog_axi
     if not isinstance(rhs, torch.Tensor) or not rhs.is_cuda or rhs.dtype != torch.float64 or \
             not rhs.is_contiguous() or rhs.numel() != n3:
         raise ValueError(f"rhs must be a contiguous CUDA float64 tensor with {n3} elements")
-    d = dict(nu1=2, nu2=2, max_outer=20, max_cycles=40, max_coarse=64, fused=-1, inner_reduction=1e-4, shift=0.0)
+    d = dict(nu1=2, nu2=2, max_outer=20, max_cycles=40, max_coarse=64, fused=-1, inner_reduction=1e-4, shift=0.0,
+             bottom_cells=0)
     unknown = set(base) - set(d)
     if unknown:
         raise ValueError(f"unknown options {sorted(unknown)}")
     d.update(base)
-    opt = _Options(_PREC[precision], *(d[k] for k in _OPTION_NAMES))
+    opt = _Options(_PREC[precision], *(d[k] for k in _OPTION_NAMES), bottom_cells=int(d["bottom_cells"]))
     best, rep = _Options(), _TuneReport()
     arr, keep = _marshal_blocks(blocks)
     stream = ctypes.c_void_p(torch.cuda.current_stream(rhs.device).cuda_stream)
     _check(lib().snac_autotune(len(blocks), arr, homog_axis, ctypes.byref(opt), ctypes.c_void_p(rhs.data_ptr()),
                                float(tol), ctypes.byref(best), ctypes.byref(rep), stream))
     del keep
-    chosen = {k: getattr(best, k) for k in _OPTION_NAMES}
+    chosen = {k: getattr(best, k) for k in _OPTION_NAMES + _TUNED_EXTRA}
     chosen["onchip"] = best.onchip == 0
     chosen["precision"] = precision
     return chosen, {k: getattr(rep, k) for k, _ in _TuneReport._fields_}

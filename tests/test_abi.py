@@ -114,6 +114,16 @@ def test_option_validation(lib):
         assert st == -1 and "options" in msg, (kw, st, msg)
 
 
+def test_bottom_and_onchip_option_validation(lib):
+    """onchip is 0 or -1; bottom_cells is 0, -1 or 16 .. 8192; refused before any device work."""
+    blocks = make("1", n=4, nz=8, zpair="NN")
+    for oc, bc, word in ((1, 0, "onchip"), (0, 5, "bottom_cells"), (0, 8193, "bottom_cells"),
+                         (0, -2, "bottom_cells")):
+        opt = snac._Options(0, 2, 2, 20, 40, 64, -1, 1e-3, 0.0, 0, 0, oc, bc)
+        st, msg = _create(lib, blocks, opt=ctypes.byref(opt))
+        assert st == -1 and word in msg, (oc, bc, st, msg)
+
+
 def test_homogeneous_axis_validation(lib):
     """homog_axis is 0, 1 or 2; the chosen axis must be the one the blocks are not split along."""
     blocks = make("L", n=4, nz=6, zpair="DN", walls=("D", "N", "N", "N"))

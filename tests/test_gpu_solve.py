@@ -54,6 +54,22 @@ def test_workloads_vs_oracle(precision, name, scale):
     assert rel(p, po) <= PARITY, (rel(p, po), info)
 
 
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("bottom_cells", [512, 2048, -1])
+def test_bottom_start_vs_oracle(precision, bottom_cells):
+    """Where the bottom sub-cycle starts (an autotuner dimension) changes only the launch shape: the
+    solution still matches the oracle, and -1 (no sub-cycle: every level level by level and the
+    dense coarsest solve) runs no bottom launch."""
+    blocks, f = inputs.config("mb2x2", seed=0, scale=4)
+    po, _ = osv.solve(blocks, f)
+    p, info, pl = gpu_solve(blocks, f, precision, bottom_cells=bottom_cells)
+    assert info["status"] == 0 and info["rel_res"] <= TOL
+    assert osv.rel_residual(blocks, f, p) <= 1.01 * TOL
+    assert rel(p, po) <= PARITY, (rel(p, po), info)
+    if bottom_cells == -1:
+        assert pl.kernel_stats()["bottom"]["launches"] == 0
+
+
 def _table2_blocks(refine, nz, z_bc):
     """The four-block layout of Table 2 (its index-space corners, from the golden fixture), refined."""
     import os
