@@ -72,8 +72,8 @@ TRAFFIC = {
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
-    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["snac", "reference"], default="snac")
     ap.add_argument("--workload", default="chan")
     ap.add_argument("--scale", type=int, default=1, help="divide every cell count by this (profiling cases)")
