@@ -54,6 +54,17 @@ struct LevelSmem {
   T* inv;  // smoothed levels only
 };
 
+// n / d for 0 <= n < 2^22 and 1 <= d < 2^22 (the on-chip levels have at most 8192 cells): a
+// single-precision estimate, whose error is below one half, corrected by one step either way --
+// no integer division in the per-cell index arithmetic.
+__device__ __forceinline__ int small_div(int n, int d) {
+  int q = __float2int_rz(__fmul_rn((float)n, __frcp_rn((float)d)));
+  const int r = n - q * d;
+  q += r >= d ? 1 : 0;
+  q -= r < 0 ? 1 : 0;
+  return q;
+}
+
 // Cell (b, i, j) of the idx-th cell of colour c of a level (blocks in order, rows of each block in
 // order, the colour's cells of a row in order of i). Returns false past the last cell.
 __device__ __forceinline__ bool colour_cell(const BlockDev* __restrict__ blk, int nblk, int idx, int c, int& b,
@@ -63,7 +74,7 @@ __device__ __forceinline__ bool colour_cell(const BlockDev* __restrict__ blk, in
     const int half = (B.nx >> 1) * B.ny;
     if (idx < half) {
       const int hx = B.nx >> 1;
-      j = idx / hx;
+      j = small_div(idx, hx);
       i = 2 * (idx - j * hx) + ((c ^ B.par ^ j) & 1);
       return true;
     }
@@ -80,8 +91,35 @@ __device__ __forceinline__ void plane_cell(const BlockDev* __restrict__ blk, int
   }
   B = blk[b];
   const int l = c - (int)B.off;
-  j = l / B.nx;
+  j = small_div(l, B.nx);
   i = l - j * B.nx;
+}
+
+// Plane indices of the four neighbours of cell c = (i, j) of block B (the same cells nbr_plane
+// gives, in int arithmetic for the on-chip levels): inside the block directly; across a face the
+// connected block's cell from the block table, or the cell itself on a physical face.
+__device__ __forceinline__ void nbr_int(const BlockDev* __restrict__ blk, const BlockDev& B, int i, int j, int c,
+                                        int& w, int& e, int& s, int& n) {
+  w = c - 1;
+  e = c + 1;
+  s = c - B.nx;
+  n = c + B.nx;
+  if (i == 0) {
+    const int k = B.nbr[0];
+    w = k >= 0 ? (int)blk[k].off + j * blk[k].nx + blk[k].nx - 1 : c;
+  }
+  if (i == B.nx - 1) {
+    const int k = B.nbr[1];
+    e = k >= 0 ? (int)blk[k].off + j * blk[k].nx : c;
+  }
+  if (j == 0) {
+    const int k = B.nbr[2];
+    s = k >= 0 ? (int)blk[k].off + (blk[k].ny - 1) * blk[k].nx + i : c;
+  }
+  if (j == B.ny - 1) {
+    const int k = B.nbr[3];
+    n = k >= 0 ? (int)blk[k].off + i : c;
+  }
 }
 
 // One Gauss-Seidel half-sweep of colour c on a level.
@@ -92,9 +130,9 @@ __device__ void half_sweep(const LevelView<T>& L, const LevelSmem<T>& S, int c) 
     int b, i, j;
     BlockDev B;
     if (!colour_cell(L.blk, L.nblk, idx, c, b, B, i, j)) break;
-    long long w, e, s, n;
-    nbr_plane(L.blk, B, b, i, j, w, e, s, n);
-    const int cc = (int)(B.off + (long long)j * B.nx + i);
+    const int cc = (int)B.off + j * B.nx + i;
+    int w, e, s, n;
+    nbr_int(L.blk, B, i, j, cc, w, e, s, n);
     const Coef<T> cx = L.cx[B.xo + i], cy = L.cy[B.yo + j];
     T a = cx.lo * S.u[w];
     a = fma(cx.hi, S.u[e], a);
@@ -123,9 +161,9 @@ __device__ void restrict_to(const LevelView<T>& F, const LevelSmem<T>& SF, const
       for (int di = 0; di < 2; ++di) {
         const int i = 2 * I + di, j = 2 * J + dj;
         if ((Bf.par + i + j) & 1) continue;
-        long long w, e, s, n;
-        nbr_plane(F.blk, Bf, b, i, j, w, e, s, n);
-        const int c = (int)(Bf.off + (long long)j * Bf.nx + i);
+        const int c = (int)Bf.off + j * Bf.nx + i;
+        int w, e, s, n;
+        nbr_int(F.blk, Bf, i, j, c, w, e, s, n);
         const Coef<T> cx = F.cx[Bf.xo + i], cy = F.cy[Bf.yo + j];
         T a = cx.lo * SF.u[w];
         a = fma(cx.hi, SF.u[e], a);
@@ -157,9 +195,10 @@ __device__ void prolong_from(const LevelView<T>& F, const LevelSmem<T>& SF, cons
     }
     const BlockDev Bc = C.blk[b];
     const int I = i >> 1, J = j >> 1;
-    long long w, e, s, n;
-    nbr_plane(C.blk, Bc, b, I, J, w, e, s, n);
-    const T eC = SC.u[Bc.off + (long long)J * Bc.nx + I];
+    const int cI = (int)Bc.off + J * Bc.nx + I;
+    int w, e, s, n;
+    nbr_int(C.blk, Bc, I, J, cI, w, e, s, n);
+    const T eC = SC.u[cI];
     const T eX = SC.u[(i & 1) ? e : w];
     const T eY = SC.u[(j & 1) ? n : s];
     const PW<T> px = F.px[Bf.xo + i], py = F.py[Bf.yo + j];
@@ -337,9 +376,9 @@ __device__ double colour0_resid2(const LevelView<T>& L, const LevelSmem<T>& S, T
     int b, i, j;
     BlockDev B;
     if (!colour_cell(L.blk, L.nblk, idx, 0, b, B, i, j)) break;
-    long long w, e, s, n;
-    nbr_plane(L.blk, B, b, i, j, w, e, s, n);
-    const int c = (int)(B.off + (long long)j * B.nx + i);
+    const int c = (int)B.off + j * B.nx + i;
+    int w, e, s, n;
+    nbr_int(L.blk, B, i, j, c, w, e, s, n);
     const Coef<T> cx = L.cx[B.xo + i], cy = L.cy[B.yo + j];
     T a = cx.lo * S.u[w];
     a = fma(cx.hi, S.u[e], a);
@@ -451,7 +490,7 @@ __device__ void onchip_mode(const OnchipArgs<T>& O, int q, unsigned char* smem_r
 
 // One plan: CTA k solves wavenumber active[k].
 template <typename T>
-__global__ void __launch_bounds__(BT) k_onchip(const OnchipArgs<T> O) {
+__global__ void __launch_bounds__(BT, 1) k_onchip(const OnchipArgs<T> O) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   onchip_mode(O, O.B.active[blockIdx.x], smem_raw);
 }
