@@ -40,6 +40,7 @@ struct BottomArgs {
   const T* f_top;                           // right-hand side of the top level, [q][cell]
   T* u_top;                                 // its correction, [q][cell]
   const double* Q;
+  const double* QT;
   const double* lam;
   const double* sqa;
   int nc;
@@ -54,11 +55,12 @@ struct LevelSmem {
   T* inv;  // smoothed levels only
 };
 
-// n / d for 0 <= n < 2^22 and 1 <= d < 2^22 (the on-chip levels have at most 8192 cells): a
-// single-precision estimate, whose error is below one half, corrected by one step either way --
-// no integer division in the per-cell index arithmetic.
+// n / d for 0 <= n < 2^16 and 1 <= d < 2^16 (the on-chip levels have at most 8192 cells): a
+// single-precision estimate from the approximate reciprocal (relative error below 2^-21, so the
+// estimate is within 2^-5 of n / d), corrected by one step either way -- no integer division in
+// the per-cell index arithmetic.
 __device__ __forceinline__ int small_div(int n, int d) {
-  int q = __float2int_rz(__fmul_rn((float)n, __frcp_rn((float)d)));
+  int q = __float2int_rz(__fdividef((float)n, (float)d));
   const int r = n - q * d;
   q += r >= d ? 1 : 0;
   q -= r < 0 ? 1 : 0;
@@ -211,26 +213,35 @@ __device__ void prolong_from(const LevelView<T>& F, const LevelSmem<T>& SF, cons
 }
 
 // Coarsest plane: u = V^-1/2 Q (Lam + sigma)^-1 Q^T V^1/2 f (the null eigenvector dropped for a
-// singular mode), in FP64.
+// singular mode), in FP64. The wavenumber's factors come once per CTA and wavenumber
+// (coarse_factors); each product is one thread per entry reading a row of Q^T or Q, so that a cycle
+// issues no FP64 division and no cross-lane reduction (GB300's FP64 pipe is 1/64 of FP32).
+__device__ void coarse_factors(const double* __restrict__ lam, const double* __restrict__ sqa, int nc, int null_index,
+                               double sg, bool sing, double* dinv, double* isq) {
+  for (int k = threadIdx.x; k < nc; k += BT) {
+    dinv[k] = (sing && k == null_index) ? 0.0 : 1.0 / (lam[k] + sg);
+    isq[k] = 1.0 / sqa[k];
+  }
+}
+
 template <typename T>
-__device__ void coarse_solve(const double* __restrict__ Q, const double* __restrict__ lam,
-                             const double* __restrict__ sqa, int nc, int null_index, const LevelSmem<T>& S, double sg,
-                             bool sing, double* b, double* y) {
+__device__ void coarse_solve(const double* __restrict__ Q, const double* __restrict__ QT,
+                             const double* __restrict__ sqa, int nc, const LevelSmem<T>& S, const double* dinv,
+                             const double* isq, double* b, double* y) {
   for (int i = threadIdx.x; i < nc; i += BT) b[i] = sqa[i] * (double)S.f[i];
   __syncthreads();
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int k = warp; k < nc; k += BT / 32) {
+  for (int k = threadIdx.x; k < nc; k += BT) {  // y = (Lam + sigma)^-1 Q^T b
+    const double* qk = QT + (long long)k * nc;
     double s = 0.0;
-    for (int i = lane; i < nc; i += 32) s = fma(Q[(long long)i * nc + k], b[i], s);
-    s = warp_sum(s);
-    if (lane == 0) y[k] = (sing && k == null_index) ? 0.0 : s / (lam[k] + sg);
+    for (int i = 0; i < nc; ++i) s = fma(qk[i], b[i], s);
+    y[k] = s * dinv[k];
   }
   __syncthreads();
-  for (int i = warp; i < nc; i += BT / 32) {
+  for (int i = threadIdx.x; i < nc; i += BT) {  // u = V^-1/2 Q y
+    const double* qi = Q + (long long)i * nc;
     double s = 0.0;
-    for (int k = lane; k < nc; k += 32) s = fma(Q[(long long)i * nc + k], y[k], s);
-    s = warp_sum(s);
-    if (lane == 0) S.u[i] = (T)(s / sqa[i]);
+    for (int k = 0; k < nc; ++k) s = fma(qi[k], y[k], s);
+    S.u[i] = (T)(s * isq[i]);
   }
   __syncthreads();
 }
@@ -258,6 +269,8 @@ __global__ void __launch_bounds__(BT) k_bottom(const BottomArgs<T> A) {
   const int nl = A.nlev;  // levels 0 .. nl-1 of the sub-cycle; the last is the coarsest
   double* b = reinterpret_cast<double*>(smem_raw + A.coarse_off);
   double* y = b + MAX_COARSE;
+  double* dinv = y + MAX_COARSE;  // the coarsest solve's factors of this wavenumber
+  double* isq = dinv + MAX_COARSE;
   const T sg = A.sigma[q];
   const double sg64 = A.sigma64[q];
   const bool sing = A.singular_mode[q] != 0;
@@ -278,6 +291,7 @@ __global__ void __launch_bounds__(BT) k_bottom(const BottomArgs<T> A) {
       for (int c = threadIdx.x; c < (int)top.L.ncell; c += BT) f0[c] = f0g[c];
     }
   }
+  coarse_factors(A.lam, A.sqa, A.nc, A.null_index, sg64, sing, dinv, isq);
   __syncthreads();
   for (int l = 0; l + 1 < nl; ++l) {
     const BottomLevel<T> bl = level_at(A, smem_raw, l);
@@ -322,7 +336,7 @@ __global__ void __launch_bounds__(BT) k_bottom(const BottomArgs<T> A) {
   }
   {
     const BottomLevel<T> C = level_at(A, smem_raw, nl - 1);
-    coarse_solve(A.Q, A.lam, A.sqa, A.nc, A.null_index, level_smem(smem_raw, C, f0g), sg64, sing, b, y);
+    coarse_solve(A.Q, A.QT, A.sqa, A.nc, level_smem(smem_raw, C, f0g), dinv, isq, b, y);
   }
   // up: prolongation onto the colour-1 cells, nu2 sweeps
   for (int l = nl - 2; l >= 0; --l) {
@@ -408,6 +422,8 @@ __device__ void onchip_mode(const OnchipArgs<T>& O, int q, unsigned char* smem_r
   const int nl = A.nlev;
   double* b = reinterpret_cast<double*>(smem_raw + A.coarse_off);
   double* y = b + MAX_COARSE;
+  double* dinv = y + MAX_COARSE;  // the coarsest solve's factors of this wavenumber
+  double* isq = dinv + MAX_COARSE;
   const T sg = A.sigma[q];
   const double sg64 = A.sigma64[q];
   const bool sing = A.singular_mode[q] != 0;
@@ -426,6 +442,7 @@ __device__ void onchip_mode(const OnchipArgs<T>& O, int q, unsigned char* smem_r
       for (int c = threadIdx.x; c < (int)top.L.ncell; c += BT) f0[c] = f0g[c];
     }
   }
+  coarse_factors(A.lam, A.sqa, A.nc, A.null_index, sg64, sing, dinv, isq);
   __syncthreads();
   for (int l = 0; l + 1 < nl; ++l) {
     const BottomLevel<T> bl = level_at(A, smem_raw, l);
@@ -462,7 +479,7 @@ __device__ void onchip_mode(const OnchipArgs<T>& O, int q, unsigned char* smem_r
       }
       {
         const BottomLevel<T> C = level_at(A, smem_raw, nl - 1);
-        coarse_solve(A.Q, A.lam, A.sqa, A.nc, A.null_index, level_smem(smem_raw, C, f0g), sg64, sing, b, y);
+        coarse_solve(A.Q, A.QT, A.sqa, A.nc, level_smem(smem_raw, C, f0g), dinv, isq, b, y);
       }
       for (int l = nl - 2; l >= 0; --l) {
         const BottomLevel<T> F = level_at(A, smem_raw, l), C = level_at(A, smem_raw, l + 1);
@@ -498,7 +515,7 @@ __global__ void __launch_bounds__(BT, 1) k_onchip(const OnchipArgs<T> O) {
 // Many plans in one persistent launch: every CTA takes (problem, wavenumber) items from a queue
 // (an atomic counter, zero at launch) until none is left; each item uses its own problem's tables.
 template <typename T>
-__global__ void __launch_bounds__(BT) k_onchip_batch(const OnchipArgs<T>* __restrict__ args, const int2* __restrict__ items,
+__global__ void __launch_bounds__(BT, 1) k_onchip_batch(const OnchipArgs<T>* __restrict__ args, const int2* __restrict__ items,
                                                      int nitems, int* __restrict__ next) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int item;
@@ -620,7 +637,7 @@ __global__ void __launch_bounds__(BT, 1) k_fwd_onchip(const FwdArgs<T> F, const 
 // Several plans: items (type, plan, index) from a table -- every plan's chunks first, then every
 // plan's wavenumbers.
 template <typename T, int TC>
-__global__ void __launch_bounds__(BT) k_fwd_onchip_batch(const FwdArgs<T>* __restrict__ fargs,
+__global__ void __launch_bounds__(BT, 1) k_fwd_onchip_batch(const FwdArgs<T>* __restrict__ fargs,
                                                          const OnchipArgs<T>* __restrict__ args,
                                                          const int4* __restrict__ items, int nitems,
                                                          int* __restrict__ next, long long wait_ns) {
@@ -663,6 +680,7 @@ OnchipArgs<T> onchip_args(snac_plan* P, double target) {
   A.f_top = (const T*)P->lev[0].d_f;
   A.u_top = (T*)P->lev[0].d_u;
   A.Q = P->d_Q;
+  A.QT = P->d_QT;
   A.lam = P->d_lam;
   A.sqa = P->d_sqa;
   A.nc = P->nc;
@@ -714,6 +732,7 @@ cudaError_t bottom_t(snac_plan* P, int nact, cudaStream_t s) {
   A.f_top = (const T*)P->lev[lb].d_f;
   A.u_top = (T*)P->lev[lb].d_u;
   A.Q = P->d_Q;
+  A.QT = P->d_QT;
   A.lam = P->d_lam;
   A.sqa = P->d_sqa;
   A.nc = P->nc;
@@ -753,7 +772,7 @@ BottomLayout bottom_layout(const snac_plan* P, int lb, size_t w) {
   }
   size_t bytes = (el * w + 15) / 16 * 16;
   lay.coarse_off = (int)bytes;
-  bytes += 2 * MAX_COARSE * sizeof(double);
+  bytes += 4 * MAX_COARSE * sizeof(double);  // the coarsest solve's b, y and factors
   for (int l = lb; l <= L && l - lb < BOTTOM_MAX_LEVELS; ++l) {
     lay.sblk[l - lb] = (int)bytes;
     bytes += (size_t)P->lev[l].nblk * sizeof(BlockDev);

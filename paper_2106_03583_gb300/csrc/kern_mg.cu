@@ -254,31 +254,33 @@ __global__ void __launch_bounds__(TILE_THREADS) k_prolong(LevelView<T> F, LevelV
 // (A + sigma)^-1 b = V^-1/2 Q (Lam + sigma)^-1 Q^T V^1/2 b. For a singular mode the null eigenvector
 // (constant in the V-weighted sense) is dropped: the zero-mean solution. One CTA per mode, in FP64.
 template <typename T>
-__global__ void __launch_bounds__(256) k_coarse(const double* __restrict__ Q, const double* __restrict__ lam,
-                                                const double* __restrict__ sqa, int nc, const int* __restrict__ active,
-                                                const double* __restrict__ sigma, const int* __restrict__ singular_mode,
-                                                int null_index, const T* __restrict__ fcoarse, T* __restrict__ ucoarse,
+__global__ void __launch_bounds__(256) k_coarse(const double* __restrict__ Q, const double* __restrict__ QT,
+                                                const double* __restrict__ lam, const double* __restrict__ sqa, int nc,
+                                                const int* __restrict__ active, const double* __restrict__ sigma,
+                                                const int* __restrict__ singular_mode, int null_index,
+                                                const T* __restrict__ fcoarse, T* __restrict__ ucoarse,
                                                 long long ncell) {
   __shared__ double b[MAX_COARSE], y[MAX_COARSE];
   const int q = active[blockIdx.x];
   const long long base = (long long)q * ncell;
   for (int i = threadIdx.x; i < nc; i += blockDim.x) b[i] = sqa[i] * (double)fcoarse[base + i];
   __syncthreads();
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
   const double sg = sigma[q];
   const bool sing = singular_mode[q] != 0;
-  for (int k = warp; k < nc; k += nwarp) {
+  // one thread per entry, reading a row of Q^T (then of Q): no cross-lane reductions, and the FP64
+  // divisions of the lanes of a warp run together
+  for (int k = threadIdx.x; k < nc; k += blockDim.x) {
+    const double* qk = QT + (long long)k * nc;
     double s = 0.0;
-    for (int i = lane; i < nc; i += 32) s = fma(Q[(long long)i * nc + k], b[i], s);
-    s = warp_sum(s);
-    if (lane == 0) y[k] = (sing && k == null_index) ? 0.0 : s / (lam[k] + sg);
+    for (int i = 0; i < nc; ++i) s = fma(qk[i], b[i], s);
+    y[k] = (sing && k == null_index) ? 0.0 : s / (lam[k] + sg);
   }
   __syncthreads();
-  for (int i = warp; i < nc; i += nwarp) {
+  for (int i = threadIdx.x; i < nc; i += blockDim.x) {
+    const double* qi = Q + (long long)i * nc;
     double s = 0.0;
-    for (int k = lane; k < nc; k += 32) s = fma(Q[(long long)i * nc + k], y[k], s);
-    s = warp_sum(s);
-    if (lane == 0) ucoarse[base + i] = (T)(s / sqa[i]);
+    for (int k = 0; k < nc; ++k) s = fma(qi[k], y[k], s);
+    ucoarse[base + i] = (T)(s / sqa[i]);
   }
 }
 
@@ -495,7 +497,7 @@ cudaError_t vcycle_t(snac_plan* P, int nact, cudaStream_t st, bool skip_first0) 
   } else {
     const HostLevel& h = P->lev[L];
     LaunchScope ls(P, K_COARSE, 2.0 * w * P->nc * nact + 8.0 * P->nc * P->nc, 4.0 * P->nc * P->nc * nact, st);
-    k_coarse<T><<<nact, 256, 0, st>>>(P->d_Q, P->d_lam, P->d_sqa, P->nc, act, P->d_sigma64, P->d_singular_mode,
+    k_coarse<T><<<nact, 256, 0, st>>>(P->d_Q, P->d_QT, P->d_lam, P->d_sqa, P->nc, act, P->d_sigma64, P->d_singular_mode,
                                       P->null_index, (const T*)h.d_f, (T*)h.d_u, h.ncell);
   }
   for (int l = top - 1; l >= 0; --l) {

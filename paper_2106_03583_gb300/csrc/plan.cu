@@ -416,8 +416,13 @@ int build_coarse(snac_plan* P) {
       if (std::fabs(lam[i]) < std::fabs(lam[k])) k = i;
     P->null_index = k;
   }
+  std::vector<double> QT((size_t)n * n);  // its transpose, so that both products of the solve read whole rows
+  for (int i = 0; i < n; ++i)
+    for (int k = 0; k < n; ++k) QT[(size_t)k * n + i] = Q[(size_t)i * n + k];
   int st;
-  if ((st = upload(P, &P->d_Q, Q)) || (st = upload(P, &P->d_lam, lam)) || (st = upload(P, &P->d_sqa, sqa))) return st;
+  if ((st = upload(P, &P->d_Q, Q)) || (st = upload(P, &P->d_QT, QT)) || (st = upload(P, &P->d_lam, lam)) ||
+      (st = upload(P, &P->d_sqa, sqa)))
+    return st;
   return SNAC_OK;
 }
 

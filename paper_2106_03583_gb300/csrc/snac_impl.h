@@ -235,6 +235,7 @@ struct snac_plan {
   int nc = 0;
   int null_index = -1;
   double* d_Q = nullptr;      // nc x nc, row-major, column k = eigenvector k
+  double* d_QT = nullptr;     // its transpose (row k = eigenvector k)
   double* d_lam = nullptr;    // nc
   double* d_sqa = nullptr;    // sqrt(area) of the coarsest cells
   int* d_singular_mode = nullptr;  // per mode: 1 if the reduced system is singular
