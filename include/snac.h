@@ -97,8 +97,10 @@ typedef struct {
                           shared memory) on levels whose blocks are all >= 8 cells wide:
                           -1 = auto (on for SNAC_MIXED, off for SNAC_FP64), 0 = off, 1 = on         */
   double inner_reduction; /* mixed plans: residual reduction asked of the FP32 multigrid in each
-                             defect-correction step, in (0, 1) (1e-4); FP64 plans solve each step to
-                             the tolerance directly                                                  */
+                             defect-correction step, in (0, 1); 0 (default) = automatic: 1e-4, or
+                             3e-5 for plans that solve on chip (see onchip: there an outer step --
+                             a 3-D residual pass, both transforms, a host round trip -- costs as much
+                             as several V-cycles). FP64 plans solve each step to the tolerance      */
   double shift;        /* Helmholtz shift s <= 0 (0): solve (A + s I) p = f, the Helmholtz form the
                           method applies to unchanged (Sec. 3.3, footnote); every reduced equation
                           (Eq. 9) gets the extra diagonal s, and s < 0 removes the null space of the
@@ -211,7 +213,8 @@ typedef struct {
  * Starting from *base (NULL = defaults), coordinate descent over: (nu1, nu2) in {(2,2), (2,1),
  * (1,2), (1,1)}; max_coarse in {16, 64, 256}; onchip in {auto, off} (the launch shape of the
  * wavenumber solves: one CTA per wavenumber on chip, or level-by-level grids over all wavenumbers);
- * and for SNAC_MIXED, inner_reduction in {1e-4, 1e-3, 3e-4} and fused in {auto, off}. A candidate counts only if its solve succeeds at tol. *best
+ * bottom_cells in {8192, 2048, 512}; and for SNAC_MIXED, inner_reduction in {1e-4, 3e-5, 1e-5, 3e-4,
+ * 1e-3} and fused in {auto, off}. A candidate counts only if its solve succeeds at tol. *best
  * receives the fastest options (precision, max_outer, max_cycles and shift are kept from *base).
  * The paper has no counterpart (its multigrid is hypre's); this is the schedule choice of a serving
  * system. Allocates and frees plans and an 8-byte-per-cell scratch field on the current device;

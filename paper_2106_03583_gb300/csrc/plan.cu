@@ -691,7 +691,7 @@ int create(snac_plan** out, int32_t nblocks, const snac_block* blocks_in, int32_
       delete P;
       return fail(SNAC_ERR_INVALID_ARG, "bad snac_options: bottom_cells must be 0, -1 or 16 .. 8192");
     }
-    if (!(P->inner_reduction > 0.0 && P->inner_reduction < 1.0) || !(P->shift <= 0.0) || !std::isfinite(P->shift) || (P->precision != SNAC_FP64 && P->precision != SNAC_MIXED) || P->nu1 < 0 || P->nu2 < 0 ||
+    if (!(P->inner_reduction >= 0.0 && P->inner_reduction < 1.0) || !(P->shift <= 0.0) || !std::isfinite(P->shift) || (P->precision != SNAC_FP64 && P->precision != SNAC_MIXED) || P->nu1 < 0 || P->nu2 < 0 ||
         P->nu1 + P->nu2 < 1 || P->nu1 > 16 || P->nu2 > 16 || P->max_outer < 1 || P->max_cycles < 1 ||
         P->max_coarse < 1 || P->max_coarse > MAX_COARSE) {
       delete P;
@@ -837,6 +837,9 @@ int create(snac_plan** out, int32_t nblocks, const snac_block* blocks_in, int32_
       P->onchip = P->onchip_opt == 0 && P->nu1 >= 1 && P->nu2 >= 1 && L >= 1 && L < BOTTOM_MAX_LEVELS &&
                   P->lev[0].ncell <= BOTTOM_MAX_CELLS && bottom_layout(P, 0, inner).bytes <= (size_t)BOTTOM_MAX_SMEM;
     }
+    // the automatic inner reduction: an on-chip plan's V-cycles are cheap next to an outer step,
+    // so it asks more of each step (measured on c64: 3 outer steps at 1e-4, 2 at 3e-5, 18 % faster)
+    if (P->inner_reduction == 0.0) P->inner_reduction = P->onchip ? 3e-5 : 1e-4;
     // fused FP32 tile kernels on the levels whose blocks all keep the halo inside their neighbours
     // (above the bottom sub-cycle; not needed when the whole solve runs on chip)
     const bool want_fused = !P->onchip && (P->fused == 1 || (P->fused < 0 && P->precision == SNAC_MIXED));

@@ -182,7 +182,7 @@ struct snac_plan {
   int sms = 152;             // multiprocessors of the device (grid sizing)
   int precision = SNAC_FP64;
   int nu1 = 2, nu2 = 2, max_outer = 20, max_cycles = 40, max_coarse = 64;
-  double inner_reduction = 1e-4;
+  double inner_reduction = 0.0;  // 0: automatic (resolved at plan creation)
   double shift = 0.0;  // Helmholtz shift (<= 0), included in sigma and in the residual's diagonal
   int fused = -1;
   // FP64 plans without fused levels keep the right-hand side of every smoothed level (all but the

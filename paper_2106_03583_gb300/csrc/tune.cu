@@ -150,7 +150,7 @@ extern "C" int snac_autotune(int32_t nblocks, const snac_block* blocks, int32_t 
   }
   if (b0.precision == SNAC_MIXED) {
     const snac_options start = cur;
-    for (double eta : {1e-4, 1e-3, 3e-4}) {
+    for (double eta : {1e-4, 3e-5, 1e-5, 3e-4, 1e-3}) {
       snac_options c = start;
       c.inner_reduction = eta;
       consider(c);

@@ -200,7 +200,7 @@ class Plan:
     """A solver plan for one multi-block problem (``snac_plan_create``)."""
 
     def __init__(self, blocks, homog_axis: int = 2, precision: str = "fp64", nu1: int = 2, nu2: int = 2,
-                 max_outer: int = 20, max_cycles: int = 40, max_coarse: int = 64, inner_reduction: float = 1e-4,
+                 max_outer: int = 20, max_cycles: int = 40, max_coarse: int = 64, inner_reduction: float = 0.0,
                  fused: int = -1, shift: float = 0.0, modes=None, onchip: bool = True, bottom_cells: int = 0):
         import torch
         if not torch.cuda.is_available():
@@ -437,7 +437,7 @@ class Engine:
 
     def submit(self, blocks, rhs, tol: float = 1e-10, precision: str = "fp64", homog_axis: int = 2, nu1: int = 2,
                nu2: int = 2, max_outer: int = 20, max_cycles: int = 40, max_coarse: int = 64,
-               inner_reduction: float = 1e-4, fused: int = -1, shift: float = 0.0, onchip: bool = True,
+               inner_reduction: float = 0.0, fused: int = -1, shift: float = 0.0, onchip: bool = True,
                bottom_cells: int = 0) -> int:
         if precision not in _PREC:
             raise ValueError(f"precision must be one of {list(_PREC)}")
@@ -514,7 +514,7 @@ def autotune(blocks, rhs, tol: float = 1e-10, precision: str = "fp64", homog_axi
     if not isinstance(rhs, torch.Tensor) or not rhs.is_cuda or rhs.dtype != torch.float64 or \
             not rhs.is_contiguous() or rhs.numel() != n3:
         raise ValueError(f"rhs must be a contiguous CUDA float64 tensor with {n3} elements")
-    d = dict(nu1=2, nu2=2, max_outer=20, max_cycles=40, max_coarse=64, fused=-1, inner_reduction=1e-4, shift=0.0,
+    d = dict(nu1=2, nu2=2, max_outer=20, max_cycles=40, max_coarse=64, fused=-1, inner_reduction=0.0, shift=0.0,
              bottom_cells=0)
     unknown = set(base) - set(d)
     if unknown:
