@@ -125,72 +125,119 @@ int onchip_results(snac_plan* P, int* cycles_out) {
   return SNAC_OK;
 }
 
-int mode_solves(snac_plan* P, double target, cudaStream_t s, int* cycles_out) {
-  const int nz = P->nz;
-  int st = set_active_all(P, s);
-  if (st) return st;
-  if (P->onchip) {  // every wavenumber's whole solve in one CTA; convergence decided on the device
-    CK(launch_onchip(P, nz, target, s));
-    CK(cudaStreamSynchronize(s));
-    profile_resolve(P);
-    return onchip_results(P, cycles_out);
+// The level-by-level wavenumber solves of one plan as a state machine, so that several plans can
+// run them in lock-step: each round's launches of all of them go out together and one stream
+// synchronisation serves every plan that reads norms back in that round. A single plan is a set of
+// one (the same launches and synchronisations as a dedicated loop).
+struct ModeRun {
+  snac_plan* P = nullptr;
+  double target = 0.0;
+  int* cycles = nullptr;
+  int st = SNAC_OK;
+  bool done = false;
+  // state between rounds
+  std::vector<double> thr2, prev;  // prev: norm^2 at the mode's last check
+  std::vector<int> list, prev_cycle, next_check;
+  std::vector<char> checked;
+  bool predictive = false, sweep_checks = false, red_done = false, list_changed = true, pending = false;
+  int c = 0, total = 0;
+
+  int fail(int status) {
+    st = status;
+    done = true;
+    return status;
   }
+
   // norms of the zero iterate (the right-hand side), which the same pass sets to zero
-  CK(launch_mode_norms(P, nz, false, s, nullptr, true));
-  CK(launch_to_host(P->d_mode_norm2, P->dh_mode_norm2, nz, s));
-  CK(cudaStreamSynchronize(s));
-    profile_resolve(P);
-  std::vector<double> thr2(nz), prev(nz);  // prev: norm^2 at the mode's last check
-  std::vector<int> list, prev_cycle(nz, 0), next_check(nz, 1);
-  for (int q = 0; q < nz; ++q) {
-    thr2[q] = target * target / (P->nzt * P->pweight[q]);
-    prev[q] = P->h_mode_norm2[q];
-    cycles_out[q] = 0;
-    if (!std::isfinite(prev[q])) return SNAC_ERR_NONFINITE;
-    if (prev[q] > thr2[q]) list.push_back(q);
+  int begin(cudaStream_t s) {
+    if (set_active_all(P, s)) return fail(SNAC_ERR_CUDA);
+    cudaError_t e = launch_mode_norms(P, P->nz, false, s, nullptr, true);
+    if (e == cudaSuccess) e = launch_to_host(P->d_mode_norm2, P->dh_mode_norm2, P->nz, s);
+    return e == cudaSuccess ? SNAC_OK : fail(cuda_fail(e, "mode norms"));
   }
-  // Where the level-0 norms need a pass of their own (the fused up kernel gives them for free), a
-  // mode is checked only when its observed per-cycle reduction says it should have reached its
-  // share, at most 3 cycles after its last check; rounds without a check need no synchronisation.
-  // A mode stops only at a check, so at worst it runs one cycle more than needed.
-  const bool predictive = !P->lev[0].fused;
-  // scaled FP64 plans take the norms of a check from the next cycle's first colour-0 half-sweep at
-  // level 0 (done for every active mode), so the check costs no pass of its own
-  const bool sweep_checks = predictive && P->scaled_f && P->nu1 >= 1;
-  bool red_done = false;  // that half-sweep of the coming cycle is done
-  const double stag2 = 0.6 * 0.6;  // a cycle that reduces the norm less than 0.6x: the precision floor
-  int total = 0;
-  bool list_changed = true;
-  std::vector<char> checked(nz, 0);
-  for (int c = 0; c < P->max_cycles && !list.empty(); ++c) {
+
+  // after a synchronisation
+  void begin_read() {
+    profile_resolve(P);
+    const int nz = P->nz;
+    thr2.assign(nz, 0.0);
+    prev.assign(nz, 0.0);
+    prev_cycle.assign(nz, 0);
+    next_check.assign(nz, 1);
+    checked.assign(nz, 0);
+    list.clear();
+    for (int q = 0; q < nz; ++q) {
+      thr2[q] = target * target / (P->nzt * P->pweight[q]);
+      prev[q] = P->h_mode_norm2[q];
+      cycles[q] = 0;
+      if (!std::isfinite(prev[q])) {
+        fail(SNAC_ERR_NONFINITE);
+        return;
+      }
+      if (prev[q] > thr2[q]) list.push_back(q);
+    }
+    // Where the level-0 norms need a pass of their own (the fused up kernel gives them for free), a
+    // mode is checked only when its observed per-cycle reduction says it should have reached its
+    // share, at most 3 cycles after its last check; rounds without a check need no synchronisation.
+    // A mode stops only at a check, so at worst it runs one cycle more than needed.
+    predictive = !P->lev[0].fused;
+    // scaled FP64 plans take the norms of a check from the next cycle's first colour-0 half-sweep at
+    // level 0 (done for every active mode), so the check costs no pass of its own
+    sweep_checks = predictive && P->scaled_f && P->nu1 >= 1;
+    done = list.empty();
+  }
+
+  // One V-cycle round of the active modes and, if some mode is due a check, its norms on their way
+  // to the host (pending: read them after the next synchronisation).
+  int round(cudaStream_t s) {
+    pending = false;
+    if (done) return SNAC_OK;
+    if (c >= P->max_cycles || list.empty()) {
+      done = true;
+      return SNAC_OK;
+    }
     const int nact = (int)list.size();
+    cudaError_t e = cudaSuccess;
     if (list_changed) {  // the previous upload has completed: every list change follows a synchronisation
       std::copy(list.begin(), list.end(), P->h_active);
-      CK(launch_from_host(P->dh_active, P->d_active, nact, s));
+      e = launch_from_host(P->dh_active, P->d_active, nact, s);
       list_changed = false;
     }
-    CK(run_round(P, nact, !predictive, s, &P->info.graph_rounds, red_done));
+    if (e == cudaSuccess) e = run_round(P, nact, !predictive, s, &P->info.graph_rounds, red_done);
+    if (e != cudaSuccess) return fail(cuda_fail(e, "V-cycle round"));
     red_done = false;
+    ++c;
     int ncheck = 0;
     for (int q : list) {
-      ++cycles_out[q];
+      ++cycles[q];
       ++total;
-      checked[q] = !predictive || cycles_out[q] >= next_check[q];
+      checked[q] = !predictive || cycles[q] >= next_check[q];
       if (checked[q]) P->h_check[ncheck++] = q;
     }
-    if (ncheck == 0) continue;
+    if (ncheck == 0) return SNAC_OK;
     if (predictive) {
-      CK(launch_from_host(P->dh_check, P->d_check, ncheck, s));
-      if (sweep_checks) {
-        CK(launch_check_sweep(P, nact, ncheck, s));
-        red_done = true;  // for every mode that stays active
-      } else {
-        CK(launch_mode_norms(P, ncheck, true, s, P->d_check));
+      e = launch_from_host(P->dh_check, P->d_check, ncheck, s);
+      if (e == cudaSuccess) {
+        if (sweep_checks) {
+          e = launch_check_sweep(P, nact, ncheck, s);
+          red_done = true;  // for every mode that stays active
+        } else {
+          e = launch_mode_norms(P, ncheck, true, s, P->d_check);
+        }
       }
     }
-    CK(launch_to_host(P->d_mode_norm2, P->dh_mode_norm2, nz, s));
-    CK(cudaStreamSynchronize(s));
+    if (e == cudaSuccess) e = launch_to_host(P->d_mode_norm2, P->dh_mode_norm2, P->nz, s);
+    if (e != cudaSuccess) return fail(cuda_fail(e, "mode norms"));
+    pending = true;
+    return SNAC_OK;
+  }
+
+  // after a synchronisation, when a round left norms pending
+  void read() {
+    if (!pending || done) return;
+    pending = false;
     profile_resolve(P);
+    const double stag2 = 0.6 * 0.6;  // a cycle that reduces the norm less than 0.6x: the precision floor
     std::vector<int> next;
     for (int q : list) {
       if (!checked[q]) {
@@ -198,23 +245,74 @@ int mode_solves(snac_plan* P, double target, cudaStream_t s, int* cycles_out) {
         continue;
       }
       const double r2 = P->h_mode_norm2[q];
-      if (!std::isfinite(r2)) return SNAC_ERR_NONFINITE;
-      const int dc = cycles_out[q] - prev_cycle[q];
-      const bool done = r2 <= thr2[q] || r2 > std::pow(stag2, dc) * prev[q];
-      if (!done && predictive) {
+      if (!std::isfinite(r2)) {
+        fail(SNAC_ERR_NONFINITE);
+        return;
+      }
+      const int dc = cycles[q] - prev_cycle[q];
+      const bool ok = r2 <= thr2[q] || r2 > std::pow(stag2, dc) * prev[q];
+      if (!ok && predictive) {
         const double rho2 = std::pow(r2 / prev[q], 1.0 / dc);  // per-cycle factor of the norm^2, < 1
         const double need = std::log(thr2[q] / r2) / std::log(rho2);
-        next_check[q] = cycles_out[q] + std::max(1, std::min(3, (int)std::ceil(need - 0.25)));
+        next_check[q] = cycles[q] + std::max(1, std::min(3, (int)std::ceil(need - 0.25)));
       }
       prev[q] = r2;
-      prev_cycle[q] = cycles_out[q];
-      if (!done) next.push_back(q);
+      prev_cycle[q] = cycles[q];
+      if (!ok) next.push_back(q);
     }
     list_changed = next.size() != list.size();
     list.swap(next);
   }
-  P->info.total_cycles += total;
-  return SNAC_OK;
+
+  void finish() { P->info.total_cycles += total; }
+};
+
+// V-cycles of every mode of every plan until its share of the plan's target is met, it stagnates,
+// or max_cycles; the plans in lock-step. Each run's status in its st.
+void mode_solves_many(const std::vector<ModeRun*>& runs, cudaStream_t s) {
+  auto sync = [&]() -> bool {
+    const cudaError_t e = cudaStreamSynchronize(s);
+    if (e == cudaSuccess) return true;
+    const int st = cuda_fail(e, "cudaStreamSynchronize");
+    for (ModeRun* r : runs)
+      if (!r->done) r->fail(st);
+    return false;
+  };
+  for (ModeRun* r : runs) r->begin(s);
+  if (!sync()) return;
+  for (ModeRun* r : runs)
+    if (!r->done) r->begin_read();
+  for (;;) {
+    bool active = false, pending = false;
+    for (ModeRun* r : runs) {
+      r->round(s);
+      active = active || !r->done;
+      pending = pending || r->pending;
+    }
+    if (!active) break;
+    if (!pending) continue;
+    if (!sync()) return;
+    for (ModeRun* r : runs) r->read();
+  }
+  for (ModeRun* r : runs)
+    if (r->st == SNAC_OK) r->finish();
+}
+
+int mode_solves(snac_plan* P, double target, cudaStream_t s, int* cycles_out) {
+  if (P->onchip) {  // every wavenumber's whole solve in one CTA; convergence decided on the device
+    const int st = set_active_all(P, s);
+    if (st) return st;
+    CK(launch_onchip(P, P->nz, target, s));
+    CK(cudaStreamSynchronize(s));
+    profile_resolve(P);
+    return onchip_results(P, cycles_out);
+  }
+  ModeRun r;
+  r.P = P;
+  r.target = target;
+  r.cycles = cycles_out;
+  mode_solves_many({&r}, s);
+  return r.st;
 }
 
 int read_sums(snac_plan* P, cudaStream_t s, int n = 4) {
@@ -523,11 +621,26 @@ int run_jobs(std::vector<Job>& jobs, cudaStream_t s) {
         for (Job* J : chip[g]) job_cuda(*J, e, "on-chip wavenumber solves");
     }
     if (status) break;
-    for (Job& J : jobs)
-      if (!J.finished && !J.P->onchip) {
-        const int st = mode_solves(J.P, J.target, s, J.cyc.data());
-        if (st) J.finish(st);
+    {  // the level-by-level plans' wavenumber solves, in lock-step with one another
+      std::vector<ModeRun> runs;
+      std::vector<Job*> owners;
+      for (Job& J : jobs)
+        if (!J.finished && !J.P->onchip) {
+          ModeRun r;
+          r.P = J.P;
+          r.target = J.target;
+          r.cycles = J.cyc.data();
+          runs.push_back(std::move(r));
+          owners.push_back(&J);
+        }
+      if (!runs.empty()) {
+        std::vector<ModeRun*> ptrs;
+        for (ModeRun& r : runs) ptrs.push_back(&r);
+        mode_solves_many(ptrs, s);
+        for (size_t k = 0; k < runs.size(); ++k)
+          if (runs[k].st) owners[k]->finish(runs[k].st);
       }
+    }
     if (!chip[0].empty() || !chip[1].empty() || !fusedj[0].empty() || !fusedj[1].empty()) {
       if ((e = sync()) != cudaSuccess) { status = cuda_fail(e, "cudaStreamSynchronize"); break; }
       for (int g = 0; g < 2; ++g) {
