@@ -131,6 +131,7 @@ int onchip_results(snac_plan* P, int* cycles_out) {
 // one (the same launches and synchronisations as a dedicated loop).
 struct ModeRun {
   snac_plan* P = nullptr;
+  cudaStream_t s = nullptr;  // the stream of this plan's launches
   double target = 0.0;
   int* cycles = nullptr;
   int st = SNAC_OK;
@@ -268,24 +269,26 @@ struct ModeRun {
 };
 
 // V-cycles of every mode of every plan until its share of the plan's target is met, it stagnates,
-// or max_cycles; the plans in lock-step. Each run's status in its st.
-void mode_solves_many(const std::vector<ModeRun*>& runs, cudaStream_t s) {
+// or max_cycles; the plans in lock-step, each on its own stream (r->s). `wait` makes the host wait
+// for every stream the runs use. Each run's status in its st.
+template <typename Wait>
+void mode_solves_many(const std::vector<ModeRun*>& runs, Wait&& wait) {
   auto sync = [&]() -> bool {
-    const cudaError_t e = cudaStreamSynchronize(s);
+    const cudaError_t e = wait();
     if (e == cudaSuccess) return true;
     const int st = cuda_fail(e, "cudaStreamSynchronize");
     for (ModeRun* r : runs)
       if (!r->done) r->fail(st);
     return false;
   };
-  for (ModeRun* r : runs) r->begin(s);
+  for (ModeRun* r : runs) r->begin(r->s);
   if (!sync()) return;
   for (ModeRun* r : runs)
     if (!r->done) r->begin_read();
   for (;;) {
     bool active = false, pending = false;
     for (ModeRun* r : runs) {
-      r->round(s);
+      r->round(r->s);
       active = active || !r->done;
       pending = pending || r->pending;
     }
@@ -309,9 +312,10 @@ int mode_solves(snac_plan* P, double target, cudaStream_t s, int* cycles_out) {
   }
   ModeRun r;
   r.P = P;
+  r.s = s;
   r.target = target;
   r.cycles = cycles_out;
-  mode_solves_many({&r}, s);
+  mode_solves_many({&r}, [&] { return cudaStreamSynchronize(s); });
   return r.st;
 }
 
@@ -518,10 +522,69 @@ int job_cuda(Job& J, cudaError_t e, const char* where) {
 }
 
 // Run the jobs to completion on stream s (all plans on the current device).
+// Several problems at once: each problem's own launches go to one of a few side streams, forked
+// from the caller's stream at the start and joined back into it before every synchronisation and
+// before a launch on the caller's stream that reads their results, so that the kernels of
+// different problems can run at the same time. Without side streams everything runs on `main`.
+struct SideStreams {
+  cudaStream_t main;
+  std::vector<cudaStream_t> side;
+  std::vector<cudaEvent_t> ev;  // one per side stream, then the fork event
+  SideStreams(cudaStream_t s, int n) : main(s) {
+    for (int k = 0; k < n; ++k) {
+      cudaStream_t t = nullptr;
+      cudaEvent_t e = nullptr;
+      if (cudaStreamCreateWithFlags(&t, cudaStreamNonBlocking) != cudaSuccess ||
+          cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        if (t) cudaStreamDestroy(t);
+        break;
+      }
+      side.push_back(t);
+      ev.push_back(e);
+    }
+    cudaEvent_t f = nullptr;
+    if (!side.empty() && cudaEventCreateWithFlags(&f, cudaEventDisableTiming) != cudaSuccess) {
+      cudaGetLastError();
+      release();
+    }
+    if (f) ev.push_back(f);
+  }
+  ~SideStreams() { release(); }
+  void release() {
+    for (cudaStream_t t : side) cudaStreamDestroy(t);
+    for (cudaEvent_t e : ev) cudaEventDestroy(e);
+    side.clear();
+    ev.clear();
+  }
+  cudaStream_t of(size_t k) const { return side.empty() ? main : side[k % side.size()]; }
+  cudaError_t fork() {
+    if (side.empty()) return cudaSuccess;
+    cudaError_t e = cudaEventRecord(ev.back(), main);
+    for (size_t k = 0; k < side.size() && e == cudaSuccess; ++k) e = cudaStreamWaitEvent(side[k], ev.back(), 0);
+    return e;
+  }
+  cudaError_t join() {
+    cudaError_t e = cudaSuccess;
+    for (size_t k = 0; k < side.size() && e == cudaSuccess; ++k) {
+      e = cudaEventRecord(ev[k], side[k]);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(main, ev[k], 0);
+    }
+    return e;
+  }
+};
+
 int run_jobs(std::vector<Job>& jobs, cudaStream_t s) {
-  auto sync = [&]() -> cudaError_t { return cudaStreamSynchronize(s); };
-  for (Job& J : jobs) job_cuda(J, job_begin(J, s), "pre-pass");
-  cudaError_t e = sync();
+  SideStreams ss(s, jobs.size() > 1 ? (int)std::min<size_t>(4, jobs.size()) : 0);
+  auto js = [&](const Job& J) { return ss.of((size_t)(&J - jobs.data())); };
+  auto sync = [&]() -> cudaError_t {
+    const cudaError_t e = ss.join();
+    return e != cudaSuccess ? e : cudaStreamSynchronize(s);
+  };
+  cudaError_t e = ss.fork();  // the caller's earlier work on s (f, p) comes first
+  if (e != cudaSuccess) return cuda_fail(e, "cudaStreamWaitEvent");
+  for (Job& J : jobs) job_cuda(J, job_begin(J, js(J)), "pre-pass");
+  e = sync();
   if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
   for (Job& J : jobs)
     if (!J.finished) job_begin_read(J);
@@ -534,21 +597,23 @@ int run_jobs(std::vector<Job>& jobs, cudaStream_t s) {
     for (Job& J : jobs) any = any || !J.finished;
     if (!any) break;
     for (Job& J : jobs)
-      if (!J.finished) job_cuda(J, job_resid_launch(J, s), "residual");
+      if (!J.finished) job_cuda(J, job_resid_launch(J, js(J)), "residual");
     if ((e = sync()) != cudaSuccess) { status = cuda_fail(e, "cudaStreamSynchronize"); break; }
     bool redo = false;
     for (Job& J : jobs)
-      if (!J.finished && job_cuda(J, job_resid_read(J, s), "residual") == SNAC_OK) redo = redo || J.redo;
+      if (!J.finished && job_cuda(J, job_resid_read(J, js(J)), "residual") == SNAC_OK) redo = redo || J.redo;
     if (redo) {
       if ((e = sync()) != cudaSuccess) { status = cuda_fail(e, "cudaStreamSynchronize"); break; }
       for (Job& J : jobs)
-        if (!J.finished && J.redo) job_cuda(J, job_resid_read(J, s), "residual");
+        if (!J.finished && J.redo) job_cuda(J, job_resid_read(J, js(J)), "residual");
     }
     for (Job& J : jobs)
       if (!J.finished) {
-        const int st = job_decide(J, s);
+        const int st = job_decide(J, js(J));
         if (st) J.finish(st);
       }
+    // the forward transforms of the on-chip plans come before their solves on s
+    if ((e = ss.join()) != cudaSuccess) { status = cuda_fail(e, "cudaStreamWaitEvent"); break; }
     // the wavenumber solves: on-chip plans together (one persistent launch per precision), the
     // others level by level
     std::vector<Job*> chip[2], fusedj[2];
@@ -628,6 +693,7 @@ int run_jobs(std::vector<Job>& jobs, cudaStream_t s) {
         if (!J.finished && !J.P->onchip) {
           ModeRun r;
           r.P = J.P;
+          r.s = js(J);
           r.target = J.target;
           r.cycles = J.cyc.data();
           runs.push_back(std::move(r));
@@ -636,7 +702,7 @@ int run_jobs(std::vector<Job>& jobs, cudaStream_t s) {
       if (!runs.empty()) {
         std::vector<ModeRun*> ptrs;
         for (ModeRun& r : runs) ptrs.push_back(&r);
-        mode_solves_many(ptrs, s);
+        mode_solves_many(ptrs, sync);
         for (size_t k = 0; k < runs.size(); ++k)
           if (runs[k].st) owners[k]->finish(runs[k].st);
       }
@@ -664,12 +730,11 @@ int run_jobs(std::vector<Job>& jobs, cudaStream_t s) {
       }
     }
     for (Job& J : jobs)
-      if (!J.finished) job_cuda(J, job_update(J, s), "update");
+      if (!J.finished) job_cuda(J, job_update(J, js(J)), "update");
   }
-  if (scratch) {
-    cudaFreeAsync(scratch, s);
-    cudaStreamSynchronize(s);
-  }
+  if (scratch) cudaFreeAsync(scratch, s);
+  const cudaError_t ef = sync();  // every problem's last launches are complete on return
+  if (ef != cudaSuccess && status == SNAC_OK) status = cuda_fail(ef, "cudaStreamSynchronize");
   return status;
 }
 
