@@ -782,8 +782,10 @@ def run_serve(args):
 
 def run_batch(args):
     """64 independent problems (32^3 .. 256x256x128 log-uniform, 1-4 blocks, random walls and z pair,
-    U[-1, 1] right-hand sides), mixed precision at tol 1e-10: all submitted at once to the engine,
-    against the same problems solved one after another with the plain plan/solve calls."""
+    U[-1, 1] right-hand sides), mixed precision at tol 1e-10: solved together by the batched solve
+    with device-resident data (the line's value), one after another with the plain plan/solve
+    calls, and all submitted at once to the engine with host arrays (with and without merging, and
+    autotuned)."""
     import numpy as np
     import torch
     from paper_2106_03583_gb300 import build, inputs, snac
@@ -845,7 +847,10 @@ def run_batch(args):
                                    "walls and z pair, f ~ U[-1,1]; mixed precision, tol 1e-10",
                        "workers": args.workers, "max_group": args.max_group,
                        "cells": int(sum(len(f) for _, f, _ in probs))},
-            "value": max(best["solves_per_s"], tuned["solves_per_s"]), "host_inputs_in_timed_region": True,
+            # value: the batched solve with the inputs resident in HBM; e2e: the same problems
+            # through the engine with host arrays in and out
+            "value": max(reps), "e2e": {"value": max(best["solves_per_s"], tuned["solves_per_s"]), "unit": "solves/s",
+                                        "path": "engine, host arrays in and out"},
             "one_at_a_time_device_resident_solves_per_s": seq,
             "lockstep_batch_device_resident_solves_per_s": max(reps), "lockstep_batch_all_converged": batch_ok,
             "lockstep_batch_onchip_problems": onchip_plans, "engine": best, "engine_unmerged": unmerged,
