@@ -165,7 +165,7 @@ int snac_poisson_solve(snac_plan *plan, const double *d_rhs, double *d_p, double
 /* Solve n problems together (each as snac_poisson_solve would): plans[k] (distinct plans, all on
  * the current device), d_rhs[k], d_p[k] as in snac_poisson_solve, one tolerance. The problems run
  * in lock-step: each phase's launches of all of them go out together and one synchronisation
- * serves them all; each problem's own launches go to one of up to four streams the call creates,
+ * serves them all; each problem's own launches go to one of up to 16 streams the call creates,
  * forked from `stream` and joined back into it, so that the kernels of different problems overlap;
  * and the wavenumber solves of every plan whose hierarchy fits on chip (see snac_options.onchip)
  * share one persistent launch per precision -- CTAs take (problem, wavenumber)

@@ -575,7 +575,7 @@ struct SideStreams {
 };
 
 int run_jobs(std::vector<Job>& jobs, cudaStream_t s) {
-  SideStreams ss(s, jobs.size() > 1 ? (int)std::min<size_t>(4, jobs.size()) : 0);
+  SideStreams ss(s, jobs.size() > 1 ? (int)std::min<size_t>(16, jobs.size()) : 0);
   auto js = [&](const Job& J) { return ss.of((size_t)(&J - jobs.data())); };
   auto sync = [&]() -> cudaError_t {
     const cudaError_t e = ss.join();
