@@ -87,7 +87,7 @@ def parse():
     ap.add_argument("--batch", action="store_true", help="64 independent mixed problems at once through the engine")
     ap.add_argument("--requests", type=int, default=400, help="--serve: requests per arrival rate")
     ap.add_argument("--pool", type=int, default=16, help="--serve: distinct problems the requests draw from")
-    ap.add_argument("--workers", type=int, default=8, help="--serve/--batch: engine worker streams")
+    ap.add_argument("--workers", type=int, default=4, help="--serve/--batch: engine worker streams")
     ap.add_argument("--max-group", type=int, default=16,
                     help="--serve/--batch: most ready on-chip requests the engine solves together (1 = never merge)")
     return ap.parse_args()

@@ -65,7 +65,7 @@ extern "C" {
 typedef struct snac_engine snac_engine;
 
 typedef struct {
-  int32_t workers;          /* worker threads / CUDA streams, 1..64 (8)                                  */
+  int32_t workers;          /* worker threads / CUDA streams, 1..64 (4)                                  */
   int32_t max_cached_plans; /* idle plans kept resident, 0..4096 (64)                                     */
   uint64_t hbm_budget;      /* device bytes the engine may hold (150e9); must cover the largest request  */
   int32_t autotune;         /* 1: the first request of each problem runs snac_autotune on its own

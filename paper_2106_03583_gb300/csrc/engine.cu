@@ -460,7 +460,7 @@ double snac_engine_clock(void) { return now_s(); }
 int snac_engine_create(snac_engine** out, const snac_engine_options* opt) {
   if (!out) return SNAC_ERR_INVALID_ARG;
   *out = nullptr;
-  snac_engine_options o{8, 64, 150000000000ull, 0, 16};
+  snac_engine_options o{4, 64, 150000000000ull, 0, 16};
   if (opt) o = *opt;
   if (o.workers < 1 || o.workers > 64 || o.max_cached_plans < 0 || o.max_cached_plans > 4096 || o.hbm_budget == 0 ||
       (o.autotune != 0 && o.autotune != 1) || o.max_group < 1 || o.max_group > 256)

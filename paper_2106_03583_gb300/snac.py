@@ -417,12 +417,12 @@ class Engine:
     with resident cached plans; requests of small (on-chip) problems that are ready together are
     solved in one batched solve of up to ``max_group``. Host arrays in, host arrays out.
 
-        eng = snac.Engine(workers=8, hbm_budget=150e9)
+        eng = snac.Engine(workers=4, hbm_budget=150e9)
         t = eng.submit(blocks, f, tol=1e-10, precision="mixed")
         p, info, times = eng.wait(t)
     """
 
-    def __init__(self, workers: int = 8, hbm_budget: float = 150e9, max_cached_plans: int = 64,
+    def __init__(self, workers: int = 4, hbm_budget: float = 150e9, max_cached_plans: int = 64,
                  autotune: bool = False, max_group: int = 16):
         import torch
         if not torch.cuda.is_available():
