@@ -476,12 +476,14 @@ def e2e_serial(plan, f, f_host, K, tol, barrier, world):
 
 def e2e_pipelined(plan, f, f_host, K, tol, barrier, world):
     """ms for K solves through the public API with every step's host copies (right-hand side in from
-    pinned memory, solution out), as a stream of solves runs them: two device buffers, the copies on
-    a copy stream, so that step k+1's input and step k-1's output move while step k solves. Returns
-    (ms, every solve converged and the last solution arrived on the host intact)."""
+    pinned memory, solution out), as a stream of solves runs them: two device buffers, the inputs on
+    one copy stream and the outputs on another (the host link carries both directions at once), so
+    that step k+1's input and step k-1's output move while step k solves. Returns (ms, every solve
+    converged and the last solution arrived on the host intact)."""
     import torch
     comp = torch.cuda.current_stream()
-    cs = torch.cuda.Stream()
+    cs = torch.cuda.Stream()    # host -> device
+    co = torch.cuda.Stream()    # device -> host
     p_host = [torch.empty_like(f_host).pin_memory() for _ in range(2)]
     fd = [torch.empty_like(f) for _ in range(2)]
     pd = [torch.empty_like(f) for _ in range(2)]
@@ -508,10 +510,10 @@ def e2e_pipelined(plan, f, f_host, K, tol, barrier, world):
             info = plan.solve(fd[b], pd[b], tol=tol)
             ok = ok and info["status"] == 0 and info["rel_res"] <= tol
             ev_solved[b].record(comp)
-            cs.wait_event(ev_solved[b])
-            with torch.cuda.stream(cs):
+            co.wait_event(ev_solved[b])
+            with torch.cuda.stream(co):
                 p_host[b].copy_(pd[b], non_blocking=True)
-                ev_out[b].record(cs)
+                ev_out[b].record(co)
         comp.wait_event(ev_out[(n - 1) % 2])
         return ok
 
